@@ -1,0 +1,120 @@
+"""MLP router oracle (float64, numpy) -- TEST INFRASTRUCTURE ONLY.
+
+The paper routes each point to its t nearest binary centres (Section 3.2) and has
+no learned router; this network is the learned alternative that picks the top-P
+partitions instead. The oracle states the network and its gradients plainly:
+
+  h1 = relu(x W1^T + b1)          x: [B, d_in]
+  h2 = relu(h1 W2^T + b2)
+  z  = h2 W3^T + b3               z: [B, m] logits, one per partition
+  loss = -(1/B) sum_i sum_p q_ip log softmax(z_i)_p
+
+with q_i the target distribution over partitions (the share of point i's exact
+neighbours whose home partition is p). Gradients are the analytic chain rule;
+``adam`` is Kingma & Ba's update with bias correction.
+
+With ``bf16=True`` the float64 computation rounds to bfloat16 (round to nearest,
+ties to even) exactly where a bf16 pipeline stores a tensor: the inputs, the
+weights, h1, h2 and the logit gradient and hidden-layer gradients that feed the
+backward products. Everything else stays float64.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def round_bf16(a) -> np.ndarray:
+    """Round float values to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    out = (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32).astype(np.float64)
+    nan = np.isnan(f)
+    if nan.any():
+        out[nan] = np.nan
+    return out
+
+
+def _q(a, bf16):
+    return round_bf16(a) if bf16 else np.asarray(a, dtype=np.float64)
+
+
+def forward(params, x, bf16=True):
+    """Returns (z, cache). params: dict W1,b1,W2,b2,W3,b3 (float arrays)."""
+    W1, W2, W3 = (_q(params[k], bf16) for k in ("W1", "W2", "W3"))
+    b1, b2, b3 = (np.asarray(params[k], np.float64) for k in ("b1", "b2", "b3"))
+    x = _q(x, bf16)
+    a1 = x @ W1.T + b1
+    h1 = _q(np.maximum(a1, 0.0), bf16)
+    a2 = h1 @ W2.T + b2
+    h2 = _q(np.maximum(a2, 0.0), bf16)
+    z = h2 @ W3.T + b3
+    return z, dict(x=x, h1=h1, h2=h2, W1=W1, W2=W2, W3=W3)
+
+
+def softmax(z):
+    z = np.asarray(z, np.float64)
+    e = np.exp(z - z.max(axis=1, keepdims=True))
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def loss_and_grads(params, x, q, bf16=True):
+    """Mean soft-target cross-entropy and its gradients w.r.t. every parameter."""
+    z, c = forward(params, x, bf16)
+    B = z.shape[0]
+    p = softmax(z)
+    q = np.asarray(q, np.float64)
+    logp = np.log(np.maximum(p, 1e-300))
+    loss = float(-(q * logp).sum() / B)
+    dz = (p - q) / B
+    dzq = _q(dz, bf16)
+    g = {}
+    g["W3"] = dzq.T @ c["h2"]
+    g["b3"] = dz.sum(0)
+    dh2 = (dzq @ c["W3"]) * (c["h2"] > 0)
+    dh2q = _q(dh2, bf16)
+    g["W2"] = dh2q.T @ c["h1"]
+    g["b2"] = dh2.sum(0)
+    dh1 = (dh2q @ c["W2"]) * (c["h1"] > 0)
+    dh1q = _q(dh1, bf16)
+    g["W1"] = dh1q.T @ c["x"]
+    g["b1"] = dh1.sum(0)
+    return loss, g, z
+
+
+def adam(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (bias-corrected) on float64 copies; returns new params, state."""
+    t = state.get("t", 0) + 1
+    newp, news = {}, {"t": t}
+    for k, w in params.items():
+        gk = np.asarray(grads[k], np.float64)
+        m = beta1 * state.get("m_" + k, 0.0) + (1 - beta1) * gk
+        v = beta2 * state.get("v_" + k, 0.0) + (1 - beta2) * gk * gk
+        mh = m / (1 - beta1 ** t)
+        vh = v / (1 - beta2 ** t)
+        newp[k] = np.asarray(w, np.float64) - lr * mh / (np.sqrt(vh) + eps)
+        news["m_" + k], news["v_" + k] = m, v
+    return newp, news
+
+
+def topp(z, P):
+    """First P partitions of sort over (-z_p, p) per row."""
+    z = np.asarray(z, np.float64)
+    out = np.empty((z.shape[0], P), np.int32)
+    for i, row in enumerate(z):
+        order = np.lexsort((np.arange(row.size), -row))
+        out[i] = order[:P]
+    return out
+
+
+def neighbour_partition_targets(knn_ids, home, m):
+    """q_ip = #{j in G*(i) : home(j) = p} / k (ids -1 ignored, k = row width)."""
+    knn_ids = np.asarray(knn_ids)
+    B, k = knn_ids.shape
+    q = np.zeros((B, m), np.float64)
+    for i in range(B):
+        for j in knn_ids[i]:
+            if j >= 0:
+                q[i, home[j]] += 1.0 / k
+    return q

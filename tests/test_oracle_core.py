@@ -1,0 +1,300 @@
+"""Pins of the CPU oracle against things other than itself: per-bit brute force,
+metric axioms, the +-1 dot-product identity, hand-worked fixtures under
+tests/golden/, closed forms and invariants (Section 3 / 3.2 / 3.5 of the paper)."""
+import os
+
+import numpy as np
+import pytest
+
+import datagen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_codes(n, bits, seed):
+    return datagen.random_codes(n, bits, seed).numpy().view(np.uint64)
+
+
+def _bits(c, bits):
+    return datagen.unpack_bits(c, bits).astype(np.int64)
+
+
+# ---------------------------------------------------------------- Hamming
+@pytest.mark.parametrize("bits", [64, 128, 256, 512])
+def test_hamming_matches_per_bit_count(oracle_lib, bits):
+    c = _rand_codes(40, bits, 7 + bits)
+    b = _bits(c, bits)
+    for i in range(0, 40, 3):
+        for j in range(1, 40, 5):
+            want = int((b[i] != b[j]).sum())
+            assert oracle_lib.hamming(c[i], c[j]) == want
+
+
+def test_hamming_metric_axioms(oracle_lib):
+    c = _rand_codes(60, 256, 3)
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        i, j, l = rng.integers(0, 60, 3)
+        dij = oracle_lib.hamming(c[i], c[j])
+        assert oracle_lib.hamming(c[i], c[i]) == 0
+        assert dij == oracle_lib.hamming(c[j], c[i])
+        assert dij <= oracle_lib.hamming(c[i], c[l]) + oracle_lib.hamming(c[l], c[j])
+
+
+def test_hamming_pm1_dot_identity(oracle_lib):
+    # with s = 2y - 1 in {-1, +1}: <s_a, s_b> = bits - 2 d(a, b)
+    bits = 512
+    c = _rand_codes(20, bits, 11)
+    s = 2 * _bits(c, bits) - 1
+    dot = s @ s.T
+    for i in range(20):
+        for j in range(20):
+            assert (bits - dot[i, j]) // 2 == oracle_lib.hamming(c[i], c[j])
+
+
+# ---------------------------------------------------------------- exact kNN
+def _read_knn_golden():
+    rows = {}
+    codes = None
+    with open(os.path.join(GOLDEN, "knn_tiny.txt")) as f:
+        lines = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+    codes = np.array([int(x, 16) for x in lines[0].split()], dtype=np.uint64)[:, None]
+    for ln in lines[1:]:
+        p, rest = ln.split(":")
+        pairs = [tuple(int(v) for v in tok.split(",")) for tok in rest.split()]
+        rows[int(p)] = pairs
+    return codes, rows
+
+
+def test_knn_exact_hand_worked_fixture(oracle_lib):
+    codes, rows = _read_knn_golden()
+    ids, dist = oracle_lib.knn_exact(codes, 2)
+    for p, pairs in rows.items():
+        assert [(int(a), int(b)) for a, b in zip(ids[p], dist[p])] == pairs
+
+
+def test_knn_exact_pads_when_k_exceeds_candidates(oracle_lib):
+    codes, _ = _read_knn_golden()
+    ids, dist = oracle_lib.knn_exact(codes, 7)
+    assert (ids[:, 5:] == -1).all() and (ids[:, 6] == -1).all()
+    assert (dist[:, 5:] == 65).all()
+    assert (ids[:, :5] >= 0).all()
+
+
+@pytest.mark.parametrize("bits,n,k", [(64, 200, 8), (256, 300, 32), (512, 150, 16)])
+def test_knn_exact_brute_force_and_separation(oracle_lib, bits, n, k):
+    c = _rand_codes(n, bits, 100 + bits)
+    # add exact duplicates so that d = 0 ties with id tie-break are exercised
+    c[5] = c[17]
+    c[40] = c[17]
+    b = _bits(c, bits)
+    full = (b[:, None, :] != b[None, :, :]).sum(2)  # per-bit brute force
+    ids, dist = oracle_lib.knn_exact(c, k)
+    for i in range(n):
+        d = full[i].copy()
+        order = [j for j in np.lexsort((np.arange(n), d)) if j != i][:k]
+        assert list(ids[i]) == order
+        assert list(dist[i]) == [int(d[j]) for j in order]
+        # separation: every returned key is below every key left out
+        keys = d.astype(np.int64) * (1 << 32) + np.arange(n)
+        keys[i] = -1
+        kept = keys[ids[i]]
+        rest = np.setdiff1d(np.arange(n), np.append(ids[i], i))
+        assert kept.max() < keys[rest].min()
+
+
+def test_knn_exact_all_equal_codes_is_pure_id_order(oracle_lib):
+    c = np.zeros((50, 4), np.uint64)
+    ids, dist = oracle_lib.knn_exact(c, 10)
+    for i in range(50):
+        want = [j for j in range(50) if j != i][:10]
+        assert list(ids[i]) == want
+        assert (dist[i] == 0).all()
+
+
+# ---------------------------------------------------------------- Bk-means
+def test_bkmeans_hand_worked_fixture(oracle_lib):
+    vals = {}
+    with open(os.path.join(GOLDEN, "bkmeans_tiny.txt")) as f:
+        for ln in f:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            key, rest = ln.split(":")
+            vals[key.strip()] = rest.split()
+    codes = np.array([int(x, 16) for x in vals["codes"]], np.uint64)[:, None]
+    sample = np.array([int(x) for x in vals["sample"]], np.int64)
+    cent, loss, assign = oracle_lib.bkmeans(codes, sample, 2, 1)
+    assert [int(x) for x in cent[:, 0]] == [int(x, 16) for x in vals["centroids"]]
+    assert list(loss) == [int(x) for x in vals["loss"]]
+    assert list(assign) == [int(x) for x in vals["assign"]]
+
+
+def test_bkmeans_loss_non_increasing(oracle_lib):
+    spec = datagen.MixtureSpec(3000, 32, 16, 128, seed=5)
+    c = datagen.make_codes(spec).numpy().view(np.uint64)
+    sample = datagen.sample_ids(3000, 2000, 9)
+    _, loss, _ = oracle_lib.bkmeans(c, sample, 16, 8)
+    assert all(loss[i + 1] <= loss[i] for i in range(len(loss) - 1))
+    assert loss[-1] < loss[0]
+
+
+def test_bkmeans_single_centre_is_bitwise_majority(oracle_lib):
+    bits = 128
+    c = _rand_codes(101, bits, 21)  # odd count: no ties
+    sample = np.arange(101, dtype=np.int64)
+    cent, _, _ = oracle_lib.bkmeans(c, sample, 1, 1)
+    maj = (_bits(c, bits).sum(0) * 2 > 101).astype(np.uint8)
+    assert (datagen.unpack_bits(cent, bits)[0] == maj).all()
+
+
+def test_bkmeans_tie_keeps_previous_bit(oracle_lib):
+    # two codes, one centre: every differing bit is a 1-of-2 tie -> keeps init bits
+    c = _rand_codes(2, 128, 33)
+    cent, _, _ = oracle_lib.bkmeans(c, np.array([1, 0], np.int64), 1, 3)
+    assert (cent[0] == c[1]).all()
+
+
+def test_bkmeans_recovers_planted_centres(oracle_lib):
+    bits, m, per = 256, 8, 50
+    rng = np.random.default_rng(4)
+    centres = _rand_codes(m, bits, 44)
+    cb = _bits(centres, bits)
+    pts = []
+    for j in range(m):
+        for _ in range(per):
+            b = cb[j].copy()
+            flip = rng.choice(bits, 10, replace=False)
+            b[flip] ^= 1
+            pts.append(b)
+    pts = np.array(pts, np.uint64)
+    packed = np.zeros((len(pts), bits // 64), np.uint64)
+    for w in range(bits // 64):
+        for s in range(64):
+            packed[:, w] |= pts[:, w * 64 + s] << np.uint64(s)
+    sample = np.array([j * per for j in range(m)] + [i for i in range(m * per) if i % per],
+                      np.int64)
+    cent, _, assign = oracle_lib.bkmeans(packed, sample, m, 2)
+    assert (cent == centres).all()
+    assert (assign[:m] == np.arange(m)).all()
+
+
+# ---------------------------------------------------------------- routing + partitioned graph
+def test_route_matches_brute_force(oracle_lib):
+    bits = 256
+    c = _rand_codes(120, bits, 51)
+    ce = _rand_codes(13, bits, 52)
+    ce[4] = ce[9]  # duplicate centre: tie broken by centre index
+    r, d = oracle_lib.route(c, ce, 5)
+    full = (_bits(c, bits)[:, None, :] != _bits(ce, bits)[None, :, :]).sum(2)
+    for i in range(120):
+        order = np.lexsort((np.arange(13), full[i]))[:5]
+        assert list(r[i]) == list(order)
+        assert list(d[i]) == [int(full[i, o]) for o in order]
+
+
+def test_partitioned_probe_all_equals_exact(oracle_lib):
+    spec = datagen.MixtureSpec(600, 32, 8, 128, seed=61)
+    c = datagen.make_codes(spec).numpy().view(np.uint64)
+    ce, _, _ = oracle_lib.bkmeans(c, datagen.sample_ids(600, 600, 62), 6, 4)
+    r, _ = oracle_lib.route(c, ce, 6)  # t = m: every partition is probed
+    ids_p, dist_p = oracle_lib.knn_partitioned(c, r, 16)
+    ids_e, dist_e = oracle_lib.knn_exact(c, 16)
+    assert (ids_p == ids_e).all() and (dist_p == dist_e).all()
+    r1 = np.zeros((600, 1), np.int32)  # m = 1
+    ids_1, _ = oracle_lib.knn_partitioned(c, r1, 16)
+    assert (ids_1 == ids_e).all()
+
+
+def test_partitioned_rows_lie_in_candidate_set(oracle_lib):
+    spec = datagen.MixtureSpec(800, 32, 8, 128, seed=71)
+    c = datagen.make_codes(spec).numpy().view(np.uint64)
+    ce, _, _ = oracle_lib.bkmeans(c, datagen.sample_ids(800, 512, 72), 8, 4)
+    r, _ = oracle_lib.route(c, ce, 2)
+    ids, dist = oracle_lib.knn_partitioned(c, r, 8)
+    home = r[:, 0]
+    b = _bits(c, 128)
+    for i in range(0, 800, 7):
+        cand = [j for j in range(800) if j != i and home[j] in set(r[i])]
+        d = {j: int((b[i] != b[j]).sum()) for j in cand}
+        want = sorted(cand, key=lambda j: (d[j], j))[:8]
+        got = [int(x) for x in ids[i] if x >= 0]
+        assert got == want
+        assert all(int(x) in set(cand) for x in got)
+
+
+# ---------------------------------------------------------------- search
+def _thermometer(n, bits=64):
+    c = np.zeros((n, bits // 64), np.uint64)
+    for i in range(n):
+        for b in range(i):
+            c[i, b // 64] |= np.uint64(1) << np.uint64(b % 64)
+    return c
+
+
+def test_search_hand_worked_greedy_walk(oracle_lib):
+    # 16 points on a line (thermometer codes: d(i, j) = |i - j|), graph = i-1, i+1;
+    # entry sample {0}; query at 12; ef = 1 walks 0 -> 1 -> ... -> 12:
+    # 13 expansions, 1 + 13 distance evaluations (entry + nodes 1..13), result (12, 0).
+    c = _thermometer(16)
+    g = np.array([[i - 1 if i > 0 else -1, i + 1 if i < 15 else -1] for i in range(16)],
+                 np.int32)
+    ids, dist, cnt = oracle_lib.search(c, g, np.array([0], np.int32), c[12:13], 1, 1)
+    assert ids[0, 0] == 12 and dist[0, 0] == 0
+    assert list(cnt[0]) == [13, 14]
+
+
+def test_search_complete_graph_equals_brute_force(oracle_lib):
+    n, bits = 90, 256
+    c = _rand_codes(n, bits, 81)
+    g = np.array([[j for j in range(n) if j != i] for i in range(n)], np.int32)
+    q = _rand_codes(12, bits, 82)
+    ids, dist, cnt = oracle_lib.search(c, g, np.array([3, 50], np.int32), q, n, n)
+    full = (_bits(q, bits)[:, None, :] != _bits(c, bits)[None, :, :]).sum(2)
+    for i in range(12):
+        order = np.lexsort((np.arange(n), full[i]))
+        assert list(ids[i]) == list(order)
+        assert list(dist[i]) == [int(full[i, o]) for o in order]
+    assert (cnt[:, 1] == n + 1).all()  # entry sample (2) + every other point once
+
+
+def test_search_pads_short_pools(oracle_lib):
+    c = _thermometer(4)
+    g = np.array([[1, -1], [0, -1], [3, -1], [2, -1]], np.int32)  # two components
+    ids, dist, _ = oracle_lib.search(c, g, np.array([0], np.int32), c[1:2], 8, 5)
+    assert list(ids[0]) == [1, 0, -1, -1, -1]
+    assert list(dist[0]) == [0, 1, 65, 65, 65]
+
+
+# ---------------------------------------------------------------- re-rank
+def test_rerank_integer_grid_exact(oracle_lib):
+    # integer-valued features: squared L2 is exact in both precisions
+    f = np.array([[0, 0], [1, 0], [0, 2], [3, 4], [1, 1], [1, 0]], np.float32)
+    qf = np.array([[1, 0]], np.float32)
+    cand = np.array([[3, 5, 2, 1, -1, 0, 4]], np.int32)
+    for prec in ("f32", "f64"):
+        ids, d = oracle_lib.rerank(f, qf, cand, 4, prec)
+        assert list(ids[0]) == [1, 5, 0, 4]  # d = 0, 0 (id tie), 1, 1 (id tie)
+        assert list(d[0]) == [0, 0, 1, 1]
+
+
+def test_rerank_f32_within_tolerance_of_f64(oracle_lib):
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((500, 128)).astype(np.float32)
+    qf = rng.standard_normal((20, 128)).astype(np.float32)
+    cand = np.array([rng.permutation(500)[:100] for _ in range(20)], np.int32)
+    i32, d32 = oracle_lib.rerank(f, qf, cand, 10, "f32")
+    i64, d64 = oracle_lib.rerank(f, qf, cand, 10, "f64")
+    brute = ((qf[:, None, :].astype(np.float64) - f[cand].astype(np.float64)) ** 2).sum(2)
+    for q in range(20):
+        order = cand[q][np.lexsort((cand[q], brute[q]))][:10]
+        assert list(i64[q]) == list(order)
+    assert np.allclose(d32, d64, rtol=1e-5, atol=0)
+
+
+# ---------------------------------------------------------------- recall (Eq. 3)
+def test_recall_definitions(oracle_lib):
+    exact = np.array([[1, 2, 3, 4]])
+    assert oracle_lib.recall_ids(np.array([[4, 3, 9, 1]]), exact) == 0.75
+    ed = np.array([[1, 2, 2, 2]])
+    assert oracle_lib.recall_tie_aware(np.array([[1, 2, 2, 2]]), ed) == 1.0
+    assert oracle_lib.recall_tie_aware(np.array([[1, 2, 3, 3]]), ed) == 0.5
