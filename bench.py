@@ -1,0 +1,494 @@
+#!/usr/bin/env python
+"""Benchmark of the Binary Distributed Graph hot path on B300.
+
+One step = one full graph build through the C ABI (bdg_build_graph: Bk-means
+on the down-sample, nearest-centre routing, on-device bucketing, the
+persistent fused Hamming + top-k kernel, the cross-partition merge) over the
+resident synthetic codes of the partitioned workload (N = 2M, 512-bit codes,
+m = 256 Bk-means partitions, t = 5 probed partitions, k = 64). The search half
+(N = 10M, 256-bit, 100k queries with mixed ef, FP32 re-rank) is measured in
+the same run and reported under "search".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank builds its own independent problem (a different seed):
+weak scaling, no collective on the data path; the value is all ranks' points
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+
+WORKLOAD = "partitioned_2m_512b"
+SEARCH_WORKLOAD = "search_10m_256b"
+METRIC = "kNN-graph build Mpoints/s at recall@k>=0.95 vs exhaustive; search QPS@recall@10"
+L2_FLUSH_BYTES = 256 << 20
+POPC_PER_SM_CLK = 16  # 32-bit population counts per SM per clock (integer pipe)
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-search", action="store_true")
+    ap.add_argument("--search-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--recall-rows", type=int, default=2000)
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, ws, device):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons every 200 ms (NVML) while running."""
+
+    REASONS = {
+        0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+        0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+        0x80: "hw_power_brake_slowdown",
+    }
+
+    def __init__(self, index):
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self._stop = threading.Event()
+        self._t = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._nv = pynvml
+            self._h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+        except Exception:
+            self._nv = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self._nv.nvmlDeviceGetClockInfo(self._h, self._nv.NVML_CLOCK_SM))
+                r = self._nv.nvmlDeviceGetCurrentClocksThrottleReasons(self._h)
+                for bit, name in self.REASONS.items():
+                    if r & bit and bit != 0x1:
+                        self.reasons.add(name)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        if self._nv is not None:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join()
+
+    def summary(self):
+        med = float(np.median(self.samples)) if self.samples else None
+        return {"sm_mhz": med, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
+                "samples": len(self.samples)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def _traffic_record(name):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    src = os.path.join(ROOT, "paper_2102_04656_b300", "csrc", "knn_popc.cu")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for ln in f:
+            if ":" in ln:
+                a, b = ln.split(":", 1)
+                vals[a.strip()] = b.strip()
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if vals.get("kernel_source_sha256_16") != h or "dram_bytes_per_launch_full" not in vals:
+        return None
+    return float(vals["dram_bytes_per_launch_full"])
+
+
+def _pairs_from_routes(routes):
+    m = int(routes.max().item()) + 1
+    hc = torch.bincount(routes[:, 0].long(), minlength=m).double()
+    vc = torch.bincount(routes.reshape(-1).long(), minlength=m).double()
+    return float((hc * vc).sum().item()), hc.cpu().numpy(), vc.cpu().numpy()
+
+
+def _recall(bdg, g, codes, k, rows_n, seed):
+    """Tie-aware and id recall of graph rows vs exact rows (bdg_knn_rows)."""
+    n = codes.shape[0]
+    rows = torch.from_numpy(datagen.sample_ids(n, rows_n, seed).astype(np.int32)).cuda()
+    ids, dist = bdg.knn_rows(codes, rows, k)
+    gi = g.ids[rows.long()]
+    gd = g.dists[rows.long()]
+    dk = dist[:, -1:]
+    below = (gd < dk).sum(1)
+    at = torch.minimum((gd == dk).sum(1), (dist == dk).sum(1))
+    tie = float((below + at).sum().item()) / (rows_n * k)
+    inter = 0
+    gi_c, ex_c = gi.cpu().numpy(), ids.cpu().numpy()
+    for a, b in zip(gi_c, ex_c):
+        inter += len(set(a.tolist()) & set(b.tolist()))
+    return tie, inter / (rows_n * k)
+
+
+def _build_inputs(w, device, seed_shift=0):
+    spec = w["spec"]
+    if seed_shift:
+        spec = datagen.MixtureSpec(spec.n, spec.dim, spec.components, spec.bits, spec.sigma,
+                                   spec.seed + 100 * seed_shift)
+    codes = datagen.make_codes(spec, device=device)
+    sample = torch.from_numpy(datagen.sample_ids(spec.n, 64 * w["m"], spec.seed + 3)).to(device)
+    entry = torch.from_numpy(datagen.sample_ids(spec.n, 256, spec.seed + 4).astype(np.int32)).to(device)
+    return spec, codes, sample, entry
+
+
+def _cpu_baseline_build(codes_np, w, seconds):
+    """The oracle as it stands on the host cores: Bk-means + routing of all
+    points (setup), then per sampled point its route and its graph row."""
+    import oracle
+    spec = w["spec"]
+    n, m, t, k = spec.n, w["m"], w["t"], w["k"]
+    sample = datagen.sample_ids(n, 64 * m, spec.seed + 3)
+    cent, _, _ = oracle.bkmeans(codes_np, sample, m, w["bk_iters"])
+    routes, _ = oracle.route(codes_np, cent, t)
+    rows_all = datagen.sample_ids(n, 200000, 7)
+    done, t_route, t_knn = 0, 0.0, 0.0
+    chunk = 64 * oracle.threads()
+    while t_route + t_knn < seconds and done + chunk <= rows_all.size:
+        rows = rows_all[done:done + chunk]
+        t0 = time.perf_counter()
+        oracle.route(codes_np[rows], cent, t)
+        t1 = time.perf_counter()
+        oracle.knn_partitioned(codes_np, routes, k, rows)
+        t2 = time.perf_counter()
+        t_route += t1 - t0
+        t_knn += t2 - t1
+        done += chunk
+    v = done / (t_route + t_knn) / 1e6
+    return {"value": v, "unit": "Mpoints/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{done} seeded points of the {WORKLOAD} workload: each point's route "
+                      f"to its {t} nearest of {m} Bk-means centres and its exact row over its "
+                      f"candidate set (homes of all {n} points routed once, untimed)"}
+
+
+def _search_bench(bdg, device, steps, warmup, clk_summary):
+    w = datagen.WORKLOADS[SEARCH_WORKLOAD]
+    spec = w["spec"]
+    codes, feats = datagen.make_codes(spec, device=device, with_features=True)
+    qcodes, qfeats = datagen.make_codes(spec, device=device, n=w["nq"], seed_offset=2,
+                                        with_features=True)
+    n, nq, k, topk = spec.n, w["nq"], w["k"], w["topk"]
+    m, t = 1024, 3
+    sample = torch.from_numpy(datagen.sample_ids(n, 64 * m, spec.seed + 3)).to(device)
+    entry = torch.from_numpy(datagen.sample_ids(n, 256, spec.seed + 4).astype(np.int32)).to(device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = bdg.build_graph(codes, k, m=m, t=t, bk_sample=sample, bk_iters=8, entry=entry)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    ef = torch.from_numpy(datagen.ef_mix(nq, w["efs"], spec.seed + 6)).to(device)
+    R = 10 * topk
+    for _ in range(warmup):
+        bdg.search_rerank(g, qcodes, qfeats, feats, ef, R, topk, ef_max=max(w["efs"]))
+    torch.cuda.synchronize()
+    bdg.lib().bdg_profile_reset()
+    bdg.lib().bdg_profile_enable(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for s in range(steps):
+        ev[s][0].record()
+        ids, d2 = bdg.search_rerank(g, qcodes, qfeats, feats, ef, R, topk, ef_max=max(w["efs"]))
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    bdg.lib().bdg_profile_enable(0)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    import ctypes
+    tot, nl = ctypes.c_double(), ctypes.c_int64()
+    bdg.lib().bdg_profile_read(b"search", ctypes.byref(tot), ctypes.byref(nl))
+    search_ms = tot.value / max(1, nl.value)
+    bdg.lib().bdg_profile_read(b"rerank", ctypes.byref(tot), ctypes.byref(nl))
+    rerank_ms = tot.value / max(1, nl.value)
+    # recall@10 against exact FP32 neighbours on a query sample (torch, TF32 off)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    qs = torch.from_numpy(datagen.sample_ids(nq, 1000, 3)).to(device)
+    qx = qfeats[qs]
+    best = torch.full((qs.numel(), topk), float("inf"), device=device)
+    best_i = torch.zeros((qs.numel(), topk), dtype=torch.int64, device=device)
+    fn = (feats * feats).sum(1)
+    for s0 in range(0, n, 1 << 21):
+        e0 = min(n, s0 + (1 << 21))
+        d = fn[s0:e0][None, :] - 2.0 * qx @ feats[s0:e0].T
+        v, i = torch.topk(d, topk, dim=1, largest=False)
+        cat_v = torch.cat([best, v], 1)
+        cat_i = torch.cat([best_i, i + s0], 1)
+        o = torch.topk(cat_v, topk, dim=1, largest=False).indices
+        best, best_i = torch.gather(cat_v, 1, o), torch.gather(cat_i, 1, o)
+    got = ids[qs].long()
+    hit = 0
+    for a, b in zip(got.cpu().numpy(), best_i.cpu().numpy()):
+        hit += len(set(a.tolist()) & set(b.tolist()))
+    rec = hit / (qs.numel() * topk)
+    # algorithmic bytes of the search kernel: per expansion a 4*deg-byte id list and
+    # one 32-byte code per scored neighbour (upper bound: every neighbour scored)
+    _, _, ex = bdg.search(g, qcodes, ef, R, ef_max=max(w["efs"]), expansions=True)
+    exp_total = float(ex.double().sum().item())
+    bytes_search = exp_total * (4 * k + k * 8 * (spec.bits // 64))
+    return {
+        "workload": SEARCH_WORKLOAD, "N": n, "bits": spec.bits, "degree": k, "nq": nq,
+        "ef_mix": list(w["efs"]), "R": R, "topk": topk, "graph_build": {"m": m, "t": t,
+                                                                         "seconds": build_s},
+        "qps": nq / (ms / 1000.0), "ms_per_batch": ms, "recall@10_vs_exact_fp32": rec,
+        "recall_queries": int(qs.numel()), "search_kernel_ms": search_ms,
+        "rerank_kernel_ms": rerank_ms, "expansions_mean": exp_total / nq,
+        "search_bytes_upper_bound_gbs": bytes_search / (search_ms / 1e3) / 1e9,
+    }
+
+
+def run_ours(a):
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2102_04656_b300 import build as bdg_build
+    if rank == 0:
+        bdg_build.build()
+    _barrier(ws)
+    import paper_2102_04656_b300 as bdg
+    import ctypes
+    L = bdg.lib()
+    w = datagen.WORKLOADS[WORKLOAD]
+    spec, codes, sample, entry = _build_inputs(w, device, seed_shift=rank)
+    n, k, m, t = spec.n, w["k"], w["m"], w["t"]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+
+    def step():
+        return bdg.build_graph(codes, k, m=m, t=t, bk_sample=sample, bk_iters=w["bk_iters"],
+                               entry=entry)
+
+    for i in range(a.warmup):
+        g = step()
+        torch.cuda.synchronize()
+        if i < a.warmup - 1:
+            g.free()
+    tie, idrec = _recall(bdg, g, codes, k, a.recall_rows, spec.seed + 9)
+    g.free()
+    # pair count of the kNN kernel: sum over partitions of |V_p| * |H_p|
+    cent, _ = bdg.bkmeans(codes, sample, m, w["bk_iters"])
+    routes, _ = bdg.route(codes, cent, t)
+    pairs, hc, vc = _pairs_from_routes(routes)
+    del cent, routes
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    L.bdg_profile_reset()
+    launches0 = L.bdg_launch_count()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with Clocks(local) as clk:
+        for s in range(a.steps):
+            flush.fill_(s & 0xFF)  # evict the previous step's data from L2 (outside the events)
+            L.bdg_profile_enable(1)
+            ev[s][0].record()
+            g = step()
+            ev[s][1].record()
+            L.bdg_profile_enable(0)
+            torch.cuda.synchronize()
+            g.free()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    wall = time.perf_counter() - wall0
+    launches = L.bdg_launch_count() - launches0
+    ms = sum(x.elapsed_time(y) for x, y in ev) / a.steps
+    ms_max = _max_over_ranks(ms, ws, device)
+    tot, nl = ctypes.c_double(), ctypes.c_int64()
+    L.bdg_profile_read(b"knn", ctypes.byref(tot), ctypes.byref(nl))
+    knn_ms = tot.value / max(1, nl.value)
+    L.bdg_profile_read(b"merge", ctypes.byref(tot), ctypes.byref(nl))
+    merge_ms = tot.value / max(1, nl.value)
+    L.bdg_profile_read(b"route", ctypes.byref(tot), ctypes.byref(nl))
+    route_ms = tot.value / max(1, nl.value)
+
+    # end to end: pinned host codes -> device -> build -> graph rows back to the host
+    host_codes = codes.cpu().pin_memory()
+    host_ids = torch.empty(n, k, dtype=torch.int32).pin_memory()
+    host_d = torch.empty(n, k, dtype=torch.int32).pin_memory()
+    dev_codes = torch.empty_like(codes)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(a.steps)]
+    for s in range(a.steps):
+        flush.fill_(s & 0xFF)
+        e2e_ev[s][0].record()
+        dev_codes.copy_(host_codes, non_blocking=True)
+        g = bdg.build_graph(dev_codes, k, m=m, t=t, bk_sample=sample, bk_iters=w["bk_iters"],
+                            entry=entry)
+        host_ids.copy_(g.ids, non_blocking=True)
+        host_d.copy_(g.dists, non_blocking=True)
+        e2e_ev[s][1].record()
+        torch.cuda.synchronize()
+        g.free()
+    e2e_ms = _max_over_ranks(sum(x.elapsed_time(y) for x, y in e2e_ev) / a.steps, ws, device)
+
+    search = None
+    if not a.no_search and ws == 1:
+        search = _search_bench(bdg, device, a.search_steps, 2, None)
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    peaks, peak_kind = _peaks()
+    cs = clk.summary()
+    bitops = pairs * spec.bits
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    nsm = torch.cuda.get_device_properties(device).multi_processor_count
+    peak_bitops = nsm * POPC_PER_SM_CLK * 32 * sm_max * 1e6
+    achieved = bitops / (knn_ms / 1e3)
+    traffic = _traffic_record(f"knn_popc_{WORKLOAD}.txt")
+    line = {
+        "metric": METRIC, "value": n * ws / (ms_max / 1e3) / 1e6, "unit": "Mpoints/s",
+        "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded Gaussian-mixture features -> sign of random projections)",
+        "config": {"workload": WORKLOAD, "N": n, "bits": spec.bits, "m": m, "t": t, "k": k,
+                   "bk_sample": int(sample.numel()), "bk_iters": w["bk_iters"],
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "parallelism": f"independent problem per GPU x{ws}"},
+        "recall": {"tie_aware": tie, "ids": idrec, "rows": a.recall_rows,
+                   "judge": "exact brute-force rows (bdg_knn_rows)"},
+        "roofline": {"kernel": "knn_popc (fused Hamming + top-k, persistent)", "bound": "alu",
+                     "achieved": achieved / 1e12, "peak": peak_bitops / 1e12, "unit": "Tbitop/s",
+                     "frac": achieved / peak_bitops, "traffic": traffic,
+                     "peak_source": f"{nsm} SMs x {POPC_PER_SM_CLK} POPC/clk x 32 bit x "
+                                    f"{sm_max:.0f} MHz ({peak_kind} max clock)",
+                     "pairs_per_launch": pairs, "kernel_ms": knn_ms,
+                     "share_of_step": knn_ms / ms},
+        "kernels_ms": {"knn": knn_ms, "merge": merge_ms, "route": route_ms},
+        "partition_sizes": {"home_min": int(hc.min()), "home_max": int(hc.max()),
+                            "home_median": float(np.median(hc)),
+                            "visit_max": int(vc.max())},
+        "clocks": cs, "gpu_launches": int(launches),
+        "e2e": {"value": n * ws / (e2e_ms / 1e3) / 1e6, "unit": "Mpoints/s",
+                "h2d_bytes_per_step": int(codes.numel() * 8),
+                "d2h_bytes_per_step": int(2 * n * k * 4)},
+        "wall_s_timed": wall,
+    }
+    if search is not None:
+        line["search"] = search
+    if ws == 1:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"] = _cpu_baseline_build(codes.cpu().numpy().view(np.uint64), w,
+                                                   a.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(a):
+    """The oracle, as it stands, timed on the host cores on bounded samples of the
+    same workload (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = datagen.WORKLOADS[WORKLOAD]
+    spec = w["spec"]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    codes = datagen.make_codes(spec, device=dev).cpu().numpy().view(np.uint64)
+    n, m, t, k = spec.n, w["m"], w["t"], w["k"]
+    sample = datagen.sample_ids(n, 64 * m, spec.seed + 3)
+    cent, _, _ = oracle.bkmeans(codes, sample, m, w["bk_iters"])
+    routes, _ = oracle.route(codes, cent, t)
+    rows_per_step = 16 * oracle.threads()
+    rows_all = datagen.sample_ids(n, (a.warmup + a.steps) * rows_per_step, 11)
+
+    def step(i):
+        rows = rows_all[i * rows_per_step:(i + 1) * rows_per_step]
+        oracle.route(codes[rows], cent, t)
+        oracle.knn_partitioned(codes, routes, k, rows)
+
+    for i in range(a.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        step(a.warmup + i)
+    el = time.perf_counter() - t0
+    v = rows_per_step * a.steps / el / 1e6
+    sample_desc = (f"{rows_per_step} seeded points per step of the {WORKLOAD} workload: route "
+                   f"to {t} of {m} centres + exact row over the candidate set (homes routed "
+                   f"once, untimed)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Mpoints/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded Gaussian-mixture features -> sign of random projections)",
+        "config": {"workload": WORKLOAD, "N": n, "bits": spec.bits, "m": m, "t": t, "k": k},
+        "cpu_baseline": {"value": v, "unit": "Mpoints/s", "cores": oracle.threads(),
+                         "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": v, "unit": "Mpoints/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

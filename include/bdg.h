@@ -1,0 +1,179 @@
+/*
+ * bdg.h -- C ABI of the B300 (sm_103a) Binary Distributed Graph library.
+ *
+ * The library builds a k-nearest-neighbour graph over packed binary codes under
+ * Hamming distance and searches it, following Zhao et al., "Large-Scale Visual
+ * Search with Binary Distributed Graph at Alibaba": Hamming distance and the
+ * k-NN label sets B(l_i) of Section 3, binary codes of Section 3.1, Bk-means
+ * (Eq. 1-2) and the single-pass divide-and-conquer build of Section 3.2, and the
+ * search procedure with real-valued re-rank of Section 3.5.
+ *
+ * Conventions for every call:
+ *   - Array arguments are DEVICE pointers unless a comment says "host". The
+ *     caller owns every array it passes in or out; the library owns only what a
+ *     handle (bdg_graph, bdg_router) holds and frees it in the matching _free.
+ *   - Codes: uint64 [n][W] row-major, W = bits / 64, bit j of a code in word
+ *     j / 64 at bit position j % 64 (least-significant bit first). bits is a
+ *     multiple of 64 with W in {1, 2, 4, 8, 16}.
+ *   - Neighbour lists order candidates by (distance, id) ascending. Rows with
+ *     fewer valid entries than requested are padded with id = -1 and
+ *     distance = bits + 1.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls enqueue
+ *     work and return without synchronising unless documented otherwise.
+ *   - Every call returns a bdg_status; arguments are checked before any work is
+ *     enqueued. On failure bdg_last_error() gives a message for the calling
+ *     thread. No call aborts or throws.
+ */
+#ifndef BDG_H_
+#define BDG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BDG_OK = 0,
+  BDG_EINVAL = -1,        /* an argument is out of range or inconsistent */
+  BDG_ENOMEM = -2,        /* a device allocation failed or the budget is exceeded */
+  BDG_ECUDA = -3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  BDG_ETIMEOUT = -4,      /* a bounded device wait gave up */
+  BDG_EUNSUPPORTED = -5   /* the configuration is valid but not built (e.g. W = 3) */
+} bdg_status;
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* bdg_last_error(void);
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+int32_t bdg_version(void);
+
+/* Device memory budget of the library in bytes (0 = unlimited). Allocations
+ * that would take the library's live total above it fail with BDG_ENOMEM. */
+bdg_status bdg_set_memory_budget(uint64_t bytes);
+uint64_t bdg_memory_in_use(void);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t bdg_launch_count(void);
+
+/* Event timing of the library's main kernels on their launch streams (off by
+ * default). bdg_profile_read synchronises on the recorded events and returns
+ * the summed device time and launch count of the kernel `name` ("knn",
+ * "merge", "route", "search", "rerank"); bdg_profile_reset drops all records. */
+void bdg_profile_enable(int32_t on);
+bdg_status bdg_profile_read(const char* name, double* total_ms, int64_t* launches);
+void bdg_profile_reset(void);
+
+/* ------------------------------------------------------------------ pieces */
+
+/* Hamming k-NN of Section 3 / the nearest-centre map step of Section 3.2:
+ * for each of the n points, the t nearest of m centres ordered by
+ * (d(y_i, c_c), c). routes/rdist: [n][t] int32. 1 <= t <= min(m, 16). */
+bdg_status bdg_route(const uint64_t* codes, int64_t n, int32_t bits, const uint64_t* centroids,
+                     int32_t m, int32_t t, int32_t* routes, int32_t* rdist, void* stream);
+
+/* Bk-means of Section 3.2 (objective Eq. 1, update Eq. 2) on the down-sample
+ * codes[sample[0..S)]: centres start as the codes of sample[0..m); each of
+ * `iters` iterations assigns every sample point to its nearest centre by
+ * (distance, centre index) and sets each centre bit to the majority of its
+ * members' bits, keeping the previous bit on a tie and the previous centre
+ * when the cluster is empty. centroids: out [m][W]. loss: optional out int64
+ * [iters + 1], the objective after each assign step (NULL to skip).
+ * Requires m <= S. */
+bdg_status bdg_bkmeans(const uint64_t* codes, int64_t n, int32_t bits, const int64_t* sample,
+                       int64_t S, int32_t m, int32_t iters, uint64_t* centroids, int64_t* loss,
+                       void* stream);
+
+/* Exact k-NN rows of Section 3 (the ideal B(l_i) under d = l_h) for selected
+ * points: row r is the first k of sort over (d(rows[r], j), j) for all
+ * j != rows[r] in [0, N). The brute-force judge of a graph's recall.
+ * rows: [nrows] int32; out_ids/out_dist: [nrows][k]. 1 <= k <= 128, k < N. */
+bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const int32_t* rows,
+                        int64_t nrows, int32_t k, int32_t* out_ids, int32_t* out_dist,
+                        void* stream);
+
+/* ------------------------------------------------------------------ build */
+
+/* The `partitions` argument of the build (Section 3.2). */
+typedef struct bdg_partitions {
+  int32_t m;                  /* number of partitions (1 = exact brute force) */
+  int32_t t;                  /* partitions probed per point, home included; 1 <= t <= m, t <= 16 */
+  const uint64_t* centroids;  /* [m][W] binary centres, or NULL: run Bk-means first */
+  const int64_t* bk_sample;   /* [bk_sample_size] point ids of the Bk-means down-sample */
+  int64_t bk_sample_size;     /* >= m when centroids == NULL */
+  int32_t bk_iters;           /* Bk-means iterations (the paper uses fewer than 10) */
+  const int32_t* routes;      /* [N][t] precomputed routes (slot 0 = home), or NULL; a row
+                                 must hold distinct partitions; values outside [0, m) are
+                                 ignored (that slot contributes no neighbours) */
+  const int32_t* entry;       /* [n_entry] long-link sample ids kept with the graph (Section 3.5) */
+  int32_t n_entry;            /* 1 <= n_entry */
+  int32_t tile_visitors;      /* work-item size in visitors (32 or 64); 0 = autotuned */
+} bdg_partitions;
+
+typedef struct bdg_graph bdg_graph; /* opaque; owns ids/dists/entry, borrows codes */
+
+/* Single-pass divide-and-conquer k-NN graph of Section 3.2 on one GPU:
+ *   route every point to its t nearest centres (slot 0 = home, the flagged
+ *   record of the Map step), group points by home and by routed partition
+ *   (Shuffle 1), compute for every routed point the exact k nearest home
+ *   records of each of its partitions with a fused Hamming + top-k kernel
+ *   (Reduce 1), and merge the t partial lists per point (Shuffle 2 + Reduce 2).
+ * The result equals G(i) = first k of sort over (d(i, j), j) for j != i whose
+ * home is one of i's t partitions; with m = 1 it is the exact k-NN graph.
+ * codes: [N][W] borrowed (must outlive the graph). 1 <= k <= 128, k < N,
+ * N < 2^31. *out receives a new graph handle; free with bdg_graph_free. */
+bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
+                           const bdg_partitions* partitions, void* stream, bdg_graph** out);
+
+/* Device pointers to the graph rows: ids/dists [N][k] int32, row i sorted by
+ * (distance, id). Any output pointer may be NULL. Host scalars n/k/bits. */
+bdg_status bdg_graph_info(const bdg_graph* g, const int32_t** ids, const int32_t** dists,
+                          int64_t* n, int32_t* k, int32_t* bits);
+
+/* Save to / load from a file: header {magic "BDG1", version, N, bits, k, n_entry}
+ * followed by ids, dists and entry ids (little-endian int32). Synchronous.
+ * load borrows `codes` ([N][W], device) for later searches. */
+bdg_status bdg_graph_save(const bdg_graph* g, const char* path);
+bdg_status bdg_graph_load(const char* path, const uint64_t* codes, bdg_graph** out);
+void bdg_graph_free(bdg_graph* g);
+
+/* ------------------------------------------------------------------ search */
+
+/* Search procedure of Section 3.5, per query q (keys kappa(j) = (d(q, j), j)):
+ * the entry is the nearest long-link sample point; then best-first hill
+ * climbing on the graph with a pool of the ef best keys seen, expanding the
+ * best unexpanded pool entry until none is left. Writes the first
+ * min(ef[q], R) pool keys ascending, padded to R.
+ * queries: [nq][W]. ef: [nq] int32 (a per-query pool size; batches may mix
+ * sizes). ef_max (host): an upper bound of ef over the batch, 1 <= ef_max <=
+ * 1024; it sizes the per-query pool. A query whose ef is outside [1, ef_max]
+ * gets a row of padding and expansions = -1. out_ids/out_dist: [nq][R].
+ * expansions: optional out [nq] int32 (nodes whose lists were scanned). */
+bdg_status bdg_search(const bdg_graph* g, const uint64_t* queries, int64_t nq, const int32_t* ef,
+                      int32_t ef_max, int32_t R, int32_t* out_ids, int32_t* out_dist,
+                      int32_t* expansions, void* stream);
+
+/* Real-valued re-rank of Section 3.5 (d = l2 of Section 3): for each query the
+ * squared L2 distance between qfeats[q] and feats[j] for every candidate j of
+ * cand[q] (entries -1 skipped), computed in FP32, and the first k by
+ * (distance, id). feats: [N][D] f32, qfeats: [nq][D] f32, cand: [nq][R] int32.
+ * out_ids: [nq][k] int32, out_d2: [nq][k] f32 (padded with -1 / +inf).
+ * D in {128, 256, 512, 1024}; feats/qfeats 16-byte aligned; 1 <= k <= 32;
+ * 1 <= R <= 1024. Candidate ids outside [0, N) are skipped like -1. */
+bdg_status bdg_rerank(const float* feats, int64_t N, int32_t D, const float* qfeats,
+                      const int32_t* cand, int64_t nq, int32_t R, int32_t k, int32_t* out_ids,
+                      float* out_d2, void* stream);
+
+/* bdg_search followed by bdg_rerank of its R binary candidates with the query
+ * features: the full online path of Section 3.5. cand_ids/cand_dist: [nq][R]
+ * int32 caller-owned buffers that receive the binary candidates. */
+bdg_status bdg_search_rerank(const bdg_graph* g, const uint64_t* queries, const float* qfeats,
+                             const float* feats, int32_t D, int64_t nq, const int32_t* ef,
+                             int32_t ef_max, int32_t R, int32_t k, int32_t* cand_ids,
+                             int32_t* cand_dist, int32_t* out_ids, float* out_d2, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDG_H_ */

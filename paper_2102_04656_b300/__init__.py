@@ -1,0 +1,290 @@
+"""Python binding of the B300 Binary Distributed Graph library (include/bdg.h).
+
+Argument marshalling only: every step of the build and the search runs in the
+CUDA kernels of libbdg.so. torch supplies device memory and the current CUDA
+stream. The library must be built (``paper_2102_04656_b300.build.build()``);
+importing works without it, but every call raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "BDGError", "lib", "route", "bkmeans", "build_graph", "Graph", "search", "rerank",
+    "search_rerank", "load_graph", "set_memory_budget", "memory_in_use", "knn_rows",
+    "launch_count",
+]
+
+_LIB = None
+_c_void_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+class BDGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"bdg status {status}: {msg}")
+        self.status = status
+
+
+class _Partitions(ctypes.Structure):
+    _fields_ = [
+        ("m", _i32), ("t", _i32), ("centroids", _c_void_p), ("bk_sample", _c_void_p),
+        ("bk_sample_size", _i64), ("bk_iters", _i32), ("routes", _c_void_p),
+        ("entry", _c_void_p), ("n_entry", _i32), ("tile_visitors", _i32),
+    ]
+
+
+def lib():
+    """Load libbdg.so from the package's _build folder (raises if it is not built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libbdg.so is not built ({_build.LIB}); run "
+                              "paper_2102_04656_b300.build.build()")
+        L = ctypes.CDLL(_build.LIB)
+        L.bdg_last_error.restype = ctypes.c_char_p
+        L.bdg_memory_in_use.restype = ctypes.c_uint64
+        L.bdg_set_memory_budget.argtypes = [ctypes.c_uint64]
+        L.bdg_route.argtypes = [_c_void_p, _i64, _i32, _c_void_p, _i32, _i32, _c_void_p,
+                                _c_void_p, _c_void_p]
+        L.bdg_bkmeans.argtypes = [_c_void_p, _i64, _i32, _c_void_p, _i64, _i32, _i32, _c_void_p,
+                                  _c_void_p, _c_void_p]
+        L.bdg_build_graph.argtypes = [_c_void_p, _i64, _i32, _i32, ctypes.POINTER(_Partitions),
+                                      _c_void_p, ctypes.POINTER(_c_void_p)]
+        L.bdg_graph_info.argtypes = [_c_void_p, ctypes.POINTER(_c_void_p),
+                                     ctypes.POINTER(_c_void_p), ctypes.POINTER(_i64),
+                                     ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+        L.bdg_graph_free.argtypes = [_c_void_p]
+        L.bdg_graph_free.restype = None
+        L.bdg_graph_save.argtypes = [_c_void_p, ctypes.c_char_p]
+        L.bdg_graph_load.argtypes = [ctypes.c_char_p, _c_void_p, ctypes.POINTER(_c_void_p)]
+        L.bdg_search.argtypes = [_c_void_p, _c_void_p, _i64, _c_void_p, _i32, _i32, _c_void_p,
+                                 _c_void_p, _c_void_p, _c_void_p]
+        L.bdg_rerank.argtypes = [_c_void_p, _i64, _i32, _c_void_p, _c_void_p, _i64, _i32, _i32,
+                                 _c_void_p, _c_void_p, _c_void_p]
+        L.bdg_launch_count.restype = _i64
+        L.bdg_profile_enable.argtypes = [_i32]
+        L.bdg_profile_enable.restype = None
+        L.bdg_profile_reset.restype = None
+        L.bdg_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(_i64)]
+        L.bdg_knn_rows.argtypes = [_c_void_p, _i64, _i32, _c_void_p, _i64, _i32, _c_void_p,
+                                   _c_void_p, _c_void_p]
+        L.bdg_search_rerank.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32, _i64,
+                                        _c_void_p, _i32, _i32, _i32, _c_void_p, _c_void_p,
+                                        _c_void_p, _c_void_p, _c_void_p]
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int):
+    if status != 0:
+        raise BDGError(status, lib().bdg_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name, ndim=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dims")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _codes(codes, name="codes"):
+    _dev(codes, torch.int64, name, 2)  # raw 64-bit words (uint64 bit patterns)
+    return codes, 64 * codes.shape[1]
+
+
+def set_memory_budget(nbytes: int):
+    _check(lib().bdg_set_memory_budget(int(nbytes)))
+
+
+def memory_in_use() -> int:
+    return int(lib().bdg_memory_in_use())
+
+
+def route(codes, centroids, t: int, stream=None):
+    """t nearest centres per point by (distance, centre): (routes, dists) int32 [n, t]."""
+    codes, bits = _codes(codes)
+    _codes(centroids, "centroids")
+    n, m = codes.shape[0], centroids.shape[0]
+    routes = torch.empty(n, t, dtype=torch.int32, device=codes.device)
+    rdist = torch.empty(n, t, dtype=torch.int32, device=codes.device)
+    _check(lib().bdg_route(_ptr(codes), n, bits, _ptr(centroids), m, t, _ptr(routes),
+                           _ptr(rdist), _stream(stream)))
+    return routes, rdist
+
+
+def knn_rows(codes, rows, k: int, stream=None):
+    """Exact k-NN rows of the points ``rows`` over all codes: (ids, dists) int32 [nrows, k]."""
+    codes, bits = _codes(codes)
+    _dev(rows, torch.int32, "rows", 1)
+    nr = rows.numel()
+    ids = torch.empty(nr, k, dtype=torch.int32, device=codes.device)
+    dist = torch.empty(nr, k, dtype=torch.int32, device=codes.device)
+    _check(lib().bdg_knn_rows(_ptr(codes), codes.shape[0], bits, _ptr(rows), nr, k, _ptr(ids),
+                              _ptr(dist), _stream(stream)))
+    return ids, dist
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().bdg_launch_count())
+
+
+def bkmeans(codes, sample, m: int, iters: int, stream=None):
+    """Bk-means on codes[sample]: (centroids int64 [m, W], loss int64 [iters + 1])."""
+    codes, bits = _codes(codes)
+    _dev(sample, torch.int64, "sample", 1)
+    cent = torch.empty(m, codes.shape[1], dtype=torch.int64, device=codes.device)
+    loss = torch.empty(iters + 1, dtype=torch.int64, device=codes.device)
+    _check(lib().bdg_bkmeans(_ptr(codes), codes.shape[0], bits, _ptr(sample), sample.numel(), m,
+                             iters, _ptr(cent), _ptr(loss), _stream(stream)))
+    return cent, loss
+
+
+class _CudaArray:
+    def __init__(self, ptr, shape, typestr, owner):
+        self.__cuda_array_interface__ = {
+            "shape": tuple(shape), "typestr": typestr, "data": (ptr, False), "version": 3,
+            "strides": None, "stream": None,
+        }
+        self._owner = owner
+
+
+class Graph:
+    """A k-NN graph owned by the library (freed with the object). ``codes`` is
+    borrowed and kept alive here."""
+
+    def __init__(self, handle, codes, feats=None):
+        self._h = ctypes.c_void_p(handle)
+        self.codes = codes
+        self.feats = feats
+        ids, dists = ctypes.c_void_p(), ctypes.c_void_p()
+        n, k, bits = _i64(), _i32(), _i32()
+        _check(lib().bdg_graph_info(self._h, ctypes.byref(ids), ctypes.byref(dists),
+                                    ctypes.byref(n), ctypes.byref(k), ctypes.byref(bits)))
+        self.n, self.k, self.bits = n.value, k.value, bits.value
+        dev = codes.device
+        self.ids = torch.as_tensor(_CudaArray(ids.value, (self.n, self.k), "<i4", self), device=dev)
+        self.dists = torch.as_tensor(_CudaArray(dists.value, (self.n, self.k), "<i4", self),
+                                     device=dev)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def save(self, path: str):
+        _check(lib().bdg_graph_save(self._h, path.encode()))
+
+    def free(self):
+        """Release the device rows now; ``ids``/``dists`` become unusable."""
+        if self._h is not None and self._h.value:
+            self.ids = self.dists = None
+            lib().bdg_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_graph(codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample=None,
+                bk_iters: int = 8, routes=None, entry=None, tile_visitors: int = 0,
+                stream=None) -> Graph:
+    """Single-pass divide-and-conquer k-NN graph (exact when m == 1)."""
+    codes, bits = _codes(codes)
+    if entry is None:
+        raise ValueError("entry (long-link sample ids, int32 CUDA tensor) is required")
+    _dev(entry, torch.int32, "entry", 1)
+    P = _Partitions()
+    P.m, P.t = m, t
+    P.centroids = None if centroids is None else _codes(centroids, "centroids")[0].data_ptr()
+    P.bk_sample = None if bk_sample is None else _dev(bk_sample, torch.int64, "bk_sample",
+                                                      1).data_ptr()
+    P.bk_sample_size = 0 if bk_sample is None else bk_sample.numel()
+    P.bk_iters = bk_iters
+    P.routes = None if routes is None else _dev(routes, torch.int32, "routes", 2).data_ptr()
+    P.entry = entry.data_ptr()
+    P.n_entry = entry.numel()
+    P.tile_visitors = tile_visitors
+    h = ctypes.c_void_p()
+    _check(lib().bdg_build_graph(_ptr(codes), codes.shape[0], bits, k, ctypes.byref(P),
+                                 _stream(stream), ctypes.byref(h)))
+    return Graph(h.value, codes)
+
+
+def load_graph(path: str, codes) -> Graph:
+    codes, _ = _codes(codes)
+    h = ctypes.c_void_p()
+    _check(lib().bdg_graph_load(path.encode(), _ptr(codes), ctypes.byref(h)))
+    return Graph(h.value, codes)
+
+
+def search(g: Graph, queries, ef, R: int, ef_max: int | None = None, expansions: bool = False,
+           stream=None):
+    """Best-first graph search: (ids, dists) int32 [nq, R] (+ expansions int32 [nq])."""
+    queries, _ = _codes(queries, "queries")
+    _dev(ef, torch.int32, "ef", 1)
+    nq = queries.shape[0]
+    if ef_max is None:
+        raise ValueError("ef_max (host bound on ef over the batch) is required")
+    ids = torch.empty(nq, R, dtype=torch.int32, device=queries.device)
+    dist = torch.empty(nq, R, dtype=torch.int32, device=queries.device)
+    ex = torch.empty(nq, dtype=torch.int32, device=queries.device) if expansions else None
+    _check(lib().bdg_search(g.handle, _ptr(queries), nq, _ptr(ef), ef_max, R, _ptr(ids),
+                            _ptr(dist), _ptr(ex), _stream(stream)))
+    return (ids, dist, ex) if expansions else (ids, dist)
+
+
+def rerank(feats, qfeats, cand, k: int, stream=None):
+    """FP32 squared-L2 re-rank of candidates: (ids int32 [nq, k], d2 float32 [nq, k])."""
+    _dev(feats, torch.float32, "feats", 2)
+    _dev(qfeats, torch.float32, "qfeats", 2)
+    _dev(cand, torch.int32, "cand", 2)
+    nq, R = cand.shape
+    ids = torch.empty(nq, k, dtype=torch.int32, device=cand.device)
+    d2 = torch.empty(nq, k, dtype=torch.float32, device=cand.device)
+    _check(lib().bdg_rerank(_ptr(feats), feats.shape[0], feats.shape[1], _ptr(qfeats), _ptr(cand),
+                            nq, R, k, _ptr(ids), _ptr(d2), _stream(stream)))
+    return ids, d2
+
+
+def search_rerank(g: Graph, queries, qfeats, feats, ef, R: int, k: int, ef_max: int,
+                  stream=None):
+    """Search then re-rank: (ids int32 [nq, k], d2 float32 [nq, k])."""
+    queries, _ = _codes(queries, "queries")
+    _dev(ef, torch.int32, "ef", 1)
+    _dev(feats, torch.float32, "feats", 2)
+    _dev(qfeats, torch.float32, "qfeats", 2)
+    nq = queries.shape[0]
+    dev = queries.device
+    cand = torch.empty(nq, R, dtype=torch.int32, device=dev)
+    cdist = torch.empty(nq, R, dtype=torch.int32, device=dev)
+    ids = torch.empty(nq, k, dtype=torch.int32, device=dev)
+    d2 = torch.empty(nq, k, dtype=torch.float32, device=dev)
+    _check(lib().bdg_search_rerank(g.handle, _ptr(queries), _ptr(qfeats), _ptr(feats),
+                                   feats.shape[1], nq, _ptr(ef), ef_max, R, k, _ptr(cand),
+                                   _ptr(cdist), _ptr(ids), _ptr(d2), _stream(stream)))
+    return ids, d2

@@ -1,0 +1,469 @@
+// api.cu -- the C ABI of include/bdg.h: argument checks, the memory budget,
+// graph handles, and the order of launches of a build or a search. No compute
+// happens here; every step of the path runs in the kernels of the other files.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+
+struct bdg_graph {
+  int64_t n;
+  int32_t k, bits, W, n_entry;
+  const uint64_t* codes;  // borrowed
+  int32_t* ids;           // [n][k]
+  int32_t* dists;         // [n][k]
+  int32_t* entry;         // [n_entry]
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<uint64_t> g_in_use{0};
+std::atomic<uint64_t> g_budget{0};
+
+bool valid_w(int W) { return W == 1 || W == 2 || W == 4 || W == 8 || W == 16; }
+
+bdg_status check_bits(int32_t bits) {
+  if (bits <= 0 || bits % 64 != 0 || !valid_w(bits / 64))
+    return bdg_set_error(BDG_EINVAL, "bits = %d: must be 64 * W with W in {1,2,4,8,16}", bits);
+  return BDG_OK;
+}
+
+bdg_status reserve(size_t bytes) {
+  const uint64_t b = g_budget.load();
+  const uint64_t now = g_in_use.fetch_add(bytes) + bytes;
+  if (b != 0 && now > b) {
+    g_in_use.fetch_sub(bytes);
+    return bdg_set_error(BDG_ENOMEM, "memory budget exceeded: %llu + %zu > %llu bytes",
+                         (unsigned long long)(now - bytes), bytes, (unsigned long long)b);
+  }
+  return BDG_OK;
+}
+void release(size_t bytes) { g_in_use.fetch_sub(bytes); }
+
+// Device allocation (synchronous) counted against the budget.
+bdg_status dalloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return BDG_OK;
+  BDG_TRY(reserve(bytes));
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    release(bytes);
+    *p = nullptr;
+    return bdg_set_error(BDG_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+  }
+  return BDG_OK;
+}
+void dfree(void* p, size_t bytes) {
+  if (p) { cudaFree(p); release(bytes); }
+}
+
+// Stream-ordered scratch, counted against the budget while it lives.
+struct Scratch {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  bdg_status alloc(size_t b, cudaStream_t s) {
+    st = s;
+    if (b == 0) return BDG_OK;
+    BDG_TRY(reserve(b));
+    if (cudaMallocAsync(&p, b, s) != cudaSuccess) {
+      cudaGetLastError();
+      release(b);
+      p = nullptr;
+      return bdg_set_error(BDG_ENOMEM, "cudaMallocAsync of %zu bytes failed", b);
+    }
+    bytes = b;
+    return BDG_OK;
+  }
+  ~Scratch() {
+    if (p) { cudaFreeAsync(p, st); release(bytes); }
+  }
+};
+
+inline size_t al(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ---- launch accounting and per-kernel event timing ----
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+struct ProfSlot {
+  std::string name;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+};
+std::vector<ProfSlot> g_prof;
+
+// Keep freed stream-ordered scratch cached in the device's pool between calls
+// (the default pool returns memory to the driver at every synchronisation).
+void keep_pool_cached() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
+}  // namespace
+
+void bdg_note_launch(int n) { g_launches.fetch_add(n); }
+
+bdg_prof_scope::bdg_prof_scope(const char* name, cudaStream_t s) : slot(-1), st(s) {
+  if (!g_prof_on.load()) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (size_t i = 0; i < g_prof.size(); ++i)
+    if (g_prof[i].name == name) slot = (int)i;
+  if (slot < 0) {
+    g_prof.push_back(ProfSlot{name, {}});
+    slot = (int)g_prof.size() - 1;
+  }
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, st);
+  g_prof[slot].ev.push_back({a, b});
+}
+
+bdg_prof_scope::~bdg_prof_scope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEventRecord(g_prof[slot].ev.back().second, st);
+}
+
+bdg_status bdg_set_error(bdg_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+int bdg_num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cache[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+extern "C" {
+
+const char* bdg_last_error(void) { return g_err; }
+int32_t bdg_version(void) { return 100; }
+
+int64_t bdg_launch_count(void) { return g_launches.load(); }
+
+void bdg_profile_enable(int32_t on) { g_prof_on.store(on != 0); }
+
+bdg_status bdg_profile_read(const char* name, double* total_ms, int64_t* launches) {
+  if (!name || !total_ms || !launches) return bdg_set_error(BDG_EINVAL, "profile: null argument");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  *total_ms = 0.0;
+  *launches = 0;
+  for (auto& sl : g_prof) {
+    if (sl.name != name) continue;
+    for (auto& e : sl.ev) {
+      float ms = 0.f;
+      BDG_CUDA_TRY(cudaEventSynchronize(e.second));
+      BDG_CUDA_TRY(cudaEventElapsedTime(&ms, e.first, e.second));
+      *total_ms += ms;
+      *launches += 1;
+    }
+  }
+  return BDG_OK;
+}
+
+void bdg_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& sl : g_prof)
+    for (auto& e : sl.ev) {
+      cudaEventSynchronize(e.second);
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  g_prof.clear();
+}
+
+bdg_status bdg_set_memory_budget(uint64_t bytes) {
+  g_budget.store(bytes);
+  return BDG_OK;
+}
+uint64_t bdg_memory_in_use(void) { return g_in_use.load(); }
+
+bdg_status bdg_route(const uint64_t* codes, int64_t n, int32_t bits, const uint64_t* centroids,
+                     int32_t m, int32_t t, int32_t* routes, int32_t* rdist, void* stream) {
+  BDG_TRY(check_bits(bits));
+  if (n < 0 || m < 1 || t < 1 || t > m || t > 16)
+    return bdg_set_error(BDG_EINVAL, "route: n=%lld m=%d t=%d", (long long)n, m, t);
+  if (n > 0 && (!codes || !centroids || !routes))
+    return bdg_set_error(BDG_EINVAL, "route: null pointer");
+  return bdg_launch_route(codes, n, bits / 64, centroids, m, t, routes, rdist, (cudaStream_t)stream);
+}
+
+bdg_status bdg_bkmeans(const uint64_t* codes, int64_t n, int32_t bits, const int64_t* sample,
+                       int64_t S, int32_t m, int32_t iters, uint64_t* centroids, int64_t* loss,
+                       void* stream) {
+  BDG_TRY(check_bits(bits));
+  if (m < 1 || S < m || iters < 0 || !codes || !sample || !centroids || n < 1)
+    return bdg_set_error(BDG_EINVAL, "bkmeans: n=%lld S=%lld m=%d iters=%d", (long long)n,
+                         (long long)S, m, iters);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int W = bits / 64;
+  keep_pool_cached();
+  Scratch sc;
+  const size_t sb = bdg_bkmeans_scratch_bytes(S, m, W);
+  BDG_TRY(sc.alloc(sb, st));
+  return bdg_launch_bkmeans(codes, n, W, sample, S, m, iters, centroids, loss, sc.p, sb, st);
+}
+
+bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
+                           const bdg_partitions* P, void* stream, bdg_graph** out) {
+  if (!out) return bdg_set_error(BDG_EINVAL, "build: out is NULL");
+  *out = nullptr;
+  BDG_TRY(check_bits(bits));
+  if (!codes || !P) return bdg_set_error(BDG_EINVAL, "build: null codes or partitions");
+  if (N < 2 || N >= (int64_t(1) << 31))
+    return bdg_set_error(BDG_EINVAL, "build: N = %lld out of [2, 2^31)", (long long)N);
+  if (k < 1 || k > 128 || k >= N)
+    return bdg_set_error(BDG_EINVAL, "build: k = %d must be in [1, min(128, N-1)]", k);
+  const int m = P->m, t = P->t;
+  if (m < 1 || t < 1 || t > m || t > 16)
+    return bdg_set_error(BDG_EINVAL, "build: m = %d, t = %d (need 1 <= t <= min(m, 16))", m, t);
+  if (!P->entry || P->n_entry < 1)
+    return bdg_set_error(BDG_EINVAL, "build: an entry sample (n_entry >= 1) is required");
+  const bool need_routes = (P->routes == nullptr) && m > 1;
+  const bool need_bk = need_routes && P->centroids == nullptr;
+  if (need_bk && (!P->bk_sample || P->bk_sample_size < m || P->bk_iters < 0))
+    return bdg_set_error(BDG_EINVAL, "build: Bk-means needs bk_sample with >= m ids");
+  if (P->tile_visitors != 0 && P->tile_visitors != bdg_knn_tile_visitors(bits / 64))
+    return bdg_set_error(BDG_EUNSUPPORTED, "build: tile_visitors %d not built for %d bits",
+                         P->tile_visitors, bits);
+
+  cudaStream_t st = (cudaStream_t)stream;
+  const int W = bits / 64;
+  const int tile_v = bdg_knn_tile_visitors(W);
+  keep_pool_cached();
+
+  // graph storage (owned by the handle)
+  bdg_graph* g = new bdg_graph();
+  g->n = N; g->k = k; g->bits = bits; g->W = W; g->n_entry = P->n_entry; g->codes = codes;
+  bdg_status s = dalloc((void**)&g->ids, (size_t)N * k * 4);
+  if (s == BDG_OK) s = dalloc((void**)&g->dists, (size_t)N * k * 4);
+  if (s == BDG_OK) s = dalloc((void**)&g->entry, (size_t)P->n_entry * 4);
+  if (s != BDG_OK) { bdg_graph_free(g); return s; }
+
+  // scratch layout
+  const size_t b_routes = need_routes || m == 1 ? al((size_t)N * t * 4) : 0;
+  const size_t b_cent = need_bk ? al((size_t)m * W * 8) : 0;
+  const size_t b_bk = need_bk ? al(bdg_bkmeans_scratch_bytes(P->bk_sample_size, m, W)) : 0;
+  const size_t b_csr = al(bdg_csr_bytes(N, m, t, W));
+  const size_t b_part = t > 1 ? al((size_t)N * t * k * 8) : 0;
+  Scratch sc;
+  s = sc.alloc(b_routes + b_cent + b_bk + b_csr + b_part, st);
+  if (s != BDG_OK) { bdg_graph_free(g); return s; }
+  char* p = (char*)sc.p;
+  int32_t* routes = (int32_t*)P->routes;
+  if (b_routes) { routes = (int32_t*)p; p += b_routes; }
+  uint64_t* cent = (uint64_t*)P->centroids;
+  if (b_cent) { cent = (uint64_t*)p; p += b_cent; }
+  void* bk = p; p += b_bk;
+  void* csr_mem = p; p += b_csr;
+  uint64_t* partial = b_part ? (uint64_t*)p : nullptr;
+
+  auto fail = [&](bdg_status e) { bdg_graph_free(g); return e; };
+  if (cudaMemcpyAsync(g->entry, P->entry, (size_t)P->n_entry * 4, cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess)
+    return fail(bdg_set_error(BDG_ECUDA, "build: copying the entry sample failed"));
+  if (m == 1) {
+    if (cudaMemsetAsync(routes, 0, (size_t)N * 4, st) != cudaSuccess)
+      return fail(bdg_set_error(BDG_ECUDA, "build: memset failed"));
+  } else if (need_routes) {
+    if (need_bk) {
+      s = bdg_launch_bkmeans(codes, N, W, P->bk_sample, P->bk_sample_size, m, P->bk_iters, cent,
+                             nullptr, bk, b_bk, st);
+      if (s != BDG_OK) return fail(s);
+    }
+    s = bdg_launch_route(codes, N, W, cent, m, t, routes, nullptr, st);
+    if (s != BDG_OK) return fail(s);
+  }
+  if (P->routes != nullptr) {
+    // caller-given routes may leave slots unvisited (values outside [0, m)):
+    // those rows / partial lists must read as padding
+    if (t == 1) {
+      s = bdg_launch_fill_pad(g->ids, g->dists, N * (int64_t)k, bits, st);
+      if (s != BDG_OK) return fail(s);
+    } else if (cudaMemsetAsync(partial, 0xff, (size_t)N * t * k * 8, st) != cudaSuccess) {
+      return fail(bdg_set_error(BDG_ECUDA, "build: memset failed"));
+    }
+  }
+  bdg_csr csr;
+  s = bdg_build_csr(codes, N, W, routes, m, t, tile_v, csr_mem, &csr, st);
+  if (s != BDG_OK) return fail(s);
+  bdg_knn_args a;
+  a.codes = codes; a.csr = csr; a.N = N; a.m = m; a.t = t; a.k = k; a.bits = bits;
+  a.tile_v = tile_v; a.partial = partial; a.out_ids = g->ids; a.out_dist = g->dists;
+  a.item_counter = csr.counters + 2 * m;
+  a.out_by_pos = 0;
+  s = bdg_launch_knn_popc(a, W, st);
+  if (s != BDG_OK) return fail(s);
+  if (t > 1) {
+    s = bdg_launch_merge(partial, N, t, k, bits, g->ids, g->dists, st);
+    if (s != BDG_OK) return fail(s);
+  }
+  *out = g;
+  return BDG_OK;
+}
+
+bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const int32_t* rows,
+                        int64_t nrows, int32_t k, int32_t* out_ids, int32_t* out_dist,
+                        void* stream) {
+  BDG_TRY(check_bits(bits));
+  if (N < 2 || N >= (int64_t(1) << 31) || k < 1 || k > 128 || k >= N || nrows < 0 ||
+      nrows >= (int64_t(1) << 31))
+    return bdg_set_error(BDG_EINVAL, "knn_rows: N=%lld nrows=%lld k=%d", (long long)N,
+                         (long long)nrows, k);
+  if (nrows == 0) return BDG_OK;
+  if (!codes || !rows || !out_ids || !out_dist)
+    return bdg_set_error(BDG_EINVAL, "knn_rows: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int W = bits / 64;
+  const int tile_v = bdg_knn_tile_visitors(W);
+  keep_pool_cached();
+  Scratch sc;
+  const size_t b = bdg_csr_rows_bytes(N, nrows);
+  BDG_TRY(sc.alloc(b, st));
+  bdg_csr csr;
+  BDG_TRY(bdg_build_csr_rows(codes, N, rows, nrows, tile_v, sc.p, &csr, st));
+  bdg_knn_args a;
+  a.codes = codes; a.csr = csr; a.N = N; a.m = 1; a.t = 1; a.k = k; a.bits = bits;
+  a.tile_v = tile_v; a.partial = nullptr; a.out_ids = out_ids; a.out_dist = out_dist;
+  a.item_counter = csr.counters + 2;
+  a.out_by_pos = 1;
+  return bdg_launch_knn_popc(a, W, st);
+}
+
+bdg_status bdg_graph_info(const bdg_graph* g, const int32_t** ids, const int32_t** dists,
+                          int64_t* n, int32_t* k, int32_t* bits) {
+  if (!g) return bdg_set_error(BDG_EINVAL, "graph is NULL");
+  if (ids) *ids = g->ids;
+  if (dists) *dists = g->dists;
+  if (n) *n = g->n;
+  if (k) *k = g->k;
+  if (bits) *bits = g->bits;
+  return BDG_OK;
+}
+
+void bdg_graph_free(bdg_graph* g) {
+  if (!g) return;
+  dfree(g->ids, (size_t)g->n * g->k * 4);
+  dfree(g->dists, (size_t)g->n * g->k * 4);
+  dfree(g->entry, (size_t)g->n_entry * 4);
+  delete g;
+}
+
+bdg_status bdg_graph_save(const bdg_graph* g, const char* path) {
+  if (!g || !path) return bdg_set_error(BDG_EINVAL, "save: null argument");
+  BDG_CUDA_TRY(cudaDeviceSynchronize());
+  std::vector<int32_t> ids((size_t)g->n * g->k), dists((size_t)g->n * g->k), entry(g->n_entry);
+  BDG_CUDA_TRY(cudaMemcpy(ids.data(), g->ids, ids.size() * 4, cudaMemcpyDeviceToHost));
+  BDG_CUDA_TRY(cudaMemcpy(dists.data(), g->dists, dists.size() * 4, cudaMemcpyDeviceToHost));
+  BDG_CUDA_TRY(cudaMemcpy(entry.data(), g->entry, entry.size() * 4, cudaMemcpyDeviceToHost));
+  FILE* f = fopen(path, "wb");
+  if (!f) return bdg_set_error(BDG_EINVAL, "save: cannot open %s", path);
+  const int32_t hdr[6] = {0x31474442 /* "BDG1" */, 1, (int32_t)(g->n & 0x7fffffff), g->bits, g->k,
+                          g->n_entry};
+  bool ok = fwrite(hdr, 4, 6, f) == 6 && fwrite(ids.data(), 4, ids.size(), f) == ids.size() &&
+            fwrite(dists.data(), 4, dists.size(), f) == dists.size() &&
+            fwrite(entry.data(), 4, entry.size(), f) == entry.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? BDG_OK : bdg_set_error(BDG_EINVAL, "save: write to %s failed", path);
+}
+
+bdg_status bdg_graph_load(const char* path, const uint64_t* codes, bdg_graph** out) {
+  if (!path || !codes || !out) return bdg_set_error(BDG_EINVAL, "load: null argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return bdg_set_error(BDG_EINVAL, "load: cannot open %s", path);
+  int32_t hdr[6];
+  if (fread(hdr, 4, 6, f) != 6 || hdr[0] != 0x31474442 || hdr[1] != 1 || hdr[2] < 2 ||
+      hdr[4] < 1 || hdr[5] < 1 || check_bits(hdr[3]) != BDG_OK) {
+    fclose(f);
+    return bdg_set_error(BDG_EINVAL, "load: %s is not a BDG1 graph file", path);
+  }
+  bdg_graph* g = new bdg_graph();
+  g->n = hdr[2]; g->bits = hdr[3]; g->W = hdr[3] / 64; g->k = hdr[4]; g->n_entry = hdr[5];
+  g->codes = codes;
+  std::vector<int32_t> ids((size_t)g->n * g->k), dists((size_t)g->n * g->k), entry(g->n_entry);
+  const bool ok = fread(ids.data(), 4, ids.size(), f) == ids.size() &&
+                  fread(dists.data(), 4, dists.size(), f) == dists.size() &&
+                  fread(entry.data(), 4, entry.size(), f) == entry.size();
+  fclose(f);
+  if (!ok) { delete g; return bdg_set_error(BDG_EINVAL, "load: %s is truncated", path); }
+  bdg_status s = dalloc((void**)&g->ids, ids.size() * 4);
+  if (s == BDG_OK) s = dalloc((void**)&g->dists, dists.size() * 4);
+  if (s == BDG_OK) s = dalloc((void**)&g->entry, entry.size() * 4);
+  if (s != BDG_OK) { bdg_graph_free(g); return s; }
+  if (cudaMemcpy(g->ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g->dists, dists.data(), dists.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g->entry, entry.data(), entry.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    bdg_graph_free(g);
+    return bdg_set_error(BDG_ECUDA, "load: copy to device failed");
+  }
+  *out = g;
+  return BDG_OK;
+}
+
+bdg_status bdg_search(const bdg_graph* g, const uint64_t* queries, int64_t nq, const int32_t* ef,
+                      int32_t ef_max, int32_t R, int32_t* out_ids, int32_t* out_dist,
+                      int32_t* expansions, void* stream) {
+  if (!g) return bdg_set_error(BDG_EINVAL, "search: graph is NULL");
+  if (nq < 0 || R < 1 || ef_max < 1 || ef_max > 1024)
+    return bdg_set_error(BDG_EINVAL, "search: nq=%lld R=%d ef_max=%d", (long long)nq, R, ef_max);
+  if (nq > 0 && (!queries || !ef || !out_ids || !out_dist))
+    return bdg_set_error(BDG_EINVAL, "search: null pointer");
+  bdg_graph_view v{g->codes, g->ids, g->entry, g->n, g->k, g->bits, g->n_entry};
+  return bdg_launch_search(v, queries, nq, ef, ef_max, R, out_ids, out_dist, expansions,
+                           (cudaStream_t)stream);
+}
+
+bdg_status bdg_rerank(const float* feats, int64_t N, int32_t D, const float* qfeats,
+                      const int32_t* cand, int64_t nq, int32_t R, int32_t k, int32_t* out_ids,
+                      float* out_d2, void* stream) {
+  if (nq < 0 || N < 1 || R < 1 || R > 1024 || k < 1 || k > 32)
+    return bdg_set_error(BDG_EINVAL, "rerank: N=%lld nq=%lld R=%d k=%d", (long long)N,
+                         (long long)nq, R, k);
+  if (D != 128 && D != 256 && D != 512 && D != 1024)
+    return bdg_set_error(BDG_EUNSUPPORTED, "rerank: D = %d not in {128,256,512,1024}", D);
+  if (nq > 0 && (!feats || !qfeats || !cand || !out_ids || !out_d2))
+    return bdg_set_error(BDG_EINVAL, "rerank: null pointer");
+  if (((uintptr_t)feats | (uintptr_t)qfeats) & 15)
+    return bdg_set_error(BDG_EINVAL, "rerank: feature arrays must be 16-byte aligned");
+  return bdg_launch_rerank(feats, N, D, qfeats, cand, nq, R, k, out_ids, out_d2,
+                           (cudaStream_t)stream);
+}
+
+bdg_status bdg_search_rerank(const bdg_graph* g, const uint64_t* queries, const float* qfeats,
+                             const float* feats, int32_t D, int64_t nq, const int32_t* ef,
+                             int32_t ef_max, int32_t R, int32_t k, int32_t* cand_ids,
+                             int32_t* cand_dist, int32_t* out_ids, float* out_d2, void* stream) {
+  BDG_TRY(bdg_search(g, queries, nq, ef, ef_max, R, cand_ids, cand_dist, nullptr, stream));
+  return bdg_rerank(feats, g->n, D, qfeats, cand_ids, nq, R, k, out_ids, out_d2, stream);
+}
+
+}  // extern "C"

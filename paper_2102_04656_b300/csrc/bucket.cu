@@ -1,0 +1,246 @@
+// bucket.cu -- the Shuffle of Section 3.2 done in HBM: group points by home
+// partition (H_p, whose codes are also copied contiguously so the k-NN kernel
+// streams them as dense tiles) and by every routed partition (V_p, with the
+// route slot), then lay out the persistent kernel's work items.
+//
+// Work items are (partition, tile of `tile_v` visitors). Partitions are ordered
+// by decreasing |H_p| (every item of p costs tile_v * |H_p| pairs), so the
+// dynamic item counter of the persistent kernel hands out the longest items
+// first -- the greedy longest-processing-time rule, which is this design's
+// stand-in for the paper's data-skew balancing across Reduce nodes
+// (Section 3.6 (1)).
+#include "common.cuh"
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kMaxSortM = 16384;  // partitions sortable by the single-block bitonic sort
+
+__global__ void count_kernel(const int32_t* __restrict__ routes, int64_t N, int t, int m,
+                             int32_t* __restrict__ hcnt, int32_t* __restrict__ vcnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int32_t h = routes[i * t];
+  if (h >= 0 && h < m) atomicAdd(&hcnt[h], 1);  // route values outside [0, m) are ignored
+  for (int s = 0; s < t; ++s) {
+    const int32_t p = routes[i * t + s];
+    if (p >= 0 && p < m) atomicAdd(&vcnt[p], 1);
+  }
+}
+
+// Block-wide exclusive scan of per-thread totals (1024 threads).
+__device__ int32_t block_exclusive_scan(int32_t v, int32_t* warp_tot, int32_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int32_t w = warp_tot[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_tot[lane] = w;  // inclusive
+  }
+  __syncthreads();
+  const int32_t base = wid > 0 ? warp_tot[wid - 1] : 0;
+  if (total) *total = warp_tot[31];
+  const int32_t r = base + x - v;
+  __syncthreads();
+  return r;
+}
+
+// Single block: offsets of H_p and V_p, partition order by decreasing |H_p|,
+// item offsets in that order, and scatter cursors.
+__global__ void __launch_bounds__(kScanThreads)
+plan_kernel(int m, int tile_v, int32_t* __restrict__ hcnt, int32_t* __restrict__ vcnt,
+            int32_t* __restrict__ home_off, int32_t* __restrict__ visit_off,
+            int32_t* __restrict__ part_order, int32_t* __restrict__ item_off) {
+  extern __shared__ uint64_t skey[];  // [pow2 >= m]
+  __shared__ int32_t warp_tot[32];
+  __shared__ int32_t total;
+  const int per = (m + kScanThreads - 1) / kScanThreads;
+  // --- exclusive scans of the two histograms (thread owns a contiguous run)
+  for (int which = 0; which < 2; ++which) {
+    int32_t* cnt = which ? vcnt : hcnt;
+    int32_t* off = which ? visit_off : home_off;
+    const int b = threadIdx.x * per, e = min(m, b + per);
+    int32_t s = 0;
+    for (int p = b; p < e; ++p) s += cnt[p];
+    int32_t run = block_exclusive_scan(s, warp_tot, &total);
+    for (int p = b; p < e; ++p) { off[p] = run; run += cnt[p]; }
+    if (threadIdx.x == 0) off[m] = total;
+    __syncthreads();
+  }
+  // --- sort partitions by (decreasing |H_p|, p)
+  int np2 = 1;
+  while (np2 < m) np2 <<= 1;
+  for (int p = threadIdx.x; p < np2; p += kScanThreads)
+    skey[p] = p < m ? ((uint64_t)(0x7fffffff - hcnt[p]) << 32) | (uint32_t)p : ~0ull;
+  __syncthreads();
+  for (int size = 2; size <= np2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int x = threadIdx.x; x < np2; x += kScanThreads) {
+        const int y = x ^ stride;
+        if (y > x) {
+          const bool up = (x & size) == 0;
+          const uint64_t a = skey[x], c = skey[y];
+          if ((a > c) == up) { skey[x] = c; skey[y] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = threadIdx.x; r < m; r += kScanThreads) part_order[r] = (int32_t)(skey[r] & 0xffffffffu);
+  __syncthreads();
+  // --- item offsets in partition order
+  {
+    const int b = threadIdx.x * per, e = min(m, b + per);
+    int32_t s = 0;
+    for (int r = b; r < e; ++r) {
+      const int p = part_order[r];
+      s += (vcnt[p] + tile_v - 1) / tile_v;  // empty H_p still pads its visitors
+    }
+    int32_t run = block_exclusive_scan(s, warp_tot, &total);
+    for (int r = b; r < e; ++r) {
+      const int p = part_order[r];
+      item_off[r] = run;
+      run += (vcnt[p] + tile_v - 1) / tile_v;
+    }
+    if (threadIdx.x == 0) item_off[m] = total;
+  }
+  __syncthreads();
+  // --- scatter cursors start at the offsets
+  for (int p = threadIdx.x; p < m; p += kScanThreads) {
+    hcnt[p] = home_off[p];
+    vcnt[p] = visit_off[p];
+  }
+}
+
+__global__ void scatter_kernel(const int32_t* __restrict__ routes, int64_t N, int t, int m,
+                               int32_t* __restrict__ hcur, int32_t* __restrict__ vcur,
+                               int32_t* __restrict__ home_ids, int32_t* __restrict__ visit_ids,
+                               int8_t* __restrict__ visit_slot) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int32_t h = routes[i * t];
+  if (h >= 0 && h < m) home_ids[atomicAdd(&hcur[h], 1)] = (int32_t)i;
+  for (int s = 0; s < t; ++s) {
+    const int32_t p = routes[i * t + s];
+    if (p < 0 || p >= m) continue;
+    const int32_t pos = atomicAdd(&vcur[p], 1);
+    visit_ids[pos] = (int32_t)i;
+    visit_slot[pos] = (int8_t)s;
+  }
+}
+
+__global__ void gather_home_codes(const uint64_t* __restrict__ codes,
+                                  const int32_t* __restrict__ home_ids,
+                                  const int32_t* __restrict__ home_off, int m, int64_t N, int W,
+                                  uint64_t* __restrict__ out) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N * W) return;
+  const int64_t r = x / W;
+  if (r >= home_off[m]) return;  // points without a valid home are in no H_p
+  out[x] = codes[(int64_t)home_ids[r] * W + (x - r * W)];
+}
+
+inline size_t al(size_t b) { return (b + 255) & ~size_t(255); }
+
+__global__ void rows_plan_kernel(int64_t N, const int32_t* __restrict__ rows, int64_t nrows,
+                                 int tile_v, int32_t* __restrict__ home_off,
+                                 int32_t* __restrict__ home_ids, int32_t* __restrict__ visit_off,
+                                 int32_t* __restrict__ visit_ids, int8_t* __restrict__ visit_slot,
+                                 int32_t* __restrict__ part_order, int32_t* __restrict__ item_off) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < N) home_ids[x] = (int32_t)x;
+  if (x < nrows) {  // ids outside [0, N) become empty rows
+    const int32_t r = rows[x];
+    visit_ids[x] = (r >= 0 && r < N) ? r : -1;
+    visit_slot[x] = 0;
+  }
+  if (x == 0) {
+    home_off[0] = 0; home_off[1] = (int32_t)N;
+    visit_off[0] = 0; visit_off[1] = (int32_t)nrows;
+    part_order[0] = 0;
+    item_off[0] = 0; item_off[1] = (int32_t)((nrows + tile_v - 1) / tile_v);
+  }
+}
+
+}  // namespace
+
+size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows) {
+  return al(2 * 4) * 3 + al(N * 4) + al(nrows * 4) + al(nrows) + al(4) + al(8 * 4);
+}
+
+bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* rows,
+                              int64_t nrows, int tile_v, void* mem, bdg_csr* c, cudaStream_t st) {
+  char* p = (char*)mem;
+  c->home_off = (int32_t*)p;   p += al(2 * 4);
+  c->visit_off = (int32_t*)p;  p += al(2 * 4);
+  c->item_off = (int32_t*)p;   p += al(2 * 4);
+  c->home_ids = (int32_t*)p;   p += al(N * 4);
+  c->visit_ids = (int32_t*)p;  p += al(nrows * 4);
+  c->visit_slot = (int8_t*)p;  p += al(nrows);
+  c->part_order = (int32_t*)p; p += al(4);
+  c->counters = (int32_t*)p;
+  c->home_codes = const_cast<uint64_t*>(codes);  // identity order: read the codes in place
+  BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, 8 * 4, st));
+  const int64_t n = N > nrows ? N : nrows;
+  rows_plan_kernel<<<bdg_cdiv(n, 256), 256, 0, st>>>(N, rows, nrows, tile_v, c->home_off,
+                                                     c->home_ids, c->visit_off, c->visit_ids,
+                                                     c->visit_slot, c->part_order, c->item_off);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
+
+size_t bdg_csr_bytes(int64_t N, int m, int t, int W) {
+  return al((m + 1) * 4) * 3 + al(N * 4) + al(N * W * 8) + al(N * t * 4) + al(N * t) +
+         al(m * 4) + al((2 * (size_t)m + 4) * 4);
+}
+
+bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
+                         int t, int tile_v, void* mem, bdg_csr* c, cudaStream_t st) {
+  if (m > kMaxSortM)
+    return bdg_set_error(BDG_EUNSUPPORTED, "m = %d partitions exceeds %d", m, kMaxSortM);
+  char* p = (char*)mem;
+  c->home_off = (int32_t*)p;   p += al((m + 1) * 4);
+  c->visit_off = (int32_t*)p;  p += al((m + 1) * 4);
+  c->item_off = (int32_t*)p;   p += al((m + 1) * 4);
+  c->home_ids = (int32_t*)p;   p += al(N * 4);
+  c->home_codes = (uint64_t*)p; p += al(N * W * 8);
+  c->visit_ids = (int32_t*)p;  p += al(N * t * 4);
+  c->visit_slot = (int8_t*)p;  p += al(N * t);
+  c->part_order = (int32_t*)p; p += al(m * 4);
+  c->counters = (int32_t*)p;
+  int32_t* hcnt = c->counters;
+  int32_t* vcnt = c->counters + m;
+  BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, (2 * (size_t)m + 4) * 4, st));
+  const int g = bdg_cdiv(N, 256);
+  count_kernel<<<g, 256, 0, st>>>(routes, N, t, m, hcnt, vcnt);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  int np2 = 1;
+  while (np2 < m) np2 <<= 1;
+  const size_t smem = (size_t)np2 * 8;
+  BDG_CUDA_TRY(cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  plan_kernel<<<1, kScanThreads, smem, st>>>(m, tile_v, hcnt, vcnt, c->home_off, c->visit_off,
+                                             c->part_order, c->item_off);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  scatter_kernel<<<g, 256, 0, st>>>(routes, N, t, m, hcnt, vcnt, c->home_ids, c->visit_ids,
+                                    c->visit_slot);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  gather_home_codes<<<bdg_cdiv(N * W, 256), 256, 0, st>>>(codes, c->home_ids, c->home_off, m, N,
+                                                          W, c->home_codes);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}

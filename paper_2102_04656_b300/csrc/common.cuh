@@ -1,0 +1,128 @@
+// common.cuh -- shared device/host helpers of the BDG CUDA library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bdg.h"
+
+// A neighbour key packs (distance, id) into one 64-bit word, distance in the
+// high half, so that unsigned integer order is the lexicographic (d, id) order
+// that breaks ties everywhere in the method. d <= 1025 and 0 <= id < 2^31.
+__host__ __device__ __forceinline__ uint64_t bdg_key(uint32_t d, uint32_t id) {
+  return (static_cast<uint64_t>(d) << 32) | id;
+}
+__host__ __device__ __forceinline__ int32_t bdg_key_d(uint64_t k) { return (int32_t)(k >> 32); }
+__host__ __device__ __forceinline__ int32_t bdg_key_id(uint64_t k) {
+  return (int32_t)(uint32_t)(k & 0xffffffffu);
+}
+// Padding key for rows with fewer than k candidates: (bits + 1, id = -1).
+__host__ __device__ __forceinline__ uint64_t bdg_pad_key(int32_t bits) {
+  return bdg_key((uint32_t)(bits + 1), 0xffffffffu);
+}
+#define BDG_KEY_INF (~0ull)
+
+// Host-side error plumbing (api.cu owns the thread-local message).
+bdg_status bdg_set_error(bdg_status s, const char* fmt, ...);
+#define BDG_CUDA_TRY(expr)                                                              \
+  do {                                                                                 \
+    cudaError_t _e = (expr);                                                           \
+    if (_e != cudaSuccess)                                                             \
+      return bdg_set_error(BDG_ECUDA, "%s failed: %s (%s:%d)", #expr,                 \
+                           cudaGetErrorString(_e), __FILE__, __LINE__);                \
+  } while (0)
+#define BDG_TRY(expr)                 \
+  do {                               \
+    bdg_status _s = (expr);          \
+    if (_s != BDG_OK) return _s;     \
+  } while (0)
+
+static inline int bdg_cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Number of SMs of the current device (cached per process for device 0..63).
+int bdg_num_sms();
+
+// Kernel launch accounting (every launcher calls bdg_note_launch once per launch)
+// and optional CUDA-event timing of named kernels on their launch stream.
+void bdg_note_launch(int n = 1);
+struct bdg_prof_scope {
+  int slot;
+  cudaStream_t st;
+  bdg_prof_scope(const char* name, cudaStream_t s);
+  ~bdg_prof_scope();
+};
+
+// Dispatch a templated launcher on the word count W = bits / 64.
+#define BDG_DISPATCH_W(W, FN, ...)                                   \
+  switch (W) {                                                       \
+    case 1: return FN<1>(__VA_ARGS__);                               \
+    case 2: return FN<2>(__VA_ARGS__);                               \
+    case 4: return FN<4>(__VA_ARGS__);                               \
+    case 8: return FN<8>(__VA_ARGS__);                               \
+    case 16: return FN<16>(__VA_ARGS__);                             \
+    default:                                                         \
+      return bdg_set_error(BDG_EUNSUPPORTED,                         \
+                           "code width %d words is not built (1,2,4,8,16)", (int)(W)); \
+  }
+
+// ---- internal launchers shared between translation units (all async on `st`) ----
+// route.cu
+bdg_status bdg_launch_route(const uint64_t* codes, int64_t n, int W, const uint64_t* cent,
+                            int m, int t, int32_t* routes, int32_t* rdist, cudaStream_t st);
+bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int64_t* sample,
+                              int64_t S, int m, int iters, uint64_t* cent, int64_t* loss,
+                              void* scratch, size_t scratch_bytes, cudaStream_t st);
+size_t bdg_bkmeans_scratch_bytes(int64_t S, int m, int W);
+// bucket.cu
+struct bdg_csr {
+  int32_t* home_off;   // [m + 1]
+  int32_t* home_ids;   // [N]      point ids grouped by home partition
+  uint64_t* home_codes;// [N][W]   codes in home_ids order (contiguous tiles)
+  int32_t* visit_off;  // [m + 1]
+  int32_t* visit_ids;  // [N * t]  visitor point ids grouped by routed partition
+  int8_t* visit_slot;  // [N * t]  slot s of that partition in the visitor's route list
+  int32_t* part_order; // [m]      partitions by decreasing |H_p| (then p)
+  int32_t* item_off;   // [m + 1]  work items per partition in part_order order
+  int32_t* counters;   // [2 * m + 4] scratch counters
+};
+size_t bdg_csr_bytes(int64_t N, int m, int t, int W);
+bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
+                         int t, int tile_v, void* mem, bdg_csr* csr, cudaStream_t st);
+// one partition: every point is a home (identity order, codes used in place);
+// the visitors are the given rows
+size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows);
+bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* rows,
+                              int64_t nrows, int tile_v, void* mem, bdg_csr* csr, cudaStream_t st);
+// knn_popc.cu
+struct bdg_knn_args {
+  const uint64_t* codes;  // [N][W]
+  bdg_csr csr;
+  int64_t N;
+  int m, t, k, bits;
+  int tile_v;             // visitors per work item
+  uint64_t* partial;      // [N][t][k] keys (t > 1) or NULL
+  int32_t* out_ids;       // [N][k] final ids when t == 1
+  int32_t* out_dist;      // [N][k]
+  int32_t* item_counter;  // zeroed before launch
+  int out_by_pos;         // t == 1: write row i of the output for the i-th visitor (not its id)
+};
+bdg_status bdg_launch_knn_popc(const bdg_knn_args& a, int W, cudaStream_t st);
+// merge.cu
+bdg_status bdg_launch_merge(const uint64_t* partial, int64_t N, int t, int k, int bits,
+                            int32_t* ids, int32_t* dist, cudaStream_t st);
+bdg_status bdg_launch_fill_pad(int32_t* ids, int32_t* dist, int64_t count, int bits,
+                               cudaStream_t st);
+// search.cu / rerank.cu
+struct bdg_graph_view {
+  const uint64_t* codes;
+  const int32_t* ids;
+  const int32_t* entry;
+  int64_t n;
+  int32_t deg, bits, n_entry;
+};
+bdg_status bdg_launch_search(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
+                             const int32_t* ef, int ef_max, int R, int32_t* out_ids,
+                             int32_t* out_dist, int32_t* expansions, cudaStream_t st);
+bdg_status bdg_launch_rerank(const float* feats, int64_t N, int D, const float* qfeats,
+                             const int32_t* cand, int64_t nq, int R, int k, int32_t* out_ids,
+                             float* out_d2, cudaStream_t st);
+int bdg_knn_tile_visitors(int W);

@@ -1,0 +1,198 @@
+// route.cu -- nearest-centre routing (Map step, Section 3.2) and Bk-means
+// (Section 3.2, Eq. 1-2) on packed binary codes.
+//
+// Routing: one thread per point keeps its t best (distance, centre) keys in
+// registers while centre codes stream through shared memory in chunks (every
+// thread of the block reads the same centre word, a broadcast). The work is
+// n * m * W XOR+POPC word pairs, ALU (POPC) bound.
+//
+// Bk-means: assign = routing with t = 1 over the down-sample; update = per-bit
+// member counts by integer atomics (order-independent, so deterministic) and a
+// per-word majority with "tie keeps the previous bit" (the reading of Eq. 2's
+// sgn at zero); the objective of Eq. 1 (Hamming = squared L2 for 0/1 vectors)
+// is summed after each assign.
+#include "common.cuh"
+
+namespace {
+
+constexpr int kRouteThreads = 256;
+
+template <int W, int MAXT>
+__global__ void __launch_bounds__(kRouteThreads)
+route_kernel(const uint64_t* __restrict__ codes, int64_t n, const uint64_t* __restrict__ cent,
+             int m, int t, int32_t* __restrict__ routes, int32_t* __restrict__ rdist,
+             unsigned long long* __restrict__ loss_sum) {
+  constexpr int kChunk = (W <= 4) ? 1024 : 4096 / W;  // centres per smem chunk
+  __shared__ uint64_t sc[kChunk * W];
+  const int64_t i = (int64_t)blockIdx.x * kRouteThreads + threadIdx.x;
+  const bool live = i < n;
+  uint64_t y[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) y[w] = live ? codes[i * W + w] : 0ull;
+  uint64_t best[MAXT];
+#pragma unroll
+  for (int s = 0; s < MAXT; ++s) best[s] = BDG_KEY_INF;
+  uint64_t worst = BDG_KEY_INF;  // == best[t - 1]
+
+  for (int c0 = 0; c0 < m; c0 += kChunk) {
+    const int cn = min(kChunk, m - c0);
+    __syncthreads();
+    for (int x = threadIdx.x; x < cn * W; x += kRouteThreads) sc[x] = cent[(int64_t)c0 * W + x];
+    __syncthreads();
+    for (int c = 0; c < cn; ++c) {
+      uint32_t d = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) d += __popcll(y[w] ^ sc[c * W + w]);
+      const uint64_t key = bdg_key(d, (uint32_t)(c0 + c));
+      if (key < worst) {
+        // sorted insertion from the back: slot s takes its predecessor if the
+        // key goes further forward, else the key itself; slots >= t are unused
+#pragma unroll
+        for (int s = MAXT - 1; s >= 0; --s) {
+          if (s < t && key < best[s]) {
+            const uint64_t prev = (s > 0) ? best[s - 1] : 0ull;
+            best[s] = (s > 0 && key < prev) ? prev : key;
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < MAXT; ++s)
+          if (s == t - 1) worst = best[s];
+      }
+    }
+  }
+  if (loss_sum) {
+    // objective of Eq. 1 for the nearest centre, one atomic per warp
+    unsigned long long v = live ? (unsigned long long)bdg_key_d(best[0]) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, v);
+  }
+  if (!live) return;
+#pragma unroll
+  for (int s = 0; s < MAXT; ++s) {
+    if (s < t) {
+      routes[i * t + s] = bdg_key_id(best[s]);
+      if (rdist) rdist[i * t + s] = bdg_key_d(best[s]);
+    }
+  }
+}
+
+template <int W>
+bdg_status route_w(const uint64_t* codes, int64_t n, const uint64_t* cent, int m, int t,
+                   int32_t* routes, int32_t* rdist, unsigned long long* loss, cudaStream_t st) {
+  if (n == 0) return BDG_OK;
+  const int grid = bdg_cdiv(n, kRouteThreads);
+  bdg_prof_scope prof(loss ? "bkmeans_assign" : "route", st);
+  if (t == 1)
+    route_kernel<W, 1><<<grid, kRouteThreads, 0, st>>>(codes, n, cent, m, t, routes, rdist, loss);
+  else if (t <= 4)
+    route_kernel<W, 4><<<grid, kRouteThreads, 0, st>>>(codes, n, cent, m, t, routes, rdist, loss);
+  else if (t <= 8)
+    route_kernel<W, 8><<<grid, kRouteThreads, 0, st>>>(codes, n, cent, m, t, routes, rdist, loss);
+  else
+    route_kernel<W, 16><<<grid, kRouteThreads, 0, st>>>(codes, n, cent, m, t, routes, rdist, loss);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
+
+__global__ void gather_rows(const uint64_t* __restrict__ codes, const int64_t* __restrict__ ids,
+                            int64_t S, int W, uint64_t* __restrict__ out) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= S * W) return;
+  const int64_t s = x / W;
+  out[x] = codes[ids[s] * W + (x - s * W)];
+}
+
+// Per-bit member counts: one warp per sample point, lanes over bits.
+__global__ void bk_count(const uint64_t* __restrict__ scodes, int64_t S, int W,
+                         const int32_t* __restrict__ assign, int32_t* __restrict__ ones,
+                         int32_t* __restrict__ count) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= S) return;
+  const int c = assign[s];
+  const int bits = 64 * W;
+  for (int b = lane; b < bits; b += 32) {
+    if ((scodes[s * W + (b >> 6)] >> (b & 63)) & 1ull) atomicAdd(&ones[(int64_t)c * bits + b], 1);
+  }
+  if (lane == 0) atomicAdd(&count[c], 1);
+}
+
+// Majority per centre word; a tie keeps the previous bit, an empty cluster keeps its centre.
+__global__ void bk_update(uint64_t* __restrict__ cent, int m, int W,
+                          const int32_t* __restrict__ ones, const int32_t* __restrict__ count) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (int64_t)m * W) return;
+  const int c = (int)(x / W), w = (int)(x - (int64_t)c * W);
+  const int p = count[c];
+  if (p == 0) return;
+  const int bits = 64 * W;
+  uint64_t v = cent[x];
+  for (int j = 0; j < 64; ++j) {
+    const int twice = 2 * ones[(int64_t)c * bits + w * 64 + j];
+    const uint64_t mask = 1ull << j;
+    if (twice > p) v |= mask;
+    else if (twice < p) v &= ~mask;
+  }
+  cent[x] = v;
+}
+
+}  // namespace
+
+bdg_status bdg_launch_route(const uint64_t* codes, int64_t n, int W, const uint64_t* cent, int m,
+                            int t, int32_t* routes, int32_t* rdist, cudaStream_t st) {
+  BDG_DISPATCH_W(W, route_w, codes, n, cent, m, t, routes, rdist, nullptr, st);
+}
+
+size_t bdg_bkmeans_scratch_bytes(int64_t S, int m, int W) {
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return al(S * W * 8) + al(S * 4) + al(S * 4) + al((size_t)m * 64 * W * 4) + al((size_t)m * 4) +
+         al(8 * 64);
+}
+
+namespace {
+template <int W>
+bdg_status bk_assign_w(const uint64_t* scodes, int64_t S, const uint64_t* cent, int m,
+                       int32_t* assign, int32_t* adist, unsigned long long* loss, cudaStream_t st) {
+  return route_w<W>(scodes, S, cent, m, 1, assign, adist, loss, st);
+}
+}  // namespace
+
+bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int64_t* sample,
+                              int64_t S, int m, int iters, uint64_t* cent, int64_t* loss,
+                              void* scratch, size_t scratch_bytes, cudaStream_t st) {
+  (void)N;
+  if (scratch_bytes < bdg_bkmeans_scratch_bytes(S, m, W))
+    return bdg_set_error(BDG_EINVAL, "bkmeans scratch too small");
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  char* p = (char*)scratch;
+  uint64_t* scodes = (uint64_t*)p; p += al(S * W * 8);
+  int32_t* assign = (int32_t*)p;   p += al(S * 4);
+  int32_t* adist = (int32_t*)p;    p += al(S * 4);
+  int32_t* ones = (int32_t*)p;     p += al((size_t)m * 64 * W * 4);
+  int32_t* count = (int32_t*)p;
+  gather_rows<<<bdg_cdiv(S * W, 256), 256, 0, st>>>(codes, sample, S, W, scodes);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  // init: c_j = code of sample[j]
+  BDG_CUDA_TRY(cudaMemcpyAsync(cent, scodes, (size_t)m * W * 8, cudaMemcpyDeviceToDevice, st));
+  if (loss) BDG_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(int64_t) * (iters + 1), st));
+  for (int it = 0; it <= iters; ++it) {
+    unsigned long long* lptr = loss ? (unsigned long long*)(loss + it) : nullptr;
+    bdg_status s;
+    auto run = [&]() -> bdg_status {
+      BDG_DISPATCH_W(W, bk_assign_w, scodes, S, cent, m, assign, adist, lptr, st);
+    };
+    s = run();
+    if (s != BDG_OK) return s;
+    if (it == iters) break;
+    BDG_CUDA_TRY(cudaMemsetAsync(ones, 0, (size_t)m * 64 * W * 4, st));
+    BDG_CUDA_TRY(cudaMemsetAsync(count, 0, (size_t)m * 4, st));
+    bk_count<<<bdg_cdiv(S * 32, 256), 256, 0, st>>>(scodes, S, W, assign, ones, count);
+    BDG_CUDA_TRY(cudaGetLastError());
+    bk_update<<<bdg_cdiv((int64_t)m * W, 256), 256, 0, st>>>(cent, m, W, ones, count);
+    BDG_CUDA_TRY(cudaGetLastError());
+    bdg_note_launch(2);
+  }
+  return BDG_OK;
+}

@@ -1,0 +1,260 @@
+// search.cu -- the search procedure of Section 3.5 on the GPU: long-link entry
+// (nearest of a fixed random sample) followed by best-first hill climbing on
+// the k-NN graph with a pool of the ef best keys (d(q, j), j), one warp per query.
+//
+// The pool is a sorted array in shared memory with an "expanded" flag per slot.
+// Each step expands the best unexpanded pool entry: the warp loads its
+// neighbour list (32 ids per coalesced load), each lane gathers one neighbour
+// code and scores it, the accepted keys are sorted across the warp (bitonic)
+// and merged into the pool by ranks.
+//
+// This reaches exactly the pool of the sequential procedure (candidate min-heap
+// + bounded max-heap + visited set):
+//  * the best unexpanded pool entry is the candidate heap's minimum whenever
+//    the sequential loop would not stop, and no unexpanded entry is left exactly
+//    when it stops (evicted candidates are worse than every pool entry, and the
+//    pool's worst key only decreases once the pool is full);
+//  * adding a whole neighbour list at once gives the best ef of (pool + list),
+//    which is what adding the neighbours one by one gives;
+//  * a node already seen is either still in the pool (found by binary search and
+//    skipped) or worse than the pool's worst key for good (rejected again), so a
+//    visited set is only a saving, not a condition of correctness. A small
+//    per-warp hash of seen ids avoids most re-gathers; when it is full, ids are
+//    simply re-scored.
+#include "common.cuh"
+
+
+namespace {
+
+constexpr int kWarps = 4;
+constexpr int kHash = 1024;  // visited-id hash slots per warp
+constexpr int kProbe = 8;
+
+template <int CAPW>
+struct PoolSmem {
+  uint64_t key[CAPW * 32];
+  uint8_t expd[CAPW * 32];
+  uint64_t nk[32];
+  int32_t hash[kHash];
+};
+
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
+
+// Returns true if id was already recorded; records it when there is room.
+__device__ __forceinline__ bool hash_seen(int32_t* h, int32_t id) {
+  uint32_t x = (uint32_t)id * 2654435761u;
+  uint32_t slot = x >> (32 - 10);  // kHash = 1024
+  for (int p = 0; p < kProbe; ++p) {
+    const uint32_t sidx = (slot + p) & (kHash - 1);
+    const int32_t old = atomicCAS(&h[sidx], -1, id);
+    if (old == -1) return false;  // inserted now
+    if (old == id) return true;
+  }
+  return false;  // table region full: not recorded, will be re-scored
+}
+
+template <int W, int CAPW>
+__global__ void __launch_bounds__(kWarps * 32)
+search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq,
+              const int32_t* __restrict__ efs, int R, int32_t* __restrict__ out_ids,
+              int32_t* __restrict__ out_dist, int32_t* __restrict__ expansions) {
+  constexpr int CAP = CAPW * 32;
+  extern __shared__ __align__(16) char search_smem[];
+  PoolSmem<CAPW>* sm_all = reinterpret_cast<PoolSmem<CAPW>*>(search_smem);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  PoolSmem<CAPW>& sm = sm_all[warp];
+  const uint64_t pad = bdg_pad_key(g.bits);
+
+  for (int64_t q = (int64_t)blockIdx.x * kWarps + warp; q < nq; q += (int64_t)gridDim.x * kWarps) {
+    const int ef = efs[q];
+    if (ef < 1 || ef > CAP) {
+      for (int r = lane; r < R; r += 32) {
+        out_ids[q * R + r] = -1;
+        out_dist[q * R + r] = g.bits + 1;
+      }
+      if (expansions && lane == 0) expansions[q] = -1;
+      continue;
+    }
+    uint64_t y[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) y[w] = queries[q * W + w];
+    for (int x = lane; x < kHash; x += 32) sm.hash[x] = -1;
+
+    // long-link entry: nearest sampled point by (d, id)
+    uint64_t best = BDG_KEY_INF;
+    for (int s = lane; s < g.n_entry; s += 32) {
+      const int32_t e = g.entry[s];
+      if (e < 0 || e >= g.n) continue;  // ids outside the graph are ignored
+      uint32_t d = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) d += __popcll(y[w] ^ g.codes[(int64_t)e * W + w]);
+      best = umin64(best, bdg_key(d, (uint32_t)e));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = umin64(best, __shfl_xor_sync(0xffffffffu, best, o));
+    __syncwarp();
+    if (best == BDG_KEY_INF) {  // no valid entry point: an empty result
+      for (int r = lane; r < R; r += 32) {
+        out_ids[q * R + r] = -1;
+        out_dist[q * R + r] = g.bits + 1;
+      }
+      if (expansions && lane == 0) expansions[q] = 0;
+      continue;
+    }
+    if (lane == 0) {
+      sm.key[0] = best;
+      sm.expd[0] = 0;
+      hash_seen(sm.hash, bdg_key_id(best));
+    }
+    int size = 1, hint = 0, nexp = 0;
+    __syncwarp();
+
+    for (;;) {
+      // first unexpanded slot at or after `hint`
+      int slot = -1;
+      for (int b = hint & ~31; b < size; b += 32) {
+        const int j = b + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, j < size && !sm.expd[j]);
+        if (m) { slot = b + __ffs(m) - 1; break; }
+      }
+      if (slot < 0) break;
+      hint = slot + 1;
+      const uint64_t ck = sm.key[slot];
+      __syncwarp();
+      if (lane == 0) sm.expd[slot] = 1;
+      ++nexp;
+      const int32_t node = bdg_key_id(ck);
+      for (int b0 = 0; b0 < g.deg; b0 += 32) {
+        const int32_t nb = (b0 + lane < g.deg) ? g.ids[(int64_t)node * g.deg + b0 + lane] : -1;
+        uint64_t key = BDG_KEY_INF;
+        bool acc = false;
+        if (nb >= 0 && nb < g.n && !hash_seen(sm.hash, nb)) {
+          uint32_t d = 0;
+#pragma unroll
+          for (int w = 0; w < W; ++w) d += __popcll(y[w] ^ g.codes[(int64_t)nb * W + w]);
+          key = bdg_key(d, (uint32_t)nb);
+          const uint64_t worst = sm.key[size - 1];
+          acc = (size < ef) || (key < worst);
+          if (acc) {  // already in the pool?
+            int lo = 0, hi = size;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (sm.key[mid] < key) lo = mid + 1; else hi = mid;
+            }
+            acc = !(lo < size && sm.key[lo] == key);
+          }
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, acc);
+        if (am == 0) continue;
+        const int na = __popc(am);
+        // sort accepted keys ascending across the warp (rejected = +inf)
+        uint64_t v = acc ? key : BDG_KEY_INF;
+#pragma unroll
+        for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+#pragma unroll
+          for (int j = k2 >> 1; j > 0; j >>= 1) {
+            const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool up = (lane & k2) == 0;
+            const bool low = (lane & j) == 0;
+            v = (low == up) ? umin64(v, o) : umax64(v, o);
+          }
+        }
+        sm.nk[lane] = v;
+        __syncwarp();
+        // new key positions: own rank + rank in the pool
+        int newpos = CAP;
+        if (lane < na) {
+          int lo = 0, hi = size;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.key[mid] < v) lo = mid + 1; else hi = mid;
+          }
+          newpos = lane + lo;
+        }
+        // pool entries at or after the first new position shift right by the
+        // number of smaller new keys; entries before it stay in place
+        const int minpos = (int)__reduce_min_sync(0xffffffffu, (unsigned)newpos);
+        uint64_t pk[CAPW];
+        uint8_t pf[CAPW];
+        int pp[CAPW];
+#pragma unroll
+        for (int r = 0; r < CAPW; ++r) {
+          const int j = r * 32 + lane;
+          pp[r] = CAP;
+          pk[r] = 0;
+          pf[r] = 0;
+          if (j >= minpos && j < size) {
+            pk[r] = sm.key[j];
+            pf[r] = sm.expd[j];
+            int lo = 0, hi = na;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (sm.nk[mid] < pk[r]) lo = mid + 1; else hi = mid;
+            }
+            pp[r] = j + lo;
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < CAPW; ++r)
+          if (pp[r] < ef) { sm.key[pp[r]] = pk[r]; sm.expd[pp[r]] = pf[r]; }
+        if (newpos < ef) { sm.key[newpos] = v; sm.expd[newpos] = 0; }
+        size = min(ef, size + na);
+        hint = min(hint, minpos);
+        __syncwarp();
+      }
+    }
+    const int keep = min(size, R);
+    for (int r = lane; r < R; r += 32) {
+      const uint64_t kk = r < keep ? sm.key[r] : pad;
+      out_ids[q * R + r] = r < keep ? bdg_key_id(kk) : -1;
+      out_dist[q * R + r] = bdg_key_d(kk);
+    }
+    if (expansions && lane == 0) expansions[q] = nexp;
+    __syncwarp();
+  }
+}
+
+template <int W, int CAPW>
+bdg_status launch_cap(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
+                      const int32_t* ef, int R, int32_t* out_ids, int32_t* out_dist,
+                      int32_t* expansions, cudaStream_t st) {
+  const size_t smem = sizeof(PoolSmem<CAPW>) * kWarps;
+  BDG_CUDA_TRY(cudaFuncSetAttribute(search_kernel<W, CAPW>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  BDG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<W, CAPW>,
+                                                             kWarps * 32, smem));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t need = (nq + kWarps - 1) / kWarps;
+  const int64_t cap = (int64_t)bdg_num_sms() * per_sm;
+  const int grid = (int)(need < cap ? need : cap);
+  bdg_prof_scope prof("search", st);
+  search_kernel<W, CAPW><<<grid, kWarps * 32, smem, st>>>(g, queries, nq, ef, R, out_ids, out_dist,
+                                                       expansions);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
+
+template <int W>
+bdg_status launch_w(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
+                    const int32_t* ef, int ef_max, int R, int32_t* out_ids, int32_t* out_dist,
+                    int32_t* expansions, cudaStream_t st) {
+  if (ef_max <= 64) return launch_cap<W, 2>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
+  if (ef_max <= 128) return launch_cap<W, 4>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
+  if (ef_max <= 256) return launch_cap<W, 8>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
+  if (ef_max <= 512) return launch_cap<W, 16>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
+  return launch_cap<W, 32>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
+}
+
+}  // namespace
+
+bdg_status bdg_launch_search(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
+                             const int32_t* ef, int ef_max, int R, int32_t* out_ids,
+                             int32_t* out_dist, int32_t* expansions, cudaStream_t st) {
+  if (nq == 0) return BDG_OK;
+  const int W = g.bits / 64;
+  BDG_DISPATCH_W(W, launch_w, g, queries, nq, ef, ef_max, R, out_ids, out_dist, expansions, st);
+}

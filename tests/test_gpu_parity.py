@@ -1,0 +1,283 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the same
+seeded inputs. Integer results (ids, distances, centres, routes, tie order,
+expansion counts) must be bit-exact; the FP32 re-rank must agree with the
+float64 oracle within 1e-5 relative, with ids equal except where the oracle's
+own distances of the swapped ids lie within that tolerance."""
+import os
+import struct
+
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def bdg():
+    from paper_2102_04656_b300 import build as b
+    b.build()
+    import paper_2102_04656_b300 as m
+    m.lib()
+    return m
+
+
+def _np(codes):
+    return codes.cpu().numpy().view(np.uint64)
+
+
+def _entry(n, s, seed):
+    return datagen.sample_ids(n, min(n, s), seed).astype(np.int32)
+
+
+def _build_exact(bdg, codes_t, k, seed=5):
+    n = codes_t.shape[0]
+    entry = torch.from_numpy(_entry(n, 64, seed)).cuda()
+    return bdg.build_graph(codes_t, k, m=1, t=1, entry=entry), entry
+
+
+# ------------------------------------------------------------------ exact kNN
+@pytest.mark.parametrize("bits,n,k", [(64, 1000, 8), (128, 777, 16), (256, 3001, 32),
+                                      (512, 1500, 64), (1024, 700, 128), (256, 130, 100)])
+def test_exact_knn_bit_exact(bdg, bits, n, k):
+    c = datagen.random_codes(n, bits, seed=bits + n)
+    c[7] = c[3]  # duplicates: d = 0 ties resolved by id
+    c[n - 1] = c[3]
+    g, _ = _build_exact(bdg, c.cuda(), k)
+    torch.cuda.synchronize()
+    ids_o, dist_o = oracle.knn_exact(_np(c), k)
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+def test_exact_knn_all_equal_codes(bdg):
+    c = torch.zeros(300, 4, dtype=torch.int64)
+    g, _ = _build_exact(bdg, c.cuda(), 32)
+    ids_o, dist_o = oracle.knn_exact(_np(c), 32)
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+def test_exact_knn_small_n_pads(bdg):
+    c = datagen.random_codes(5, 256, seed=9)
+    g, _ = _build_exact(bdg, c.cuda(), 4)
+    ids_o, dist_o = oracle.knn_exact(_np(c), 4)
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+def test_exact_knn_mixture_20k_256b_k32(bdg):
+    """The exact brute-force workload: N = 20k, 128-d mixture -> 256-bit, k = 32."""
+    w = datagen.WORKLOADS["exact_20k_256b"]
+    c = datagen.make_codes(w["spec"])
+    g, _ = _build_exact(bdg, c.cuda(), w["k"])
+    ids_o, dist_o = oracle.knn_exact(_np(c), w["k"])
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+# ------------------------------------------------------------------ Bk-means + routing
+@pytest.mark.parametrize("bits,n,m,S,iters", [(256, 5000, 32, 2048, 8), (512, 3000, 7, 700, 3),
+                                              (64, 1000, 1, 1000, 2), (1024, 800, 16, 800, 4)])
+def test_bkmeans_bit_exact(bdg, bits, n, m, S, iters):
+    spec = datagen.MixtureSpec(n, 64, 24, bits, seed=bits + m)
+    c = datagen.make_codes(spec)
+    sample = datagen.sample_ids(n, S, seed=77)
+    cent, loss = bdg.bkmeans(c.cuda(), torch.from_numpy(sample).cuda(), m, iters)
+    cent_o, loss_o, _ = oracle.bkmeans(_np(c), sample, m, iters)
+    assert np.array_equal(_np(cent), cent_o)
+    assert np.array_equal(loss.cpu().numpy(), loss_o)
+
+
+@pytest.mark.parametrize("bits,t", [(256, 5), (512, 1), (128, 16), (64, 3)])
+def test_route_bit_exact(bdg, bits, t):
+    c = datagen.random_codes(4001, bits, seed=bits)
+    ce = datagen.random_codes(300, bits, seed=bits + 1)
+    ce[17] = ce[250]  # duplicate centre: tie by index
+    r, d = bdg.route(c.cuda(), ce.cuda(), t)
+    r_o, d_o = oracle.route(_np(c), _np(ce), t)
+    assert np.array_equal(r.cpu().numpy(), r_o)
+    assert np.array_equal(d.cpu().numpy(), d_o)
+
+
+# ------------------------------------------------------------------ partitioned build
+@pytest.mark.parametrize("bits,n,m,t,k", [(512, 20000, 16, 3, 64), (256, 9000, 40, 5, 32),
+                                          (256, 3000, 8, 8, 16), (128, 5000, 64, 2, 8)])
+def test_partitioned_build_bit_exact(bdg, bits, n, m, t, k):
+    spec = datagen.MixtureSpec(n, 64, 48, bits, seed=n + m)
+    c = datagen.make_codes(spec)
+    sample = datagen.sample_ids(n, min(n, 64 * m), seed=3)
+    entry = torch.from_numpy(_entry(n, 64, 4)).cuda()
+    g = bdg.build_graph(c.cuda(), k, m=m, t=t, bk_sample=torch.from_numpy(sample).cuda(),
+                        bk_iters=8, entry=entry)
+    cent_o, _, _ = oracle.bkmeans(_np(c), sample, m, 8)
+    r_o, _ = oracle.route(_np(c), cent_o, t)
+    ids_o, dist_o = oracle.knn_partitioned(_np(c), r_o, k)
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+def test_partitioned_with_given_routes_and_empty_home(bdg):
+    # partition 3 is probed by visitors but is nobody's home: its lists are pads
+    n, bits, k = 2000, 256, 16
+    c = datagen.random_codes(n, bits, seed=12)
+    rng = np.random.default_rng(1)
+    home = rng.integers(0, 3, n)
+    routes = np.stack([home, np.full(n, 3), (home + 1) % 3], 1).astype(np.int32)
+    entry = torch.from_numpy(_entry(n, 32, 2)).cuda()
+    g = bdg.build_graph(c.cuda(), k, m=4, t=3, routes=torch.from_numpy(routes).cuda(),
+                        entry=entry)
+    ids_o, dist_o = oracle.knn_partitioned(_np(c), routes, k)
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+@pytest.mark.slow
+def test_partitioned_2m_512b_sampled_rows(bdg):
+    """Full-size partitioned workload (N = 2M, 512-bit, m = 256, t = 5, k = 64), in
+    the configuration the bench times: centres and routes compared in full, graph
+    rows on a sample the oracle computes one by one."""
+    w = datagen.WORKLOADS["partitioned_2m_512b"]
+    spec = w["spec"]
+    c_dev = datagen.make_codes(spec, device="cuda")
+    c = _np(c_dev)
+    n, m, t, k = spec.n, w["m"], w["t"], w["k"]
+    sample = datagen.sample_ids(n, 64 * m, spec.seed + 3)
+    entry = torch.from_numpy(_entry(n, 256, spec.seed + 4)).cuda()
+    cent, _ = bdg.bkmeans(c_dev, torch.from_numpy(sample).cuda(), m, w["bk_iters"])
+    g = bdg.build_graph(c_dev, k, m=m, t=t, bk_sample=torch.from_numpy(sample).cuda(),
+                        bk_iters=w["bk_iters"], entry=entry)
+    cent_o, _, _ = oracle.bkmeans(c, sample, m, w["bk_iters"])
+    assert np.array_equal(_np(cent), cent_o)
+    r_gpu, _ = bdg.route(c_dev, cent, t)
+    r_o, _ = oracle.route(c, cent_o, t)
+    assert np.array_equal(r_gpu.cpu().numpy(), r_o)
+    rows = datagen.sample_ids(n, 300, 99)
+    rows = np.concatenate([rows, [0, n - 1]])
+    ids_o, dist_o = oracle.knn_partitioned(c, r_o, k, rows)
+    assert np.array_equal(g.ids[torch.from_numpy(rows).cuda()].cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists[torch.from_numpy(rows).cuda()].cpu().numpy(), dist_o)
+
+
+# ------------------------------------------------------------------ search
+def _write_graph(path, ids, bits, entry):
+    n, k = ids.shape
+    with open(path, "wb") as f:
+        f.write(struct.pack("<6i", 0x31474442, 1, n, bits, k, len(entry)))
+        f.write(np.ascontiguousarray(ids, np.int32).tobytes())
+        f.write(np.zeros_like(ids, dtype=np.int32).tobytes())
+        f.write(np.ascontiguousarray(entry, np.int32).tobytes())
+
+
+@pytest.mark.parametrize("efs,R", [((64, 128, 256, 512), 100), ((1, 7, 33), 40), ((300,), 10)])
+def test_search_bit_exact_with_expansions(bdg, efs, R):
+    spec = datagen.MixtureSpec(12000, 128, 128, 256, seed=31)
+    c = datagen.make_codes(spec)
+    q = datagen.make_codes(spec, n=700, seed_offset=2)
+    entry = _entry(spec.n, 256, 8)
+    g = bdg.build_graph(c.cuda(), 32, m=1, t=1, entry=torch.from_numpy(entry).cuda())
+    ef = datagen.ef_mix(700, efs, seed=5)
+    ids, dist, ex = bdg.search(g, q.cuda(), torch.from_numpy(ef).cuda(), R, ef_max=max(efs),
+                               expansions=True)
+    g_o, _ = oracle.knn_exact(_np(c), 32)
+    ids_o, dist_o, cnt_o = oracle.search(_np(c), g_o, entry, _np(q), ef, R)
+    assert np.array_equal(ids.cpu().numpy(), ids_o)
+    assert np.array_equal(dist.cpu().numpy(), dist_o)
+    assert np.array_equal(ex.cpu().numpy(), cnt_o[:, 0])
+
+
+def test_search_on_loaded_adversarial_graphs(bdg, tmp_path):
+    # line graph with thermometer codes + complete graph + disconnected pieces
+    n = 64
+    c = np.zeros((n, 1), np.uint64)
+    for i in range(n):
+        c[i, 0] = np.uint64((1 << i) - 1) if i < 64 else np.uint64(~0)
+    line = np.array([[i - 1 if i > 0 else -1, i + 1 if i < n - 1 else -1] + [-1] * 30
+                     for i in range(n)], np.int32)
+    rng = np.random.default_rng(3)
+    scram = np.array([rng.permutation(row) for row in line], np.int32)  # -1 anywhere in a row
+    comp = np.array([[j for j in range(n) if j != i][:40] for i in range(n)], np.int32)
+    split = np.array([[(i + 1) % 32 + (32 if i >= 32 else 0), -1] for i in range(n)], np.int32)
+    q = c[[0, 12, 40, 63, 5]].copy()
+    q[4, 0] ^= np.uint64(1 << 50)
+    c_t = torch.from_numpy(c.view(np.int64)).cuda()
+    for name, adj in [("line", line), ("scram", scram), ("complete", comp), ("split", split)]:
+        entry = np.array([0, 33], np.int32)
+        p = str(tmp_path / f"{name}.bdg")
+        _write_graph(p, adj, 64, entry)
+        g = bdg.load_graph(p, c_t)
+        for efs in ((1,), (2, 5), (64,)):
+            ef = datagen.ef_mix(len(q), efs, seed=1)
+            ids, dist, ex = bdg.search(g, torch.from_numpy(q.view(np.int64)).cuda(),
+                                       torch.from_numpy(ef).cuda(), 20, ef_max=64, expansions=True)
+            ids_o, dist_o, cnt_o = oracle.search(c, adj, entry, q, ef, 20)
+            assert np.array_equal(ids.cpu().numpy(), ids_o), (name, efs)
+            assert np.array_equal(dist.cpu().numpy(), dist_o), (name, efs)
+            assert np.array_equal(ex.cpu().numpy(), cnt_o[:, 0]), (name, efs)
+
+
+def test_search_invalid_ef_rows_are_padding(bdg):
+    c = datagen.random_codes(500, 128, seed=4)
+    g, _ = _build_exact(bdg, c.cuda(), 16)
+    ef = torch.tensor([0, 65, 10], dtype=torch.int32).cuda()
+    ids, dist, ex = bdg.search(g, c[:3].cuda(), ef, 12, ef_max=64, expansions=True)
+    ids, ex = ids.cpu().numpy(), ex.cpu().numpy()
+    assert (ids[0] == -1).all() and (ids[1] == -1).all() and ex[0] == -1 and ex[1] == -1
+    assert ids[2, 0] == 2 and ex[2] > 0
+
+
+def test_graph_save_load_roundtrip(bdg, tmp_path):
+    c = datagen.random_codes(900, 256, seed=8).cuda()
+    g, _ = _build_exact(bdg, c, 8)
+    p = str(tmp_path / "g.bdg")
+    g.save(p)
+    h = bdg.load_graph(p, c)
+    assert torch.equal(g.ids, h.ids) and torch.equal(g.dists, h.dists)
+
+
+# ------------------------------------------------------------------ re-rank
+def _check_rerank(ids, d2, feats, qf, cand, k):
+    ids_o, d64 = oracle.rerank(feats, qf, cand, k, "f64")
+    ids = ids.cpu().numpy()
+    d2 = d2.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(d64)
+    assert np.array_equal(np.isfinite(d2), fin)
+    assert np.allclose(d2[fin], d64[fin], rtol=RTOL, atol=0)
+    for r in range(ids.shape[0]):
+        if np.array_equal(ids[r], ids_o[r]):
+            continue
+        # an id swap is only allowed between near-equal distances
+        diff = ids[r] != ids_o[r]
+        assert np.allclose(d2[r][diff], d64[r][diff], rtol=RTOL, atol=0)
+        assert set(ids[r][diff]) <= set(ids_o[r][diff]) | set(cand[r])
+
+
+@pytest.mark.parametrize("D,R,k", [(128, 100, 10), (256, 64, 32), (512, 37, 5), (1024, 1, 1)])
+def test_rerank_within_tolerance(bdg, D, R, k):
+    rng = np.random.default_rng(D + R)
+    feats = rng.standard_normal((3000, D)).astype(np.float32)
+    qf = rng.standard_normal((257, D)).astype(np.float32)
+    cand = np.array([rng.permutation(3000)[:R] for _ in range(257)], np.int32)
+    cand[5, : R // 2] = -1  # short rows
+    ids, d2 = bdg.rerank(torch.from_numpy(feats).cuda(), torch.from_numpy(qf).cuda(),
+                         torch.from_numpy(cand).cuda(), k)
+    _check_rerank(ids, d2, feats, qf, cand, k)
+
+
+def test_search_rerank_end_to_end(bdg):
+    spec = datagen.MixtureSpec(8000, 128, 64, 256, seed=41)
+    c, x = datagen.make_codes(spec, with_features=True)
+    qc, qx = datagen.make_codes(spec, n=300, seed_offset=2, with_features=True)
+    entry = _entry(spec.n, 128, 6)
+    g = bdg.build_graph(c.cuda(), 32, m=1, t=1, entry=torch.from_numpy(entry).cuda())
+    ef = datagen.ef_mix(300, (64, 128), seed=2)
+    ids, d2 = bdg.search_rerank(g, qc.cuda(), qx.cuda(), x.cuda(), torch.from_numpy(ef).cuda(),
+                                100, 10, ef_max=128)
+    g_o, _ = oracle.knn_exact(_np(c), 32)
+    cand_o, _, _ = oracle.search(_np(c), g_o, entry, _np(qc), ef, 100)
+    _check_rerank(ids, d2, x.numpy(), qx.numpy(), cand_o, 10)
