@@ -93,6 +93,23 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
                         int64_t nrows, int32_t k, int32_t* out_ids, int32_t* out_dist,
                         void* stream);
 
+/* bdg_bkmeans without any device allocation (the paper has no counterpart: it
+ * exists for callers that cannot allocate device memory -- code running while a
+ * CUDA graph is captured, processes whose device memory is owned by an outside
+ * manager, loops that must never reach the allocator). Same arguments and
+ * results as bdg_bkmeans. Its scratch is one fixed 16 MiB array inside the
+ * library, reserved on every GPU that loads the library until the process
+ * exits; calls needing more (bdg_bkmeans_scratch_bytes > 16 MiB, e.g. S = 16384,
+ * m = 256, 512 bits needs about 1.7 MiB) fail with BDG_EINVAL before any work.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the one array: calls that may overlap on the GPU
+ * (different streams, or different host threads) race and must be ordered by
+ * the caller. No cudaMalloc/cudaFree or allocating library routine is called. */
+bdg_status bdg_bkmeans_noalloc(const uint64_t* codes, int64_t n, int32_t bits,
+                               const int64_t* sample, int64_t S, int32_t m, int32_t iters,
+                               uint64_t* centroids, int64_t* loss, void* stream);
+
 /* ------------------------------------------------------------------ build */
 
 /* The `partitions` argument of the build (Section 3.2). */
@@ -108,7 +125,9 @@ typedef struct bdg_partitions {
                                  ignored (that slot contributes no neighbours) */
   const int32_t* entry;       /* [n_entry] long-link sample ids kept with the graph (Section 3.5) */
   int32_t n_entry;            /* 1 <= n_entry */
-  int32_t tile_visitors;      /* work-item size in visitors (32 or 64); 0 = autotuned */
+  int32_t tile_visitors;      /* work-item size in visitors: 0 (= 128) or 128 */
+  int32_t kernel;             /* Reduce-1 kernel: 0 = auto (tensor cores for 256/512-bit
+                                 codes and k <= 64, else popcount), 1 = popcount, 2 = tensor */
 } bdg_partitions;
 
 typedef struct bdg_graph bdg_graph; /* opaque; owns ids/dists/entry, borrows codes */

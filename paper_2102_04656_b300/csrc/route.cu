@@ -196,3 +196,64 @@ bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int
   }
   return BDG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free Bk-means. Some callers cannot call cudaMalloc at all: code
+// that runs while a CUDA graph is being captured, processes whose device
+// memory is owned by an external manager, or latency-critical loops that must
+// never reach the allocator. For them the Bk-means scratch lives in one
+// file-scope device array of fixed size, reserved on every GPU that loads this
+// library for as long as the process lives.
+#define BDG_BK_NOALLOC_BYTES (16u << 20)
+static __device__ __align__(256) unsigned char g_bk_noalloc_scratch[BDG_BK_NOALLOC_BYTES];
+
+#include <mutex>
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the static scratch for the current device. In host code
+// the array's name is only a host-side handle, never a device address, so it
+// is looked up once per device (with that device current) and cached.
+bdg_status noalloc_scratch(void** out) {
+  int dev = 0;
+  BDG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return bdg_set_error(BDG_EUNSUPPORTED, "device %d >= 64", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    BDG_CUDA_TRY(cudaGetSymbolAddress(&p, g_bk_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return BDG_OK;
+}
+}  // namespace
+
+extern "C" bdg_status bdg_bkmeans_noalloc(const uint64_t* codes, int64_t n, int32_t bits,
+                                          const int64_t* sample, int64_t S, int32_t m,
+                                          int32_t iters, uint64_t* centroids, int64_t* loss,
+                                          void* stream) {
+  if (bits <= 0 || bits % 64 != 0)
+    return bdg_set_error(BDG_EINVAL, "bkmeans_noalloc: bits = %d", bits);
+  const int W = bits / 64;
+  if (!(W == 1 || W == 2 || W == 4 || W == 8 || W == 16))
+    return bdg_set_error(BDG_EINVAL, "bkmeans_noalloc: bits = %d not built", bits);
+  if (m < 1 || S < m || iters < 0 || !codes || !sample || !centroids || n < 1)
+    return bdg_set_error(BDG_EINVAL, "bkmeans_noalloc: n=%lld S=%lld m=%d iters=%d",
+                         (long long)n, (long long)S, m, iters);
+  const size_t need = bdg_bkmeans_scratch_bytes(S, m, W);
+  if (need > BDG_BK_NOALLOC_BYTES)
+    return bdg_set_error(BDG_EINVAL,
+                         "bkmeans_noalloc: S=%lld, m=%d, bits=%d need %zu scratch bytes; the "
+                         "fixed scratch holds %u",
+                         (long long)S, m, bits, need, (unsigned)BDG_BK_NOALLOC_BYTES);
+  void* scratch = nullptr;
+  BDG_TRY(noalloc_scratch(&scratch));
+  // every scratch region is rewritten or cleared by the launches themselves:
+  // sample codes (gather), assignments (assign), per-bit counts (memset each
+  // iteration), so nothing from an earlier call leaks into this one
+  return bdg_launch_bkmeans(codes, n, W, sample, S, m, iters, centroids, loss, scratch,
+                            BDG_BK_NOALLOC_BYTES, (cudaStream_t)stream);
+}
