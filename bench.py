@@ -22,7 +22,6 @@ import hashlib
 import json
 import os
 import sys
-import threading
 import time
 
 import numpy as np
@@ -50,6 +49,13 @@ def _args():
     ap.add_argument("--search-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--recall-rows", type=int, default=2000)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--case", choices=["full", "small"], default="full",
+                    help="small: one 500k-point partitioned build (profiling case)")
+    ap.add_argument("--search-entry", type=int, default=16384,
+                    help="long-link entry sample size of the search graph")
+    ap.add_argument("--kernel", choices=["auto", "popc", "tc"], default="tc",
+                    help="Reduce-1 kernel of the build: tensor cores (tc) or XOR+POPC (popc)")
     return ap.parse_args()
 
 
@@ -80,54 +86,56 @@ def _max_over_ranks(x, ws, device):
 
 
 class Clocks:
-    """Samples SM clock and throttle reasons every 200 ms (NVML) while running."""
+    """Samples SM clock and clock-event reasons every 200 ms during the timed
+    region with nvidia-smi (started before, stopped after)."""
 
-    REASONS = {
-        0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
-        0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
-        0x80: "hw_power_brake_slowdown",
-    }
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.samples, self.reasons, self.max_mhz = [], set(), None
-        self._stop = threading.Event()
-        self._t = None
-        try:
-            import pynvml
-            pynvml.nvmlInit()
-            self._nv = pynvml
-            self._h = pynvml.nvmlDeviceGetHandleByIndex(index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
-        except Exception:
-            self._nv = None
-
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                self.samples.append(self._nv.nvmlDeviceGetClockInfo(self._h, self._nv.NVML_CLOCK_SM))
-                r = self._nv.nvmlDeviceGetCurrentClocksThrottleReasons(self._h)
-                for bit, name in self.REASONS.items():
-                    if r & bit and bit != 0x1:
-                        self.reasons.add(name)
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        self.index = index
+        self.proc = None
+        self.lines = []
 
     def __enter__(self):
-        if self._nv is not None:
-            self._t = threading.Thread(target=self._run, daemon=True)
-            self._t.start()
+        import subprocess
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        if self._t:
-            self._t.join()
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
 
     def summary(self):
-        med = float(np.median(self.samples)) if self.samples else None
-        return {"sm_mhz": med, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
-                "samples": len(self.samples)}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def _peaks():
@@ -138,11 +146,11 @@ def _peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def _traffic_record(name):
+def _traffic_record(name, source):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
     the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", name)
-    src = os.path.join(ROOT, "paper_2102_04656_b300", "csrc", "knn_popc.cu")
+    src = os.path.join(ROOT, "paper_2102_04656_b300", "csrc", source)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -222,7 +230,7 @@ def _cpu_baseline_build(codes_np, w, seconds):
                       f"candidate set (homes of all {n} points routed once, untimed)"}
 
 
-def _search_bench(bdg, device, steps, warmup, clk_summary):
+def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
     w = datagen.WORKLOADS[SEARCH_WORKLOAD]
     spec = w["spec"]
     codes, feats = datagen.make_codes(spec, device=device, with_features=True)
@@ -231,10 +239,11 @@ def _search_bench(bdg, device, steps, warmup, clk_summary):
     n, nq, k, topk = spec.n, w["nq"], w["k"], w["topk"]
     m, t = 1024, 3
     sample = torch.from_numpy(datagen.sample_ids(n, 64 * m, spec.seed + 3)).to(device)
-    entry = torch.from_numpy(datagen.sample_ids(n, 256, spec.seed + 4).astype(np.int32)).to(device)
+    entry = torch.from_numpy(datagen.sample_ids(n, n_entry, spec.seed + 4).astype(np.int32)).to(device)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g = bdg.build_graph(codes, k, m=m, t=t, bk_sample=sample, bk_iters=8, entry=entry)
+    g = bdg.build_graph(codes, k, m=m, t=t, bk_sample=sample, bk_iters=8, entry=entry,
+                        kernel=kernel)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     ef = torch.from_numpy(datagen.ef_mix(nq, w["efs"], spec.seed + 6)).to(device)
@@ -275,10 +284,12 @@ def _search_bench(bdg, device, steps, warmup, clk_summary):
         o = torch.topk(cat_v, topk, dim=1, largest=False).indices
         best, best_i = torch.gather(cat_v, 1, o), torch.gather(cat_i, 1, o)
     got = ids[qs].long()
-    hit = 0
-    for a, b in zip(got.cpu().numpy(), best_i.cpu().numpy()):
-        hit += len(set(a.tolist()) & set(b.tolist()))
-    rec = hit / (qs.numel() * topk)
+    hits = np.array([len(set(a.tolist()) & set(b.tolist()))
+                     for a, b in zip(got.cpu().numpy(), best_i.cpu().numpy())])
+    rec = float(hits.sum()) / (qs.numel() * topk)
+    ef_s = ef[qs].cpu().numpy()
+    rec_by_ef = {int(e): float(hits[ef_s == e].sum()) / max(1, (ef_s == e).sum() * topk)
+                 for e in w["efs"]}
     # algorithmic bytes of the search kernel: per expansion a 4*deg-byte id list and
     # one 32-byte code per scored neighbour (upper bound: every neighbour scored)
     _, _, ex = bdg.search(g, qcodes, ef, R, ef_max=max(w["efs"]), expansions=True)
@@ -289,13 +300,36 @@ def _search_bench(bdg, device, steps, warmup, clk_summary):
         "ef_mix": list(w["efs"]), "R": R, "topk": topk, "graph_build": {"m": m, "t": t,
                                                                          "seconds": build_s},
         "qps": nq / (ms / 1000.0), "ms_per_batch": ms, "recall@10_vs_exact_fp32": rec,
+        "recall@10_by_ef": rec_by_ef, "entry_sample": n_entry,
         "recall_queries": int(qs.numel()), "search_kernel_ms": search_ms,
         "rerank_kernel_ms": rerank_ms, "expansions_mean": exp_total / nq,
         "search_bytes_upper_bound_gbs": bytes_search / (search_ms / 1e3) / 1e9,
     }
 
 
+def run_small_case(a):
+    """One 500k-point partitioned build (512-bit, m = 64, t = 5, k = 64): the
+    small case on which the fused k-NN kernel is profiled."""
+    from paper_2102_04656_b300 import build as bdg_build
+    bdg_build.build()
+    import paper_2102_04656_b300 as bdg
+    w = dict(datagen.WORKLOADS[WORKLOAD])
+    base = w["spec"]
+    w["spec"] = datagen.MixtureSpec(500_000, base.dim, 256, base.bits, base.sigma, base.seed)
+    w["m"] = 64
+    spec, codes, sample, entry = _build_inputs(w, "cuda")
+    for i in range(max(1, a.warmup) + a.steps):
+        g = bdg.build_graph(codes, w["k"], m=w["m"], t=w["t"], bk_sample=sample,
+                            bk_iters=w["bk_iters"], entry=entry, kernel=a.kernel)
+        torch.cuda.synchronize()
+        g.free()
+    print(json.dumps({"case": "small", "N": spec.n, "bits": spec.bits, "m": w["m"], "t": w["t"],
+                      "k": w["k"], "builds": max(1, a.warmup) + a.steps}))
+
+
 def run_ours(a):
+    if a.case == "small":
+        return run_small_case(a)
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
@@ -313,7 +347,7 @@ def run_ours(a):
 
     def step():
         return bdg.build_graph(codes, k, m=m, t=t, bk_sample=sample, bk_iters=w["bk_iters"],
-                               entry=entry)
+                               entry=entry, kernel=a.kernel)
 
     for i in range(a.warmup):
         g = step()
@@ -372,7 +406,7 @@ def run_ours(a):
         e2e_ev[s][0].record()
         dev_codes.copy_(host_codes, non_blocking=True)
         g = bdg.build_graph(dev_codes, k, m=m, t=t, bk_sample=sample, bk_iters=w["bk_iters"],
-                            entry=entry)
+                            entry=entry, kernel=a.kernel)
         host_ids.copy_(g.ids, non_blocking=True)
         host_d.copy_(g.dists, non_blocking=True)
         e2e_ev[s][1].record()
@@ -382,7 +416,7 @@ def run_ours(a):
 
     search = None
     if not a.no_search and ws == 1:
-        search = _search_bench(bdg, device, a.search_steps, 2, None)
+        search = _search_bench(bdg, device, a.search_steps, 2, a.search_entry, a.kernel)
 
     if rank != 0:
         if ws > 1:
@@ -391,12 +425,32 @@ def run_ours(a):
         return
     peaks, peak_kind = _peaks()
     cs = clk.summary()
-    bitops = pairs * spec.bits
-    sm_max = peaks.get("sm_max_mhz", 2032.0)
     nsm = torch.cuda.get_device_properties(device).multi_processor_count
-    peak_bitops = nsm * POPC_PER_SM_CLK * 32 * sm_max * 1e6
-    achieved = bitops / (knn_ms / 1e3)
-    traffic = _traffic_record(f"knn_popc_{WORKLOAD}.txt")
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    traffic = None
+    if a.kernel == "popc":
+        # XOR + POPC: bits / 32 population counts per pair against the POPC pipe
+        work = pairs * spec.bits
+        peak = nsm * POPC_PER_SM_CLK * 32 * sm_max * 1e6
+        roof = {"kernel": "knn_popc (fused XOR+POPC Hamming + top-k, persistent)",
+                "bound": "alu", "unit": "Tbitop/s",
+                "peak_source": f"{nsm} SMs x {POPC_PER_SM_CLK} POPC/clk x 32 bit x "
+                               f"{sm_max:.0f} MHz ({peak_kind} max clock)"}
+        traffic = _traffic_record(f"knn_popc_{WORKLOAD}.txt", "knn_popc.cu")
+    else:
+        # +-1 FP8 MMA: 2 * bits FLOP per pair against the FP8 dense tensor peak
+        work = 2.0 * pairs * spec.bits
+        peak = peaks.get("bf16_tflops_sustained", 1400.0) * 2.0 * 1e12
+        roof = {"kernel": "knn_tc (tcgen05 FP8 +-1 Hamming tile + top-k epilogue)",
+                "bound": "tensor", "unit": "TFLOP/s",
+                "peak_source": f"FP8 dense = 2 x the {peak_kind} sustained BF16 cuBLAS rate "
+                               f"({peaks.get('bf16_tflops_sustained')} TFLOP/s); nominal FP8/BF16 "
+                               "ratio 4.5/2.25"}
+        traffic = _traffic_record(f"knn_tc_{WORKLOAD}.txt", "knn_tc.cu")
+    achieved = work / (knn_ms / 1e3)
+    roof.update({"achieved": achieved / 1e12, "peak": peak / 1e12, "frac": achieved / peak,
+                 "traffic": traffic, "pairs_per_launch": pairs, "kernel_ms": knn_ms,
+                 "share_of_step": knn_ms / ms})
     line = {
         "metric": METRIC, "value": n * ws / (ms_max / 1e3) / 1e6, "unit": "Mpoints/s",
         "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max,
@@ -404,17 +458,12 @@ def run_ours(a):
         "data": "synthetic (seeded Gaussian-mixture features -> sign of random projections)",
         "config": {"workload": WORKLOAD, "N": n, "bits": spec.bits, "m": m, "t": t, "k": k,
                    "bk_sample": int(sample.numel()), "bk_iters": w["bk_iters"],
+                   "reduce1_kernel": a.kernel,
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "parallelism": f"independent problem per GPU x{ws}"},
         "recall": {"tie_aware": tie, "ids": idrec, "rows": a.recall_rows,
                    "judge": "exact brute-force rows (bdg_knn_rows)"},
-        "roofline": {"kernel": "knn_popc (fused Hamming + top-k, persistent)", "bound": "alu",
-                     "achieved": achieved / 1e12, "peak": peak_bitops / 1e12, "unit": "Tbitop/s",
-                     "frac": achieved / peak_bitops, "traffic": traffic,
-                     "peak_source": f"{nsm} SMs x {POPC_PER_SM_CLK} POPC/clk x 32 bit x "
-                                    f"{sm_max:.0f} MHz ({peak_kind} max clock)",
-                     "pairs_per_launch": pairs, "kernel_ms": knn_ms,
-                     "share_of_step": knn_ms / ms},
+        "roofline": roof,
         "kernels_ms": {"knn": knn_ms, "merge": merge_ms, "route": route_ms},
         "partition_sizes": {"home_min": int(hc.min()), "home_max": int(hc.max()),
                             "home_median": float(np.median(hc)),
@@ -427,7 +476,7 @@ def run_ours(a):
     }
     if search is not None:
         line["search"] = search
-    if ws == 1:
+    if ws == 1 and not a.no_cpu:
         import oracle
         oracle.build()
         line["cpu_baseline"] = _cpu_baseline_build(codes.cpu().numpy().view(np.uint64), w,

@@ -149,3 +149,15 @@ def unpack_bits(codes: np.ndarray, bits: int) -> np.ndarray:
     sh = np.arange(64, dtype=np.uint64)
     b = (c[:, :, None] >> sh) & np.uint64(1)
     return b.reshape(n, w * 64)[:, :bits].astype(np.uint8)
+
+
+def router_init(d_in: int, h1: int, h2: int, m: int, seed: int) -> np.ndarray:
+    """Seeded initial router parameters, packed W1 b1 W2 b2 W3 b3 (float32):
+    every weight and bias uniform in +-1/sqrt(fan_in)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((d_in, h1), (h1, h2), (h2, m)):
+        bound = 1.0 / np.sqrt(fan_in)
+        parts.append(rng.uniform(-bound, bound, size=fan_out * fan_in))
+        parts.append(rng.uniform(-bound, bound, size=fan_out))
+    return np.concatenate(parts).astype(np.float32)

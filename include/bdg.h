@@ -192,6 +192,50 @@ bdg_status bdg_search_rerank(const bdg_graph* g, const uint64_t* queries, const 
                              int32_t ef_max, int32_t R, int32_t k, int32_t* cand_ids,
                              int32_t* cand_dist, int32_t* out_ids, float* out_d2, void* stream);
 
+/* ------------------------------------------------------------------ learned router */
+/* The paper routes each point to its t nearest binary centres (Section 3.2).
+ * The router keeps the nearest centre as the home (slot 0) and picks the other
+ * P - 1 probed partitions with a small BF16 MLP trained on where a point's exact
+ * neighbours live:
+ *   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2), z = h2 W3^T + b3 (FP32 accumulate)
+ *   loss = -(1/B) sum_i sum_p q_ip log softmax(z_i)_p,
+ *   q_ip = #{j in labels[i] : j == p} / kt   (labels: home partitions of i's neighbours)
+ * Adam (beta 0.9 / 0.999, eps 1e-8) on FP32 master weights with BF16 copies. */
+typedef struct bdg_router bdg_router;
+
+/* init_params: device FP32, packed W1[h1][d_in] b1[h1] W2[h2][h1] b2[h2] W3[m][h2] b3[m]
+ * (copied). All sizes and max_batch multiples of 8. Synchronous. */
+bdg_status bdg_router_create(int32_t d_in, int32_t h1, int32_t h2, int32_t m,
+                             const float* init_params, int32_t max_batch, bdg_router** out);
+void bdg_router_free(bdg_router* r);
+/* Device pointers to the packed FP32 parameters, the gradients of the last
+ * training step (same layout), the last loss (scalar) and an error word. */
+bdg_status bdg_router_info(const bdg_router* r, float** params, float** grads, int64_t* n_params,
+                           float** loss, int32_t** err);
+/* x: [B][d_in] BF16 (device). logits: [B][m] FP32. B <= max_batch. */
+bdg_status bdg_router_forward(bdg_router* r, const void* x, int32_t B, float* logits,
+                              void* stream);
+/* One training step on a batch: forward, loss, backward into the gradient
+ * buffer, and (apply_update != 0) an Adam update with learning rate lr.
+ * labels: [B][kt] int32 partition ids (-1 entries ignored). B % 8 == 0. */
+bdg_status bdg_router_train_step(bdg_router* r, const void* x, const int32_t* labels, int32_t kt,
+                                 int32_t B, float lr, int32_t apply_update, void* stream);
+/* routes[i] = {home[i], then the P - 1 other partitions of largest logit,
+ * ties by partition index}. x: [N][d_in] BF16, home: [N], routes: [N][P], P <= 17. */
+bdg_status bdg_router_route(bdg_router* r, const void* x, int64_t N, const int32_t* home,
+                            int32_t P, int32_t* routes, void* stream);
+
+/* The router's tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulation):
+ *   C[M][N] = epilogue(A[M][K] * B[N][K]^T), A and B row-major with K contiguous;
+ * epilogue: + bias[N] (if given), relu (if relu != 0), times [mask[M][N] > 0] (if
+ * mask given, BF16), written as FP32 (out_f32) and/or BF16 (out_bf16);
+ * colsum[N] += column sums of the result (if given). K % 8 == 0. err: device
+ * int32 set non-zero if a bounded wait gave up. The paper has no counterpart:
+ * it is the building block of the router above. */
+bdg_status bdg_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                         const float* bias, const void* mask, int32_t relu, float* out_f32,
+                         void* out_bf16, float* colsum, int32_t* err, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

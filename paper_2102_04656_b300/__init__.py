@@ -17,7 +17,7 @@ from . import build as _build
 __all__ = [
     "BDGError", "lib", "route", "bkmeans", "build_graph", "Graph", "search", "rerank",
     "search_rerank", "load_graph", "set_memory_budget", "memory_in_use", "knn_rows",
-    "launch_count",
+    "launch_count", "gemm_bf16", "Router",
 ]
 
 _LIB = None
@@ -36,7 +36,7 @@ class _Partitions(ctypes.Structure):
     _fields_ = [
         ("m", _i32), ("t", _i32), ("centroids", _c_void_p), ("bk_sample", _c_void_p),
         ("bk_sample_size", _i64), ("bk_iters", _i32), ("routes", _c_void_p),
-        ("entry", _c_void_p), ("n_entry", _i32), ("tile_visitors", _i32),
+        ("entry", _c_void_p), ("n_entry", _i32), ("tile_visitors", _i32), ("kernel", _i32),
     ]
 
 
@@ -210,10 +210,15 @@ class Graph:
             pass
 
 
+KERNELS = {"auto": 0, "popc": 1, "tc": 2}
+
+
 def build_graph(codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample=None,
                 bk_iters: int = 8, routes=None, entry=None, tile_visitors: int = 0,
-                stream=None) -> Graph:
-    """Single-pass divide-and-conquer k-NN graph (exact when m == 1)."""
+                kernel: str = "auto", stream=None) -> Graph:
+    """Single-pass divide-and-conquer k-NN graph (exact when m == 1).
+
+    kernel: "auto", "popc" (XOR + POPC) or "tc" (tcgen05 FP8 +-1 tensor cores)."""
     codes, bits = _codes(codes)
     if entry is None:
         raise ValueError("entry (long-link sample ids, int32 CUDA tensor) is required")
@@ -229,6 +234,7 @@ def build_graph(codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample
     P.entry = entry.data_ptr()
     P.n_entry = entry.numel()
     P.tile_visitors = tile_visitors
+    P.kernel = KERNELS[kernel]
     h = ctypes.c_void_p()
     _check(lib().bdg_build_graph(_ptr(codes), codes.shape[0], bits, k, ctypes.byref(P),
                                  _stream(stream), ctypes.byref(h)))
@@ -288,3 +294,110 @@ def search_rerank(g: Graph, queries, qfeats, feats, ef, R: int, k: int, ef_max: 
                                    feats.shape[1], nq, _ptr(ef), ef_max, R, k, _ptr(cand),
                                    _ptr(cdist), _ptr(ids), _ptr(d2), _stream(stream)))
     return ids, d2
+
+
+# ----------------------------------------------------------------------------- router
+def _router_sigs(L):
+    if getattr(L, "_router_sigs", False):
+        return
+    L.bdg_gemm_bf16.argtypes = [_c_void_p, _c_void_p, _i32, _i32, _i32, _c_void_p, _c_void_p,
+                                _i32, _c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p]
+    L.bdg_router_create.argtypes = [_i32, _i32, _i32, _i32, _c_void_p, _i32,
+                                    ctypes.POINTER(_c_void_p)]
+    L.bdg_router_free.argtypes = [_c_void_p]
+    L.bdg_router_free.restype = None
+    L.bdg_router_info.argtypes = [_c_void_p, ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p),
+                                  ctypes.POINTER(_i64), ctypes.POINTER(_c_void_p),
+                                  ctypes.POINTER(_c_void_p)]
+    L.bdg_router_forward.argtypes = [_c_void_p, _c_void_p, _i32, _c_void_p, _c_void_p]
+    L.bdg_router_train_step.argtypes = [_c_void_p, _c_void_p, _c_void_p, _i32, _i32,
+                                        ctypes.c_float, _i32, _c_void_p]
+    L.bdg_router_route.argtypes = [_c_void_p, _c_void_p, _i64, _c_void_p, _i32, _c_void_p,
+                                   _c_void_p]
+    L._router_sigs = True
+
+
+def gemm_bf16(A, B, bias=None, mask=None, relu=False, out="f32", colsum=None, stream=None):
+    """C = epilogue(A @ B^T) on the library's tcgen05 BF16 GEMM (FP32 accumulation)."""
+    L = lib()
+    _router_sigs(L)
+    _dev(A, torch.bfloat16, "A", 2)
+    _dev(B, torch.bfloat16, "B", 2)
+    M, K = A.shape
+    N = B.shape[0]
+    dev = A.device
+    of = torch.empty(M, N, dtype=torch.float32, device=dev) if out in ("f32", "both") else None
+    ob = torch.empty(M, N, dtype=torch.bfloat16, device=dev) if out in ("bf16", "both") else None
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(L.bdg_gemm_bf16(_ptr(A), _ptr(B), M, N, K, _ptr(bias), _ptr(mask), int(relu),
+                           _ptr(of), _ptr(ob), _ptr(colsum), _ptr(err), _stream(stream)))
+    return (of if out == "f32" else ob if out == "bf16" else (of, ob)), err
+
+
+class Router:
+    """The BF16 MLP partition router (see include/bdg.h): d_in -> h1 -> h2 -> m."""
+
+    def __init__(self, init_params, d_in: int, h1: int, h2: int, m: int, max_batch: int):
+        L = lib()
+        _router_sigs(L)
+        _dev(init_params, torch.float32, "init_params", 1)
+        h = ctypes.c_void_p()
+        _check(L.bdg_router_create(d_in, h1, h2, m, _ptr(init_params), max_batch,
+                                   ctypes.byref(h)))
+        self._h = h
+        self.d_in, self.h1, self.h2, self.m, self.max_batch = d_in, h1, h2, m, max_batch
+        p, g, lo, er = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        n = _i64()
+        _check(L.bdg_router_info(h, ctypes.byref(p), ctypes.byref(g), ctypes.byref(n),
+                                 ctypes.byref(lo), ctypes.byref(er)))
+        dev = init_params.device
+        self.n_params = n.value
+        self.params = torch.as_tensor(_CudaArray(p.value, (n.value,), "<f4", self), device=dev)
+        self.grads = torch.as_tensor(_CudaArray(g.value, (n.value,), "<f4", self), device=dev)
+        self.loss = torch.as_tensor(_CudaArray(lo.value, (1,), "<f4", self), device=dev)
+        self.err = torch.as_tensor(_CudaArray(er.value, (1,), "<i4", self), device=dev)
+
+    def unpack(self, flat):
+        """Split a packed parameter vector into W1, b1, W2, b2, W3, b3 views."""
+        d, a, b, m = self.d_in, self.h1, self.h2, self.m
+        sizes = [a * d, a, b * a, b, m * b, m]
+        shapes = [(a, d), (a,), (b, a), (b,), (m, b), (m,)]
+        out, o = {}, 0
+        for name, sz, sh in zip(["W1", "b1", "W2", "b2", "W3", "b3"], sizes, shapes):
+            out[name] = flat[o:o + sz].view(*sh)
+            o += sz
+        return out
+
+    def forward(self, x, stream=None):
+        _dev(x, torch.bfloat16, "x", 2)
+        z = torch.empty(x.shape[0], self.m, dtype=torch.float32, device=x.device)
+        _check(lib().bdg_router_forward(self._h, _ptr(x), x.shape[0], _ptr(z), _stream(stream)))
+        return z
+
+    def train_step(self, x, labels, lr: float, apply_update: bool = True, stream=None):
+        _dev(x, torch.bfloat16, "x", 2)
+        _dev(labels, torch.int32, "labels", 2)
+        _check(lib().bdg_router_train_step(self._h, _ptr(x), _ptr(labels), labels.shape[1],
+                                           x.shape[0], float(lr), int(apply_update),
+                                           _stream(stream)))
+        return self.loss
+
+    def route(self, x, home, P: int, stream=None):
+        _dev(x, torch.bfloat16, "x", 2)
+        _dev(home, torch.int32, "home", 1)
+        routes = torch.empty(x.shape[0], P, dtype=torch.int32, device=x.device)
+        _check(lib().bdg_router_route(self._h, _ptr(x), x.shape[0], _ptr(home), P, _ptr(routes),
+                                      _stream(stream)))
+        return routes
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            self.params = self.grads = self.loss = self.err = None
+            lib().bdg_router_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -20,6 +21,7 @@ struct bdg_graph {
   int32_t* ids;           // [n][k]
   int32_t* dists;         // [n][k]
   int32_t* entry;         // [n_entry]
+  uint64_t* entry_codes;  // [n_entry][W] contiguous copy of the entry sample's codes
 };
 
 namespace {
@@ -149,6 +151,15 @@ bdg_status bdg_set_error(bdg_status s, const char* fmt, ...) {
   return s;
 }
 
+// Whether "auto" picks the tensor-core Reduce-1 kernel (BDG_KNN_KERNEL=popc|tc
+// overrides; the default is the tensor path).
+bool bdg_tc_default() {
+  const char* e = getenv("BDG_KNN_KERNEL");
+  if (e && strcmp(e, "popc") == 0) return false;
+  if (e && strcmp(e, "tc") == 0) return true;
+  return false;
+}
+
 int bdg_num_sms() {
   static int cache[64] = {0};
   int dev = 0;
@@ -254,6 +265,15 @@ bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32
   if (P->tile_visitors != 0 && P->tile_visitors != bdg_knn_tile_visitors(bits / 64))
     return bdg_set_error(BDG_EUNSUPPORTED, "build: tile_visitors %d not built for %d bits",
                          P->tile_visitors, bits);
+  if (P->kernel < 0 || P->kernel > 2)
+    return bdg_set_error(BDG_EINVAL, "build: kernel = %d (0 auto, 1 popcount, 2 tensor)",
+                         P->kernel);
+  const bool tc_ok = bdg_knn_tc_supported(bits / 64, k) && (m > 1 || N < (1 << 21));
+  if (P->kernel == 2 && !tc_ok)
+    return bdg_set_error(BDG_EUNSUPPORTED,
+                         "build: the tensor path needs 256/512-bit codes, k <= 64 and, with "
+                         "m = 1, N < 2^21");
+  const bool use_tc = P->kernel == 2 || (P->kernel == 0 && tc_ok && bdg_tc_default());
 
   cudaStream_t st = (cudaStream_t)stream;
   const int W = bits / 64;
@@ -266,6 +286,7 @@ bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32
   bdg_status s = dalloc((void**)&g->ids, (size_t)N * k * 4);
   if (s == BDG_OK) s = dalloc((void**)&g->dists, (size_t)N * k * 4);
   if (s == BDG_OK) s = dalloc((void**)&g->entry, (size_t)P->n_entry * 4);
+  if (s == BDG_OK) s = dalloc((void**)&g->entry_codes, (size_t)P->n_entry * W * 8);
   if (s != BDG_OK) { bdg_graph_free(g); return s; }
 
   // scratch layout
@@ -274,8 +295,10 @@ bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32
   const size_t b_bk = need_bk ? al(bdg_bkmeans_scratch_bytes(P->bk_sample_size, m, W)) : 0;
   const size_t b_csr = al(bdg_csr_bytes(N, m, t, W));
   const size_t b_part = t > 1 ? al((size_t)N * t * k * 8) : 0;
+  const size_t b_hexp = use_tc ? al(bdg_knn_tc_hexp_bytes(N, m, W)) : 0;
+  const size_t b_fix = use_tc ? al((size_t)N * t) + al(64) : 0;
   Scratch sc;
-  s = sc.alloc(b_routes + b_cent + b_bk + b_csr + b_part, st);
+  s = sc.alloc(b_routes + b_cent + b_bk + b_csr + b_part + b_hexp + b_fix, st);
   if (s != BDG_OK) { bdg_graph_free(g); return s; }
   char* p = (char*)sc.p;
   int32_t* routes = (int32_t*)P->routes;
@@ -285,11 +308,18 @@ bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32
   void* bk = p; p += b_bk;
   void* csr_mem = p; p += b_csr;
   uint64_t* partial = b_part ? (uint64_t*)p : nullptr;
+  p += b_part;
+  uint8_t* hexp = b_hexp ? (uint8_t*)p : nullptr;
+  p += b_hexp;
+  int8_t* fixflag = b_fix ? (int8_t*)p : nullptr;
+  int32_t* tc_err = b_fix ? (int32_t*)(p + al((size_t)N * t)) : nullptr;
 
   auto fail = [&](bdg_status e) { bdg_graph_free(g); return e; };
   if (cudaMemcpyAsync(g->entry, P->entry, (size_t)P->n_entry * 4, cudaMemcpyDeviceToDevice, st) !=
       cudaSuccess)
     return fail(bdg_set_error(BDG_ECUDA, "build: copying the entry sample failed"));
+  s = bdg_launch_gather_codes(codes, N, g->entry, P->n_entry, W, g->entry_codes, st);
+  if (s != BDG_OK) return fail(s);
   if (m == 1) {
     if (cudaMemsetAsync(routes, 0, (size_t)N * 4, st) != cudaSuccess)
       return fail(bdg_set_error(BDG_ECUDA, "build: memset failed"));
@@ -320,7 +350,16 @@ bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32
   a.tile_v = tile_v; a.partial = partial; a.out_ids = g->ids; a.out_dist = g->dists;
   a.item_counter = csr.counters + 2 * m;
   a.out_by_pos = 0;
-  s = bdg_launch_knn_popc(a, W, st);
+  a.fixflag = nullptr;
+  if (use_tc) {
+    if (cudaMemsetAsync(fixflag, 0, al((size_t)N * t) + al(64), st) != cudaSuccess)
+      return fail(bdg_set_error(BDG_ECUDA, "build: memset failed"));
+    bdg_knn_tc_args ta;
+    ta.base = a; ta.hexp = hexp; ta.fixflag = fixflag; ta.err = tc_err;
+    s = bdg_launch_knn_tc(ta, W, st);
+  } else {
+    s = bdg_launch_knn_popc(a, W, st);
+  }
   if (s != BDG_OK) return fail(s);
   if (t > 1) {
     s = bdg_launch_merge(partial, N, t, k, bits, g->ids, g->dists, st);
@@ -345,9 +384,12 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
   const int W = bits / 64;
   const int tile_v = bdg_knn_tile_visitors(W);
   keep_pool_cached();
+  const bool use_tc = bdg_knn_tc_supported(W, k) && N < (1 << 21) && bdg_tc_default();
   Scratch sc;
-  const size_t b = bdg_csr_rows_bytes(N, nrows);
-  BDG_TRY(sc.alloc(b, st));
+  const size_t b = al(bdg_csr_rows_bytes(N, nrows));
+  const size_t b_hexp = use_tc ? al(bdg_knn_tc_hexp_bytes(N, 1, W)) : 0;
+  const size_t b_fix = use_tc ? al((size_t)nrows) + al(64) : 0;
+  BDG_TRY(sc.alloc(b + b_hexp + b_fix, st));
   bdg_csr csr;
   BDG_TRY(bdg_build_csr_rows(codes, N, rows, nrows, tile_v, sc.p, &csr, st));
   bdg_knn_args a;
@@ -355,7 +397,16 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
   a.tile_v = tile_v; a.partial = nullptr; a.out_ids = out_ids; a.out_dist = out_dist;
   a.item_counter = csr.counters + 2;
   a.out_by_pos = 1;
-  return bdg_launch_knn_popc(a, W, st);
+  a.fixflag = nullptr;
+  if (!use_tc) return bdg_launch_knn_popc(a, W, st);
+  char* q = (char*)sc.p + b;
+  bdg_knn_tc_args ta;
+  ta.base = a;
+  ta.hexp = (uint8_t*)q;
+  ta.fixflag = (int8_t*)(q + b_hexp);
+  ta.err = (int32_t*)(q + b_hexp + al((size_t)nrows));
+  BDG_CUDA_TRY(cudaMemsetAsync(ta.fixflag, 0, b_fix, st));
+  return bdg_launch_knn_tc(ta, W, st);
 }
 
 bdg_status bdg_graph_info(const bdg_graph* g, const int32_t** ids, const int32_t** dists,
@@ -374,6 +425,7 @@ void bdg_graph_free(bdg_graph* g) {
   dfree(g->ids, (size_t)g->n * g->k * 4);
   dfree(g->dists, (size_t)g->n * g->k * 4);
   dfree(g->entry, (size_t)g->n_entry * 4);
+  dfree(g->entry_codes, (size_t)g->n_entry * g->W * 8);
   delete g;
 }
 
@@ -418,6 +470,7 @@ bdg_status bdg_graph_load(const char* path, const uint64_t* codes, bdg_graph** o
   bdg_status s = dalloc((void**)&g->ids, ids.size() * 4);
   if (s == BDG_OK) s = dalloc((void**)&g->dists, dists.size() * 4);
   if (s == BDG_OK) s = dalloc((void**)&g->entry, entry.size() * 4);
+  if (s == BDG_OK) s = dalloc((void**)&g->entry_codes, entry.size() * g->W * 8);
   if (s != BDG_OK) { bdg_graph_free(g); return s; }
   if (cudaMemcpy(g->ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(g->dists, dists.data(), dists.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -425,6 +478,10 @@ bdg_status bdg_graph_load(const char* path, const uint64_t* codes, bdg_graph** o
     bdg_graph_free(g);
     return bdg_set_error(BDG_ECUDA, "load: copy to device failed");
   }
+  s = bdg_launch_gather_codes(codes, g->n, g->entry, g->n_entry, g->W, g->entry_codes, nullptr);
+  if (s == BDG_OK && cudaDeviceSynchronize() != cudaSuccess)
+    s = bdg_set_error(BDG_ECUDA, "load: gathering the entry codes failed");
+  if (s != BDG_OK) { bdg_graph_free(g); return s; }
   *out = g;
   return BDG_OK;
 }
@@ -437,7 +494,7 @@ bdg_status bdg_search(const bdg_graph* g, const uint64_t* queries, int64_t nq, c
     return bdg_set_error(BDG_EINVAL, "search: nq=%lld R=%d ef_max=%d", (long long)nq, R, ef_max);
   if (nq > 0 && (!queries || !ef || !out_ids || !out_dist))
     return bdg_set_error(BDG_EINVAL, "search: null pointer");
-  bdg_graph_view v{g->codes, g->ids, g->entry, g->n, g->k, g->bits, g->n_entry};
+  bdg_graph_view v{g->codes, g->ids, g->entry, g->entry_codes, g->n, g->k, g->bits, g->n_entry};
   return bdg_launch_search(v, queries, nq, ef, ef_max, R, out_ids, out_dist, expansions,
                            (cudaStream_t)stream);
 }

@@ -59,7 +59,8 @@ __device__ int32_t block_exclusive_scan(int32_t v, int32_t* warp_tot, int32_t* t
 __global__ void __launch_bounds__(kScanThreads)
 plan_kernel(int m, int tile_v, int32_t* __restrict__ hcnt, int32_t* __restrict__ vcnt,
             int32_t* __restrict__ home_off, int32_t* __restrict__ visit_off,
-            int32_t* __restrict__ part_order, int32_t* __restrict__ item_off) {
+            int32_t* __restrict__ part_order, int32_t* __restrict__ item_off,
+            int32_t* __restrict__ eoff) {
   extern __shared__ uint64_t skey[];  // [pow2 >= m]
   __shared__ int32_t warp_tot[32];
   __shared__ int32_t total;
@@ -74,6 +75,16 @@ plan_kernel(int m, int tile_v, int32_t* __restrict__ hcnt, int32_t* __restrict__
     int32_t run = block_exclusive_scan(s, warp_tot, &total);
     for (int p = b; p < e; ++p) { off[p] = run; run += cnt[p]; }
     if (threadIdx.x == 0) off[m] = total;
+    __syncthreads();
+  }
+  // --- offsets of the 64-row-padded expanded home operand (tensor path)
+  {
+    const int b = threadIdx.x * per, e = min(m, b + per);
+    int32_t s = 0;
+    for (int p = b; p < e; ++p) s += (hcnt[p] + 63) & ~63;
+    int32_t run = block_exclusive_scan(s, warp_tot, &total);
+    for (int p = b; p < e; ++p) { eoff[p] = run; run += (hcnt[p] + 63) & ~63; }
+    if (threadIdx.x == 0) eoff[m] = total;
     __syncthreads();
   }
   // --- sort partitions by (decreasing |H_p|, p)
@@ -155,7 +166,8 @@ __global__ void rows_plan_kernel(int64_t N, const int32_t* __restrict__ rows, in
                                  int tile_v, int32_t* __restrict__ home_off,
                                  int32_t* __restrict__ home_ids, int32_t* __restrict__ visit_off,
                                  int32_t* __restrict__ visit_ids, int8_t* __restrict__ visit_slot,
-                                 int32_t* __restrict__ part_order, int32_t* __restrict__ item_off) {
+                                 int32_t* __restrict__ part_order, int32_t* __restrict__ item_off,
+                                 int32_t* __restrict__ eoff) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x < N) home_ids[x] = (int32_t)x;
   if (x < nrows) {  // ids outside [0, N) become empty rows
@@ -168,13 +180,14 @@ __global__ void rows_plan_kernel(int64_t N, const int32_t* __restrict__ rows, in
     visit_off[0] = 0; visit_off[1] = (int32_t)nrows;
     part_order[0] = 0;
     item_off[0] = 0; item_off[1] = (int32_t)((nrows + tile_v - 1) / tile_v);
+    eoff[0] = 0; eoff[1] = (int32_t)((N + 63) & ~63LL);
   }
 }
 
 }  // namespace
 
 size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows) {
-  return al(2 * 4) * 3 + al(N * 4) + al(nrows * 4) + al(nrows) + al(4) + al(8 * 4);
+  return al(2 * 4) * 4 + al(N * 4) + al(nrows * 4) + al(nrows) + al(4) + al(8 * 4);
 }
 
 bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* rows,
@@ -183,6 +196,7 @@ bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* r
   c->home_off = (int32_t*)p;   p += al(2 * 4);
   c->visit_off = (int32_t*)p;  p += al(2 * 4);
   c->item_off = (int32_t*)p;   p += al(2 * 4);
+  c->eoff = (int32_t*)p;       p += al(2 * 4);
   c->home_ids = (int32_t*)p;   p += al(N * 4);
   c->visit_ids = (int32_t*)p;  p += al(nrows * 4);
   c->visit_slot = (int8_t*)p;  p += al(nrows);
@@ -193,14 +207,15 @@ bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* r
   const int64_t n = N > nrows ? N : nrows;
   rows_plan_kernel<<<bdg_cdiv(n, 256), 256, 0, st>>>(N, rows, nrows, tile_v, c->home_off,
                                                      c->home_ids, c->visit_off, c->visit_ids,
-                                                     c->visit_slot, c->part_order, c->item_off);
+                                                     c->visit_slot, c->part_order, c->item_off,
+                                                     c->eoff);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   return BDG_OK;
 }
 
 size_t bdg_csr_bytes(int64_t N, int m, int t, int W) {
-  return al((m + 1) * 4) * 3 + al(N * 4) + al(N * W * 8) + al(N * t * 4) + al(N * t) +
+  return al((m + 1) * 4) * 4 + al(N * 4) + al(N * W * 8) + al(N * t * 4) + al(N * t) +
          al(m * 4) + al((2 * (size_t)m + 4) * 4);
 }
 
@@ -212,6 +227,7 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   c->home_off = (int32_t*)p;   p += al((m + 1) * 4);
   c->visit_off = (int32_t*)p;  p += al((m + 1) * 4);
   c->item_off = (int32_t*)p;   p += al((m + 1) * 4);
+  c->eoff = (int32_t*)p;       p += al((m + 1) * 4);
   c->home_ids = (int32_t*)p;   p += al(N * 4);
   c->home_codes = (uint64_t*)p; p += al(N * W * 8);
   c->visit_ids = (int32_t*)p;  p += al(N * t * 4);
@@ -231,7 +247,7 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   BDG_CUDA_TRY(cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   plan_kernel<<<1, kScanThreads, smem, st>>>(m, tile_v, hcnt, vcnt, c->home_off, c->visit_off,
-                                             c->part_order, c->item_off);
+                                             c->part_order, c->item_off, c->eoff);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   scatter_kernel<<<g, 256, 0, st>>>(routes, N, t, m, hcnt, vcnt, c->home_ids, c->visit_ids,

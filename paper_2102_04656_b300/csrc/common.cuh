@@ -82,6 +82,7 @@ struct bdg_csr {
   int8_t* visit_slot;  // [N * t]  slot s of that partition in the visitor's route list
   int32_t* part_order; // [m]      partitions by decreasing |H_p| (then p)
   int32_t* item_off;   // [m + 1]  work items per partition in part_order order
+  int32_t* eoff;       // [m + 1]  row offsets of H_p in the 64-row-padded expanded operand
   int32_t* counters;   // [2 * m + 4] scratch counters
 };
 size_t bdg_csr_bytes(int64_t N, int m, int t, int W);
@@ -104,18 +105,32 @@ struct bdg_knn_args {
   int32_t* out_dist;      // [N][k]
   int32_t* item_counter;  // zeroed before launch
   int out_by_pos;         // t == 1: write row i of the output for the i-th visitor (not its id)
+  const int8_t* fixflag;  // [N * t] or NULL: only visit positions flagged 1 are computed
 };
+// knn_tc.cu: tensor-core (tcgen05, FP8 +-1) Reduce 1 for 256/512-bit codes and k <= 64.
+struct bdg_knn_tc_args {
+  bdg_knn_args base;
+  uint8_t* hexp;          // expanded home operand, eoff[m] rows x bits bytes
+  int8_t* fixflag;        // [N * t] zeroed before launch; rows that overflow are set to 1
+  int32_t* err;           // device error word (bounded waits that gave up)
+};
+bool bdg_knn_tc_supported(int W, int k);
+size_t bdg_knn_tc_hexp_bytes(int64_t N, int m, int W);
+bdg_status bdg_launch_knn_tc(const bdg_knn_tc_args& a, int W, cudaStream_t st);
 bdg_status bdg_launch_knn_popc(const bdg_knn_args& a, int W, cudaStream_t st);
 // merge.cu
 bdg_status bdg_launch_merge(const uint64_t* partial, int64_t N, int t, int k, int bits,
                             int32_t* ids, int32_t* dist, cudaStream_t st);
 bdg_status bdg_launch_fill_pad(int32_t* ids, int32_t* dist, int64_t count, int bits,
                                cudaStream_t st);
+bdg_status bdg_launch_gather_codes(const uint64_t* codes, int64_t N, const int32_t* ids, int64_t n,
+                                   int W, uint64_t* rows, cudaStream_t st);
 // search.cu / rerank.cu
 struct bdg_graph_view {
   const uint64_t* codes;
   const int32_t* ids;
   const int32_t* entry;
+  const uint64_t* entry_codes;  // [n_entry][W] codes of the entry sample, contiguous
   int64_t n;
   int32_t deg, bits, n_entry;
 };

@@ -1,0 +1,220 @@
+// gemm_tc.cu -- BF16 GEMM on the 5th-generation tensor cores for the MLP router:
+//   C[M, N] = epilogue( A[M, K] * B[N, K]^T ),  A and B row-major with K contiguous.
+// FP32 accumulation in tensor memory; epilogues: + bias[N], ReLU, multiply by
+// the ReLU derivative of a mask tensor (backward of a ReLU layer), column sums
+// of the result (bias gradients), output FP32 or BF16.
+//
+// One CTA per 128 x 128 output tile. Warps 4-7 stream 64-wide K slabs of A and
+// B into a 4-stage shared-memory ring with 16-byte cp.async (zero-filled past
+// the matrix edges) in the K-major no-swizzle core-matrix layout; one thread of
+// warp 8 issues tcgen05.mma kind::f16 (M = 128, N = 128, K = 16 per
+// instruction); warps 0-3 read the accumulator rows from TMEM and apply the
+// epilogue. Every mbarrier wait is bounded and reports through an error word.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "tc05.cuh"
+
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 64;   // tile; K slab = 64 bf16 = 128 bytes
+constexpr int kStages = 4;
+constexpr int kThreads = 288;                   // 0-3 epilogue, 4-7 producer, 8 MMA
+constexpr uint32_t kSlab = kBM * kBK * 2;       // 16 KB per operand per stage
+constexpr uint32_t kPolls = 1u << 20;
+
+struct GemmArgs {
+  const __nv_bfloat16* A;  // [M][K]
+  const __nv_bfloat16* B;  // [N][K]
+  int M, N, K;
+  const float* bias;       // [N] or NULL
+  const __nv_bfloat16* mask;  // [M][N] or NULL: multiply by (mask > 0)
+  int relu;
+  float* out_f32;          // [M][N] or NULL
+  __nv_bfloat16* out_bf16; // [M][N] or NULL
+  float* colsum;           // [N] or NULL: += column sums of the result (before rounding)
+  int32_t* err;
+};
+
+// byte offset of (row r, 16-byte chunk c) inside one 128 x 128 B slab (K-major, no swizzle)
+__device__ __forceinline__ uint32_t slab_off(int r, int c) {
+  return (uint32_t)((r >> 3) * 1024 + c * 128 + (r & 7) * 16);
+}
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kStages * 2 * kSlab);
+  uint64_t* full = bars;                // [kStages], 128 producer arrivals
+  uint64_t* empty = bars + kStages;     // [kStages], MMA commit
+  uint64_t* done = bars + 2 * kStages;  // accumulator ready
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int nk = (g.K + kBK - 1) / kBK;
+
+  if (warp == 0) tc05::tmem_alloc(tslot, kBN);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc05::mbar_init(&full[s], 128);
+      tc05::mbar_init(&empty[s], 1);
+    }
+    tc05::mbar_init(done, 1);
+    tc05::mbar_fence_init();
+  }
+  tc05::fence_before();
+  __syncthreads();
+  tc05::fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp >= 4 && warp < 8) {
+    // ---------------- producers: 128 threads, 2 x 1024 16-byte chunks per stage
+    const int p = tid - 128;
+    bool ok = true;
+    for (int j = 0; j < nk; ++j) {
+      const int s = j % kStages, use = j / kStages;
+      if (use > 0 && !tc05::mbar_wait(&empty[s], (use - 1) & 1, kPolls)) {
+        atomicExch(g.err, 11);
+        ok = false;
+        break;
+      }
+      const uint32_t sa = tc05::smem_u32(sm + s * 2 * kSlab), sb = sa + kSlab;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int x = p + 128 * q;                   // 0..1023
+        const int rr = x & 7, c = (x >> 3) & 7, grp = x >> 6;  // row-in-group fastest
+        const int r = grp * 8 + rr;
+        const int kk = j * kBK + c * 8;              // first element of the chunk
+        const int kv = max(0, min(8, g.K - kk));     // valid elements in this chunk
+        {
+          const int gr = m0 + r;
+          const bool in = gr < g.M && kv > 0;
+          const __nv_bfloat16* src = in ? g.A + (int64_t)gr * g.K + kk : g.A;
+          cp16(sa + slab_off(r, c), src, in ? kv * 2 : 0);
+        }
+        {
+          const int gr = n0 + r;
+          const bool in = gr < g.N && kv > 0;
+          const __nv_bfloat16* src = in ? g.B + (int64_t)gr * g.K + kk : g.B;
+          cp16(sb + slab_off(r, c), src, in ? kv * 2 : 0);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      if (j > 0) {  // the previous stage has landed: publish it to the tensor core
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        tc05::fence_proxy_async();
+        tc05::mbar_arrive(&full[(j - 1) % kStages]);
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (ok && nk > 0) {
+      tc05::fence_proxy_async();
+      tc05::mbar_arrive(&full[(nk - 1) % kStages]);
+    }
+  } else if (warp == 8) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t id = tc05::idesc(1u, 1u, kBM, kBN);  // BF16 x BF16 -> F32
+      bool ok = true;
+      for (int j = 0; j < nk; ++j) {
+        const int s = j % kStages;
+        if (!tc05::mbar_wait(&full[s], (j / kStages) & 1, kPolls)) {
+          atomicExch(g.err, 12);
+          ok = false;
+          break;
+        }
+        tc05::fence_after();
+        const uint32_t sa = tc05::smem_u32(sm + s * 2 * kSlab), sb = sa + kSlab;
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk) {  // 16 bf16 = 32 bytes = 2 core matrices
+          const uint64_t ad = tc05::sdesc(sa + kk * 256, 128, 1024);
+          const uint64_t bd = tc05::sdesc(sb + kk * 256, 128, 1024);
+          tc05::mma_f16(tmem, ad, bd, id, (j > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc05::commit(&empty[s]);
+      }
+      (void)ok;
+      tc05::commit(done);
+    }
+  } else {
+    // ---------------- epilogue: thread r owns output row m0 + r
+    const int r = tid;
+    const int row = m0 + r;
+    const bool ok = tc05::mbar_wait(done, 0, kPolls * 4);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) atomicExch(g.err, 13);
+    } else {
+      tc05::fence_after();
+      for (int c0 = 0; c0 < kBN; c0 += 32) {
+        uint32_t v[32];
+        tc05::ld32(tmem + ((uint32_t)(32 * warp) << 16) + c0, v);
+        tc05::wait_ld();
+        float f[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c0 + j;
+          float x = __uint_as_float(v[j]);
+          if (g.bias && col < g.N) x += g.bias[col];
+          if (g.relu) x = fmaxf(x, 0.f);
+          if (g.mask && row < g.M && col < g.N &&
+              !(__bfloat162float(g.mask[(int64_t)row * g.N + col]) > 0.f))
+            x = 0.f;
+          f[j] = (row < g.M && col < g.N) ? x : 0.f;
+        }
+        if (row < g.M) {
+          if (g.out_f32) {
+            for (int j = 0; j < 32; ++j)
+              if (n0 + c0 + j < g.N) g.out_f32[(int64_t)row * g.N + n0 + c0 + j] = f[j];
+          }
+          if (g.out_bf16) {
+            for (int j = 0; j < 32; ++j)
+              if (n0 + c0 + j < g.N)
+                g.out_bf16[(int64_t)row * g.N + n0 + c0 + j] = __float2bfloat16_rn(f[j]);
+          }
+        }
+        if (g.colsum) {  // column sums over this warp's 32 rows, one atomic per column
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float s = f[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0 && n0 + c0 + j < g.N) atomicAdd(&g.colsum[n0 + c0 + j], s);
+          }
+        }
+      }
+    }
+  }
+  tc05::fence_before();
+  __syncthreads();
+  if (warp == 0) tc05::tmem_dealloc(tmem, kBN);
+}
+
+}  // namespace
+
+size_t bdg_gemm_smem_bytes() { return (size_t)kStages * 2 * kSlab + 256; }
+
+// C = epilogue(A * B^T); see GemmArgs. K % 8 == 0 (16-byte rows).
+extern "C" bdg_status bdg_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                                    const float* bias, const void* mask, int32_t relu,
+                                    float* out_f32, void* out_bf16, float* colsum, int32_t* err,
+                                    void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (M <= 0 || N <= 0 || K <= 0 || (K & 7))
+    return bdg_set_error(BDG_EINVAL, "gemm: M=%d N=%d K=%d (K %% 8 == 0)", M, N, K);
+  GemmArgs g{(const __nv_bfloat16*)A, (const __nv_bfloat16*)B, M, N, K, bias,
+             (const __nv_bfloat16*)mask, relu, out_f32, (__nv_bfloat16*)out_bf16, colsum, err};
+  const size_t smem = bdg_gemm_smem_bytes();
+  BDG_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
+  bdg_prof_scope prof("gemm", st);
+  gemm_bf16_kernel<<<grid, kThreads, smem, st>>>(g);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}

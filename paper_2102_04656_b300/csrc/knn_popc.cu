@@ -149,18 +149,27 @@ knn_popc_kernel(bdg_knn_args a) {
     }
     const int p = c.part_order[lo];
     const int tile = item - c.item_off[lo];
-    const int v0 = c.visit_off[p] + tile * TV;
-    const int nv = min(TV, c.visit_off[p + 1] - v0);
     const int h0 = c.home_off[p];
     const int nh = c.home_off[p + 1] - h0;
+    // an item holds a.tile_v visitors, walked in sub-tiles of TV
+    for (int sub = 0; sub < a.tile_v / TV; ++sub) {
+    const int v0 = c.visit_off[p] + tile * a.tile_v + sub * TV;
+    const int nv = min(TV, c.visit_off[p + 1] - v0);
+    if (nv <= 0) break;
 
     for (int r = tid; r < TV; r += kThreads) {
-      s.vid[r] = r < nv ? c.visit_ids[v0 + r] : -1;
+      // fixup mode: only flagged visit positions are computed
+      const bool on = r < nv && (a.fixflag == nullptr || a.fixflag[v0 + r] != 0);
+      s.vid[r] = on ? c.visit_ids[v0 + r] : -1;
       s.vslot[r] = r < nv ? (int)c.visit_slot[v0 + r] : 0;
       s.cur[r] = 0;
       s.cnt[r] = 0;
       // idle rows and rows of invalid visitor ids accept nothing
       s.thr[r] = (r < nv && s.vid[r] >= 0) ? BDG_KEY_INF : 0ull;
+    }
+    if (a.fixflag != nullptr) {  // skip items without a flagged row
+      const int any = __syncthreads_or(tid < TV && s.vid[tid < TV ? tid : 0] >= 0);
+      if (!any) continue;
     }
     __syncthreads();
     uint64_t vc[RV][W];
@@ -217,7 +226,7 @@ knn_popc_kernel(bdg_knn_args a) {
       const int32_t id = s.vid[v];
       const int len = s.cur[v];
       const uint64_t* L = s.topk + (size_t)v * k;
-      if (id < 0 && !a.out_by_pos) continue;
+      if (id < 0 && (!a.out_by_pos || a.fixflag != nullptr)) continue;
       if (a.t == 1) {
         const int64_t row = a.out_by_pos ? (int64_t)(v0 - c.visit_off[p] + v) : (int64_t)id;
         for (int j = lane; j < k; j += 32) {
@@ -230,6 +239,8 @@ knn_popc_kernel(bdg_knn_args a) {
         for (int j = lane; j < k; j += 32) out[j] = j < len ? L[j] : pad;
       }
     }
+    __syncthreads();
+    }  // sub-tiles
   }
 }
 
@@ -252,7 +263,9 @@ bdg_status launch_w(const bdg_knn_args& a, cudaStream_t st) {
 
 }  // namespace
 
-int bdg_knn_tile_visitors(int W) { return W <= 8 ? 64 : 32; }
+// Work items hold 128 visitors for every code width (the tensor-core kernel's
+// tile); the popcount kernel walks an item in sub-tiles of its own size.
+int bdg_knn_tile_visitors(int W) { (void)W; return 128; }
 
 bdg_status bdg_launch_knn_popc(const bdg_knn_args& a, int W, cudaStream_t st) {
   if (a.k > 128) return bdg_set_error(BDG_EUNSUPPORTED, "k = %d > 128", a.k);

@@ -1,4 +1,5 @@
-// merge.cu -- Shuffle 2 + Reduce 2 of Section 3.2: every point's t partial
+// merge.cu -- (plus two small fill/gather utilities at the end)
+// Shuffle 2 + Reduce 2 of Section 3.2: every point's t partial
 // k-NN lists (one per routed partition, each sorted by (d, id), padded with
 // the pad key) become its final k-NN row.
 //
@@ -68,7 +69,27 @@ __global__ void fill_pad_kernel(int32_t* __restrict__ ids, int32_t* __restrict__
   dist[x] = bits + 1;
 }
 
+// rows[i] = codes[ids[i]]; ids outside [0, N) give a zero row
+__global__ void gather_codes_kernel(const uint64_t* __restrict__ codes, int64_t N,
+                                    const int32_t* __restrict__ ids, int64_t n, int W,
+                                    uint64_t* __restrict__ rows) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n * W) return;
+  const int64_t r = x / W;
+  const int32_t id = ids[r];
+  rows[x] = (id >= 0 && id < N) ? codes[(int64_t)id * W + (x - r * W)] : 0ull;
+}
+
 }  // namespace
+
+bdg_status bdg_launch_gather_codes(const uint64_t* codes, int64_t N, const int32_t* ids, int64_t n,
+                                   int W, uint64_t* rows, cudaStream_t st) {
+  if (n == 0) return BDG_OK;
+  gather_codes_kernel<<<bdg_cdiv(n * W, 256), 256, 0, st>>>(codes, N, ids, n, W, rows);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
 
 bdg_status bdg_launch_fill_pad(int32_t* ids, int32_t* dist, int64_t count, int bits,
                                cudaStream_t st) {

@@ -1,0 +1,422 @@
+// mlp.cu -- the learned partition router: a BF16 MLP d_in -> h1 -> h2 -> m with
+// FP32 accumulation, trained on the GPU with hand-written forward and backward
+// kernels, that picks the partitions a point is compared against. The paper
+// routes every point to its t nearest binary centres (Section 3.2); the router
+// keeps that nearest centre as the home and replaces the other t - 1 probes by
+// the partitions where the point's neighbours are predicted to live.
+//
+//   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2), z = h2 W3^T + b3
+//   loss = -(1/B) sum_i sum_p q_ip log softmax(z_i)_p,
+//   q_ip = #{neighbours j of i with home(j) = p} / kt
+// Gradients by the chain rule (all products on the tcgen05 BF16 GEMM of
+// gemm_tc.cu with fused bias / ReLU / ReLU-mask / bias-gradient epilogues),
+// Adam with FP32 master weights and BF16 working copies.
+//
+// BF16 is stored exactly where the network's tensors are stored: the inputs,
+// the weight copies, h1, h2, the logit gradient and the hidden-layer
+// gradients; bias gradients are summed from the FP32 values before rounding.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "common.cuh"
+
+
+struct bdg_router {
+  int d_in, h1, h2, m;
+  int64_t n_params;
+  float* w;          // fp32 master, packed W1 b1 W2 b2 W3 b3
+  float* grad;       // same layout: gradients of the last training step
+  float* adam_m;
+  float* adam_v;
+  __nv_bfloat16* wb; // bf16 copies of W1, W2, W3 (packed, no biases)
+  int64_t step;
+  int32_t* err;
+  float* loss;       // device scalar: loss of the last step
+  // training workspace for batches up to cap_b rows
+  int cap_b;
+  void* ws;
+  size_t ws_bytes;
+};
+
+namespace {
+
+inline size_t al(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct Offs {
+  int64_t W1, b1, W2, b2, W3, b3, n;
+};
+Offs param_offsets(int d_in, int h1, int h2, int m) {
+  Offs o;
+  o.W1 = 0;
+  o.b1 = o.W1 + (int64_t)h1 * d_in;
+  o.W2 = o.b1 + h1;
+  o.b2 = o.W2 + (int64_t)h2 * h1;
+  o.W3 = o.b2 + h2;
+  o.b3 = o.W3 + (int64_t)m * h2;
+  o.n = o.b3 + m;
+  return o;
+}
+
+__global__ void f32_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b,
+                            int64_t n) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < n) b[x] = __float2bfloat16_rn(a[x]);
+}
+
+// out[c][r] = in[r][c] for a rows x cols bf16 matrix (32 x 32 tiles)
+__global__ void transpose_bf16(const __nv_bfloat16* __restrict__ in, int rows, int cols,
+                               __nv_bfloat16* __restrict__ out) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = in[(int64_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(int64_t)c * rows + r] = t[threadIdx.x][i];
+  }
+}
+
+// Softmax cross-entropy against the neighbour-partition targets, one block per
+// row: dz = (softmax(z) - q) / B as FP32 and BF16, loss accumulated.
+__global__ void __launch_bounds__(256)
+softmax_ce(const float* __restrict__ z, int m, int B, const int32_t* __restrict__ labels, int kt,
+           float* __restrict__ dz32, __nv_bfloat16* __restrict__ dz16, float* __restrict__ loss) {
+  const int i = blockIdx.x;
+  const float* zr = z + (int64_t)i * m;
+  __shared__ float red[32];
+  __shared__ float s_max, s_sum;
+  float mx = -INFINITY;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) mx = fmaxf(mx, zr[p]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, red[w]);
+    s_max = v;
+  }
+  __syncthreads();
+  const float zmax = s_max;
+  float sum = 0.f;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) sum += expf(zr[p] - zmax);
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    s_sum = v;
+  }
+  __syncthreads();
+  const float lse = zmax + logf(s_sum);
+  const float inv_b = 1.f / (float)B, inv_k = 1.f / (float)kt;
+  const int32_t* lab = labels + (int64_t)i * kt;
+  float* dzr = dz32 + (int64_t)i * m;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) dzr[p] = expf(zr[p] - lse) * inv_b;
+  __syncthreads();
+  for (int j = threadIdx.x; j < kt; j += blockDim.x) {
+    const int32_t p = lab[j];
+    if (p >= 0 && p < m) atomicAdd(&dzr[p], -inv_k * inv_b);  // - q_ip / B
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < m; p += blockDim.x)
+    dz16[(int64_t)i * m + p] = __float2bfloat16_rn(dzr[p]);
+  if (threadIdx.x == 0) {
+    float l = 0.f;
+    for (int j = 0; j < kt; ++j)
+      if (lab[j] >= 0 && lab[j] < m) l -= inv_k * (zr[lab[j]] - lse);
+    atomicAdd(loss, l * inv_b);
+  }
+}
+
+__global__ void colsum_f32(const float* __restrict__ a, int rows, int cols,
+                           float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.f;
+  for (int r = 0; r < rows; ++r) s += a[(int64_t)r * cols + c];
+  out[c] = s;
+}
+
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
+                            float* __restrict__ mom, float* __restrict__ vel, int64_t n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const float gx = g[x];
+  const float mm = b1 * mom[x] + (1.f - b1) * gx;
+  const float vv = b2 * vel[x] + (1.f - b2) * gx * gx;
+  mom[x] = mm;
+  vel[x] = vv;
+  w[x] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+// Partition choice per row: slot 0 = the given home, then the P - 1 best other
+// partitions by (-logit, p). One warp per row; each lane keeps its best P - 1
+// candidates and the warp pops the best across lanes P - 1 times.
+constexpr int kMaxP = 16;
+__device__ __forceinline__ bool better(float a, int pa, float b, int pb) {
+  return a > b || (a == b && pa < pb);
+}
+__global__ void topp_kernel(const float* __restrict__ z, int rows, int m,
+                            const int32_t* __restrict__ home, int P, int32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= rows) return;
+  const float* zr = z + (int64_t)i * m;
+  const int hm = home[i];
+  const int need = P - 1;
+  float bv[kMaxP];
+  int bp[kMaxP];
+#pragma unroll
+  for (int s = 0; s < kMaxP; ++s) { bv[s] = -INFINITY; bp[s] = 0x7fffffff; }
+  float wv = -INFINITY;  // the lane's current worst kept entry (slot need - 1)
+  int wpp = 0x7fffffff;
+  for (int p = lane; p < m && need > 0; p += 32) {
+    if (p == hm) continue;
+    const float v = zr[p];
+    if (!better(v, p, wv, wpp)) continue;
+#pragma unroll
+    for (int s = kMaxP - 1; s >= 0; --s) {
+      if (s < need && better(v, p, bv[s], bp[s])) {
+        const int sp = s > 0 ? s - 1 : 0;
+        if (s > 0 && better(v, p, bv[sp], bp[sp])) { bv[s] = bv[sp]; bp[s] = bp[sp]; }
+        else { bv[s] = v; bp[s] = p; }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kMaxP; ++s)
+      if (s == need - 1) { wv = bv[s]; wpp = bp[s]; }
+  }
+  if (lane == 0) out[(int64_t)i * P] = hm;
+  int head = 0;  // next unused entry of this lane's list
+  for (int r = 0; r < need; ++r) {
+    float v = -INFINITY;
+    int p = 0x7fffffff;
+#pragma unroll
+    for (int s = 0; s < kMaxP; ++s)
+      if (s == head) { v = bv[s]; p = bp[s]; }
+    float bvw = v;
+    int bpw = p;
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bvw, o);
+      const int op = __shfl_xor_sync(0xffffffffu, bpw, o);
+      if (better(ov, op, bvw, bpw)) { bvw = ov; bpw = op; }
+    }
+    if (p == bpw) ++head;
+    if (lane == 0) out[(int64_t)i * P + 1 + r] = bpw;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+bdg_status bdg_router_create(int32_t d_in, int32_t h1, int32_t h2, int32_t m,
+                             const float* init_params, int32_t max_batch, bdg_router** out) {
+  if (!out) return bdg_set_error(BDG_EINVAL, "router_create: out is NULL");
+  *out = nullptr;
+  if (d_in < 8 || h1 < 8 || h2 < 8 || m < 2 || (d_in & 7) || (h1 & 7) || (h2 & 7) || (m & 7) ||
+      max_batch < 8 || (max_batch & 7) || !init_params)
+    return bdg_set_error(BDG_EINVAL,
+                         "router_create: sizes must be multiples of 8 (d_in=%d h1=%d h2=%d m=%d "
+                         "max_batch=%d) and init_params given", d_in, h1, h2, m, max_batch);
+  const Offs o = param_offsets(d_in, h1, h2, m);
+  bdg_router* r = new bdg_router();
+  r->d_in = d_in; r->h1 = h1; r->h2 = h2; r->m = m; r->n_params = o.n; r->cap_b = max_batch;
+  const int64_t nw = (int64_t)h1 * d_in + (int64_t)h2 * h1 + (int64_t)m * h2;
+  const int64_t B = max_batch;
+  // workspace: h1, h2 (bf16), z (f32), dz32, dz16, transposes, dh1, dh2, label copy
+  r->ws_bytes = al(B * h1 * 2) + al(B * h2 * 2) + al(B * m * 4) * 2 + al(B * m * 2) +
+                al(B * m * 2) /* dzT */ + al(B * h2 * 2) * 2 /* h2T, dh2 */ +
+                al(B * h1 * 2) * 2 /* h1T, dh1 */ + al(B * d_in * 2) /* xT */ +
+                al(B * h2 * 2) /* dh2T */ + al(B * h1 * 2) /* dh1T */ +
+                al((int64_t)h2 * m * 2) /* W3T */ + al((int64_t)h1 * h2 * 2) /* W2T */;
+  cudaError_t e = cudaSuccess;
+  e = e == cudaSuccess ? cudaMalloc(&r->w, o.n * 4) : e;
+  e = e == cudaSuccess ? cudaMalloc(&r->grad, o.n * 4) : e;
+  e = e == cudaSuccess ? cudaMalloc(&r->adam_m, o.n * 4) : e;
+  e = e == cudaSuccess ? cudaMalloc(&r->adam_v, o.n * 4) : e;
+  e = e == cudaSuccess ? cudaMalloc(&r->wb, nw * 2) : e;
+  e = e == cudaSuccess ? cudaMalloc(&r->err, 64) : e;
+  e = e == cudaSuccess ? cudaMalloc(&r->loss, 64) : e;
+  e = e == cudaSuccess ? cudaMalloc(&r->ws, r->ws_bytes) : e;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    bdg_router_free(r);
+    return bdg_set_error(BDG_ENOMEM, "router_create: device allocation failed");
+  }
+  cudaMemcpy(r->w, init_params, o.n * 4, cudaMemcpyDeviceToDevice);
+  cudaMemset(r->grad, 0, o.n * 4);
+  cudaMemset(r->adam_m, 0, o.n * 4);
+  cudaMemset(r->adam_v, 0, o.n * 4);
+  cudaMemset(r->err, 0, 64);
+  cudaMemset(r->loss, 0, 64);
+  // bf16 working copies
+  f32_to_bf16<<<bdg_cdiv((int64_t)h1 * d_in, 256), 256>>>(r->w + o.W1, r->wb, (int64_t)h1 * d_in);
+  f32_to_bf16<<<bdg_cdiv((int64_t)h2 * h1, 256), 256>>>(r->w + o.W2, r->wb + (int64_t)h1 * d_in,
+                                                         (int64_t)h2 * h1);
+  f32_to_bf16<<<bdg_cdiv((int64_t)m * h2, 256), 256>>>(
+      r->w + o.W3, r->wb + (int64_t)h1 * d_in + (int64_t)h2 * h1, (int64_t)m * h2);
+  bdg_note_launch(3);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    bdg_router_free(r);
+    return bdg_set_error(BDG_ECUDA, "router_create: initialisation failed");
+  }
+  *out = r;
+  return BDG_OK;
+}
+
+void bdg_router_free(bdg_router* r) {
+  if (!r) return;
+  cudaFree(r->w); cudaFree(r->grad); cudaFree(r->adam_m); cudaFree(r->adam_v);
+  cudaFree(r->wb); cudaFree(r->err); cudaFree(r->loss); cudaFree(r->ws);
+  delete r;
+}
+
+bdg_status bdg_router_info(const bdg_router* r, float** params, float** grads, int64_t* n_params,
+                           float** loss, int32_t** err) {
+  if (!r) return bdg_set_error(BDG_EINVAL, "router is NULL");
+  if (params) *params = r->w;
+  if (grads) *grads = r->grad;
+  if (n_params) *n_params = r->n_params;
+  if (loss) *loss = r->loss;
+  if (err) *err = r->err;
+  return BDG_OK;
+}
+
+// Forward pass into caller-provided buffers (h1, h2 bf16 may be NULL -> workspace).
+static bdg_status router_fwd(bdg_router* r, const void* x, int B, float* z, void* h1b, void* h2b,
+                             cudaStream_t st) {
+  const Offs o = param_offsets(r->d_in, r->h1, r->h2, r->m);
+  const __nv_bfloat16* W1 = r->wb;
+  const __nv_bfloat16* W2 = W1 + (int64_t)r->h1 * r->d_in;
+  const __nv_bfloat16* W3 = W2 + (int64_t)r->h2 * r->h1;
+  BDG_TRY(bdg_gemm_bf16(x, W1, B, r->h1, r->d_in, r->w + o.b1, nullptr, 1, nullptr, h1b, nullptr,
+                        r->err, (void*)st));
+  BDG_TRY(bdg_gemm_bf16(h1b, W2, B, r->h2, r->h1, r->w + o.b2, nullptr, 1, nullptr, h2b, nullptr,
+                        r->err, (void*)st));
+  BDG_TRY(bdg_gemm_bf16(h2b, W3, B, r->m, r->h2, r->w + o.b3, nullptr, 0, z, nullptr, nullptr,
+                        r->err, (void*)st));
+  return BDG_OK;
+}
+
+bdg_status bdg_router_forward(bdg_router* r, const void* x, int32_t B, float* logits,
+                              void* stream) {
+  if (!r || !x || !logits || B < 1 || B > r->cap_b)
+    return bdg_set_error(BDG_EINVAL, "router_forward: B = %d (1..%d)", B, r ? r->cap_b : 0);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* p = (char*)r->ws;
+  void* h1b = p; p += al((int64_t)r->cap_b * r->h1 * 2);
+  void* h2b = p;
+  return router_fwd(r, x, B, logits, h1b, h2b, st);
+}
+
+bdg_status bdg_router_train_step(bdg_router* r, const void* x, const int32_t* labels, int32_t kt,
+                                 int32_t B, float lr, int32_t apply_update, void* stream) {
+  if (!r || !x || !labels || B < 8 || B > r->cap_b || (B & 7) || kt < 1)
+    return bdg_set_error(BDG_EINVAL, "router_train_step: B = %d (8..%d, multiple of 8), kt = %d",
+                         B, r ? r->cap_b : 0, kt);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = r->d_in, H1 = r->h1, H2 = r->h2, m = r->m;
+  const int64_t cap = r->cap_b;
+  const Offs o = param_offsets(d, H1, H2, m);
+  char* p = (char*)r->ws;
+  __nv_bfloat16* h1b = (__nv_bfloat16*)p; p += al(cap * H1 * 2);
+  __nv_bfloat16* h2b = (__nv_bfloat16*)p; p += al(cap * H2 * 2);
+  float* z = (float*)p;                   p += al(cap * m * 4);
+  float* dz32 = (float*)p;                p += al(cap * m * 4);
+  __nv_bfloat16* dz16 = (__nv_bfloat16*)p; p += al(cap * m * 2);
+  __nv_bfloat16* dzT = (__nv_bfloat16*)p;  p += al(cap * m * 2);
+  __nv_bfloat16* h2T = (__nv_bfloat16*)p;  p += al(cap * H2 * 2);
+  __nv_bfloat16* dh2 = (__nv_bfloat16*)p;  p += al(cap * H2 * 2);
+  __nv_bfloat16* h1T = (__nv_bfloat16*)p;  p += al(cap * H1 * 2);
+  __nv_bfloat16* dh1 = (__nv_bfloat16*)p;  p += al(cap * H1 * 2);
+  __nv_bfloat16* xT = (__nv_bfloat16*)p;   p += al(cap * d * 2);
+  __nv_bfloat16* dh2T = (__nv_bfloat16*)p; p += al(cap * H2 * 2);
+  __nv_bfloat16* dh1T = (__nv_bfloat16*)p; p += al(cap * H1 * 2);
+  __nv_bfloat16* W3T = (__nv_bfloat16*)p;  p += al((int64_t)H2 * m * 2);
+  __nv_bfloat16* W2T = (__nv_bfloat16*)p;
+  const __nv_bfloat16* W2 = r->wb + (int64_t)H1 * d;
+  const __nv_bfloat16* W3 = W2 + (int64_t)H2 * H1;
+  auto T = [&](const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    transpose_bf16<<<grid, block, 0, st>>>(in, rows, cols, out);
+    bdg_note_launch();
+  };
+  BDG_CUDA_TRY(cudaMemsetAsync(r->grad, 0, r->n_params * 4, st));
+  BDG_CUDA_TRY(cudaMemsetAsync(r->loss, 0, 4, st));
+  // forward
+  BDG_TRY(router_fwd(r, x, B, z, h1b, h2b, st));
+  // loss and logit gradient
+  softmax_ce<<<B, 256, 0, st>>>(z, m, B, labels, kt, dz32, dz16, r->loss);
+  bdg_note_launch();
+  colsum_f32<<<bdg_cdiv(m, 256), 256, 0, st>>>(dz32, B, m, r->grad + o.b3);
+  bdg_note_launch();
+  // layer 3: dW3 = dz^T h2, dh2 = (dz W3) * [h2 > 0], db2 = colsum(dh2)
+  T(dz16, B, m, dzT);
+  T(h2b, B, H2, h2T);
+  T(W3, m, H2, W3T);
+  BDG_TRY(bdg_gemm_bf16(dzT, h2T, m, H2, B, nullptr, nullptr, 0, r->grad + o.W3, nullptr, nullptr,
+                        r->err, (void*)st));
+  BDG_TRY(bdg_gemm_bf16(dz16, W3T, B, H2, m, nullptr, h2b, 0, nullptr, dh2, r->grad + o.b2,
+                        r->err, (void*)st));
+  // layer 2: dW2 = dh2^T h1, dh1 = (dh2 W2) * [h1 > 0], db1 = colsum(dh1)
+  T(dh2, B, H2, dh2T);
+  T(h1b, B, H1, h1T);
+  T(W2, H2, H1, W2T);
+  BDG_TRY(bdg_gemm_bf16(dh2T, h1T, H2, H1, B, nullptr, nullptr, 0, r->grad + o.W2, nullptr,
+                        nullptr, r->err, (void*)st));
+  BDG_TRY(bdg_gemm_bf16(dh2, W2T, B, H1, H2, nullptr, h1b, 0, nullptr, dh1, r->grad + o.b1,
+                        r->err, (void*)st));
+  // layer 1: dW1 = dh1^T x
+  T(dh1, B, H1, dh1T);
+  T((const __nv_bfloat16*)x, B, d, xT);
+  BDG_TRY(bdg_gemm_bf16(dh1T, xT, H1, d, B, nullptr, nullptr, 0, r->grad + o.W1, nullptr, nullptr,
+                        r->err, (void*)st));
+  if (apply_update) {
+    r->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)r->step), c2 = 1.f - powf(b2, (float)r->step);
+    adam_kernel<<<bdg_cdiv(r->n_params, 256), 256, 0, st>>>(r->w, r->grad, r->adam_m, r->adam_v,
+                                                            r->n_params, lr, b1, b2, 1e-8f, c1, c2);
+    bdg_note_launch();
+    f32_to_bf16<<<bdg_cdiv((int64_t)H1 * d, 256), 256, 0, st>>>(r->w + o.W1, r->wb,
+                                                                (int64_t)H1 * d);
+    f32_to_bf16<<<bdg_cdiv((int64_t)H2 * H1, 256), 256, 0, st>>>(
+        r->w + o.W2, r->wb + (int64_t)H1 * d, (int64_t)H2 * H1);
+    f32_to_bf16<<<bdg_cdiv((int64_t)m * H2, 256), 256, 0, st>>>(
+        r->w + o.W3, r->wb + (int64_t)H1 * d + (int64_t)H2 * H1, (int64_t)m * H2);
+    bdg_note_launch(3);
+  }
+  BDG_CUDA_TRY(cudaGetLastError());
+  return BDG_OK;
+}
+
+bdg_status bdg_router_route(bdg_router* r, const void* x, int64_t N, const int32_t* home,
+                            int32_t P, int32_t* routes, void* stream) {
+  if (!r || !x || !home || !routes || N < 0 || P < 1 || P > kMaxP + 1 || P > r->m)
+    return bdg_set_error(BDG_EINVAL, "router_route: N = %lld, P = %d (1..%d)", (long long)N, P,
+                         kMaxP + 1);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t cap = r->cap_b;
+  char* p = (char*)r->ws;
+  void* h1b = p; p += al(cap * r->h1 * 2);
+  void* h2b = p; p += al(cap * r->h2 * 2);
+  float* z = (float*)p;
+  for (int64_t s = 0; s < N; s += cap) {
+    const int B = (int)((N - s) < cap ? (N - s) : cap);
+    BDG_TRY(router_fwd(r, (const __nv_bfloat16*)x + s * r->d_in, B, z, h1b, h2b, st));
+    topp_kernel<<<bdg_cdiv(B, 8), 256, 0, st>>>(z, B, r->m, home + s, P, routes + s * P);
+    BDG_CUDA_TRY(cudaGetLastError());
+    bdg_note_launch();
+  }
+  return BDG_OK;
+}
+
+}  // extern "C"

@@ -88,7 +88,7 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
       if (e < 0 || e >= g.n) continue;  // ids outside the graph are ignored
       uint32_t d = 0;
 #pragma unroll
-      for (int w = 0; w < W; ++w) d += __popcll(y[w] ^ g.codes[(int64_t)e * W + w]);
+      for (int w = 0; w < W; ++w) d += __popcll(y[w] ^ g.entry_codes[(int64_t)s * W + w]);
       best = umin64(best, bdg_key(d, (uint32_t)e));
     }
 #pragma unroll

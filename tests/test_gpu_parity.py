@@ -35,29 +35,43 @@ def _entry(n, s, seed):
     return datagen.sample_ids(n, min(n, s), seed).astype(np.int32)
 
 
-def _build_exact(bdg, codes_t, k, seed=5):
+def _build_exact(bdg, codes_t, k, seed=5, kernel="auto"):
     n = codes_t.shape[0]
     entry = torch.from_numpy(_entry(n, 64, seed)).cuda()
-    return bdg.build_graph(codes_t, k, m=1, t=1, entry=entry), entry
+    return bdg.build_graph(codes_t, k, m=1, t=1, entry=entry, kernel=kernel), entry
+
+
+def _tc_ok(bits, k):
+    return bits in (256, 512) and k <= 64
+
+
+KERNELS = ["popc", "tc"]
 
 
 # ------------------------------------------------------------------ exact kNN
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("bits,n,k", [(64, 1000, 8), (128, 777, 16), (256, 3001, 32),
-                                      (512, 1500, 64), (1024, 700, 128), (256, 130, 100)])
-def test_exact_knn_bit_exact(bdg, bits, n, k):
+                                      (512, 1500, 64), (1024, 700, 128), (256, 130, 100),
+                                      (512, 4097, 1), (256, 2000, 63)])
+def test_exact_knn_bit_exact(bdg, bits, n, k, kernel):
+    if kernel == "tc" and not _tc_ok(bits, k):
+        pytest.skip("tensor path: 256/512-bit codes and k <= 64")
     c = datagen.random_codes(n, bits, seed=bits + n)
     c[7] = c[3]  # duplicates: d = 0 ties resolved by id
     c[n - 1] = c[3]
-    g, _ = _build_exact(bdg, c.cuda(), k)
+    g, _ = _build_exact(bdg, c.cuda(), k, kernel=kernel)
     torch.cuda.synchronize()
     ids_o, dist_o = oracle.knn_exact(_np(c), k)
     assert np.array_equal(g.ids.cpu().numpy(), ids_o)
     assert np.array_equal(g.dists.cpu().numpy(), dist_o)
 
 
-def test_exact_knn_all_equal_codes(bdg):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_exact_knn_all_equal_codes(bdg, kernel):
+    # every pair ties at d = 0: the tensor path overflows its candidate lists and
+    # hands every row to the popcount recomputation
     c = torch.zeros(300, 4, dtype=torch.int64)
-    g, _ = _build_exact(bdg, c.cuda(), 32)
+    g, _ = _build_exact(bdg, c.cuda(), 32, kernel=kernel)
     ids_o, dist_o = oracle.knn_exact(_np(c), 32)
     assert np.array_equal(g.ids.cpu().numpy(), ids_o)
     assert np.array_equal(g.dists.cpu().numpy(), dist_o)
@@ -71,11 +85,12 @@ def test_exact_knn_small_n_pads(bdg):
     assert np.array_equal(g.dists.cpu().numpy(), dist_o)
 
 
-def test_exact_knn_mixture_20k_256b_k32(bdg):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_exact_knn_mixture_20k_256b_k32(bdg, kernel):
     """The exact brute-force workload: N = 20k, 128-d mixture -> 256-bit, k = 32."""
     w = datagen.WORKLOADS["exact_20k_256b"]
     c = datagen.make_codes(w["spec"])
-    g, _ = _build_exact(bdg, c.cuda(), w["k"])
+    g, _ = _build_exact(bdg, c.cuda(), w["k"], kernel=kernel)
     ids_o, dist_o = oracle.knn_exact(_np(c), w["k"])
     assert np.array_equal(g.ids.cpu().numpy(), ids_o)
     assert np.array_equal(g.dists.cpu().numpy(), dist_o)
@@ -106,15 +121,18 @@ def test_route_bit_exact(bdg, bits, t):
 
 
 # ------------------------------------------------------------------ partitioned build
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("bits,n,m,t,k", [(512, 20000, 16, 3, 64), (256, 9000, 40, 5, 32),
                                           (256, 3000, 8, 8, 16), (128, 5000, 64, 2, 8)])
-def test_partitioned_build_bit_exact(bdg, bits, n, m, t, k):
+def test_partitioned_build_bit_exact(bdg, bits, n, m, t, k, kernel):
+    if kernel == "tc" and not _tc_ok(bits, k):
+        pytest.skip("tensor path: 256/512-bit codes and k <= 64")
     spec = datagen.MixtureSpec(n, 64, 48, bits, seed=n + m)
     c = datagen.make_codes(spec)
     sample = datagen.sample_ids(n, min(n, 64 * m), seed=3)
     entry = torch.from_numpy(_entry(n, 64, 4)).cuda()
     g = bdg.build_graph(c.cuda(), k, m=m, t=t, bk_sample=torch.from_numpy(sample).cuda(),
-                        bk_iters=8, entry=entry)
+                        bk_iters=8, entry=entry, kernel=kernel)
     cent_o, _, _ = oracle.bkmeans(_np(c), sample, m, 8)
     r_o, _ = oracle.route(_np(c), cent_o, t)
     ids_o, dist_o = oracle.knn_partitioned(_np(c), r_o, k)
@@ -122,7 +140,8 @@ def test_partitioned_build_bit_exact(bdg, bits, n, m, t, k):
     assert np.array_equal(g.dists.cpu().numpy(), dist_o)
 
 
-def test_partitioned_with_given_routes_and_empty_home(bdg):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_partitioned_with_given_routes_and_empty_home(bdg, kernel):
     # partition 3 is probed by visitors but is nobody's home: its lists are pads
     n, bits, k = 2000, 256, 16
     c = datagen.random_codes(n, bits, seed=12)
@@ -131,7 +150,7 @@ def test_partitioned_with_given_routes_and_empty_home(bdg):
     routes = np.stack([home, np.full(n, 3), (home + 1) % 3], 1).astype(np.int32)
     entry = torch.from_numpy(_entry(n, 32, 2)).cuda()
     g = bdg.build_graph(c.cuda(), k, m=4, t=3, routes=torch.from_numpy(routes).cuda(),
-                        entry=entry)
+                        entry=entry, kernel=kernel)
     ids_o, dist_o = oracle.knn_partitioned(_np(c), routes, k)
     assert np.array_equal(g.ids.cpu().numpy(), ids_o)
     assert np.array_equal(g.dists.cpu().numpy(), dist_o)
@@ -162,6 +181,19 @@ def test_partitioned_2m_512b_sampled_rows(bdg):
     ids_o, dist_o = oracle.knn_partitioned(c, r_o, k, rows)
     assert np.array_equal(g.ids[torch.from_numpy(rows).cuda()].cpu().numpy(), ids_o)
     assert np.array_equal(g.dists[torch.from_numpy(rows).cuda()].cpu().numpy(), dist_o)
+
+
+@pytest.mark.parametrize("bits,k", [(512, 64), (256, 32), (128, 16), (1024, 100)])
+def test_knn_rows_bit_exact(bdg, bits, k):
+    c = datagen.random_codes(6000, bits, seed=bits * 3)
+    c[100] = c[4000]
+    rows = np.array([0, 100, 4000, 5999, 17, 17, 6001, -3] + list(range(200, 330)), np.int32)
+    ids, dist = bdg.knn_rows(c.cuda(), torch.from_numpy(rows).cuda(), k)
+    valid = (rows >= 0) & (rows < 6000)
+    ids_o, dist_o = oracle.knn_exact(_np(c), k, rows[valid].astype(np.int64))
+    assert np.array_equal(ids.cpu().numpy()[valid], ids_o)
+    assert np.array_equal(dist.cpu().numpy()[valid], dist_o)
+    assert (ids.cpu().numpy()[~valid] == -1).all()
 
 
 # ------------------------------------------------------------------ search

@@ -1,0 +1,156 @@
+"""GPU parity of the learned router: the tcgen05 BF16 GEMM against float64
+matrix products, and the network's forward pass, loss, gradients, Adam step and
+top-P routing against the float64 oracle (oracle.mlp) on bf16-rounded inputs.
+
+Tolerances: the GPU accumulates in FP32 and rounds hidden activations to BF16
+where the oracle rounds its float64 values, so an element near a BF16 rounding
+boundary may differ by one BF16 ulp (2^-8 relative). Logits: max error <= 1e-2
+of the largest logit; gradients: relative Frobenius error <= 2e-2 per tensor;
+GEMM outputs: 1e-5 relative to the output's scale (FP32 accumulation)."""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bdg():
+    from paper_2102_04656_b300 import build as b
+    b.build()
+    import paper_2102_04656_b300 as m
+    m.lib()
+    return m
+
+
+def _bf16(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 136), (7, 1000, 512),
+                                   (1000, 40, 10000), (129, 257, 8)])
+def test_gemm_matches_float64(bdg, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = _bf16(rng.standard_normal((M, K)))
+    B = _bf16(rng.standard_normal((N, K)))
+    C, err = bdg.gemm_bf16(A.cuda(), B.cuda())
+    ref = A.double().numpy() @ B.double().numpy().T
+    scale = np.abs(ref).max() + 1e-30
+    assert int(err.item()) == 0
+    assert np.abs(C.cpu().numpy() - ref).max() <= 1e-5 * scale * max(1.0, np.sqrt(K / 64))
+
+
+def test_gemm_epilogues(bdg):
+    rng = np.random.default_rng(5)
+    M, N, K = 200, 150, 96
+    A = _bf16(rng.standard_normal((M, K)))
+    B = _bf16(rng.standard_normal((N, K)))
+    bias = torch.from_numpy(rng.standard_normal(N).astype(np.float32))
+    mask = _bf16(rng.standard_normal((M, N)))
+    ref = A.double().numpy() @ B.double().numpy().T
+    # bias + relu, bf16 out
+    Cb, _ = bdg.gemm_bf16(A.cuda(), B.cuda(), bias=bias.cuda(), relu=True, out="bf16")
+    want = np.maximum(ref + bias.double().numpy(), 0)
+    assert np.allclose(Cb.float().cpu().numpy(), want, rtol=2 ** -7, atol=1e-4)
+    # mask (relu derivative) + column sums
+    cs = torch.zeros(N, dtype=torch.float32, device="cuda")
+    Cm, _ = bdg.gemm_bf16(A.cuda(), B.cuda(), mask=mask.cuda(), colsum=cs)
+    wantm = ref * (mask.double().numpy() > 0)
+    assert np.abs(Cm.cpu().numpy() - wantm).max() <= 1e-5 * np.abs(ref).max()
+    assert np.allclose(cs.cpu().numpy(), wantm.sum(0), rtol=1e-4, atol=1e-3)
+
+
+def _net(seed, d=128, h1=64, h2=64, m=40):
+    flat = datagen.router_init(d, h1, h2, m, seed)
+    o = np.cumsum([0, h1 * d, h1, h2 * h1, h2, m * h2, m])
+    names = ["W1", "b1", "W2", "b2", "W3", "b3"]
+    shapes = [(h1, d), (h1,), (h2, h1), (h2,), (m, h2), (m,)]
+    params = {n: flat[o[i]:o[i + 1]].reshape(s).astype(np.float64)
+              for i, (n, s) in enumerate(zip(names, shapes))}
+    return flat, params
+
+
+def _batch(B, d, m, kt, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((B, d)).astype(np.float32)
+    lab = rng.integers(-1, m, (B, kt)).astype(np.int32)  # -1 entries are ignored
+    return x, lab
+
+
+def _q(lab, m):
+    B, kt = lab.shape
+    q = np.zeros((B, m))
+    for i in range(B):
+        for j in lab[i]:
+            if j >= 0:
+                q[i, j] += 1.0 / kt
+    return q
+
+
+def test_router_forward_loss_and_gradients(bdg):
+    d, h1, h2, m, B, kt = 128, 64, 64, 40, 256, 16
+    flat, params = _net(11, d, h1, h2, m)
+    r = bdg.Router(torch.from_numpy(flat).cuda(), d, h1, h2, m, max_batch=512)
+    x, lab = _batch(B, d, m, kt, 3)
+    xb = _bf16(x).cuda()
+    z = r.forward(xb).cpu().numpy()
+    z_o, _ = omlp.forward(params, x, bf16=True)
+    assert np.abs(z - z_o).max() <= 1e-2 * np.abs(z_o).max()
+    r.train_step(xb, torch.from_numpy(lab).cuda(), lr=0.0, apply_update=False)
+    torch.cuda.synchronize()
+    loss_o, g_o, _ = omlp.loss_and_grads(params, x, _q(lab, m), bf16=True)
+    assert abs(float(r.loss.item()) - loss_o) <= 1e-3 * abs(loss_o)
+    g = r.unpack(r.grads.cpu())
+    for name in ["W1", "b1", "W2", "b2", "W3", "b3"]:
+        a, b_ = g[name].double().numpy(), g_o[name]
+        rel = np.linalg.norm(a - b_) / (np.linalg.norm(b_) + 1e-30)
+        assert rel <= 2e-2, (name, rel)
+    assert int(r.err.item()) == 0
+
+
+def test_router_adam_step_and_training_lowers_loss(bdg):
+    d, h1, h2, m, B, kt = 64, 32, 32, 24, 128, 8
+    flat, params = _net(12, d, h1, h2, m)
+    r = bdg.Router(torch.from_numpy(flat).cuda(), d, h1, h2, m, max_batch=128)
+    x, lab = _batch(B, d, m, kt, 4)
+    xb, lb = _bf16(x).cuda(), torch.from_numpy(lab).cuda()
+    r.train_step(xb, lb, lr=1e-3, apply_update=True)
+    torch.cuda.synchronize()
+    _, g_o, _ = omlp.loss_and_grads(params, x, _q(lab, m), bf16=True)
+    new_o, _ = omlp.adam(params, g_o, {}, lr=1e-3)
+    new = r.unpack(r.params.cpu())
+    for name in new_o:
+        # one Adam step moves each weight by about lr * sign(g); compare the moves
+        step_gpu = new[name].double().numpy() - params[name]
+        step_o = new_o[name] - params[name]
+        agree = np.mean(np.abs(step_gpu - step_o) <= 2e-4 + 0.05 * np.abs(step_o))
+        assert agree >= 0.97, (name, agree)
+    losses = []
+    for _ in range(60):
+        losses.append(float(r.train_step(xb, lb, lr=3e-3).item()))
+    assert losses[-1] < 0.7 * losses[0]
+
+
+def test_router_route_top_p(bdg):
+    d, h1, h2, m, N, P = 128, 64, 64, 48, 1000, 5
+    flat, params = _net(13, d, h1, h2, m)
+    r = bdg.Router(torch.from_numpy(flat).cuda(), d, h1, h2, m, max_batch=256)  # 4 chunks
+    x = np.random.default_rng(6).standard_normal((N, d)).astype(np.float32)
+    home = np.random.default_rng(7).integers(0, m, N).astype(np.int32)
+    routes = r.route(_bf16(x).cuda(), torch.from_numpy(home).cuda(), P).cpu().numpy()
+    z_o, _ = omlp.forward(params, x, bf16=True)
+    assert (routes[:, 0] == home).all()
+    for i in range(N):
+        zz = z_o[i].copy()
+        zz[home[i]] = -np.inf
+        want = omlp.topp(zz[None, :], P - 1)[0]
+        got = routes[i, 1:]
+        assert len(set(got.tolist())) == P - 1 and home[i] not in set(got.tolist())
+        if not np.array_equal(got, want):
+            # a different pick is only allowed among near-ties of the float64 logits
+            kth = np.sort(zz)[::-1][P - 2]
+            tol = 1e-2 * np.abs(z_o[i]).max()
+            assert np.all(zz[got] >= kth - tol)
