@@ -54,6 +54,9 @@ def _args():
                     help="small: one 500k-point partitioned build (profiling case)")
     ap.add_argument("--search-entry", type=int, default=16384,
                     help="long-link entry sample size of the search graph")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="seconds of Poisson arrivals per offered load")
     ap.add_argument("--kernel", choices=["auto", "popc", "tc"], default="tc",
                     help="Reduce-1 kernel of the build: tensor cores (tc) or XOR+POPC (popc)")
     return ap.parse_args()
@@ -295,7 +298,9 @@ def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
     _, _, ex = bdg.search(g, qcodes, ef, R, ef_max=max(w["efs"]), expansions=True)
     exp_total = float(ex.double().sum().item())
     bytes_search = exp_total * (4 * k + k * 8 * (spec.bits // 64))
-    return {
+    ctx = {"graph": g, "qcodes": qcodes, "qfeats": qfeats, "feats": feats, "R": R,
+           "topk": topk, "ef_max": max(w["efs"]), "gt_q": qs, "gt_ids": best_i}
+    return ctx, {
         "workload": SEARCH_WORKLOAD, "N": n, "bits": spec.bits, "degree": k, "nq": nq,
         "ef_mix": list(w["efs"]), "R": R, "topk": topk, "graph_build": {"m": m, "t": t,
                                                                          "seconds": build_s},
@@ -305,6 +310,72 @@ def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
         "rerank_kernel_ms": rerank_ms, "expansions_mean": exp_total / nq,
         "search_bytes_upper_bound_gbs": bytes_search / (search_ms / 1e3) / 1e9,
     }
+
+
+def _serve_bench(bdg, ctx, seconds):
+    """Continuous batching on the resident search graph: Poisson arrivals of
+    requests of 1..4096 queries (log-uniform sizes), per-request ef in {64, 256}
+    (50/50), at several offered loads; per-request latency p50/p99 and the
+    achieved query rate, and recall@10 of the served answers against the exact
+    FP32 neighbours of the sampled ground-truth queries."""
+    import threading
+    g, qc, qf, feats = ctx["graph"], ctx["qcodes"], ctx["qfeats"], ctx["feats"]
+    nq_all = qc.shape[0]
+    qc_h, qf_h = qc.cpu().numpy(), qf.cpu().numpy()
+    gt_pos = {int(q): i for i, q in enumerate(ctx["gt_q"].cpu().numpy())}
+    gt_ids = ctx["gt_ids"].cpu().numpy()
+    out = []
+    rng = np.random.default_rng(1006)
+    for qps in (5_000, 20_000, 50_000, 100_000, 200_000):
+        srv = bdg.Server(g, feats, R=ctx["R"], k=ctx["topk"], ef_max=256, max_batch=4096,
+                         n_streams=4, memory_budget=2 << 30)
+        sizes, t_arr = [], []
+        t = 0.0
+        while t < seconds:
+            n = int(min(4096, max(1, np.exp(rng.uniform(0, np.log(4096))))))
+            sizes.append(n)
+            t_arr.append(t)
+            t += rng.exponential(n / qps)  # arrivals at qps queries per second on average
+        starts = rng.integers(0, nq_all - 4096, len(sizes))
+        efs = [np.where(rng.random(n) < 0.5, 64, 256).astype(np.int32) for n in sizes]
+        reqs = [None] * len(sizes)
+        t0 = time.perf_counter()
+
+        def producer():
+            for i, n in enumerate(sizes):
+                delay = t0 + t_arr[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                s0 = int(starts[i])
+                reqs[i] = srv.submit(qc_h[s0:s0 + n], qf_h[s0:s0 + n], efs[i])
+
+        th = threading.Thread(target=producer)
+        th.start()
+        lat, hits, judged = [], 0, 0
+        for i in range(len(sizes)):
+            while reqs[i] is None:
+                time.sleep(0.0002)
+            ids, _, l = srv.wait(reqs[i], timeout_ms=120000)
+            lat.append(l)
+            s0 = int(starts[i])
+            for r in range(sizes[i]):
+                j = gt_pos.get(s0 + r)
+                if j is not None:
+                    hits += len(set(ids[r].tolist()) & set(gt_ids[j].tolist()))
+                    judged += 1
+        t_end = time.perf_counter()
+        th.join()
+        st = srv.stats()
+        srv.free()
+        lat = np.array(lat)
+        out.append({"offered_qps": qps, "achieved_qps": float(sum(sizes)) / (t_end - t0),
+                    "requests": len(sizes), "queries": int(sum(sizes)),
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "batches": st["batches"],
+                    "recall@10": (hits / (judged * ctx["topk"])) if judged else None,
+                    "recall_queries": judged})
+    return {"streams": 4, "max_batch": 4096, "memory_budget_bytes": 2 << 30,
+            "ef_mix": [64, 256], "request_sizes": "log-uniform 1..4096", "levels": out}
 
 
 def run_small_case(a):
@@ -415,8 +486,11 @@ def run_ours(a):
     e2e_ms = _max_over_ranks(sum(x.elapsed_time(y) for x, y in e2e_ev) / a.steps, ws, device)
 
     search = None
+    serve = None
     if not a.no_search and ws == 1:
-        search = _search_bench(bdg, device, a.search_steps, 2, a.search_entry, a.kernel)
+        ctx, search = _search_bench(bdg, device, a.search_steps, 2, a.search_entry, a.kernel)
+        if not a.no_serve:
+            serve = _serve_bench(bdg, ctx, a.serve_seconds)
 
     if rank != 0:
         if ws > 1:
@@ -476,6 +550,8 @@ def run_ours(a):
     }
     if search is not None:
         line["search"] = search
+    if serve is not None:
+        line["serving"] = serve
     if ws == 1 and not a.no_cpu:
         import oracle
         oracle.build()

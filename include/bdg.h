@@ -192,6 +192,34 @@ bdg_status bdg_search_rerank(const bdg_graph* g, const uint64_t* queries, const 
                              int32_t ef_max, int32_t R, int32_t k, int32_t* cand_ids,
                              int32_t* cand_dist, int32_t* out_ids, float* out_d2, void* stream);
 
+/* ------------------------------------------------------------------ serving */
+/* Continuous-batching request loop around bdg_search_rerank (the online path of
+ * Section 3.5). A scheduler thread keeps up to n_streams batches in flight;
+ * whenever a stream is free it packs the oldest queued requests into a batch
+ * of at most max_batch queries, admitting a request only while the device
+ * memory of all in-flight batches stays within memory_budget bytes (0 = no
+ * limit; a query needs 8W + 4D + 4 + 8R + 8k bytes). Requests that arrive
+ * while batches run are admitted as streams and memory free up, so their work
+ * overlaps with the running batches. Each query's result depends only on the
+ * query and its ef. The graph and feats are borrowed and must outlive the
+ * server. */
+typedef struct bdg_server bdg_server;
+bdg_status bdg_server_create(const bdg_graph* g, const float* feats, int32_t D, int32_t R,
+                             int32_t k, int32_t ef_max, int32_t max_batch, int32_t n_streams,
+                             uint64_t memory_budget, bdg_server** out);
+/* queries [nq][W], qfeats [nq][D], ef [nq]: HOST arrays, copied before return.
+ * 1 <= nq <= max_batch. *request_id identifies the request for bdg_server_wait. */
+bdg_status bdg_server_submit(bdg_server* s, const uint64_t* queries, const float* qfeats,
+                             const int32_t* ef, int32_t nq, int64_t* request_id);
+/* Waits up to timeout_ms for the request; copies its [nq][k] ids and squared
+ * distances to HOST outputs (either may be NULL) and its latency from submit to
+ * completion; BDG_ETIMEOUT if not done in time (the request stays queued). */
+bdg_status bdg_server_wait(bdg_server* s, int64_t request_id, int32_t* out_ids, float* out_d2,
+                           double* latency_ms, int32_t timeout_ms);
+bdg_status bdg_server_stats(bdg_server* s, int64_t* batches, int64_t* queries, int64_t* pending,
+                            uint64_t* in_flight_bytes);
+void bdg_server_free(bdg_server* s);
+
 /* ------------------------------------------------------------------ learned router */
 /* The paper routes each point to its t nearest binary centres (Section 3.2).
  * The router keeps the nearest centre as the home (slot 0) and picks the other

@@ -17,7 +17,7 @@ from . import build as _build
 __all__ = [
     "BDGError", "lib", "route", "bkmeans", "build_graph", "Graph", "search", "rerank",
     "search_rerank", "load_graph", "set_memory_budget", "memory_in_use", "knn_rows",
-    "launch_count", "gemm_bf16", "Router",
+    "launch_count", "gemm_bf16", "Router", "Server",
 ]
 
 _LIB = None
@@ -394,6 +394,75 @@ class Router:
         if self._h is not None and self._h.value:
             self.params = self.grads = self.loss = self.err = None
             lib().bdg_router_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- serving
+class Server:
+    """Continuous-batching search server (see bdg_server_* in include/bdg.h)."""
+
+    def __init__(self, graph: Graph, feats, R: int, k: int, ef_max: int, max_batch: int = 4096,
+                 n_streams: int = 4, memory_budget: int = 0):
+        L = lib()
+        if not getattr(L, "_server_sigs", False):
+            L.bdg_server_create.argtypes = [_c_void_p, _c_void_p, _i32, _i32, _i32, _i32, _i32,
+                                            _i32, ctypes.c_uint64, ctypes.POINTER(_c_void_p)]
+            L.bdg_server_submit.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32,
+                                            ctypes.POINTER(_i64)]
+            L.bdg_server_wait.argtypes = [_c_void_p, _i64, _c_void_p, _c_void_p,
+                                          ctypes.POINTER(ctypes.c_double), _i32]
+            L.bdg_server_stats.argtypes = [_c_void_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                           ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_uint64)]
+            L.bdg_server_free.argtypes = [_c_void_p]
+            L.bdg_server_free.restype = None
+            L._server_sigs = True
+        _dev(feats, torch.float32, "feats", 2)
+        self.graph, self.feats, self.k = graph, feats, k
+        h = ctypes.c_void_p()
+        _check(L.bdg_server_create(graph.handle, _ptr(feats), feats.shape[1], R, k, ef_max,
+                                   max_batch, n_streams, int(memory_budget), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, queries, qfeats, ef) -> int:
+        """queries int64/uint64 [nq, W], qfeats float32 [nq, D], ef int32 [nq] (host numpy)."""
+        import numpy as np
+        q = np.ascontiguousarray(queries).view(np.uint64)
+        qf = np.ascontiguousarray(qfeats, dtype=np.float32)
+        e = np.ascontiguousarray(ef, dtype=np.int32)
+        rid = _i64()
+        _check(lib().bdg_server_submit(self._h, q.ctypes.data_as(_c_void_p),
+                                       qf.ctypes.data_as(_c_void_p), e.ctypes.data_as(_c_void_p),
+                                       q.shape[0], ctypes.byref(rid)))
+        return rid.value, q.shape[0]
+
+    def wait(self, req, timeout_ms: int = 60000):
+        """Returns (ids int32 [nq, k], d2 float32 [nq, k], latency_ms)."""
+        import numpy as np
+        rid, nq = req
+        ids = np.empty((nq, self.k), np.int32)
+        d2 = np.empty((nq, self.k), np.float32)
+        lat = ctypes.c_double()
+        _check(lib().bdg_server_wait(self._h, rid, ids.ctypes.data_as(_c_void_p),
+                                     d2.ctypes.data_as(_c_void_p), ctypes.byref(lat), timeout_ms))
+        return ids, d2, lat.value
+
+    def stats(self):
+        b, q, p = _i64(), _i64(), _i64()
+        m = ctypes.c_uint64()
+        _check(lib().bdg_server_stats(self._h, ctypes.byref(b), ctypes.byref(q), ctypes.byref(p),
+                                      ctypes.byref(m)))
+        return {"batches": b.value, "queries": q.value, "pending": p.value,
+                "in_flight_bytes": m.value}
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().bdg_server_free(self._h)
             self._h = None
 
     def __del__(self):

@@ -270,7 +270,8 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       // like any other value and dropped at selection, so k + 1 values are needed
       const int need_k = k + ((live && c.visit_slot[v0 + r] == 0) ? 1 : 0);
       int thr_d = live ? bits : -1;  // accept d <= thr_d; idle rows keep nothing
-      int cnt = 0;
+      int cnt = 0;   // entries in the row's candidate list
+      int cle = 0;   // values seen so far with d <= thr_d (all of them are in the list)
       bool overflow = false;
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
       uint32_t* crow = cand + r;
@@ -294,14 +295,28 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         const int nvalid = min(kNT, nh - j * kNT);
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
-          // room for half a tile: drop candidates the threshold has since excluded
           if (cnt > kCap - kHalf) {
+            // the histogram cannot place the threshold (outside its window or a
+            // saturated bin): select the exact need_k-th smallest distance among
+            // the list, which holds every value seen with d <= thr_d
+            if (cle >= need_k && (thr_d >= kHB || hist[thr_d * kM + r] == 255)) {
+              int lo = 0, hi = thr_d;
+              while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                int c2 = 0;
+                for (int x = 0; x < cnt; ++x) c2 += ((int)(crow[x * kCandStride] >> kPosBits) <= mid);
+                if (c2 >= need_k) hi = mid; else lo = mid + 1;
+              }
+              thr_d = lo;
+            }
+            // drop the candidates the threshold has since excluded
             int w = 0;
             for (int x = 0; x < cnt; ++x) {
               const uint32_t e = crow[x * kCandStride];
               if ((int)(e >> kPosBits) <= thr_d) crow[(w++) * kCandStride] = e;
             }
             cnt = w;
+            cle = w;
             if (cnt > kCap - kHalf) {  // still full: the popcount kernel redoes this row
               overflow = true;
               thr_d = -1;  // accept nothing more
@@ -321,7 +336,8 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             crow[cnt * kCandStride] = (d << kPosBits) | (pos0 + cc);
             cnt += pass ? 1 : 0;
           }
-          if (cnt > c_before) {  // exact threshold: k-th smallest distance so far
+          if (cnt > c_before) {
+            cle += cnt - c_before;
             for (int x = c_before; x < cnt; ++x) {
               const uint32_t d = crow[x * kCandStride] >> kPosBits;
               if (d > (uint32_t)bits) {  // cannot happen for +-1 operands
@@ -333,13 +349,13 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
                 if (h < 255) h = (uint8_t)(h + 1);
               }
             }
-            int cum = 0, nd = 0;
-            const int lim_d = min(thr_d, kHB - 1);
-            for (; nd <= lim_d; ++nd) {
-              cum += hist[nd * kM + r];
-              if (cum >= need_k) break;
+            // lower the threshold one distance at a time while k values stay below it
+            while (thr_d > 0 && thr_d < kHB) {
+              const int h = hist[thr_d * kM + r];
+              if (h == 255 || cle - h < need_k) break;
+              cle -= h;
+              --thr_d;
             }
-            if (nd <= lim_d) thr_d = nd;
           }
         }
       }
