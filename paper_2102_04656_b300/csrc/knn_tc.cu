@@ -37,9 +37,10 @@ namespace {
 constexpr int kM = 128;         // visitors per item (TMEM lanes)
 constexpr int kNT = 64;         // homes per tile (TMEM columns per accumulator)
 constexpr int kStages = 2;
-constexpr int kCap = 124;       // candidate slots per row
-constexpr int kHalf = 32;       // compaction is checked every 32 columns
-constexpr int kHB = 256;        // exact distance histogram over d in [0, 256)
+constexpr int kCap = 155;       // candidate slots per row
+constexpr int kHalf = 16;       // compaction is checked every 16 columns
+constexpr int kHB = 128;        // exact distance histogram over d in [0, 128)
+constexpr int kSortN = 128;     // keys sorted per row at selection
 constexpr int kCandStride = kM + 1;  // words between candidate slots (odd: no bank conflicts)
 constexpr int kThreads = 192;   // warps 0-3 epilogue, warp 4 producer, warp 5 MMA
 constexpr uint32_t kPolls = 1u << 20;
@@ -52,14 +53,18 @@ struct TcCfg {
   static constexpr int NB = kHB;                   // distance histogram bins (width 1)
   static constexpr uint32_t A_BYTES = kM * KB;
   static constexpr uint32_t B_BYTES = kNT * KB;
-  static constexpr uint32_t HIST_BYTES = ((NB * kM) + 15) & ~15;
-  static constexpr uint32_t CAND_BYTES = kCap * kCandStride * 4;
+  static constexpr uint32_t HIST_BYTES = ((NB * kM) + 15) & ~15u;
+  static constexpr uint32_t CAND_BYTES = ((kCap * kCandStride * 4) + 15) & ~15u;
   static constexpr uint32_t OFF_B = A_BYTES;
   static constexpr uint32_t OFF_HIST = OFF_B + kStages * B_BYTES;
   static constexpr uint32_t OFF_CAND = OFF_HIST + HIST_BYTES;
   static constexpr uint32_t OFF_SORT = OFF_CAND + CAND_BYTES;     // 4 warps x 128 keys
-  static constexpr uint32_t OFF_BAR = OFF_SORT + 4 * 128 * 8;
+  static constexpr uint32_t OFF_BAR = OFF_SORT + 4 * kSortN * 8;
   static constexpr uint32_t SMEM = OFF_BAR + 256;
+  static_assert(OFF_B % 16 == 0 && OFF_HIST % 16 == 0 && OFF_CAND % 16 == 0 &&
+                    OFF_SORT % 16 == 0 && OFF_BAR % 16 == 0,
+                "shared-memory regions must be 16-byte aligned");
+  static_assert(SMEM <= 232448, "shared memory per block exceeds 227 KB");
 };
 
 // offset of (row r, byte kb) in a K-major no-swizzle operand whose rows are KB bytes
@@ -294,7 +299,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         const uint32_t pos0 = (uint32_t)(j * kNT);
         const int nvalid = min(kNT, nh - j * kNT);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
+        for (int half = 0; half < kNT / kHalf; ++half) {
           if (cnt > kCap - kHalf) {
             // the histogram cannot place the threshold (outside its window or a
             // saturated bin): select the exact need_k-th smallest distance among
@@ -358,6 +363,16 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             }
           }
         }
+      }
+      // ---- final compaction: only candidates inside the final threshold remain
+      if (!overflow) {
+        int w = 0;
+        for (int x = 0; x < cnt; ++x) {
+          const uint32_t e = crow[x * kCandStride];
+          if ((int)(e >> kPosBits) <= thr_d) crow[(w++) * kCandStride] = e;
+        }
+        cnt = w;
+        if (cnt > kSortN) overflow = true;  // too many ties to sort here
       }
       // ---- selection: k smallest (d, id) among candidates inside the threshold
       uint64_t* sb = sortbuf + warp * 128;
