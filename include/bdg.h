@@ -145,6 +145,33 @@ typedef struct bdg_graph bdg_graph; /* opaque; owns ids/dists/entry, borrows cod
 bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
                            const bdg_partitions* partitions, void* stream, bdg_graph** out);
 
+/* A build plan: the whole build of bdg_build_graph (Bk-means, routing,
+ * bucketing, the Reduce-1 kernel, the merge) captured once into a CUDA graph
+ * over scratch and graph storage allocated once, then replayed by
+ * bdg_build_plan_run (one graph launch per build). With partitions->kernel = 0
+ * an autotuner times the popcount and the tensor-core Reduce-1 kernels on this
+ * very workload and keeps the faster; the choice is cached per (device, bits,
+ * k, N, m, t) in the file named by $BDG_AUTOTUNE_CACHE (default
+ * ~/.cache/bdg_autotune.txt; an unwritable cache is ignored). Every array the
+ * partitions reference and the codes must stay alive and are re-read at each
+ * run (their contents may change between runs; their sizes may not). Creating
+ * a plan synchronises `stream`. */
+typedef struct bdg_build_plan bdg_build_plan;
+bdg_status bdg_build_plan_create(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
+                                 const bdg_partitions* partitions, void* stream,
+                                 bdg_build_plan** out);
+bdg_status bdg_build_plan_run(bdg_build_plan* plan, void* stream);
+/* Device time in ms of the Reduce-1 step (the fused Hamming + top-k kernel and
+ * its fix-up) of the most recent run, from events recorded inside the graph.
+ * Synchronises on that run. */
+bdg_status bdg_build_plan_kernel_ms(bdg_build_plan* plan, float* ms);
+/* The plan's graph (rows rewritten by every run), the chosen kernel (1 popcount,
+ * 2 tensor) and, when the autotuner ran, both measured build times in ms (-1 if
+ * not measured). */
+bdg_status bdg_build_plan_info(const bdg_build_plan* plan, const bdg_graph** graph,
+                               int32_t* kernel, float* ms_popc, float* ms_tc);
+void bdg_build_plan_free(bdg_build_plan* plan);
+
 /* Device pointers to the graph rows: ids/dists [N][k] int32, row i sorted by
  * (distance, id). Any output pointer may be NULL. Host scalars n/k/bits. */
 bdg_status bdg_graph_info(const bdg_graph* g, const int32_t** ids, const int32_t** dists,

@@ -17,7 +17,7 @@ from . import build as _build
 __all__ = [
     "BDGError", "lib", "route", "bkmeans", "build_graph", "Graph", "search", "rerank",
     "search_rerank", "load_graph", "set_memory_budget", "memory_in_use", "knn_rows",
-    "launch_count", "gemm_bf16", "Router", "Server",
+    "launch_count", "gemm_bf16", "Router", "Server", "BuildPlan",
 ]
 
 _LIB = None
@@ -470,3 +470,86 @@ class Server:
             self.free()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- build plans
+class BuildPlan:
+    """A build captured once into a CUDA graph (bdg_build_plan_*): run() replays
+    the whole build; kernel "auto" lets the library's autotuner pick the Reduce-1
+    kernel. Arrays passed here are re-read by every run and must stay alive."""
+
+    def __init__(self, codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample=None,
+                 bk_iters: int = 8, routes=None, entry=None, kernel: str = "auto", stream=None):
+        L = lib()
+        if not getattr(L, "_plan_sigs", False):
+            L.bdg_build_plan_create.argtypes = [_c_void_p, _i64, _i32, _i32,
+                                                ctypes.POINTER(_Partitions), _c_void_p,
+                                                ctypes.POINTER(_c_void_p)]
+            L.bdg_build_plan_run.argtypes = [_c_void_p, _c_void_p]
+            L.bdg_build_plan_kernel_ms.argtypes = [_c_void_p, ctypes.POINTER(ctypes.c_float)]
+            L.bdg_build_plan_info.argtypes = [_c_void_p, ctypes.POINTER(_c_void_p),
+                                              ctypes.POINTER(_i32),
+                                              ctypes.POINTER(ctypes.c_float),
+                                              ctypes.POINTER(ctypes.c_float)]
+            L.bdg_build_plan_free.argtypes = [_c_void_p]
+            L.bdg_build_plan_free.restype = None
+            L._plan_sigs = True
+        codes, bits = _codes(codes)
+        _dev(entry, torch.int32, "entry", 1)
+        self._keep = (codes, centroids, bk_sample, routes, entry)
+        P = _Partitions()
+        P.m, P.t = m, t
+        P.centroids = None if centroids is None else centroids.data_ptr()
+        P.bk_sample = None if bk_sample is None else bk_sample.data_ptr()
+        P.bk_sample_size = 0 if bk_sample is None else bk_sample.numel()
+        P.bk_iters = bk_iters
+        P.routes = None if routes is None else routes.data_ptr()
+        P.entry = entry.data_ptr()
+        P.n_entry = entry.numel()
+        P.tile_visitors = 0
+        P.kernel = KERNELS[kernel]
+        h = ctypes.c_void_p()
+        _check(L.bdg_build_plan_create(_ptr(codes), codes.shape[0], bits, k, ctypes.byref(P),
+                                       _stream(stream), ctypes.byref(h)))
+        self._h = h
+        gp, kern = ctypes.c_void_p(), _i32()
+        mp, mt = ctypes.c_float(), ctypes.c_float()
+        _check(L.bdg_build_plan_info(h, ctypes.byref(gp), ctypes.byref(kern), ctypes.byref(mp),
+                                     ctypes.byref(mt)))
+        self.kernel = {1: "popc", 2: "tc"}[kern.value]
+        self.tuned_ms = {"popc": mp.value, "tc": mt.value}
+        self.graph = _PlanGraph(gp.value, codes, self)
+
+    def run(self, stream=None):
+        _check(lib().bdg_build_plan_run(self._h, _stream(stream)))
+
+    def kernel_ms(self) -> float:
+        ms = ctypes.c_float()
+        _check(lib().bdg_build_plan_kernel_ms(self._h, ctypes.byref(ms)))
+        return ms.value
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            self.graph = None
+            lib().bdg_build_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class _PlanGraph(Graph):
+    """The graph owned by a build plan (freed with the plan, not on its own)."""
+
+    def __init__(self, handle, codes, plan):
+        super().__init__(handle, codes)
+        self._plan = plan
+
+    def free(self):
+        self._h = None
+
+    def __del__(self):
+        pass

@@ -1,6 +1,8 @@
 // api.cu -- the C ABI of include/bdg.h: argument checks, the memory budget,
 // graph handles, and the order of launches of a build or a search. No compute
 // happens here; every step of the path runs in the kernels of the other files.
+#include <sys/stat.h>
+
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -243,10 +245,22 @@ bdg_status bdg_bkmeans(const uint64_t* codes, int64_t n, int32_t bits, const int
   return bdg_launch_bkmeans(codes, n, W, sample, S, m, iters, centroids, loss, sc.p, sb, st);
 }
 
-bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
-                           const bdg_partitions* P, void* stream, bdg_graph** out) {
-  if (!out) return bdg_set_error(BDG_EINVAL, "build: out is NULL");
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// Everything a build needs besides the data: validated settings and the
+// scratch layout (routes, centres, Bk-means, CSR, partial lists, expanded
+// homes, fix-up flags), so that a build can be enqueued into caller-provided
+// scratch (bdg_build_graph) or captured once into a CUDA graph (build plans).
+struct BuildCfg {
+  int W, m, t, tile_v;
+  bool need_routes, need_bk, use_tc, tc_ok;
+  size_t b_routes, b_cent, b_bk, b_csr, b_part, b_hexp, b_fix, total;
+};
+
+bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
+                          const bdg_partitions* P, BuildCfg* c) {
   BDG_TRY(check_bits(bits));
   if (!codes || !P) return bdg_set_error(BDG_EINVAL, "build: null codes or partitions");
   if (N < 2 || N >= (int64_t(1) << 31))
@@ -258,115 +272,318 @@ bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32
     return bdg_set_error(BDG_EINVAL, "build: m = %d, t = %d (need 1 <= t <= min(m, 16))", m, t);
   if (!P->entry || P->n_entry < 1)
     return bdg_set_error(BDG_EINVAL, "build: an entry sample (n_entry >= 1) is required");
-  const bool need_routes = (P->routes == nullptr) && m > 1;
-  const bool need_bk = need_routes && P->centroids == nullptr;
-  if (need_bk && (!P->bk_sample || P->bk_sample_size < m || P->bk_iters < 0))
+  c->W = bits / 64; c->m = m; c->t = t;
+  c->need_routes = (P->routes == nullptr) && m > 1;
+  c->need_bk = c->need_routes && P->centroids == nullptr;
+  if (c->need_bk && (!P->bk_sample || P->bk_sample_size < m || P->bk_iters < 0))
     return bdg_set_error(BDG_EINVAL, "build: Bk-means needs bk_sample with >= m ids");
-  if (P->tile_visitors != 0 && P->tile_visitors != bdg_knn_tile_visitors(bits / 64))
+  if (P->tile_visitors != 0 && P->tile_visitors != bdg_knn_tile_visitors(c->W))
     return bdg_set_error(BDG_EUNSUPPORTED, "build: tile_visitors %d not built for %d bits",
                          P->tile_visitors, bits);
   if (P->kernel < 0 || P->kernel > 2)
     return bdg_set_error(BDG_EINVAL, "build: kernel = %d (0 auto, 1 popcount, 2 tensor)",
                          P->kernel);
-  const bool tc_ok = bdg_knn_tc_supported(bits / 64, k) && (m > 1 || N < (1 << 21));
-  if (P->kernel == 2 && !tc_ok)
+  c->tc_ok = bdg_knn_tc_supported(c->W, k) && (m > 1 || N < (1 << 21));
+  if (P->kernel == 2 && !c->tc_ok)
     return bdg_set_error(BDG_EUNSUPPORTED,
                          "build: the tensor path needs 256/512-bit codes, k <= 64 and, with "
                          "m = 1, N < 2^21");
-  const bool use_tc = P->kernel == 2 || (P->kernel == 0 && tc_ok && bdg_tc_default());
+  c->use_tc = P->kernel == 2 || (P->kernel == 0 && c->tc_ok && bdg_tc_default());
+  c->tile_v = bdg_knn_tile_visitors(c->W);
+  const int W = c->W;
+  c->b_routes = c->need_routes || m == 1 ? al((size_t)N * t * 4) : 0;
+  c->b_cent = c->need_bk ? al((size_t)m * W * 8) : 0;
+  c->b_bk = c->need_bk ? al(bdg_bkmeans_scratch_bytes(P->bk_sample_size, m, W)) : 0;
+  c->b_csr = al(bdg_csr_bytes(N, m, t, W));
+  c->b_part = t > 1 ? al((size_t)N * t * k * 8) : 0;
+  c->b_hexp = c->tc_ok ? al(bdg_knn_tc_hexp_bytes(N, m, W)) : 0;
+  c->b_fix = c->tc_ok ? al((size_t)N * t) + al(64) : 0;
+  c->total = c->b_routes + c->b_cent + c->b_bk + c->b_csr + c->b_part + c->b_hexp + c->b_fix;
+  return BDG_OK;
+}
 
-  cudaStream_t st = (cudaStream_t)stream;
-  const int W = bits / 64;
-  const int tile_v = bdg_knn_tile_visitors(W);
-  keep_pool_cached();
-
-  // graph storage (owned by the handle)
+bdg_status graph_alloc(const BuildCfg& c, const uint64_t* codes, int64_t N, int32_t bits,
+                       int32_t k, const bdg_partitions* P, bdg_graph** out) {
   bdg_graph* g = new bdg_graph();
-  g->n = N; g->k = k; g->bits = bits; g->W = W; g->n_entry = P->n_entry; g->codes = codes;
+  g->n = N; g->k = k; g->bits = bits; g->W = c.W; g->n_entry = P->n_entry; g->codes = codes;
   bdg_status s = dalloc((void**)&g->ids, (size_t)N * k * 4);
   if (s == BDG_OK) s = dalloc((void**)&g->dists, (size_t)N * k * 4);
   if (s == BDG_OK) s = dalloc((void**)&g->entry, (size_t)P->n_entry * 4);
-  if (s == BDG_OK) s = dalloc((void**)&g->entry_codes, (size_t)P->n_entry * W * 8);
+  if (s == BDG_OK) s = dalloc((void**)&g->entry_codes, (size_t)P->n_entry * c.W * 8);
   if (s != BDG_OK) { bdg_graph_free(g); return s; }
+  *out = g;
+  return BDG_OK;
+}
 
-  // scratch layout
-  const size_t b_routes = need_routes || m == 1 ? al((size_t)N * t * 4) : 0;
-  const size_t b_cent = need_bk ? al((size_t)m * W * 8) : 0;
-  const size_t b_bk = need_bk ? al(bdg_bkmeans_scratch_bytes(P->bk_sample_size, m, W)) : 0;
-  const size_t b_csr = al(bdg_csr_bytes(N, m, t, W));
-  const size_t b_part = t > 1 ? al((size_t)N * t * k * 8) : 0;
-  const size_t b_hexp = use_tc ? al(bdg_knn_tc_hexp_bytes(N, m, W)) : 0;
-  const size_t b_fix = use_tc ? al((size_t)N * t) + al(64) : 0;
-  Scratch sc;
-  s = sc.alloc(b_routes + b_cent + b_bk + b_csr + b_part + b_hexp + b_fix, st);
-  if (s != BDG_OK) { bdg_graph_free(g); return s; }
-  char* p = (char*)sc.p;
+// Enqueue every step of the build into g using `scratch` (c.total bytes).
+bdg_status build_enqueue(const BuildCfg& c, bool use_tc, bdg_graph* g, const uint64_t* codes,
+                         int64_t N, int32_t bits, int32_t k, const bdg_partitions* P,
+                         void* scratch, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                         cudaEvent_t ev1 = nullptr) {
+  const int W = c.W, m = c.m, t = c.t;
+  char* p = (char*)scratch;
   int32_t* routes = (int32_t*)P->routes;
-  if (b_routes) { routes = (int32_t*)p; p += b_routes; }
+  if (c.b_routes) { routes = (int32_t*)p; p += c.b_routes; }
   uint64_t* cent = (uint64_t*)P->centroids;
-  if (b_cent) { cent = (uint64_t*)p; p += b_cent; }
-  void* bk = p; p += b_bk;
-  void* csr_mem = p; p += b_csr;
-  uint64_t* partial = b_part ? (uint64_t*)p : nullptr;
-  p += b_part;
-  uint8_t* hexp = b_hexp ? (uint8_t*)p : nullptr;
-  p += b_hexp;
-  int8_t* fixflag = b_fix ? (int8_t*)p : nullptr;
-  int32_t* tc_err = b_fix ? (int32_t*)(p + al((size_t)N * t)) : nullptr;
+  if (c.b_cent) { cent = (uint64_t*)p; p += c.b_cent; }
+  void* bk = p; p += c.b_bk;
+  void* csr_mem = p; p += c.b_csr;
+  uint64_t* partial = c.b_part ? (uint64_t*)p : nullptr;
+  p += c.b_part;
+  uint8_t* hexp = c.b_hexp ? (uint8_t*)p : nullptr;
+  p += c.b_hexp;
+  int8_t* fixflag = c.b_fix ? (int8_t*)p : nullptr;
+  int32_t* tc_err = c.b_fix ? (int32_t*)(p + al((size_t)N * t)) : nullptr;
 
-  auto fail = [&](bdg_status e) { bdg_graph_free(g); return e; };
-  if (cudaMemcpyAsync(g->entry, P->entry, (size_t)P->n_entry * 4, cudaMemcpyDeviceToDevice, st) !=
-      cudaSuccess)
-    return fail(bdg_set_error(BDG_ECUDA, "build: copying the entry sample failed"));
-  s = bdg_launch_gather_codes(codes, N, g->entry, P->n_entry, W, g->entry_codes, st);
-  if (s != BDG_OK) return fail(s);
+  BDG_CUDA_TRY(cudaMemcpyAsync(g->entry, P->entry, (size_t)P->n_entry * 4,
+                               cudaMemcpyDeviceToDevice, st));
+  BDG_TRY(bdg_launch_gather_codes(codes, N, g->entry, P->n_entry, W, g->entry_codes, st));
   if (m == 1) {
-    if (cudaMemsetAsync(routes, 0, (size_t)N * 4, st) != cudaSuccess)
-      return fail(bdg_set_error(BDG_ECUDA, "build: memset failed"));
-  } else if (need_routes) {
-    if (need_bk) {
-      s = bdg_launch_bkmeans(codes, N, W, P->bk_sample, P->bk_sample_size, m, P->bk_iters, cent,
-                             nullptr, bk, b_bk, st);
-      if (s != BDG_OK) return fail(s);
-    }
-    s = bdg_launch_route(codes, N, W, cent, m, t, routes, nullptr, st);
-    if (s != BDG_OK) return fail(s);
+    BDG_CUDA_TRY(cudaMemsetAsync(routes, 0, (size_t)N * 4, st));
+  } else if (c.need_routes) {
+    if (c.need_bk)
+      BDG_TRY(bdg_launch_bkmeans(codes, N, W, P->bk_sample, P->bk_sample_size, m, P->bk_iters,
+                                 cent, nullptr, bk, c.b_bk, st));
+    BDG_TRY(bdg_launch_route(codes, N, W, cent, m, t, routes, nullptr, st));
   }
   if (P->routes != nullptr) {
     // caller-given routes may leave slots unvisited (values outside [0, m)):
     // those rows / partial lists must read as padding
-    if (t == 1) {
-      s = bdg_launch_fill_pad(g->ids, g->dists, N * (int64_t)k, bits, st);
-      if (s != BDG_OK) return fail(s);
-    } else if (cudaMemsetAsync(partial, 0xff, (size_t)N * t * k * 8, st) != cudaSuccess) {
-      return fail(bdg_set_error(BDG_ECUDA, "build: memset failed"));
-    }
+    if (t == 1) BDG_TRY(bdg_launch_fill_pad(g->ids, g->dists, N * (int64_t)k, bits, st));
+    else BDG_CUDA_TRY(cudaMemsetAsync(partial, 0xff, (size_t)N * t * k * 8, st));
   }
   bdg_csr csr;
-  s = bdg_build_csr(codes, N, W, routes, m, t, tile_v, csr_mem, &csr, st);
-  if (s != BDG_OK) return fail(s);
+  BDG_TRY(bdg_build_csr(codes, N, W, routes, m, t, c.tile_v, csr_mem, &csr, st));
+  // Reduce 1 in two rounds: A = every point against its home partition, then
+  // B = the other probed partitions, each visitor starting from the k-th key of
+  // its home list (only closer keys can enter the merged top-k)
   bdg_knn_args a;
-  a.codes = codes; a.csr = csr; a.N = N; a.m = m; a.t = t; a.k = k; a.bits = bits;
-  a.tile_v = tile_v; a.partial = partial; a.out_ids = g->ids; a.out_dist = g->dists;
-  a.item_counter = csr.counters + 2 * m;
+  a.codes = codes; a.N = N; a.m = m; a.t = t; a.k = k; a.bits = bits;
+  a.tile_v = c.tile_v; a.partial = partial; a.out_ids = g->ids; a.out_dist = g->dists;
   a.out_by_pos = 0;
   a.fixflag = nullptr;
-  if (use_tc) {
-    if (cudaMemsetAsync(fixflag, 0, al((size_t)N * t) + al(64), st) != cudaSuccess)
-      return fail(bdg_set_error(BDG_ECUDA, "build: memset failed"));
-    bdg_knn_tc_args ta;
-    ta.base = a; ta.hexp = hexp; ta.fixflag = fixflag; ta.err = tc_err;
-    s = bdg_launch_knn_tc(ta, W, st);
-  } else {
-    s = bdg_launch_knn_popc(a, W, st);
+  // optional timing of the Reduce-1 step (recorded also inside a captured graph)
+  if (ev0) BDG_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal));
+  if (use_tc) BDG_CUDA_TRY(cudaMemsetAsync(fixflag, 0, al((size_t)N * t) + al(64), st));
+  for (int round = 0; round < (t > 1 ? 2 : 1); ++round) {
+    a.csr = round == 0 ? bdg_csr_round_a(csr) : csr;
+    a.item_counter = csr.counters + 2 * m + round;
+    a.home_kth = round == 0 ? nullptr : partial;
+    if (use_tc) {
+      bdg_knn_tc_args ta;
+      ta.base = a; ta.hexp = hexp; ta.err = tc_err;
+      ta.fixflag = fixflag + (round == 0 ? 0 : N);
+      BDG_TRY(bdg_launch_knn_tc(ta, W, round == 0, st));
+    } else {
+      BDG_TRY(bdg_launch_knn_popc(a, W, st));
+    }
   }
-  if (s != BDG_OK) return fail(s);
-  if (t > 1) {
-    s = bdg_launch_merge(partial, N, t, k, bits, g->ids, g->dists, st);
-    if (s != BDG_OK) return fail(s);
+  if (ev1) BDG_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal));
+  if (t > 1) BDG_TRY(bdg_launch_merge(partial, N, t, k, bits, g->ids, g->dists, st));
+  return BDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
+                           const bdg_partitions* P, void* stream, bdg_graph** out) {
+  if (!out) return bdg_set_error(BDG_EINVAL, "build: out is NULL");
+  *out = nullptr;
+  BuildCfg c;
+  BDG_TRY(build_validate(codes, N, bits, k, P, &c));
+  if (!c.use_tc) {  // no expanded operand or fix-up flags needed
+    c.total -= c.b_hexp + c.b_fix;
+    c.b_hexp = c.b_fix = 0;
   }
+  cudaStream_t st = (cudaStream_t)stream;
+  keep_pool_cached();
+  bdg_graph* g = nullptr;
+  BDG_TRY(graph_alloc(c, codes, N, bits, k, P, &g));
+  Scratch sc;
+  bdg_status s = sc.alloc(c.total, st);
+  if (s == BDG_OK) s = build_enqueue(c, c.use_tc, g, codes, N, bits, k, P, sc.p, st);
+  if (s != BDG_OK) { bdg_graph_free(g); return s; }
   *out = g;
   return BDG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- build plans
+struct bdg_build_plan {
+  bdg_graph* g = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int kernel = 0;          // 1 popcount, 2 tensor
+  float ms_popc = -1.f, ms_tc = -1.f;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the Reduce-1 step of each replay
+  int64_t launches = 0;    // kernels in the captured graph
+};
+
+namespace {
+
+std::string tune_key(int64_t N, int32_t bits, int32_t k, const bdg_partitions* P) {
+  cudaDeviceProp prop;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  char buf[512];
+  std::string name(prop.name);
+  for (auto& ch : name) if (ch == ' ') ch = '_';
+  snprintf(buf, sizeof(buf), "%s|bits=%d|k=%d|N=%lld|m=%d|t=%d", name.c_str(), bits, k,
+           (long long)N, P->m, P->t);
+  return buf;
+}
+
+std::string tune_path() {
+  const char* e = getenv("BDG_AUTOTUNE_CACHE");
+  if (e && *e) return e;
+  const char* h = getenv("HOME");
+  return std::string(h ? h : "/tmp") + "/.cache/bdg_autotune.txt";
+}
+
+int tune_lookup(const std::string& key) {
+  FILE* f = fopen(tune_path().c_str(), "r");
+  if (!f) return 0;
+  char line[768];
+  int found = 0;
+  while (fgets(line, sizeof(line), f)) {
+    char k2[512];
+    int kern = 0;
+    if (sscanf(line, "%511s %d", k2, &kern) == 2 && key == k2) found = kern;
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_store(const std::string& key, int kern, float ms_popc, float ms_tc) {
+  const std::string path = tune_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {
+    const std::string dir = path.substr(0, slash);
+    mkdir(dir.c_str(), 0755);  // the cache directory may not exist yet
+  }
+  FILE* f = fopen(path.c_str(), "a");
+  if (!f) return;  // the cache is an optimisation only
+  fprintf(f, "%s %d %.3f %.3f\n", key.c_str(), kern, ms_popc, ms_tc);
+  fclose(f);
+}
+
+float time_build(const BuildCfg& c, bool use_tc, bdg_graph* g, const uint64_t* codes, int64_t N,
+                 int32_t bits, int32_t k, const bdg_partitions* P, void* scratch,
+                 cudaStream_t st) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float ms = -1.f;
+  if (build_enqueue(c, use_tc, g, codes, N, bits, k, P, scratch, st) == BDG_OK) {  // warm
+    cudaEventRecord(a, st);
+    if (build_enqueue(c, use_tc, g, codes, N, bits, k, P, scratch, st) == BDG_OK) {
+      cudaEventRecord(b, st);
+      if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+bdg_status bdg_build_plan_create(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
+                                 const bdg_partitions* P, void* stream, bdg_build_plan** out) {
+  if (!out) return bdg_set_error(BDG_EINVAL, "plan: out is NULL");
+  *out = nullptr;
+  BuildCfg c;
+  BDG_TRY(build_validate(codes, N, bits, k, P, &c));
+  cudaStream_t st = (cudaStream_t)stream;
+  bdg_build_plan* plan = new bdg_build_plan();
+  auto fail = [&](bdg_status e) { bdg_build_plan_free(plan); return e; };
+  bdg_status s = graph_alloc(c, codes, N, bits, k, P, &plan->g);
+  if (s != BDG_OK) return fail(s);
+  plan->scratch_bytes = c.total;
+  s = dalloc(&plan->scratch, c.total);
+  if (s != BDG_OK) return fail(s);
+  // kernel choice: fixed by the caller, else measured once per device and shape
+  int kern = P->kernel == 1 ? 1 : P->kernel == 2 ? 2 : 0;
+  if (kern == 0 && !c.tc_ok) kern = 1;
+  if (kern == 0) {
+    const std::string key = tune_key(N, bits, k, P);
+    kern = tune_lookup(key);
+    if (kern != 1 && kern != 2) {
+      plan->ms_popc = time_build(c, false, plan->g, codes, N, bits, k, P, plan->scratch, st);
+      plan->ms_tc = time_build(c, true, plan->g, codes, N, bits, k, P, plan->scratch, st);
+      kern = (plan->ms_tc > 0.f && (plan->ms_popc < 0.f || plan->ms_tc < plan->ms_popc)) ? 2 : 1;
+      tune_store(key, kern, plan->ms_popc, plan->ms_tc);
+    }
+  }
+  plan->kernel = kern;
+  // warm once outside capture (lazy module loading, function attributes), then capture
+  s = build_enqueue(c, kern == 2, plan->g, codes, N, bits, k, P, plan->scratch, st);
+  if (s != BDG_OK) return fail(s);
+  if (cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(bdg_set_error(BDG_ECUDA, "plan: warm-up build failed"));
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&plan->ev0) != cudaSuccess || cudaEventCreate(&plan->ev1) != cudaSuccess)
+    return fail(bdg_set_error(BDG_ECUDA, "plan: stream or event creation failed"));
+  const int64_t l0 = g_launches.load();
+  bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+  const bdg_status se =
+      ok ? build_enqueue(c, kern == 2, plan->g, codes, N, bits, k, P, plan->scratch, cap,
+                         plan->ev0, plan->ev1)
+         : BDG_OK;
+  plan->launches = g_launches.load() - l0;
+  ok = (cudaStreamEndCapture(cap, &plan->graph) == cudaSuccess) && ok && se == BDG_OK;
+  ok = ok && cudaGraphInstantiate(&plan->exec, plan->graph, 0) == cudaSuccess;
+  cudaStreamDestroy(cap);
+  if (!ok) {
+    cudaGetLastError();
+    return fail(se != BDG_OK ? se : bdg_set_error(BDG_ECUDA, "plan: graph capture failed"));
+  }
+  *out = plan;
+  return BDG_OK;
+}
+
+bdg_status bdg_build_plan_run(bdg_build_plan* plan, void* stream) {
+  if (!plan || !plan->exec) return bdg_set_error(BDG_EINVAL, "plan: not instantiated");
+  BDG_CUDA_TRY(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+  bdg_note_launch((int)plan->launches);
+  return BDG_OK;
+}
+
+bdg_status bdg_build_plan_kernel_ms(bdg_build_plan* plan, float* ms) {
+  if (!plan || !ms) return bdg_set_error(BDG_EINVAL, "plan: null argument");
+  BDG_CUDA_TRY(cudaEventSynchronize(plan->ev1));
+  BDG_CUDA_TRY(cudaEventElapsedTime(ms, plan->ev0, plan->ev1));
+  return BDG_OK;
+}
+
+bdg_status bdg_build_plan_info(const bdg_build_plan* plan, const bdg_graph** graph,
+                               int32_t* kernel, float* ms_popc, float* ms_tc) {
+  if (!plan) return bdg_set_error(BDG_EINVAL, "plan is NULL");
+  if (graph) *graph = plan->g;
+  if (kernel) *kernel = plan->kernel;
+  if (ms_popc) *ms_popc = plan->ms_popc;
+  if (ms_tc) *ms_tc = plan->ms_tc;
+  return BDG_OK;
+}
+
+void bdg_build_plan_free(bdg_build_plan* plan) {
+  if (!plan) return;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->ev0) cudaEventDestroy(plan->ev0);
+  if (plan->ev1) cudaEventDestroy(plan->ev1);
+  dfree(plan->scratch, plan->scratch_bytes);
+  bdg_graph_free(plan->g);
+  delete plan;
 }
 
 bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const int32_t* rows,
@@ -398,6 +615,7 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
   a.item_counter = csr.counters + 2;
   a.out_by_pos = 1;
   a.fixflag = nullptr;
+  a.home_kth = nullptr;
   if (!use_tc) return bdg_launch_knn_popc(a, W, st);
   char* q = (char*)sc.p + b;
   bdg_knn_tc_args ta;
@@ -406,7 +624,7 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
   ta.fixflag = (int8_t*)(q + b_hexp);
   ta.err = (int32_t*)(q + b_hexp + al((size_t)nrows));
   BDG_CUDA_TRY(cudaMemsetAsync(ta.fixflag, 0, b_fix, st));
-  return bdg_launch_knn_tc(ta, W, st);
+  return bdg_launch_knn_tc(ta, W, true, st);
 }
 
 bdg_status bdg_graph_info(const bdg_graph* g, const int32_t** ids, const int32_t** dists,

@@ -22,7 +22,7 @@ __global__ void count_kernel(const int32_t* __restrict__ routes, int64_t N, int 
   if (i >= N) return;
   const int32_t h = routes[i * t];
   if (h >= 0 && h < m) atomicAdd(&hcnt[h], 1);  // route values outside [0, m) are ignored
-  for (int s = 0; s < t; ++s) {
+  for (int s = 1; s < t; ++s) {  // slot 0 (the home) is visited in round A from H_p
     const int32_t p = routes[i * t + s];
     if (p >= 0 && p < m) atomicAdd(&vcnt[p], 1);
   }
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kScanThreads)
 plan_kernel(int m, int tile_v, int32_t* __restrict__ hcnt, int32_t* __restrict__ vcnt,
             int32_t* __restrict__ home_off, int32_t* __restrict__ visit_off,
             int32_t* __restrict__ part_order, int32_t* __restrict__ item_off,
-            int32_t* __restrict__ eoff) {
+            int32_t* __restrict__ eoff, int32_t* __restrict__ item_off_a) {
   extern __shared__ uint64_t skey[];  // [pow2 >= m]
   __shared__ int32_t warp_tot[32];
   __shared__ int32_t total;
@@ -123,6 +123,16 @@ plan_kernel(int m, int tile_v, int32_t* __restrict__ hcnt, int32_t* __restrict__
       run += (vcnt[p] + tile_v - 1) / tile_v;
     }
     if (threadIdx.x == 0) item_off[m] = total;
+    __syncthreads();
+    // round A: every home visits its own partition
+    s = 0;
+    for (int r = b; r < e; ++r) s += (hcnt[part_order[r]] + tile_v - 1) / tile_v;
+    run = block_exclusive_scan(s, warp_tot, &total);
+    for (int r = b; r < e; ++r) {
+      item_off_a[r] = run;
+      run += (hcnt[part_order[r]] + tile_v - 1) / tile_v;
+    }
+    if (threadIdx.x == 0) item_off_a[m] = total;
   }
   __syncthreads();
   // --- scatter cursors start at the offsets
@@ -140,7 +150,7 @@ __global__ void scatter_kernel(const int32_t* __restrict__ routes, int64_t N, in
   if (i >= N) return;
   const int32_t h = routes[i * t];
   if (h >= 0 && h < m) home_ids[atomicAdd(&hcur[h], 1)] = (int32_t)i;
-  for (int s = 0; s < t; ++s) {
+  for (int s = 1; s < t; ++s) {
     const int32_t p = routes[i * t + s];
     if (p < 0 || p >= m) continue;
     const int32_t pos = atomicAdd(&vcur[p], 1);
@@ -203,6 +213,8 @@ bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* r
   c->part_order = (int32_t*)p; p += al(4);
   c->counters = (int32_t*)p;
   c->home_codes = const_cast<uint64_t*>(codes);  // identity order: read the codes in place
+  c->item_off_a = c->item_off;
+  c->slot_zero = c->visit_slot;
   BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, 8 * 4, st));
   const int64_t n = N > nrows ? N : nrows;
   rows_plan_kernel<<<bdg_cdiv(n, 256), 256, 0, st>>>(N, rows, nrows, tile_v, c->home_off,
@@ -215,8 +227,8 @@ bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* r
 }
 
 size_t bdg_csr_bytes(int64_t N, int m, int t, int W) {
-  return al((m + 1) * 4) * 4 + al(N * 4) + al(N * W * 8) + al(N * t * 4) + al(N * t) +
-         al(m * 4) + al((2 * (size_t)m + 4) * 4);
+  return al((m + 1) * 4) * 5 + al(N * 4) + al(N * W * 8) + al(N * t * 4) + al(N * t) +
+         al(m * 4) + al((2 * (size_t)m + 4) * 4) + al(N);
 }
 
 bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
@@ -233,10 +245,13 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   c->visit_ids = (int32_t*)p;  p += al(N * t * 4);
   c->visit_slot = (int8_t*)p;  p += al(N * t);
   c->part_order = (int32_t*)p; p += al(m * 4);
+  c->item_off_a = (int32_t*)p; p += al((m + 1) * 4);
+  c->slot_zero = (int8_t*)p;   p += al(N);
   c->counters = (int32_t*)p;
   int32_t* hcnt = c->counters;
   int32_t* vcnt = c->counters + m;
   BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, (2 * (size_t)m + 4) * 4, st));
+  BDG_CUDA_TRY(cudaMemsetAsync(c->slot_zero, 0, N, st));
   const int g = bdg_cdiv(N, 256);
   count_kernel<<<g, 256, 0, st>>>(routes, N, t, m, hcnt, vcnt);
   BDG_CUDA_TRY(cudaGetLastError());
@@ -247,7 +262,8 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   BDG_CUDA_TRY(cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   plan_kernel<<<1, kScanThreads, smem, st>>>(m, tile_v, hcnt, vcnt, c->home_off, c->visit_off,
-                                             c->part_order, c->item_off, c->eoff);
+                                             c->part_order, c->item_off, c->eoff,
+                                             c->item_off_a);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   scatter_kernel<<<g, 256, 0, st>>>(routes, N, t, m, hcnt, vcnt, c->home_ids, c->visit_ids,

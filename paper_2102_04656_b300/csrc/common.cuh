@@ -84,7 +84,21 @@ struct bdg_csr {
   int32_t* item_off;   // [m + 1]  work items per partition in part_order order
   int32_t* eoff;       // [m + 1]  row offsets of H_p in the 64-row-padded expanded operand
   int32_t* counters;   // [2 * m + 4] scratch counters
+  // round A of a partitioned build visits every point in its home partition
+  // (its visitors are H_p itself); the visit_* fields above then hold only the
+  // other probed partitions (slots >= 1, round B)
+  int32_t* item_off_a; // [m + 1]  work items of round A in part_order order
+  int8_t* slot_zero;   // [N]      zeros: the route slot of every round-A visit
 };
+// The CSR view of round A (visitors = homes).
+inline bdg_csr bdg_csr_round_a(const bdg_csr& c) {
+  bdg_csr a = c;
+  a.visit_off = c.home_off;
+  a.visit_ids = c.home_ids;
+  a.visit_slot = c.slot_zero;
+  a.item_off = c.item_off_a;
+  return a;
+}
 size_t bdg_csr_bytes(int64_t N, int m, int t, int W);
 bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
                          int t, int tile_v, void* mem, bdg_csr* csr, cudaStream_t st);
@@ -106,6 +120,9 @@ struct bdg_knn_args {
   int32_t* item_counter;  // zeroed before launch
   int out_by_pos;         // t == 1: write row i of the output for the i-th visitor (not its id)
   const int8_t* fixflag;  // [N * t] or NULL: only visit positions flagged 1 are computed
+  // round B: a visitor's threshold starts at the k-th key of its home list
+  // (partial[v][0][k-1]); nothing beyond it can enter the merged top-k. NULL = none.
+  const uint64_t* home_kth;
 };
 // knn_tc.cu: tensor-core (tcgen05, FP8 +-1) Reduce 1 for 256/512-bit codes and k <= 64.
 struct bdg_knn_tc_args {
@@ -116,7 +133,7 @@ struct bdg_knn_tc_args {
 };
 bool bdg_knn_tc_supported(int W, int k);
 size_t bdg_knn_tc_hexp_bytes(int64_t N, int m, int W);
-bdg_status bdg_launch_knn_tc(const bdg_knn_tc_args& a, int W, cudaStream_t st);
+bdg_status bdg_launch_knn_tc(const bdg_knn_tc_args& a, int W, bool expand, cudaStream_t st);
 bdg_status bdg_launch_knn_popc(const bdg_knn_args& a, int W, cudaStream_t st);
 // merge.cu
 bdg_status bdg_launch_merge(const uint64_t* partial, int64_t N, int t, int k, int bits,

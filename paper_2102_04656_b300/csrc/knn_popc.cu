@@ -164,8 +164,12 @@ knn_popc_kernel(bdg_knn_args a) {
       s.vslot[r] = r < nv ? (int)c.visit_slot[v0 + r] : 0;
       s.cur[r] = 0;
       s.cnt[r] = 0;
-      // idle rows and rows of invalid visitor ids accept nothing
-      s.thr[r] = (r < nv && s.vid[r] >= 0) ? BDG_KEY_INF : 0ull;
+      // idle rows and rows of invalid visitor ids accept nothing; in round B a
+      // row starts from the k-th key of the visitor's home list
+      uint64_t th0 = (r < nv && s.vid[r] >= 0) ? BDG_KEY_INF : 0ull;
+      if (a.home_kth != nullptr && th0 != 0ull)
+        th0 = a.home_kth[((int64_t)s.vid[r] * a.t) * k + (k - 1)];
+      s.thr[r] = th0;
     }
     if (a.fixflag != nullptr) {  // skip items without a flagged row
       const int any = __syncthreads_or(tid < TV && s.vid[tid < TV ? tid : 0] >= 0);

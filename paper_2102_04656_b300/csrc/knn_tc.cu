@@ -37,9 +37,9 @@ namespace {
 constexpr int kM = 128;         // visitors per item (TMEM lanes)
 constexpr int kNT = 64;         // homes per tile (TMEM columns per accumulator)
 constexpr int kStages = 2;
-constexpr int kCap = 155;       // candidate slots per row
+constexpr int kCap = 124;       // candidate slots per row
 constexpr int kHalf = 16;       // compaction is checked every 16 columns
-constexpr int kHB = 128;        // exact distance histogram over d in [0, 128)
+constexpr int kHB = 256;        // exact distance histogram over d in [0, 256)
 constexpr int kSortN = 128;     // keys sorted per row at selection
 constexpr int kCandStride = kM + 1;  // words between candidate slots (odd: no bank conflicts)
 constexpr int kThreads = 192;   // warps 0-3 epilogue, warp 4 producer, warp 5 MMA
@@ -275,6 +275,10 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       // like any other value and dropped at selection, so k + 1 values are needed
       const int need_k = k + ((live && c.visit_slot[v0 + r] == 0) ? 1 : 0);
       int thr_d = live ? bits : -1;  // accept d <= thr_d; idle rows keep nothing
+      if (live && a.home_kth != nullptr) {  // round B: start from the home list's k-th key
+        const int dh = bdg_key_d(a.home_kth[((int64_t)c.visit_ids[v0 + r] * a.t) * k + (k - 1)]);
+        thr_d = dh < thr_d ? dh : thr_d;
+      }
       int cnt = 0;   // entries in the row's candidate list
       int cle = 0;   // values seen so far with d <= thr_d (all of them are in the list)
       bool overflow = false;
@@ -454,16 +458,17 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
 }
 
 template <int W>
-bdg_status launch_w(const bdg_knn_tc_args& ta, cudaStream_t st) {
+bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
   using C = TcCfg<W>;
   const bdg_knn_args& a = ta.base;
-  // expanded home operand (rows are bounded by N + 64 m)
-  const int64_t max_rows = a.N + 64LL * a.m;
-  const int64_t nthreads = ((max_rows + 7) / 8) * 8 * (4 * W);
-  expand_homes_kernel<W><<<bdg_cdiv(nthreads, 256), 256, 0, st>>>(
-      a.csr.home_codes, a.csr.home_off, a.csr.eoff, a.m, max_rows, ta.hexp);
-  BDG_CUDA_TRY(cudaGetLastError());
-  bdg_note_launch();
+  if (expand) {  // expanded home operand (rows are bounded by N + 64 m)
+    const int64_t max_rows = a.N + 64LL * a.m;
+    const int64_t nthreads = ((max_rows + 7) / 8) * 8 * (4 * W);
+    expand_homes_kernel<W><<<bdg_cdiv(nthreads, 256), 256, 0, st>>>(
+        a.csr.home_codes, a.csr.home_off, a.csr.eoff, a.m, max_rows, ta.hexp);
+    BDG_CUDA_TRY(cudaGetLastError());
+    bdg_note_launch();
+  }
   BDG_CUDA_TRY(cudaFuncSetAttribute(knn_tc_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)C::SMEM));
   const int grid = bdg_num_sms();
@@ -488,8 +493,8 @@ size_t bdg_knn_tc_hexp_bytes(int64_t N, int m, int W) {
   return (size_t)(N + 64LL * m) * 64 * W;
 }
 
-bdg_status bdg_launch_knn_tc(const bdg_knn_tc_args& a, int W, cudaStream_t st) {
-  if (W == 4) return launch_w<4>(a, st);
-  if (W == 8) return launch_w<8>(a, st);
+bdg_status bdg_launch_knn_tc(const bdg_knn_tc_args& a, int W, bool expand, cudaStream_t st) {
+  if (W == 4) return launch_w<4>(a, expand, st);
+  if (W == 8) return launch_w<8>(a, expand, st);
   return bdg_set_error(BDG_EUNSUPPORTED, "tensor k-NN path needs 256- or 512-bit codes");
 }

@@ -313,3 +313,37 @@ def test_search_rerank_end_to_end(bdg):
     g_o, _ = oracle.knn_exact(_np(c), 32)
     cand_o, _, _ = oracle.search(_np(c), g_o, entry, _np(qc), ef, 100)
     _check_rerank(ids, d2, x.numpy(), qx.numpy(), cand_o, 10)
+
+
+# ------------------------------------------------------------------ build plans (CUDA graphs)
+@pytest.mark.parametrize("kernel", ["auto", "popc", "tc"])
+def test_build_plan_replays_bit_exact(bdg, kernel, tmp_path, monkeypatch):
+    monkeypatch.setenv("BDG_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    spec = datagen.MixtureSpec(12000, 64, 48, 512, seed=515)
+    c = datagen.make_codes(spec).cuda()
+    sample = torch.from_numpy(datagen.sample_ids(spec.n, 1024, 3)).cuda()
+    entry = torch.from_numpy(_entry(spec.n, 64, 4)).cuda()
+    plan = bdg.BuildPlan(c, 64, m=16, t=3, bk_sample=sample, bk_iters=6, entry=entry,
+                         kernel=kernel)
+    cent_o, _, _ = oracle.bkmeans(_np(c.cpu()), sample.cpu().numpy(), 16, 6)
+    r_o, _ = oracle.route(_np(c.cpu()), cent_o, 3)
+    ids_o, dist_o = oracle.knn_partitioned(_np(c.cpu()), r_o, 64)
+    for _ in range(2):  # replays give the same exact graph
+        plan.run()
+        torch.cuda.synchronize()
+        assert np.array_equal(plan.graph.ids.cpu().numpy(), ids_o)
+        assert np.array_equal(plan.graph.dists.cpu().numpy(), dist_o)
+        assert plan.kernel_ms() > 0
+    if kernel == "auto":
+        assert plan.tuned_ms["popc"] > 0 and plan.tuned_ms["tc"] > 0
+        assert (tmp_path / "tune.txt").exists()
+    # the plan re-reads the codes: new contents give the new graph
+    c2 = datagen.random_codes(spec.n, 512, seed=9).cuda()
+    c.copy_(c2)
+    plan.run()
+    torch.cuda.synchronize()
+    cent2, _, _ = oracle.bkmeans(_np(c2.cpu()), sample.cpu().numpy(), 16, 6)
+    r2, _ = oracle.route(_np(c2.cpu()), cent2, 3)
+    ids2, _ = oracle.knn_partitioned(_np(c2.cpu()), r2, 64)
+    assert np.array_equal(plan.graph.ids.cpu().numpy(), ids2)
+    plan.free()
