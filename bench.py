@@ -55,6 +55,7 @@ def _args():
     ap.add_argument("--search-entry", type=int, default=16384,
                     help="long-link entry sample size of the search graph")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-routing leg")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds of Poisson arrivals per offered load")
     ap.add_argument("--kernel", choices=["auto", "popc", "tc"], default="auto",
@@ -378,6 +379,88 @@ def _serve_bench(bdg, ctx, seconds):
             "ef_mix": [64, 256], "request_sizes": "log-uniform 1..4096", "levels": out}
 
 
+def _learned_bench(bdg, device, kernel, n=10_000_000):
+    """Learned vs nearest-centre routing on the learned workload's generator at
+    N = 10M (256-bit, m = 10,000, k = 32): the router (128 -> 512 -> 512 -> m,
+    BF16) is trained on the GPU on a 1M-point sample whose exact within-sample
+    neighbours give the targets; both routings build a graph at the same P and
+    are judged against exact brute-force rows."""
+    from paper_2102_04656_b300 import learned
+    w = datagen.WORKLOADS["learned_100m_256b"]
+    base = w["spec"]
+    spec = datagen.MixtureSpec(n, base.dim, base.components, base.bits, base.sigma, base.seed)
+    k, m = w["k"], w["m"]
+    out = {"workload": "learned_100m_256b generator at N = %d" % n, "N": n, "bits": spec.bits,
+           "m": m, "k": k}
+    t0 = time.perf_counter()
+    codes, feats = datagen.make_codes(spec, device=device, with_features=True)
+    xb = feats.to(torch.bfloat16).contiguous()
+    del feats
+    sample = torch.from_numpy(datagen.sample_ids(n, 64 * m, spec.seed + 3)).to(device)
+    entry = torch.from_numpy(datagen.sample_ids(n, 256, spec.seed + 4).astype(np.int32)).to(device)
+    cent, _ = bdg.bkmeans(codes, sample, m, w["bk_iters"])
+    home = bdg.route(codes, cent, 1)[0][:, 0].contiguous()
+    torch.cuda.synchronize()
+    out["setup_s"] = time.perf_counter() - t0
+    # training data and the router
+    S = 1_000_000
+    tr = torch.from_numpy(datagen.sample_ids(n, S, spec.seed + 5)).to(device)
+    t0 = time.perf_counter()
+    labels = learned.neighbour_labels(codes[tr].contiguous(), home[tr].contiguous(), k)
+    torch.cuda.synchronize()
+    out["labels_s"] = time.perf_counter() - t0
+    init = torch.from_numpy(datagen.router_init(base.dim, 512, 512, m, spec.seed + 5)).to(device)
+    cfg = learned.TrainConfig(hidden=(512, 512), batch=4096, epochs=2, lr=1e-3)
+    losses = []
+    t0 = time.perf_counter()
+    router = learned.train_router(xb[tr].contiguous(), labels, m, init, cfg, seed=spec.seed + 5,
+                                  log=lambda ep, l: losses.append(l))
+    torch.cuda.synchronize()
+    out["train"] = {"sample": S, "epochs": cfg.epochs, "batch": cfg.batch, "lr": cfg.lr,
+                    "seconds": time.perf_counter() - t0, "loss_by_epoch": losses}
+    del labels
+    rows = torch.from_numpy(datagen.sample_ids(n, 2000, spec.seed + 9).astype(np.int32)).to(device)
+    ex_ids, ex_d = bdg.knn_rows(codes, rows, k)
+
+    def judge(g):
+        gd = g.dists[rows.long()]
+        dk = ex_d[:, -1:]
+        below = (gd < dk).sum(1)
+        at = torch.minimum((gd == dk).sum(1), (ex_d == dk).sum(1))
+        return float((below + at).sum().item()) / ex_d.numel()
+
+    def build_timed(routes, P):
+        g = bdg.build_graph(codes, k, m=m, t=P, routes=routes, entry=entry, kernel=kernel)
+        g.free()  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g = bdg.build_graph(codes, k, m=m, t=P, routes=routes, entry=entry, kernel=kernel)
+        e1.record()
+        torch.cuda.synchronize()
+        hc = torch.bincount(routes[:, 0].long(), minlength=m).double()
+        vc = torch.bincount(routes.reshape(-1).long(), minlength=m).double()
+        res = {"recall_tie_aware": judge(g), "build_ms": e0.elapsed_time(e1),
+               "pairs": float((hc * vc).sum().item())}
+        g.free()
+        return res
+
+    t0 = time.perf_counter()
+    lr_routes = {}
+    for P in (2, 4, 8):
+        lr_routes[P] = learned.learned_routes(router, xb, home, P)
+    torch.cuda.synchronize()
+    out["route_s_P2_4_8"] = time.perf_counter() - t0
+    out["learned"] = {P: build_timed(lr_routes[P], P) for P in (2, 4, 8)}
+    out["exhaustive"] = {}
+    for P in (2, 4, 8, 12):
+        r_ex, _ = bdg.route(codes, cent, P)
+        out["exhaustive"][P] = build_timed(r_ex, P)
+        del r_ex
+    router.free()
+    return out
+
+
 def run_small_case(a):
     """One 500k-point partitioned build (512-bit, m = 64, t = 5, k = 64): the
     small case on which the fused k-NN kernel is profiled."""
@@ -498,6 +581,10 @@ def run_ours(a):
         if not a.no_serve:
             serve = _serve_bench(bdg, ctx, a.serve_seconds)
 
+    learned_res = None
+    if not a.no_learned and ws == 1:
+        learned_res = _learned_bench(bdg, device, "popc" if kernel_used == "popc" else "auto")
+
     if rank != 0:
         if ws > 1:
             import torch.distributed as dist
@@ -560,6 +647,8 @@ def run_ours(a):
         line["search"] = search
     if serve is not None:
         line["serving"] = serve
+    if learned_res is not None:
+        line["learned_routing"] = learned_res
     if ws == 1 and not a.no_cpu:
         import oracle
         oracle.build()

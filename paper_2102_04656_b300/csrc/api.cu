@@ -153,13 +153,12 @@ bdg_status bdg_set_error(bdg_status s, const char* fmt, ...) {
   return s;
 }
 
-// Whether "auto" picks the tensor-core Reduce-1 kernel (BDG_KNN_KERNEL=popc|tc
-// overrides; the default is the tensor path).
+// Whether "auto" picks the tensor-core Reduce-1 kernel where it applies
+// (BDG_KNN_KERNEL=popc|tc overrides; the default is the tensor path).
 bool bdg_tc_default() {
   const char* e = getenv("BDG_KNN_KERNEL");
   if (e && strcmp(e, "popc") == 0) return false;
-  if (e && strcmp(e, "tc") == 0) return true;
-  return false;
+  return true;
 }
 
 int bdg_num_sms() {

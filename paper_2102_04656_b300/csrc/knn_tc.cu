@@ -283,6 +283,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       int cle = 0;   // values seen so far with d <= thr_d (all of them are in the list)
       bool overflow = false;
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+      const float hbits = 0.5f * (float)bits;  // d = (bits - dot) / 2 = dot * -0.5 + bits / 2
       uint32_t* crow = cand + r;
       for (int j = 0; j < ntiles; ++j) {
         const uint32_t gg = g + j, b = gg & 1;
@@ -333,18 +334,30 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             }
           }
           // accept iff d <= thr_d  <=>  dot >= bits - 2 * thr_d; branch-free append:
-          // every value is written, only accepted ones advance cnt
+          // every value is written at the running slot, only accepted ones advance it
           const float lim = (float)(bits - 2 * thr_d);
           const int c_before = cnt;
+          uint32_t* wp = crow + cnt * kCandStride;
+          const uint32_t posq = pos0 + (uint32_t)(half * kHalf);
+          if (nvalid == kNT) {
 #pragma unroll
-          for (int c2 = 0; c2 < kHalf; ++c2) {
-            const int cc = half * kHalf + c2;
-            const float dot = __uint_as_float(v[cc]);
-            const bool pass = (dot >= lim) && (cc < nvalid);
-            const uint32_t d = (uint32_t)(bits - (int)dot) >> 1;
-            crow[cnt * kCandStride] = (d << kPosBits) | (pos0 + cc);
-            cnt += pass ? 1 : 0;
+            for (int c2 = 0; c2 < kHalf; ++c2) {
+              const float dot = __uint_as_float(v[half * kHalf + c2]);
+              const uint32_t d = (uint32_t)__float2int_rz(fmaf(dot, -0.5f, hbits));
+              *wp = d * (1u << kPosBits) + (posq + c2);
+              wp += (dot >= lim) ? kCandStride : 0;
+            }
+          } else {
+#pragma unroll
+            for (int c2 = 0; c2 < kHalf; ++c2) {
+              const int cc = half * kHalf + c2;
+              const float dot = __uint_as_float(v[cc]);
+              const uint32_t d = (uint32_t)__float2int_rz(fmaf(dot, -0.5f, hbits));
+              *wp = d * (1u << kPosBits) + (posq + c2);
+              wp += (dot >= lim && cc < nvalid) ? kCandStride : 0;
+            }
           }
+          cnt = (int)((wp - crow) / kCandStride);
           if (cnt > c_before) {
             cle += cnt - c_before;
             for (int x = c_before; x < cnt; ++x) {
@@ -394,34 +407,61 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           if (lane == 0) ta.fixflag[v0 + row] = 1;
           continue;
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int x = lane + 32 * q;
+        if (n_r <= 32) {
+          // few candidates: one key per lane, bitonic sort across the warp in registers
           uint64_t key = BDG_KEY_INF;
-          if (x < n_r) {
-            const uint32_t e = cand[cidx(x, row)];
+          if (lane < n_r) {
+            const uint32_t e = cand[cidx(lane, row)];
             const int d = (int)(e >> kPosBits);
             if (d <= tb) {
               const int32_t hid = c.home_ids[h0 + (int)(e & kPosMask)];
               if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
             }
           }
-          sb[x] = key;
-        }
-        __syncwarp();
-        // bitonic sort of 128 keys, ascending
-        for (int size = 2; size <= 128; size <<= 1) {
-          for (int stride = size >> 1; stride > 0; stride >>= 1) {
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              const int i = lane + 32 * q;                           // pair index 0..63
-              const int lo2 = (i / stride) * (2 * stride) + (i % stride);
-              const int hi2 = lo2 + stride;
-              const bool up = (lo2 & size) == 0;
-              const uint64_t x0 = sb[lo2], x1 = sb[hi2];
-              if ((x0 > x1) == up) { sb[lo2] = x1; sb[hi2] = x0; }
+          for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+#pragma unroll
+            for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+              const uint64_t o = __shfl_xor_sync(0xffffffffu, key, j2);
+              const bool up = (lane & k2) == 0, low = (lane & j2) == 0;
+              key = (low == up) ? (key < o ? key : o) : (key < o ? o : key);
             }
-            __syncwarp();
+          }
+          sb[lane] = key;
+          sb[lane + 32] = BDG_KEY_INF;
+          sb[lane + 64] = BDG_KEY_INF;
+          sb[lane + 96] = BDG_KEY_INF;
+          __syncwarp();
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int x = lane + 32 * q;
+            uint64_t key = BDG_KEY_INF;
+            if (x < n_r) {
+              const uint32_t e = cand[cidx(x, row)];
+              const int d = (int)(e >> kPosBits);
+              if (d <= tb) {
+                const int32_t hid = c.home_ids[h0 + (int)(e & kPosMask)];
+                if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
+              }
+            }
+            sb[x] = key;
+          }
+          __syncwarp();
+          // bitonic sort of 128 keys, ascending
+          for (int size = 2; size <= 128; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+              for (int q = 0; q < 2; ++q) {
+                const int i = lane + 32 * q;                           // pair index 0..63
+                const int lo2 = (i / stride) * (2 * stride) + (i % stride);
+                const int hi2 = lo2 + stride;
+                const bool up = (lo2 & size) == 0;
+                const uint64_t x0 = sb[lo2], x1 = sb[hi2];
+                if ((x0 > x1) == up) { sb[lo2] = x1; sb[hi2] = x0; }
+              }
+              __syncwarp();
+            }
           }
         }
         if (a.t == 1) {
