@@ -294,7 +294,7 @@ bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_
   c->b_cent = c->need_bk ? al((size_t)m * W * 8) : 0;
   c->b_bk = c->need_bk ? al(bdg_bkmeans_scratch_bytes(P->bk_sample_size, m, W)) : 0;
   c->b_csr = al(bdg_csr_bytes(N, m, t, W));
-  c->b_part = t > 1 ? al((size_t)N * t * k * 8) : 0;
+  c->b_part = t > 1 ? al((size_t)N * k * 8) : 0;  // running k-lists
   c->b_hexp = c->tc_ok ? al(bdg_knn_tc_hexp_bytes(N, m, W)) : 0;
   c->b_fix = c->tc_ok ? al((size_t)N * t) + al(64) : 0;
   c->total = c->b_routes + c->b_cent + c->b_bk + c->b_csr + c->b_part + c->b_hexp + c->b_fix;
@@ -345,17 +345,18 @@ bdg_status build_enqueue(const BuildCfg& c, bool use_tc, bdg_graph* g, const uin
                                  cent, nullptr, bk, c.b_bk, st));
     BDG_TRY(bdg_launch_route(codes, N, W, cent, m, t, routes, nullptr, st));
   }
-  if (P->routes != nullptr) {
-    // caller-given routes may leave slots unvisited (values outside [0, m)):
-    // those rows / partial lists must read as padding
-    if (t == 1) BDG_TRY(bdg_launch_fill_pad(g->ids, g->dists, N * (int64_t)k, bits, st));
-    else BDG_CUDA_TRY(cudaMemsetAsync(partial, 0xff, (size_t)N * t * k * 8, st));
+  if (t > 1) {  // running lists start empty (a point without a valid home keeps none)
+    BDG_CUDA_TRY(cudaMemsetAsync(partial, 0xff, (size_t)N * k * 8, st));
+  } else if (P->routes != nullptr) {  // rows of points without a valid home read as padding
+    BDG_TRY(bdg_launch_fill_pad(g->ids, g->dists, N * (int64_t)k, bits, st));
   }
   bdg_csr csr;
   BDG_TRY(bdg_build_csr(codes, N, W, routes, m, t, c.tile_v, csr_mem, &csr, st));
-  // Reduce 1 in two rounds: A = every point against its home partition, then
-  // B = the other probed partitions, each visitor starting from the k-th key of
-  // its home list (only closer keys can enter the merged top-k)
+  // Reduce 1: round A = every point against its home partition (it starts the
+  // point's running k-list); then one sub-round per further route slot, each
+  // point visiting one partition, its threshold starting at the k-th key of its
+  // running list and its row merged into that list (no two rows of a sub-round
+  // belong to the same point)
   bdg_knn_args a;
   a.codes = codes; a.N = N; a.m = m; a.t = t; a.k = k; a.bits = bits;
   a.tile_v = c.tile_v; a.partial = partial; a.out_ids = g->ids; a.out_dist = g->dists;
@@ -364,21 +365,22 @@ bdg_status build_enqueue(const BuildCfg& c, bool use_tc, bdg_graph* g, const uin
   // optional timing of the Reduce-1 step (recorded also inside a captured graph)
   if (ev0) BDG_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal));
   if (use_tc) BDG_CUDA_TRY(cudaMemsetAsync(fixflag, 0, al((size_t)N * t) + al(64), st));
-  for (int round = 0; round < (t > 1 ? 2 : 1); ++round) {
-    a.csr = round == 0 ? bdg_csr_round_a(csr) : csr;
-    a.item_counter = csr.counters + 2 * m + round;
+  for (int round = 0; round < t; ++round) {
+    a.csr = round == 0 ? bdg_csr_round_a(csr) : bdg_csr_subround(csr, round);
+    a.item_counter = csr.counters + (size_t)t * m + round;
     a.home_kth = round == 0 ? nullptr : partial;
+    a.merge_running = round == 0 ? 0 : 1;
     if (use_tc) {
       bdg_knn_tc_args ta;
       ta.base = a; ta.hexp = hexp; ta.err = tc_err;
-      ta.fixflag = fixflag + (round == 0 ? 0 : N);
+      ta.fixflag = fixflag + (round == 0 ? 0 : N);  // sub-round positions are absolute
       BDG_TRY(bdg_launch_knn_tc(ta, W, round == 0, st));
     } else {
       BDG_TRY(bdg_launch_knn_popc(a, W, st));
     }
   }
   if (ev1) BDG_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal));
-  if (t > 1) BDG_TRY(bdg_launch_merge(partial, N, t, k, bits, g->ids, g->dists, st));
+  if (t > 1) BDG_TRY(bdg_launch_finalize(partial, N, k, bits, g->ids, g->dists, st));
   return BDG_OK;
 }
 
@@ -615,6 +617,7 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
   a.out_by_pos = 1;
   a.fixflag = nullptr;
   a.home_kth = nullptr;
+  a.merge_running = 0;
   if (!use_tc) return bdg_launch_knn_popc(a, W, st);
   char* q = (char*)sc.p + b;
   bdg_knn_tc_args ta;

@@ -24,7 +24,7 @@ __global__ void count_kernel(const int32_t* __restrict__ routes, int64_t N, int 
   if (h >= 0 && h < m) atomicAdd(&hcnt[h], 1);  // route values outside [0, m) are ignored
   for (int s = 1; s < t; ++s) {  // slot 0 (the home) is visited in round A from H_p
     const int32_t p = routes[i * t + s];
-    if (p >= 0 && p < m) atomicAdd(&vcnt[p], 1);
+    if (p >= 0 && p < m) atomicAdd(&vcnt[(s - 1) * m + p], 1);
   }
 }
 
@@ -54,10 +54,12 @@ __device__ int32_t block_exclusive_scan(int32_t v, int32_t* warp_tot, int32_t* t
   return r;
 }
 
-// Single block: offsets of H_p and V_p, partition order by decreasing |H_p|,
-// item offsets in that order, and scatter cursors.
+// Single block: offsets of H_p and of the visits of every slot s >= 1 (each
+// slot's visits form one sub-round, laid out one after the other), partition
+// order by decreasing |H_p|, work-item offsets of round A and of every
+// sub-round in that order, and scatter cursors.
 __global__ void __launch_bounds__(kScanThreads)
-plan_kernel(int m, int tile_v, int32_t* __restrict__ hcnt, int32_t* __restrict__ vcnt,
+plan_kernel(int m, int t, int tile_v, int32_t* __restrict__ hcnt, int32_t* __restrict__ vcnt,
             int32_t* __restrict__ home_off, int32_t* __restrict__ visit_off,
             int32_t* __restrict__ part_order, int32_t* __restrict__ item_off,
             int32_t* __restrict__ eoff, int32_t* __restrict__ item_off_a) {
@@ -65,21 +67,33 @@ plan_kernel(int m, int tile_v, int32_t* __restrict__ hcnt, int32_t* __restrict__
   __shared__ int32_t warp_tot[32];
   __shared__ int32_t total;
   const int per = (m + kScanThreads - 1) / kScanThreads;
-  // --- exclusive scans of the two histograms (thread owns a contiguous run)
-  for (int which = 0; which < 2; ++which) {
-    int32_t* cnt = which ? vcnt : hcnt;
-    int32_t* off = which ? visit_off : home_off;
-    const int b = threadIdx.x * per, e = min(m, b + per);
+  const int b = threadIdx.x * per, e = min(m, b + per);
+  // --- homes
+  {
+    int32_t s = 0;
+    for (int p = b; p < e; ++p) s += hcnt[p];
+    int32_t run = block_exclusive_scan(s, warp_tot, &total);
+    for (int p = b; p < e; ++p) { home_off[p] = run; run += hcnt[p]; }
+    if (threadIdx.x == 0) home_off[m] = total;
+    __syncthreads();
+  }
+  // --- visits of slots 1 .. t-1, one block of positions per slot
+  int32_t base = 0;
+  for (int sl = 1; sl < t; ++sl) {
+    const int32_t* cnt = vcnt + (sl - 1) * m;
+    int32_t* off = visit_off + (sl - 1) * (m + 1);
     int32_t s = 0;
     for (int p = b; p < e; ++p) s += cnt[p];
     int32_t run = block_exclusive_scan(s, warp_tot, &total);
+    run += base;
     for (int p = b; p < e; ++p) { off[p] = run; run += cnt[p]; }
-    if (threadIdx.x == 0) off[m] = total;
+    const int32_t tot = total;
+    if (threadIdx.x == 0) off[m] = base + tot;
+    base += tot;
     __syncthreads();
   }
   // --- offsets of the 64-row-padded expanded home operand (tensor path)
   {
-    const int b = threadIdx.x * per, e = min(m, b + per);
     int32_t s = 0;
     for (int p = b; p < e; ++p) s += (hcnt[p] + 63) & ~63;
     int32_t run = block_exclusive_scan(s, warp_tot, &total);
@@ -108,37 +122,24 @@ plan_kernel(int m, int tile_v, int32_t* __restrict__ hcnt, int32_t* __restrict__
   }
   for (int r = threadIdx.x; r < m; r += kScanThreads) part_order[r] = (int32_t)(skey[r] & 0xffffffffu);
   __syncthreads();
-  // --- item offsets in partition order
-  {
-    const int b = threadIdx.x * per, e = min(m, b + per);
+  // --- work items in partition order: round A (homes), then each sub-round
+  for (int sl = 0; sl < t; ++sl) {
+    const int32_t* cnt = sl == 0 ? hcnt : vcnt + (sl - 1) * m;
+    int32_t* io = sl == 0 ? item_off_a : item_off + (sl - 1) * (m + 1);
     int32_t s = 0;
-    for (int r = b; r < e; ++r) {
-      const int p = part_order[r];
-      s += (vcnt[p] + tile_v - 1) / tile_v;  // empty H_p still pads its visitors
-    }
+    for (int r = b; r < e; ++r) s += (cnt[part_order[r]] + tile_v - 1) / tile_v;
     int32_t run = block_exclusive_scan(s, warp_tot, &total);
     for (int r = b; r < e; ++r) {
-      const int p = part_order[r];
-      item_off[r] = run;
-      run += (vcnt[p] + tile_v - 1) / tile_v;
+      io[r] = run;
+      run += (cnt[part_order[r]] + tile_v - 1) / tile_v;  // an empty H_p still pads its visitors
     }
-    if (threadIdx.x == 0) item_off[m] = total;
+    if (threadIdx.x == 0) io[m] = total;
     __syncthreads();
-    // round A: every home visits its own partition
-    s = 0;
-    for (int r = b; r < e; ++r) s += (hcnt[part_order[r]] + tile_v - 1) / tile_v;
-    run = block_exclusive_scan(s, warp_tot, &total);
-    for (int r = b; r < e; ++r) {
-      item_off_a[r] = run;
-      run += (hcnt[part_order[r]] + tile_v - 1) / tile_v;
-    }
-    if (threadIdx.x == 0) item_off_a[m] = total;
   }
-  __syncthreads();
   // --- scatter cursors start at the offsets
   for (int p = threadIdx.x; p < m; p += kScanThreads) {
     hcnt[p] = home_off[p];
-    vcnt[p] = visit_off[p];
+    for (int sl = 1; sl < t; ++sl) vcnt[(sl - 1) * m + p] = visit_off[(sl - 1) * (m + 1) + p];
   }
 }
 
@@ -153,7 +154,7 @@ __global__ void scatter_kernel(const int32_t* __restrict__ routes, int64_t N, in
   for (int s = 1; s < t; ++s) {
     const int32_t p = routes[i * t + s];
     if (p < 0 || p >= m) continue;
-    const int32_t pos = atomicAdd(&vcur[p], 1);
+    const int32_t pos = atomicAdd(&vcur[(s - 1) * m + p], 1);
     visit_ids[pos] = (int32_t)i;
     visit_slot[pos] = (int8_t)s;
   }
@@ -215,6 +216,8 @@ bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* r
   c->home_codes = const_cast<uint64_t*>(codes);  // identity order: read the codes in place
   c->item_off_a = c->item_off;
   c->slot_zero = c->visit_slot;
+  c->m = 1;
+  c->t = 1;
   BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, 8 * 4, st));
   const int64_t n = N > nrows ? N : nrows;
   rows_plan_kernel<<<bdg_cdiv(n, 256), 256, 0, st>>>(N, rows, nrows, tile_v, c->home_off,
@@ -227,8 +230,9 @@ bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* r
 }
 
 size_t bdg_csr_bytes(int64_t N, int m, int t, int W) {
-  return al((m + 1) * 4) * 5 + al(N * 4) + al(N * W * 8) + al(N * t * 4) + al(N * t) +
-         al(m * 4) + al((2 * (size_t)m + 4) * 4) + al(N);
+  const size_t ts = t > 1 ? (size_t)(t - 1) : 1;
+  return al((m + 1) * 4) * 3 + al(ts * (m + 1) * 4) * 2 + al(N * 4) + al(N * W * 8) +
+         al(N * t * 4) + al(N * t) + al(m * 4) + al(bdg_csr_counter_words(m, t) * 4) + al(N);
 }
 
 bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
@@ -236,9 +240,10 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   if (m > kMaxSortM)
     return bdg_set_error(BDG_EUNSUPPORTED, "m = %d partitions exceeds %d", m, kMaxSortM);
   char* p = (char*)mem;
+  const size_t ts = t > 1 ? (size_t)(t - 1) : 1;
   c->home_off = (int32_t*)p;   p += al((m + 1) * 4);
-  c->visit_off = (int32_t*)p;  p += al((m + 1) * 4);
-  c->item_off = (int32_t*)p;   p += al((m + 1) * 4);
+  c->visit_off = (int32_t*)p;  p += al(ts * (m + 1) * 4);
+  c->item_off = (int32_t*)p;   p += al(ts * (m + 1) * 4);
   c->eoff = (int32_t*)p;       p += al((m + 1) * 4);
   c->home_ids = (int32_t*)p;   p += al(N * 4);
   c->home_codes = (uint64_t*)p; p += al(N * W * 8);
@@ -250,7 +255,13 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   c->counters = (int32_t*)p;
   int32_t* hcnt = c->counters;
   int32_t* vcnt = c->counters + m;
-  BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, (2 * (size_t)m + 4) * 4, st));
+  c->m = m;
+  c->t = t;
+  BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, bdg_csr_counter_words(m, t) * 4, st));
+  if (t == 1) {  // no sub-rounds: empty visit lists
+    BDG_CUDA_TRY(cudaMemsetAsync(c->visit_off, 0, (m + 1) * 4, st));
+    BDG_CUDA_TRY(cudaMemsetAsync(c->item_off, 0, (m + 1) * 4, st));
+  }
   BDG_CUDA_TRY(cudaMemsetAsync(c->slot_zero, 0, N, st));
   const int g = bdg_cdiv(N, 256);
   count_kernel<<<g, 256, 0, st>>>(routes, N, t, m, hcnt, vcnt);
@@ -261,7 +272,7 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   const size_t smem = (size_t)np2 * 8;
   BDG_CUDA_TRY(cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-  plan_kernel<<<1, kScanThreads, smem, st>>>(m, tile_v, hcnt, vcnt, c->home_off, c->visit_off,
+  plan_kernel<<<1, kScanThreads, smem, st>>>(m, t, tile_v, hcnt, vcnt, c->home_off, c->visit_off,
                                              c->part_order, c->item_off, c->eoff,
                                              c->item_off_a);
   BDG_CUDA_TRY(cudaGetLastError());

@@ -89,7 +89,17 @@ struct bdg_csr {
   // other probed partitions (slots >= 1, round B)
   int32_t* item_off_a; // [m + 1]  work items of round A in part_order order
   int8_t* slot_zero;   // [N]      zeros: the route slot of every round-A visit
+  int m, t;
 };
+// The visits of slot s >= 1 form sub-round s: visit_off / item_off hold t - 1
+// consecutive [m + 1] arrays (positions are absolute in visit_ids).
+inline size_t bdg_csr_counter_words(int m, int t) { return (size_t)t * m + t + 8; }
+inline bdg_csr bdg_csr_subround(const bdg_csr& c, int s) {
+  bdg_csr v = c;
+  v.visit_off = c.visit_off + (size_t)(s - 1) * (c.m + 1);
+  v.item_off = c.item_off + (size_t)(s - 1) * (c.m + 1);
+  return v;
+}
 // The CSR view of round A (visitors = homes).
 inline bdg_csr bdg_csr_round_a(const bdg_csr& c) {
   bdg_csr a = c;
@@ -120,10 +130,53 @@ struct bdg_knn_args {
   int32_t* item_counter;  // zeroed before launch
   int out_by_pos;         // t == 1: write row i of the output for the i-th visitor (not its id)
   const int8_t* fixflag;  // [N * t] or NULL: only visit positions flagged 1 are computed
-  // round B: a visitor's threshold starts at the k-th key of its home list
-  // (partial[v][0][k-1]); nothing beyond it can enter the merged top-k. NULL = none.
+  // sub-rounds: a visitor's threshold starts at the k-th key of its running list
+  // (nothing beyond it can enter the final top-k). NULL = none.
   const uint64_t* home_kth;
+  // t > 1: `partial` is the running list [N][k]; round A writes it, the
+  // sub-rounds merge their rows into it
+  int merge_running;
 };
+
+// Merge a warp's sorted row L (len keys, then anything >= pad) into the sorted
+// running list R[0..k) of the same point (global memory): R becomes the k
+// smallest keys of both. The valid keys of R and L are distinct (they come from
+// disjoint home sets), so every key's rank is its index plus the number of
+// smaller keys in the other list.
+__device__ __forceinline__ int bdg_lower_bound(const uint64_t* a, int n, uint64_t x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ void bdg_warp_merge_running(uint64_t* R, const uint64_t* L, int len,
+                                                       int k, uint64_t pad, int lane) {
+  const int nr = bdg_lower_bound(R, k, pad);
+  const int nl = bdg_lower_bound(L, len, pad);
+  uint64_t rv[4], lv[4];
+  int rp[4], lp[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = lane + 32 * q;
+    rp[q] = k;
+    lp[q] = k;
+    rv[q] = 0;
+    lv[q] = 0;
+    if (j < nr) { rv[q] = R[j]; rp[q] = j + bdg_lower_bound(L, nl, rv[q]); }
+    if (j < nl) { lv[q] = L[j]; lp[q] = j + bdg_lower_bound(R, nr, lv[q]); }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (rp[q] < k) R[rp[q]] = rv[q];
+    if (lp[q] < k) R[lp[q]] = lv[q];
+  }
+  const int total = nr + nl < k ? nr + nl : k;
+  for (int j = total + lane; j < k; j += 32) R[j] = pad;
+  __syncwarp();
+}
 // knn_tc.cu: tensor-core (tcgen05, FP8 +-1) Reduce 1 for 256/512-bit codes and k <= 64.
 struct bdg_knn_tc_args {
   bdg_knn_args base;
@@ -136,8 +189,8 @@ size_t bdg_knn_tc_hexp_bytes(int64_t N, int m, int W);
 bdg_status bdg_launch_knn_tc(const bdg_knn_tc_args& a, int W, bool expand, cudaStream_t st);
 bdg_status bdg_launch_knn_popc(const bdg_knn_args& a, int W, cudaStream_t st);
 // merge.cu
-bdg_status bdg_launch_merge(const uint64_t* partial, int64_t N, int t, int k, int bits,
-                            int32_t* ids, int32_t* dist, cudaStream_t st);
+bdg_status bdg_launch_finalize(const uint64_t* running, int64_t N, int k, int bits, int32_t* ids,
+                               int32_t* dist, cudaStream_t st);
 bdg_status bdg_launch_fill_pad(int32_t* ids, int32_t* dist, int64_t count, int bits,
                                cudaStream_t st);
 bdg_status bdg_launch_gather_codes(const uint64_t* codes, int64_t N, const int32_t* ids, int64_t n,

@@ -167,8 +167,7 @@ knn_popc_kernel(bdg_knn_args a) {
       // idle rows and rows of invalid visitor ids accept nothing; in round B a
       // row starts from the k-th key of the visitor's home list
       uint64_t th0 = (r < nv && s.vid[r] >= 0) ? BDG_KEY_INF : 0ull;
-      if (a.home_kth != nullptr && th0 != 0ull)
-        th0 = a.home_kth[((int64_t)s.vid[r] * a.t) * k + (k - 1)];
+      if (a.home_kth != nullptr && th0 != 0ull) th0 = a.home_kth[(int64_t)s.vid[r] * k + (k - 1)];
       s.thr[r] = th0;
     }
     if (a.fixflag != nullptr) {  // skip items without a flagged row
@@ -238,9 +237,11 @@ knn_popc_kernel(bdg_knn_args a) {
           a.out_ids[row * k + j] = j < len ? bdg_key_id(key) : -1;
           a.out_dist[row * k + j] = bdg_key_d(key);
         }
-      } else {
-        uint64_t* out = a.partial + ((int64_t)id * a.t + s.vslot[v]) * k;
+      } else if (!a.merge_running) {  // round A: the running list starts as this row
+        uint64_t* out = a.partial + (int64_t)id * k;
         for (int j = lane; j < k; j += 32) out[j] = j < len ? L[j] : pad;
+      } else {
+        bdg_warp_merge_running(a.partial + (int64_t)id * k, L, len, k, pad, lane);
       }
     }
     __syncthreads();

@@ -275,9 +275,9 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       // like any other value and dropped at selection, so k + 1 values are needed
       const int need_k = k + ((live && c.visit_slot[v0 + r] == 0) ? 1 : 0);
       int thr_d = live ? bits : -1;  // accept d <= thr_d; idle rows keep nothing
-      if (live && a.home_kth != nullptr) {  // round B: start from the home list's k-th key
-        const int dh = bdg_key_d(a.home_kth[((int64_t)c.visit_ids[v0 + r] * a.t) * k + (k - 1)]);
-        thr_d = dh < thr_d ? dh : thr_d;
+      if (live && a.home_kth != nullptr) {  // sub-round: start from the running list's k-th key
+        const uint64_t kth = a.home_kth[(int64_t)c.visit_ids[v0 + r] * k + (k - 1)];
+        if (kth < bdg_pad_key(bits)) thr_d = min(thr_d, bdg_key_d(kth));  // else no bound yet
       }
       int cnt = 0;   // entries in the row's candidate list
       int cle = 0;   // values seen so far with d <= thr_d (all of them are in the list)
@@ -402,7 +402,6 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         if (row >= nv) continue;
         const int32_t vid = c.visit_ids[v0 + row];
         if (vid < 0) continue;
-        const int slot = c.visit_slot[v0 + row];
         if (ovf) {  // recomputed by the popcount kernel
           if (lane == 0) ta.fixflag[v0 + row] = 1;
           continue;
@@ -471,9 +470,11 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             a.out_ids[orow * k + j2] = key < pad ? bdg_key_id(key) : -1;
             a.out_dist[orow * k + j2] = bdg_key_d(key);
           }
-        } else {
-          uint64_t* out = a.partial + ((int64_t)vid * a.t + slot) * k;
+        } else if (!a.merge_running) {  // round A: the running list starts as this row
+          uint64_t* out = a.partial + (int64_t)vid * k;
           for (int j2 = lane; j2 < k; j2 += 32) out[j2] = sb[j2] < pad ? sb[j2] : pad;
+        } else {
+          bdg_warp_merge_running(a.partial + (int64_t)vid * k, sb, k, k, pad, lane);
         }
         __syncwarp();
       }
