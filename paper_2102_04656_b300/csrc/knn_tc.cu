@@ -401,7 +401,16 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         const int ovf = __shfl_sync(0xffffffffu, overflow ? 1 : 0, rr);
         if (row >= nv) continue;
         const int32_t vid = c.visit_ids[v0 + row];
-        if (vid < 0) continue;
+        if (vid < 0) {  // an invalid id: its row (written by position) is padding
+          if (a.t == 1 && a.out_by_pos) {
+            const int64_t orow = (int64_t)(tile * kM + row);
+            for (int j2 = lane; j2 < k; j2 += 32) {
+              a.out_ids[orow * k + j2] = -1;
+              a.out_dist[orow * k + j2] = bits + 1;
+            }
+          }
+          continue;
+        }
         if (ovf) {  // recomputed by the popcount kernel
           if (lane == 0) ta.fixflag[v0 + row] = 1;
           continue;

@@ -28,15 +28,18 @@ class TrainConfig:
     k_labels: int = 32
 
 
-def neighbour_labels(codes_sample, home_sample, k: int, entry=None):
+def neighbour_labels(codes_sample, home_sample, k: int, entry=None, skip_home: bool = True):
     """Home partitions of each sample point's exact k nearest neighbours within
-    the sample: int32 [S, k] (-1 where a row has fewer than k neighbours)."""
-    S = codes_sample.shape[0]
+    the sample: int32 [S, k]. -1 marks a missing neighbour and, with skip_home,
+    a neighbour living in the point's own home partition: the home is always
+    probed, so the router only has to learn where the other neighbours live."""
     if entry is None:
         entry = torch.zeros(1, dtype=torch.int32, device=codes_sample.device)
     g = build_graph(codes_sample, k, m=1, t=1, entry=entry)
     ids = g.ids.long()
     lab = torch.where(ids >= 0, home_sample[ids.clamp(min=0)], torch.full_like(ids, -1))
+    if skip_home:
+        lab = torch.where(lab == home_sample[:, None], torch.full_like(lab, -1), lab)
     out = lab.to(torch.int32).contiguous()
     g.free()
     return out
