@@ -412,7 +412,7 @@ def _learned_bench(bdg, device, kernel, n=10_000_000):
     torch.cuda.synchronize()
     out["labels_s"] = time.perf_counter() - t0
     init = torch.from_numpy(datagen.router_init(base.dim, 512, 512, m, spec.seed + 5)).to(device)
-    cfg = learned.TrainConfig(hidden=(512, 512), batch=4096, epochs=6, lr=2e-3)
+    cfg = learned.TrainConfig(hidden=(512, 512), batch=4096, epochs=6, lr=1e-3)
     losses = []
     t0 = time.perf_counter()
     router = learned.train_router(xb[tr].contiguous(), labels, m, init, cfg, seed=spec.seed + 5,

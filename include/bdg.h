@@ -254,7 +254,9 @@ void bdg_server_free(bdg_server* s);
  * neighbours live:
  *   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2), z = h2 W3^T + b3 (FP32 accumulate)
  *   loss = -(1/B) sum_i sum_p q_ip log softmax(z_i)_p,
- *   q_ip = #{j in labels[i] : j == p} / kt   (labels: home partitions of i's neighbours)
+ *   q_ip = #{j in labels[i] : j == p} / #{valid labels of i}
+ *   (labels: partitions where i's neighbours live, -1 = none; a row without a
+ *   valid label contributes neither loss nor gradient)
  * Adam (beta 0.9 / 0.999, eps 1e-8) on FP32 master weights with BF16 copies. */
 typedef struct bdg_router bdg_router;
 

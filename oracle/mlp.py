@@ -9,8 +9,10 @@ partitions instead. The oracle states the network and its gradients plainly:
   z  = h2 W3^T + b3               z: [B, m] logits, one per partition
   loss = -(1/B) sum_i sum_p q_ip log softmax(z_i)_p
 
-with q_i the target distribution over partitions (the share of point i's exact
-neighbours whose home partition is p). Gradients are the analytic chain rule;
+with q_i the target distribution over partitions: the empirical distribution of
+the partitions given as point i's labels (the homes of its exact neighbours).
+A row without any label has no target and contributes neither loss nor
+gradient. Gradients are the analytic chain rule;
 ``adam`` is Kingma & Ba's update with bias correction.
 
 With ``bf16=True`` the float64 computation rounds to bfloat16 (round to nearest,
@@ -65,9 +67,10 @@ def loss_and_grads(params, x, q, bf16=True):
     B = z.shape[0]
     p = softmax(z)
     q = np.asarray(q, np.float64)
+    has = (q.sum(axis=1) > 0)[:, None]  # rows with a target
     logp = np.log(np.maximum(p, 1e-300))
     loss = float(-(q * logp).sum() / B)
-    dz = (p - q) / B
+    dz = (p - q) / B * has
     dzq = _q(dz, bf16)
     g = {}
     g["W3"] = dzq.T @ c["h2"]
@@ -108,13 +111,22 @@ def topp(z, P):
     return out
 
 
-def neighbour_partition_targets(knn_ids, home, m):
-    """q_ip = #{j in G*(i) : home(j) = p} / k (ids -1 ignored, k = row width)."""
-    knn_ids = np.asarray(knn_ids)
-    B, k = knn_ids.shape
+def label_targets(labels, m):
+    """q_ip = #{labels of row i equal to p} / #{labels of row i in [0, m)}
+    (a row without valid labels gets q = 0)."""
+    labels = np.asarray(labels)
+    B = labels.shape[0]
     q = np.zeros((B, m), np.float64)
     for i in range(B):
-        for j in knn_ids[i]:
-            if j >= 0:
-                q[i, home[j]] += 1.0 / k
+        valid = [int(p) for p in labels[i] if 0 <= p < m]
+        for p in valid:
+            q[i, p] += 1.0 / len(valid)
     return q
+
+
+def neighbour_partition_targets(knn_ids, home, m):
+    """Targets from neighbour lists: the labels are home(j) for the listed
+    neighbours j (ids -1 ignored)."""
+    knn_ids = np.asarray(knn_ids)
+    labels = np.where(knn_ids >= 0, np.asarray(home)[np.maximum(knn_ids, 0)], -1)
+    return label_targets(labels, m)

@@ -16,12 +16,71 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kMaxSortM = 16384;  // partitions sortable by the single-block bitonic sort
 
+// ---- stable placement of the homes: H_p lists point ids in ascending order
+// (so a home's position within its partition orders like its id). Points are
+// cut into blocks of `bp` consecutive ids: each block counts its homes per
+// partition, a column scan turns the counts into each block's start within
+// every H_p, and one warp per block then walks its points in order.
+__global__ void home_block_count(const int32_t* __restrict__ routes, int64_t N, int t, int m,
+                                 int bp, int32_t* __restrict__ bcnt) {
+  extern __shared__ int32_t sc[];  // [m]
+  for (int p = threadIdx.x; p < m; p += blockDim.x) sc[p] = 0;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * bp, i1 = min(N, i0 + bp);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const int32_t h = routes[i * t];
+    if (h >= 0 && h < m) atomicAdd(&sc[h], 1);
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < m; p += blockDim.x) bcnt[(int64_t)blockIdx.x * m + p] = sc[p];
+}
+
+// hcnt[p] = total homes of p; bcnt[b][p] becomes the block's start within H_p
+__global__ void home_block_scan(int m, int nblk, int32_t* __restrict__ bcnt,
+                                int32_t* __restrict__ hcnt) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  int32_t run = 0;
+  for (int b = 0; b < nblk; ++b) {
+    const int32_t c = bcnt[(int64_t)b * m + p];
+    bcnt[(int64_t)b * m + p] = run;
+    run += c;
+  }
+  hcnt[p] = run;
+}
+
+__global__ void __launch_bounds__(32)
+home_place(const int32_t* __restrict__ routes, int64_t N, int t, int m, int bp,
+           const int32_t* __restrict__ bcnt, const int32_t* __restrict__ home_off,
+           int32_t* __restrict__ home_ids) {
+  extern __shared__ int32_t cur[];  // [m] next position of this block in each H_p
+  const int lane = threadIdx.x;
+  for (int p = lane; p < m; p += 32)
+    cur[p] = home_off[p] + bcnt[(int64_t)blockIdx.x * m + p];
+  __syncwarp();
+  const int64_t i0 = (int64_t)blockIdx.x * bp, i1 = min(N, i0 + bp);
+  for (int64_t c0 = i0; c0 < i1; c0 += 32) {
+    const int64_t i = c0 + lane;
+    int32_t h = (i < i1) ? routes[i * t] : -1;
+    if (h < 0 || h >= m) h = -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, h);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const int32_t base = (h >= 0) ? cur[h] : 0;
+    __syncwarp();
+    if (h >= 0) {
+      home_ids[base + rank] = (int32_t)i;
+      if (rank == 0) cur[h] = base + __popc(peers);  // the group's first lane advances it
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void count_kernel(const int32_t* __restrict__ routes, int64_t N, int t, int m,
-                             int32_t* __restrict__ hcnt, int32_t* __restrict__ vcnt) {
+                             int32_t* __restrict__ vcnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const int32_t h = routes[i * t];
-  if (h >= 0 && h < m) atomicAdd(&hcnt[h], 1);  // route values outside [0, m) are ignored
+  // homes are counted and placed in id order by the stable pass below; route
+  // values outside [0, m) are ignored
   for (int s = 1; s < t; ++s) {  // slot 0 (the home) is visited in round A from H_p
     const int32_t p = routes[i * t + s];
     if (p >= 0 && p < m) atomicAdd(&vcnt[(s - 1) * m + p], 1);
@@ -144,13 +203,10 @@ plan_kernel(int m, int t, int tile_v, int32_t* __restrict__ hcnt, int32_t* __res
 }
 
 __global__ void scatter_kernel(const int32_t* __restrict__ routes, int64_t N, int t, int m,
-                               int32_t* __restrict__ hcur, int32_t* __restrict__ vcur,
-                               int32_t* __restrict__ home_ids, int32_t* __restrict__ visit_ids,
+                               int32_t* __restrict__ vcur, int32_t* __restrict__ visit_ids,
                                int8_t* __restrict__ visit_slot) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const int32_t h = routes[i * t];
-  if (h >= 0 && h < m) home_ids[atomicAdd(&hcur[h], 1)] = (int32_t)i;
   for (int s = 1; s < t; ++s) {
     const int32_t p = routes[i * t + s];
     if (p < 0 || p >= m) continue;
@@ -229,10 +285,19 @@ bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* r
   return BDG_OK;
 }
 
+// points per block of the stable home placement (block counts stay <= 64M words)
+int bdg_home_block(int64_t N, int m) {
+  int64_t bp = 4096;
+  while ((N + bp - 1) / bp * (int64_t)m > (64LL << 20)) bp *= 2;
+  return (int)bp;
+}
+
 size_t bdg_csr_bytes(int64_t N, int m, int t, int W) {
   const size_t ts = t > 1 ? (size_t)(t - 1) : 1;
+  const size_t blk = (size_t)((N + bdg_home_block(N, m) - 1) / bdg_home_block(N, m)) * m * 4;
   return al((m + 1) * 4) * 3 + al(ts * (m + 1) * 4) * 2 + al(N * 4) + al(N * W * 8) +
-         al(N * t * 4) + al(N * t) + al(m * 4) + al(bdg_csr_counter_words(m, t) * 4) + al(N);
+         al(N * t * 4) + al(N * t) + al(m * 4) + al(bdg_csr_counter_words(m, t) * 4) + al(N) +
+         al(blk);
 }
 
 bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
@@ -252,6 +317,8 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   c->part_order = (int32_t*)p; p += al(m * 4);
   c->item_off_a = (int32_t*)p; p += al((m + 1) * 4);
   c->slot_zero = (int8_t*)p;   p += al(N);
+  c->home_blocks = (int32_t*)p;
+  p += al((size_t)((N + bdg_home_block(N, m) - 1) / bdg_home_block(N, m)) * m * 4);
   c->counters = (int32_t*)p;
   int32_t* hcnt = c->counters;
   int32_t* vcnt = c->counters + m;
@@ -264,7 +331,22 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   }
   BDG_CUDA_TRY(cudaMemsetAsync(c->slot_zero, 0, N, st));
   const int g = bdg_cdiv(N, 256);
-  count_kernel<<<g, 256, 0, st>>>(routes, N, t, m, hcnt, vcnt);
+  // homes: stable, in id order
+  const int bp = bdg_home_block(N, m);
+  const int nblk = bdg_cdiv(N, bp);
+  int32_t* bcnt = c->home_blocks;
+  const size_t sm_m = (size_t)m * 4;
+  BDG_CUDA_TRY(cudaFuncSetAttribute(home_block_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm_m));
+  BDG_CUDA_TRY(cudaFuncSetAttribute(home_place, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm_m));
+  home_block_count<<<nblk, 256, sm_m, st>>>(routes, N, t, m, bp, bcnt);
+  BDG_CUDA_TRY(cudaGetLastError());
+  home_block_scan<<<bdg_cdiv(m, 128), 128, 0, st>>>(m, nblk, bcnt, hcnt);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch(2);
+  // visits of slots >= 1 (their order within a list does not matter)
+  count_kernel<<<g, 256, 0, st>>>(routes, N, t, m, vcnt);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   int np2 = 1;
@@ -277,10 +359,11 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
                                              c->item_off_a);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
-  scatter_kernel<<<g, 256, 0, st>>>(routes, N, t, m, hcnt, vcnt, c->home_ids, c->visit_ids,
-                                    c->visit_slot);
+  home_place<<<nblk, 32, sm_m, st>>>(routes, N, t, m, bp, bcnt, c->home_off, c->home_ids);
   BDG_CUDA_TRY(cudaGetLastError());
-  bdg_note_launch();
+  scatter_kernel<<<g, 256, 0, st>>>(routes, N, t, m, vcnt, c->visit_ids, c->visit_slot);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch(2);
   gather_home_codes<<<bdg_cdiv(N * W, 256), 256, 0, st>>>(codes, c->home_ids, c->home_off, m, N,
                                                           W, c->home_codes);
   BDG_CUDA_TRY(cudaGetLastError());

@@ -89,8 +89,10 @@ struct bdg_csr {
   // other probed partitions (slots >= 1, round B)
   int32_t* item_off_a; // [m + 1]  work items of round A in part_order order
   int8_t* slot_zero;   // [N]      zeros: the route slot of every round-A visit
+  int32_t* home_blocks;// [blocks][m] scratch of the stable home placement
   int m, t;
 };
+int bdg_home_block(int64_t N, int m);
 // The visits of slot s >= 1 form sub-round s: visit_off / item_off hold t - 1
 // consecutive [m + 1] arrays (positions are absolute in visit_ids).
 inline size_t bdg_csr_counter_words(int m, int t) { return (size_t)t * m + t + 8; }

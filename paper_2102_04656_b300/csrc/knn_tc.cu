@@ -269,18 +269,21 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       }
     } else {
       // ---------------- epilogue: thread r owns visitor row r (TMEM lane r)
+      // A candidate word is (d << 21) | position of the home in H_p. The homes of
+      // a partition are stored in ascending id order, so word order is exactly
+      // (d, id) order: the row keeps an exact threshold on words.
       const int r = tid;
       const bool live = r < nv && c.visit_ids[v0 + r] >= 0;
       // v is one of its own partition's homes: its self pair (d = 0) is counted
       // like any other value and dropped at selection, so k + 1 values are needed
       const int need_k = k + ((live && c.visit_slot[v0 + r] == 0) ? 1 : 0);
-      int thr_d = live ? bits : -1;  // accept d <= thr_d; idle rows keep nothing
-      if (live && a.home_kth != nullptr) {  // sub-round: start from the running list's k-th key
+      uint32_t thr_w = live ? 0xFFFFFFFFu : 0u;  // accept word < thr_w
+      if (live && a.home_kth != nullptr) {  // sub-round: the running k-th key bounds d
         const uint64_t kth = a.home_kth[(int64_t)c.visit_ids[v0 + r] * k + (k - 1)];
-        if (kth < bdg_pad_key(bits)) thr_d = min(thr_d, bdg_key_d(kth));  // else no bound yet
+        if (kth < bdg_pad_key(bits)) thr_w = (uint32_t)(bdg_key_d(kth) + 1) << kPosBits;
       }
       int cnt = 0;   // entries in the row's candidate list
-      int cle = 0;   // values seen so far with d <= thr_d (all of them are in the list)
+      int cle = 0;   // entries with word < thr_w (every value seen below thr_w is listed)
       bool overflow = false;
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
       const float hbits = 0.5f * (float)bits;  // d = (bits - dot) / 2 = dot * -0.5 + bits / 2
@@ -306,36 +309,65 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
 #pragma unroll
         for (int half = 0; half < kNT / kHalf; ++half) {
           if (cnt > kCap - kHalf) {
-            // the histogram cannot place the threshold (outside its window or a
-            // saturated bin): select the exact need_k-th smallest distance among
-            // the list, which holds every value seen with d <= thr_d
-            if (cle >= need_k && (thr_d >= kHB || hist[thr_d * kM + r] == 255)) {
-              int lo = 0, hi = thr_d;
-              while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                int c2 = 0;
-                for (int x = 0; x < cnt; ++x) c2 += ((int)(crow[x * kCandStride] >> kPosBits) <= mid);
-                if (c2 >= need_k) hi = mid; else lo = mid + 1;
+            // compaction: the exact need_k-th smallest word of the list becomes the
+            // threshold, keeping exactly need_k entries (words are distinct)
+            if (cle >= need_k) {
+              int dk = (int)((thr_w - 1u) >> kPosBits);
+              if (dk > bits) dk = bits;
+              int c_lt = 0;
+              for (int x = 0; x < cnt; ++x) {
+                const uint32_t e = crow[x * kCandStride];
+                c_lt += (e < thr_w && (int)(e >> kPosBits) < dk);
               }
-              thr_d = lo;
+              if (c_lt >= need_k) {  // the k-th distance is below dk: binary search it
+                int lo = 0, hi = dk - 1;
+                while (lo < hi) {
+                  const int mid = (lo + hi) >> 1;
+                  int c2 = 0;
+                  for (int x = 0; x < cnt; ++x) {
+                    const uint32_t e = crow[x * kCandStride];
+                    c2 += (e < thr_w && (int)(e >> kPosBits) <= mid);
+                  }
+                  if (c2 >= need_k) hi = mid; else lo = mid + 1;
+                }
+                dk = lo;
+                c_lt = 0;
+                for (int x = 0; x < cnt; ++x) {
+                  const uint32_t e = crow[x * kCandStride];
+                  c_lt += (e < thr_w && (int)(e >> kPosBits) < dk);
+                }
+              }
+              // among the entries at distance dk, the (need_k - c_lt)-th smallest word
+              const int want = need_k - c_lt - 1;
+              uint32_t wk = ((uint32_t)dk << kPosBits) | kPosMask;
+              for (int x = 0; x < cnt; ++x) {
+                const uint32_t e = crow[x * kCandStride];
+                if (e >= thr_w || (int)(e >> kPosBits) != dk) continue;
+                int below = 0;
+                for (int y = 0; y < cnt; ++y) {
+                  const uint32_t f = crow[y * kCandStride];
+                  below += (f < e && (int)(f >> kPosBits) == dk);
+                }
+                if (below == want) wk = e;
+              }
+              thr_w = wk + 1u;
             }
-            // drop the candidates the threshold has since excluded
+            // keep the entries below the threshold
             int w = 0;
             for (int x = 0; x < cnt; ++x) {
               const uint32_t e = crow[x * kCandStride];
-              if ((int)(e >> kPosBits) <= thr_d) crow[(w++) * kCandStride] = e;
+              if (e < thr_w) crow[(w++) * kCandStride] = e;
             }
             cnt = w;
             cle = w;
             if (cnt > kCap - kHalf) {  // still full: the popcount kernel redoes this row
               overflow = true;
-              thr_d = -1;  // accept nothing more
+              thr_w = 0u;  // accept nothing more
               cnt = 0;     // (the row's list is no longer used)
             }
           }
-          // accept iff d <= thr_d  <=>  dot >= bits - 2 * thr_d; branch-free append:
-          // every value is written at the running slot, only accepted ones advance it
-          const float lim = (float)(bits - 2 * thr_d);
+          // branch-free append: every value is written at the running slot, only
+          // words below the threshold advance it
           const int c_before = cnt;
           uint32_t* wp = crow + cnt * kCandStride;
           const uint32_t posq = pos0 + (uint32_t)(half * kHalf);
@@ -344,8 +376,9 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             for (int c2 = 0; c2 < kHalf; ++c2) {
               const float dot = __uint_as_float(v[half * kHalf + c2]);
               const uint32_t d = (uint32_t)__float2int_rz(fmaf(dot, -0.5f, hbits));
-              *wp = d * (1u << kPosBits) + (posq + c2);
-              wp += (dot >= lim) ? kCandStride : 0;
+              const uint32_t word = d * (1u << kPosBits) + (posq + c2);
+              *wp = word;
+              wp += (word < thr_w) ? kCandStride : 0;
             }
           } else {
 #pragma unroll
@@ -353,8 +386,9 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
               const int cc = half * kHalf + c2;
               const float dot = __uint_as_float(v[cc]);
               const uint32_t d = (uint32_t)__float2int_rz(fmaf(dot, -0.5f, hbits));
-              *wp = d * (1u << kPosBits) + (posq + c2);
-              wp += (dot >= lim && cc < nvalid) ? kCandStride : 0;
+              const uint32_t word = d * (1u << kPosBits) + (posq + c2);
+              *wp = word;
+              wp += (word < thr_w && cc < nvalid) ? kCandStride : 0;
             }
           }
           cnt = (int)((wp - crow) / kCandStride);
@@ -371,12 +405,16 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
                 if (h < 255) h = (uint8_t)(h + 1);
               }
             }
-            // lower the threshold one distance at a time while k values stay below it
-            while (thr_d > 0 && thr_d < kHB) {
-              const int h = hist[thr_d * kM + r];
+            // lower the distance bound one step at a time while need_k values stay
+            // below it (hist may count values a compaction dropped: it only
+            // over-counts, so a lowering it allows is always safe)
+            int td = (int)((thr_w - 1u) >> kPosBits);
+            while (td > 0 && td < kHB) {
+              const int h = hist[td * kM + r];
               if (h == 255 || cle - h < need_k) break;
               cle -= h;
-              --thr_d;
+              --td;
+              thr_w = (uint32_t)(td + 1) << kPosBits;
             }
           }
         }
@@ -386,7 +424,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         int w = 0;
         for (int x = 0; x < cnt; ++x) {
           const uint32_t e = crow[x * kCandStride];
-          if ((int)(e >> kPosBits) <= thr_d) crow[(w++) * kCandStride] = e;
+          if (e < thr_w) crow[(w++) * kCandStride] = e;
         }
         cnt = w;
         if (cnt > kSortN) overflow = true;  // too many ties to sort here
@@ -397,7 +435,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       for (int rr = 0; rr < 32; ++rr) {
         const int row = warp * 32 + rr;
         const int n_r = __shfl_sync(0xffffffffu, cnt, rr);
-        const int tb = __shfl_sync(0xffffffffu, thr_d, rr);
+        const uint32_t tb = __shfl_sync(0xffffffffu, thr_w, rr);
         const int ovf = __shfl_sync(0xffffffffu, overflow ? 1 : 0, rr);
         if (row >= nv) continue;
         const int32_t vid = c.visit_ids[v0 + row];
@@ -421,7 +459,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           if (lane < n_r) {
             const uint32_t e = cand[cidx(lane, row)];
             const int d = (int)(e >> kPosBits);
-            if (d <= tb) {
+            if (e < tb) {
               const int32_t hid = c.home_ids[h0 + (int)(e & kPosMask)];
               if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
             }
@@ -448,7 +486,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             if (x < n_r) {
               const uint32_t e = cand[cidx(x, row)];
               const int d = (int)(e >> kPosBits);
-              if (d <= tb) {
+              if (e < tb) {
                 const int32_t hid = c.home_ids[h0 + (int)(e & kPosMask)];
                 if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
               }

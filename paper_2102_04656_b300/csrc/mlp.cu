@@ -7,7 +7,8 @@
 //
 //   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2), z = h2 W3^T + b3
 //   loss = -(1/B) sum_i sum_p q_ip log softmax(z_i)_p,
-//   q_ip = #{neighbours j of i with home(j) = p} / kt
+//   q_ip = #{labels of i equal to p} / #{valid labels of i}
+// (a row without a valid label contributes neither loss nor gradient)
 // Gradients by the chain rule (all products on the tcgen05 BF16 GEMM of
 // gemm_tc.cu with fused bias / ReLU / ReLU-mask / bias-gradient epilogues),
 // Adam with FP32 master weights and BF16 working copies.
@@ -114,9 +115,19 @@ softmax_ce(const float* __restrict__ z, int m, int B, const int32_t* __restrict_
   }
   __syncthreads();
   const float lse = zmax + logf(s_sum);
-  const float inv_b = 1.f / (float)B, inv_k = 1.f / (float)kt;
   const int32_t* lab = labels + (int64_t)i * kt;
+  int nval = 0;  // labels inside [0, m): the row's target is their empirical distribution
+  for (int j = 0; j < kt; ++j) nval += (lab[j] >= 0 && lab[j] < m);
+  const float inv_b = 1.f / (float)B;
   float* dzr = dz32 + (int64_t)i * m;
+  if (nval == 0) {  // no target: the row contributes neither loss nor gradient
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+      dzr[p] = 0.f;
+      dz16[(int64_t)i * m + p] = __float2bfloat16_rn(0.f);
+    }
+    return;
+  }
+  const float inv_k = 1.f / (float)nval;
   for (int p = threadIdx.x; p < m; p += blockDim.x) dzr[p] = expf(zr[p] - lse) * inv_b;
   __syncthreads();
   for (int j = threadIdx.x; j < kt; j += blockDim.x) {

@@ -50,7 +50,7 @@ def test_learned_router_gains_over_nearest_centre_probes(bdg):
     tr = torch.from_numpy(datagen.sample_ids(n, S, spec.seed + 5)).cuda()
     labels = learned.neighbour_labels(codes[tr].contiguous(), home[tr].contiguous(), k)
     init = torch.from_numpy(datagen.router_init(128, 256, 256, m, spec.seed + 5)).cuda()
-    cfg = learned.TrainConfig(hidden=(256, 256), batch=2048, epochs=6, lr=2e-3)
+    cfg = learned.TrainConfig(hidden=(256, 256), batch=2048, epochs=6, lr=1e-3)
     losses = []
     router = learned.train_router(xb[tr].contiguous(), labels, m, init, cfg, seed=spec.seed + 5,
                                   log=lambda ep, l: losses.append(l))

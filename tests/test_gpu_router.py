@@ -77,17 +77,12 @@ def _batch(B, d, m, kt, seed):
     rng = np.random.default_rng(seed)
     x = rng.standard_normal((B, d)).astype(np.float32)
     lab = rng.integers(-1, m, (B, kt)).astype(np.int32)  # -1 entries are ignored
+    lab[::17] = -1  # rows without any target
     return x, lab
 
 
 def _q(lab, m):
-    B, kt = lab.shape
-    q = np.zeros((B, m))
-    for i in range(B):
-        for j in lab[i]:
-            if j >= 0:
-                q[i, j] += 1.0 / kt
-    return q
+    return omlp.label_targets(lab, m)
 
 
 def test_router_forward_loss_and_gradients(bdg):

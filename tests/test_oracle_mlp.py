@@ -69,4 +69,18 @@ def test_topp_tie_order_and_targets():
     assert mlp.topp(z, 3).tolist() == [[1, 2, 0], [0, 1, 2]]
     home = np.array([0, 1, 1, 2, 0])
     q = mlp.neighbour_partition_targets(np.array([[1, 2, 3, -1]]), home, 3)
-    assert np.allclose(q, [[0.0, 0.5, 0.25]])
+    assert np.allclose(q, [[0.0, 2 / 3, 1 / 3]])  # normalised over the 3 valid labels
+    assert np.allclose(mlp.label_targets(np.array([[-1, -1], [2, 2]]), 3), [[0, 0, 0], [0, 0, 1]])
+
+
+def test_rows_without_target_have_no_gradient():
+    rng = np.random.default_rng(4)
+    p = _params(rng)
+    x = rng.standard_normal((3, 6))
+    q = np.zeros((3, 4))
+    q[1, 2] = 1.0
+    loss, g, z = mlp.loss_and_grads(p, x, q, bf16=False)
+    _, g1, _ = mlp.loss_and_grads(p, x[1:2], q[1:2], bf16=False)
+    # the two target-less rows change nothing but the 1/B normalisation
+    for name in g:
+        assert np.allclose(g[name] * 3, g1[name], rtol=1e-12, atol=1e-14)
