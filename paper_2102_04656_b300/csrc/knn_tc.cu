@@ -14,14 +14,16 @@
 //     accumulators (64 columns each), then tcgen05.commit frees the stage and
 //     hands the accumulator to the epilogue;
 //   * epilogue (4 warps, one thread per visitor row = TMEM lane): reads the 64
-//     dot products of its row, keeps a per-row histogram of distances in bins
-//     of 4 (8-bit saturating counters) for the values under its current
-//     threshold, and appends those values (d << 21 | home position) to a
-//     per-row candidate list in shared memory. The threshold is the bin that
-//     holds the row's k-th smallest distance so far; it only tightens, so
-//     every final neighbour is kept. A full list is compacted against the
-//     current threshold; a row whose list still overflows is flagged and
-//     recomputed exactly by the popcount kernel afterwards.
+//     dot products of its row and appends the values under its threshold as
+//     words (d << 21 | home position) to a per-row candidate list in shared
+//     memory. The homes of a partition are stored in ascending id order, so
+//     word order is (d, id) order. An exact per-row histogram of the listed
+//     distances (d < 256) lowers the threshold to the k-th smallest distance
+//     seen so far after every 16 values; it only tightens, so every final
+//     neighbour is kept. When a row's list is nearly full, the warp compacts
+//     all its rows together against their thresholds (with an exact word
+//     threshold if ties at the k-th distance fill the list); a row whose list
+//     still overflows is flagged and recomputed by the popcount kernel.
 // At the end of the item each warp selects, row by row, the k smallest
 // (d, id) keys among the candidates inside the final threshold (bitonic sort
 // of at most 128 keys) and writes the row's partial list.
@@ -134,6 +136,23 @@ __global__ void expand_homes_kernel(const uint64_t* __restrict__ home_codes,
 
 __device__ __forceinline__ uint32_t cidx(int c, int r) {  // candidate slot c of row r
   return (uint32_t)(c * kCandStride + r);
+}
+
+// Keep the row's candidates below thr_w, in order; the histogram of listed
+// distances (d < kHB) loses the dropped ones. Returns the new count.
+__device__ __forceinline__ int compact_row(uint32_t* crow, int cnt, uint32_t thr_w,
+                                           uint8_t* hist, int r) {
+  int w = 0;
+  for (int x = 0; x < cnt; ++x) {
+    const uint32_t e = crow[x * kCandStride];
+    if (e < thr_w) {
+      crow[(w++) * kCandStride] = e;
+    } else {
+      const uint32_t d = e >> kPosBits;
+      if (d < (uint32_t)kHB) hist[d * kM + r] = (uint8_t)(hist[d * kM + r] - 1);
+    }
+  }
+  return w;
 }
 
 template <int W>
@@ -308,58 +327,50 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         const int nvalid = min(kNT, nh - j * kNT);
 #pragma unroll
         for (int half = 0; half < kNT / kHalf; ++half) {
-          if (cnt > kCap - kHalf) {
-            // compaction: the exact need_k-th smallest word of the list becomes the
-            // threshold, keeping exactly need_k entries (words are distinct)
-            if (cle >= need_k) {
-              int dk = (int)((thr_w - 1u) >> kPosBits);
-              if (dk > bits) dk = bits;
-              int c_lt = 0;
-              for (int x = 0; x < cnt; ++x) {
-                const uint32_t e = crow[x * kCandStride];
-                c_lt += (e < thr_w && (int)(e >> kPosBits) < dk);
-              }
-              if (c_lt >= need_k) {  // the k-th distance is below dk: binary search it
-                int lo = 0, hi = dk - 1;
-                while (lo < hi) {
-                  const int mid = (lo + hi) >> 1;
-                  int c2 = 0;
-                  for (int x = 0; x < cnt; ++x) {
-                    const uint32_t e = crow[x * kCandStride];
-                    c2 += (e < thr_w && (int)(e >> kPosBits) <= mid);
-                  }
-                  if (c2 >= need_k) hi = mid; else lo = mid + 1;
-                }
-                dk = lo;
-                c_lt = 0;
+          // compaction, taken by the whole warp at once as soon as one row's list
+          // could not take another 16 values (lanes compacting one by one would
+          // serialise the warp)
+          if (__any_sync(0xffffffffu, cnt > kCap - kHalf)) {
+            int td = (int)((thr_w - 1u) >> kPosBits);
+            if (cle >= need_k && td >= kHB) {
+              // outside the histogram: binary search of the k-th distance over the list
+              int lo = 0, hi = min(td, bits);
+              while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                int c2 = 0;
                 for (int x = 0; x < cnt; ++x) {
                   const uint32_t e = crow[x * kCandStride];
-                  c_lt += (e < thr_w && (int)(e >> kPosBits) < dk);
+                  c2 += (e < thr_w && (int)(e >> kPosBits) <= mid);
                 }
+                if (c2 >= need_k) hi = mid; else lo = mid + 1;
               }
-              // among the entries at distance dk, the (need_k - c_lt)-th smallest word
-              const int want = need_k - c_lt - 1;
-              uint32_t wk = ((uint32_t)dk << kPosBits) | kPosMask;
+              thr_w = min(thr_w, (uint32_t)(lo + 1) << kPosBits);
+            }
+            cnt = compact_row(crow, cnt, thr_w, hist, r);
+            cle = cnt;
+            if (cnt > kCap - kHalf) {
+              // heavy ties at the k-th distance: the exact need_k-th smallest word
+              // becomes the threshold, leaving exactly need_k entries
+              td = (int)((thr_w - 1u) >> kPosBits);
+              int c_lt = 0;
+              for (int x = 0; x < cnt; ++x)
+                c_lt += ((int)(crow[x * kCandStride] >> kPosBits) < td);
+              const int want = need_k - c_lt - 1;  // rank among the entries at td
+              uint32_t wk = thr_w - 1u;
               for (int x = 0; x < cnt; ++x) {
                 const uint32_t e = crow[x * kCandStride];
-                if (e >= thr_w || (int)(e >> kPosBits) != dk) continue;
+                if ((int)(e >> kPosBits) != td) continue;
                 int below = 0;
                 for (int y = 0; y < cnt; ++y) {
                   const uint32_t f = crow[y * kCandStride];
-                  below += (f < e && (int)(f >> kPosBits) == dk);
+                  below += (f < e && (int)(f >> kPosBits) == td);
                 }
                 if (below == want) wk = e;
               }
               thr_w = wk + 1u;
+              cnt = compact_row(crow, cnt, thr_w, hist, r);
+              cle = cnt;
             }
-            // keep the entries below the threshold
-            int w = 0;
-            for (int x = 0; x < cnt; ++x) {
-              const uint32_t e = crow[x * kCandStride];
-              if (e < thr_w) crow[(w++) * kCandStride] = e;
-            }
-            cnt = w;
-            cle = w;
             if (cnt > kCap - kHalf) {  // still full: the popcount kernel redoes this row
               overflow = true;
               thr_w = 0u;  // accept nothing more
@@ -400,34 +411,26 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
                 atomicExch(ta.err, 5);
                 continue;
               }
-              if (d < (uint32_t)kHB) {
-                uint8_t& h = hist[d * kM + r];
-                if (h < 255) h = (uint8_t)(h + 1);
-              }
+              if (d < (uint32_t)kHB) hist[d * kM + r] = (uint8_t)(hist[d * kM + r] + 1);
             }
-            // lower the distance bound one step at a time while need_k values stay
-            // below it (hist may count values a compaction dropped: it only
-            // over-counts, so a lowering it allows is always safe)
+            // lower the bound one distance at a time while need_k listed words
+            // stay below it; every listed word at the bound's distance is below
+            // the bound, so hist counts them exactly
             int td = (int)((thr_w - 1u) >> kPosBits);
             while (td > 0 && td < kHB) {
               const int h = hist[td * kM + r];
-              if (h == 255 || cle - h < need_k) break;
+              if (cle - h < need_k) break;
               cle -= h;
+              thr_w = (uint32_t)td << kPosBits;
               --td;
-              thr_w = (uint32_t)(td + 1) << kPosBits;
             }
           }
         }
       }
       // ---- final compaction: only candidates inside the final threshold remain
       if (!overflow) {
-        int w = 0;
-        for (int x = 0; x < cnt; ++x) {
-          const uint32_t e = crow[x * kCandStride];
-          if (e < thr_w) crow[(w++) * kCandStride] = e;
-        }
-        cnt = w;
-        if (cnt > kSortN) overflow = true;  // too many ties to sort here
+        cnt = compact_row(crow, cnt, thr_w, hist, r);
+        if (cnt > kSortN) overflow = true;  // cannot happen: cnt <= kCap
       }
       // ---- selection: k smallest (d, id) among candidates inside the threshold
       uint64_t* sb = sortbuf + warp * 128;
