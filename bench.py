@@ -18,6 +18,7 @@ divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -58,6 +59,8 @@ def _args():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-routing leg")
     ap.add_argument("--learned-n", type=int, default=10_000_000,
                     help="points of the learned-routing leg (the workload's full size is 100M)")
+    ap.add_argument("--learned-lr", type=float, default=3e-4, help="router learning rate")
+    ap.add_argument("--learned-epochs", type=int, default=4, help="router training epochs")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds of Poisson arrivals per offered load")
     ap.add_argument("--kernel", choices=["auto", "popc", "tc"], default="auto",
@@ -381,12 +384,13 @@ def _serve_bench(bdg, ctx, seconds):
             "ef_mix": [64, 256], "request_sizes": "log-uniform 1..4096", "levels": out}
 
 
-def _learned_bench(bdg, device, kernel, n=10_000_000):
+def _learned_bench(bdg, device, kernel, n=10_000_000, lr=1e-3, lr_epochs=4):
     """Learned vs nearest-centre routing on the learned workload's generator at
     N = 10M (256-bit, m = 10,000, k = 32): the router (128 -> 512 -> 512 -> m,
-    BF16) is trained on the GPU on a 1M-point sample whose exact within-sample
-    neighbours give the targets; both routings build a graph at the same P and
-    are judged against exact brute-force rows."""
+    BF16, the last layer also fed the point's code as +-1 and started at the
+    nearest-centre logits) is trained on the GPU on a 1M-point sample whose exact
+    within-sample neighbours give the targets; both routings build a graph at
+    the same P and are judged against exact brute-force rows."""
     from paper_2102_04656_b300 import learned
     w = datagen.WORKLOADS["learned_100m_256b"]
     base = w["spec"]
@@ -404,21 +408,26 @@ def _learned_bench(bdg, device, kernel, n=10_000_000):
     home = bdg.route(codes, cent, 1)[0][:, 0].contiguous()
     torch.cuda.synchronize()
     out["setup_s"] = time.perf_counter() - t0
-    # training data and the router
-    S = 1_000_000
+    # training data: the exact neighbours (over all N points) of a seeded sample
+    # of 1M points, as the home partitions they live in (home itself left out)
+    S = min(n, 1_000_000)
     tr = torch.from_numpy(datagen.sample_ids(n, S, spec.seed + 5)).to(device)
     t0 = time.perf_counter()
-    labels = learned.neighbour_labels(codes[tr].contiguous(), home[tr].contiguous(), k)
+    labels = learned.neighbour_labels_full(codes, tr.to(torch.int32), home, k)
     torch.cuda.synchronize()
     out["labels_s"] = time.perf_counter() - t0
-    init = torch.from_numpy(datagen.router_init(base.dim, 512, 512, m, spec.seed + 5)).to(device)
-    cfg = learned.TrainConfig(hidden=(512, 512), batch=4096, epochs=6, lr=1e-3)
+    base_init = torch.from_numpy(datagen.router_init(base.dim, 512, 512, m, spec.seed + 5))
+    init = learned.prior_params(base_init.to(device), base.dim, 512, 512, m, cent)
+    cfg = learned.TrainConfig(hidden=(512, 512), batch=4096, epochs=lr_epochs, lr=lr)
     losses = []
     t0 = time.perf_counter()
     router = learned.train_router(xb[tr].contiguous(), labels, m, init, cfg, seed=spec.seed + 5,
-                                  log=lambda ep, l: losses.append(l))
+                                  log=lambda ep, l: losses.append(l), codes=codes[tr].contiguous(),
+                                  home=home[tr].contiguous())
     torch.cuda.synchronize()
     out["train"] = {"sample": S, "epochs": cfg.epochs, "batch": cfg.batch, "lr": cfg.lr,
+                    "init": "nearest-centre prior (code columns of the last layer)",
+                    "targets": "homes of exact neighbours over all N, home left out of the softmax",
                     "seconds": time.perf_counter() - t0, "loss_by_epoch": losses}
     del labels
     n_judge = 2000 if n <= 20_000_000 else 10_000
@@ -432,6 +441,8 @@ def _learned_bench(bdg, device, kernel, n=10_000_000):
         below = (gd < dk).sum(1)
         at = torch.minimum((gd == dk).sum(1), (ex_d == dk).sum(1))
         return float((below + at).sum().item()) / ex_d.numel()
+
+    L = bdg.lib()
 
     def build_timed(routes, P):
         g = bdg.build_graph(codes, k, m=m, t=P, routes=routes, entry=entry, kernel=kernel)
@@ -447,10 +458,24 @@ def _learned_bench(bdg, device, kernel, n=10_000_000):
         res = {"recall_tie_aware": judge(g), "build_ms": e0.elapsed_time(e1),
                "pairs": float((hc * vc).sum().item())}
         g.free()
+        # per-step event times of one more (untimed) build
+        L.bdg_profile_reset()
+        L.bdg_profile_enable(1)
+        g = bdg.build_graph(codes, k, m=m, t=P, routes=routes, entry=entry, kernel=kernel)
+        L.bdg_profile_enable(0)
+        torch.cuda.synchronize()
+        g.free()
+        steps = {}
+        for name in ("bucket", "expand", "knn", "knn_fixup", "merge"):
+            tot, nl = ctypes.c_double(), ctypes.c_int64()
+            L.bdg_profile_read(name.encode(), ctypes.byref(tot), ctypes.byref(nl))
+            if nl.value:
+                steps[name] = round(tot.value, 3)
+        res["steps_ms"] = steps
         return res
 
     t0 = time.perf_counter()
-    lr8 = learned.learned_routes(router, xb, home, 8)  # home + 7: the P = 2, 4 lists are prefixes
+    lr8 = learned.learned_routes(router, xb, home, 8, codes=codes)  # P = 2, 4 lists are prefixes
     lr_routes = {P: lr8[:, :P].contiguous() for P in (2, 4, 8)}
     torch.cuda.synchronize()
     out["route_s"] = time.perf_counter() - t0
@@ -587,7 +612,7 @@ def run_ours(a):
     learned_res = None
     if not a.no_learned and ws == 1:
         learned_res = _learned_bench(bdg, device, "popc" if kernel_used == "popc" else "auto",
-                                     n=a.learned_n)
+                                     n=a.learned_n, lr=a.learned_lr, lr_epochs=a.learned_epochs)
 
     if rank != 0:
         if ws > 1:

@@ -252,35 +252,46 @@ void bdg_server_free(bdg_server* s);
  * The router keeps the nearest centre as the home (slot 0) and picks the other
  * P - 1 probed partitions with a small BF16 MLP trained on where a point's exact
  * neighbours live:
- *   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2), z = h2 W3^T + b3 (FP32 accumulate)
+ *   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2),
+ *   z = [h2 | s] W3^T + b3 (FP32 accumulate), s in {-1, +1}^code_bits the
+ *   point's code (bit set = +1; code_bits = 0: z = h2 W3^T + b3)
  *   loss = -(1/B) sum_i sum_p q_ip log softmax(z_i)_p,
  *   q_ip = #{j in labels[i] : j == p} / #{valid labels of i}
  *   (labels: partitions where i's neighbours live, -1 = none; a row without a
  *   valid label contributes neither loss nor gradient)
- * Adam (beta 0.9 / 0.999, eps 1e-8) on FP32 master weights with BF16 copies. */
+ * Adam (beta 0.9 / 0.999, eps 1e-8) on FP32 master weights with BF16 copies.
+ * With W3 = [0 | (2 c_p - 1) / 2] and b3 = 0 the logits are bits / 2 - d(y, c_p):
+ * the router then routes exactly like the nearest-centre rule, and training
+ * starts from the method's own routing. */
 typedef struct bdg_router bdg_router;
 
-/* init_params: device FP32, packed W1[h1][d_in] b1[h1] W2[h2][h1] b2[h2] W3[m][h2] b3[m]
- * (copied). All sizes and max_batch multiples of 8. Synchronous. */
-bdg_status bdg_router_create(int32_t d_in, int32_t h1, int32_t h2, int32_t m,
+/* init_params: device FP32, packed W1[h1][d_in] b1[h1] W2[h2][h1] b2[h2]
+ * W3[m][h2 + code_bits] b3[m] (copied). d_in, h1, h2, m and max_batch multiples
+ * of 8; code_bits 0 or a multiple of 64 up to 1024. Synchronous. */
+bdg_status bdg_router_create(int32_t d_in, int32_t h1, int32_t h2, int32_t m, int32_t code_bits,
                              const float* init_params, int32_t max_batch, bdg_router** out);
 void bdg_router_free(bdg_router* r);
 /* Device pointers to the packed FP32 parameters, the gradients of the last
  * training step (same layout), the last loss (scalar) and an error word. */
 bdg_status bdg_router_info(const bdg_router* r, float** params, float** grads, int64_t* n_params,
                            float** loss, int32_t** err);
-/* x: [B][d_in] BF16 (device). logits: [B][m] FP32. B <= max_batch. */
-bdg_status bdg_router_forward(bdg_router* r, const void* x, int32_t B, float* logits,
-                              void* stream);
+/* x: [B][d_in] BF16 (device); codes: [B][code_bits / 64] packed codes (device;
+ * required when code_bits > 0, else ignored). logits: [B][m] FP32. B <= max_batch. */
+bdg_status bdg_router_forward(bdg_router* r, const void* x, const uint64_t* codes, int32_t B,
+                              float* logits, void* stream);
 /* One training step on a batch: forward, loss, backward into the gradient
  * buffer, and (apply_update != 0) an Adam update with learning rate lr.
- * labels: [B][kt] int32 partition ids (-1 entries ignored). B % 8 == 0. */
-bdg_status bdg_router_train_step(bdg_router* r, const void* x, const int32_t* labels, int32_t kt,
+ * labels: [B][kt] int32 partition ids (-1 entries ignored). exclude: [B] int32
+ * or NULL: partition exclude[i] (the home, which is always probed) is left out
+ * of row i's softmax and targets. B % 8 == 0. */
+bdg_status bdg_router_train_step(bdg_router* r, const void* x, const uint64_t* codes,
+                                 const int32_t* labels, int32_t kt, const int32_t* exclude,
                                  int32_t B, float lr, int32_t apply_update, void* stream);
 /* routes[i] = {home[i], then the P - 1 other partitions of largest logit,
- * ties by partition index}. x: [N][d_in] BF16, home: [N], routes: [N][P], P <= 17. */
-bdg_status bdg_router_route(bdg_router* r, const void* x, int64_t N, const int32_t* home,
-                            int32_t P, int32_t* routes, void* stream);
+ * ties by partition index}. x: [N][d_in] BF16, codes: [N][code_bits / 64]
+ * (when code_bits > 0), home: [N], routes: [N][P], P <= 17. */
+bdg_status bdg_router_route(bdg_router* r, const void* x, const uint64_t* codes, int64_t N,
+                            const int32_t* home, int32_t P, int32_t* routes, void* stream);
 
 /* The router's tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulation):
  *   C[M][N] = epilogue(A[M][K] * B[N][K]^T), A and B row-major with K contiguous;

@@ -6,13 +6,21 @@ partitions instead. The oracle states the network and its gradients plainly:
 
   h1 = relu(x W1^T + b1)          x: [B, d_in]
   h2 = relu(h1 W2^T + b2)
-  z  = h2 W3^T + b3               z: [B, m] logits, one per partition
+  z  = [h2 | s] W3^T + b3         z: [B, m] logits, one per partition
   loss = -(1/B) sum_i sum_p q_ip log softmax(z_i)_p
+
+where s is the point's code written as +-1 (a set bit is +1), an optional
+input of the last layer (without it, z = h2 W3^T + b3). With the code columns
+of W3 set to c_p / 2 (centre p as +-1) and everything else in W3 and b3 zero,
+z_p = <s, c_p> / 2 = bits / 2 - d(y, c_p): the nearest-centre rule of
+Section 3.2 written as logits.
 
 with q_i the target distribution over partitions: the empirical distribution of
 the partitions given as point i's labels (the homes of its exact neighbours).
 A row without any label has no target and contributes neither loss nor
-gradient. Gradients are the analytic chain rule;
+gradient. Optionally one partition per row (its home, which is probed anyway)
+is left out: the softmax runs over the other partitions and labels naming it
+are ignored. Gradients are the analytic chain rule;
 ``adam`` is Kingma & Ba's update with bias correction.
 
 With ``bf16=True`` the float64 computation rounds to bfloat16 (round to nearest,
@@ -42,8 +50,19 @@ def _q(a, bf16):
     return round_bf16(a) if bf16 else np.asarray(a, dtype=np.float64)
 
 
-def forward(params, x, bf16=True):
-    """Returns (z, cache). params: dict W1,b1,W2,b2,W3,b3 (float arrays)."""
+def code_pm(codes_u64, bits):
+    """Packed codes (uint64 [n, bits/64], LSB-first) as +-1 float64 [n, bits]."""
+    c = np.asarray(codes_u64, dtype=np.uint64)
+    out = np.empty((c.shape[0], bits), np.float64)
+    for b in range(bits):
+        bit = (c[:, b // 64] >> np.uint64(b % 64)) & np.uint64(1)
+        out[:, b] = np.where(bit == 1, 1.0, -1.0)
+    return out
+
+
+def forward(params, x, bf16=True, s=None):
+    """Returns (z, cache). params: dict W1,b1,W2,b2,W3,b3 (float arrays);
+    s: optional +-1 code input [B, cb] of the last layer (W3 is then [m, h2 + cb])."""
     W1, W2, W3 = (_q(params[k], bf16) for k in ("W1", "W2", "W3"))
     b1, b2, b3 = (np.asarray(params[k], np.float64) for k in ("b1", "b2", "b3"))
     x = _q(x, bf16)
@@ -51,8 +70,9 @@ def forward(params, x, bf16=True):
     h1 = _q(np.maximum(a1, 0.0), bf16)
     a2 = h1 @ W2.T + b2
     h2 = _q(np.maximum(a2, 0.0), bf16)
-    z = h2 @ W3.T + b3
-    return z, dict(x=x, h1=h1, h2=h2, W1=W1, W2=W2, W3=W3)
+    u = h2 if s is None else np.concatenate([h2, np.asarray(s, np.float64)], axis=1)
+    z = u @ W3.T + b3
+    return z, dict(x=x, h1=h1, h2=h2, u=u, W1=W1, W2=W2, W3=W3)
 
 
 def softmax(z):
@@ -61,21 +81,27 @@ def softmax(z):
     return e / e.sum(axis=1, keepdims=True)
 
 
-def loss_and_grads(params, x, q, bf16=True):
-    """Mean soft-target cross-entropy and its gradients w.r.t. every parameter."""
-    z, c = forward(params, x, bf16)
+def loss_and_grads(params, x, q, bf16=True, s=None, exclude=None):
+    """Mean soft-target cross-entropy and its gradients w.r.t. every parameter.
+    exclude: optional int [B], a partition per row left out of its softmax (q must
+    be zero there, e.g. from label_targets with the same exclude)."""
+    z, c = forward(params, x, bf16, s)
     B = z.shape[0]
-    p = softmax(z)
+    zs = z.copy()
+    if exclude is not None:
+        zs[np.arange(B), np.asarray(exclude)] = -np.inf
+    p = softmax(zs)
     q = np.asarray(q, np.float64)
     has = (q.sum(axis=1) > 0)[:, None]  # rows with a target
     logp = np.log(np.maximum(p, 1e-300))
-    loss = float(-(q * logp).sum() / B)
+    loss = float(-np.where(q > 0, q * logp, 0.0).sum() / B)
     dz = (p - q) / B * has
     dzq = _q(dz, bf16)
     g = {}
-    g["W3"] = dzq.T @ c["h2"]
+    g["W3"] = dzq.T @ c["u"]
     g["b3"] = dz.sum(0)
-    dh2 = (dzq @ c["W3"]) * (c["h2"] > 0)
+    h2n = c["h2"].shape[1]
+    dh2 = (dzq @ c["W3"][:, :h2n]) * (c["h2"] > 0)
     dh2q = _q(dh2, bf16)
     g["W2"] = dh2q.T @ c["h1"]
     g["b2"] = dh2.sum(0)
@@ -111,14 +137,16 @@ def topp(z, P):
     return out
 
 
-def label_targets(labels, m):
-    """q_ip = #{labels of row i equal to p} / #{labels of row i in [0, m)}
-    (a row without valid labels gets q = 0)."""
+def label_targets(labels, m, exclude=None):
+    """q_ip = #{labels of row i equal to p} / #{valid labels of row i}, a label
+    being valid when it is in [0, m) and not exclude[i] (a row without valid
+    labels gets q = 0)."""
     labels = np.asarray(labels)
     B = labels.shape[0]
     q = np.zeros((B, m), np.float64)
     for i in range(B):
-        valid = [int(p) for p in labels[i] if 0 <= p < m]
+        ex = -1 if exclude is None else int(exclude[i])
+        valid = [int(p) for p in labels[i] if 0 <= p < m and p != ex]
         for p in valid:
             q[i, p] += 1.0 / len(valid)
     return q

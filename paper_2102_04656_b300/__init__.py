@@ -302,18 +302,19 @@ def _router_sigs(L):
         return
     L.bdg_gemm_bf16.argtypes = [_c_void_p, _c_void_p, _i32, _i32, _i32, _c_void_p, _c_void_p,
                                 _i32, _c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p]
-    L.bdg_router_create.argtypes = [_i32, _i32, _i32, _i32, _c_void_p, _i32,
+    L.bdg_router_create.argtypes = [_i32, _i32, _i32, _i32, _i32, _c_void_p, _i32,
                                     ctypes.POINTER(_c_void_p)]
     L.bdg_router_free.argtypes = [_c_void_p]
     L.bdg_router_free.restype = None
     L.bdg_router_info.argtypes = [_c_void_p, ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p),
                                   ctypes.POINTER(_i64), ctypes.POINTER(_c_void_p),
                                   ctypes.POINTER(_c_void_p)]
-    L.bdg_router_forward.argtypes = [_c_void_p, _c_void_p, _i32, _c_void_p, _c_void_p]
-    L.bdg_router_train_step.argtypes = [_c_void_p, _c_void_p, _c_void_p, _i32, _i32,
-                                        ctypes.c_float, _i32, _c_void_p]
-    L.bdg_router_route.argtypes = [_c_void_p, _c_void_p, _i64, _c_void_p, _i32, _c_void_p,
-                                   _c_void_p]
+    L.bdg_router_forward.argtypes = [_c_void_p, _c_void_p, _c_void_p, _i32, _c_void_p,
+                                     _c_void_p]
+    L.bdg_router_train_step.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32,
+                                        _c_void_p, _i32, ctypes.c_float, _i32, _c_void_p]
+    L.bdg_router_route.argtypes = [_c_void_p, _c_void_p, _c_void_p, _i64, _c_void_p, _i32,
+                                   _c_void_p, _c_void_p]
     L._router_sigs = True
 
 
@@ -335,17 +336,20 @@ def gemm_bf16(A, B, bias=None, mask=None, relu=False, out="f32", colsum=None, st
 
 
 class Router:
-    """The BF16 MLP partition router (see include/bdg.h): d_in -> h1 -> h2 -> m."""
+    """The BF16 MLP partition router (see include/bdg.h): d_in -> h1 -> h2, then
+    [h2 | code as +-1] -> m logits (code_bits = 0: h2 -> m)."""
 
-    def __init__(self, init_params, d_in: int, h1: int, h2: int, m: int, max_batch: int):
+    def __init__(self, init_params, d_in: int, h1: int, h2: int, m: int, max_batch: int,
+                 code_bits: int = 0):
         L = lib()
         _router_sigs(L)
         _dev(init_params, torch.float32, "init_params", 1)
         h = ctypes.c_void_p()
-        _check(L.bdg_router_create(d_in, h1, h2, m, _ptr(init_params), max_batch,
+        _check(L.bdg_router_create(d_in, h1, h2, m, code_bits, _ptr(init_params), max_batch,
                                    ctypes.byref(h)))
         self._h = h
         self.d_in, self.h1, self.h2, self.m, self.max_batch = d_in, h1, h2, m, max_batch
+        self.code_bits = code_bits
         p, g, lo, er = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         n = _i64()
         _check(L.bdg_router_info(h, ctypes.byref(p), ctypes.byref(g), ctypes.byref(n),
@@ -360,34 +364,53 @@ class Router:
     def unpack(self, flat):
         """Split a packed parameter vector into W1, b1, W2, b2, W3, b3 views."""
         d, a, b, m = self.d_in, self.h1, self.h2, self.m
-        sizes = [a * d, a, b * a, b, m * b, m]
-        shapes = [(a, d), (a,), (b, a), (b,), (m, b), (m,)]
+        bs = b + self.code_bits
+        sizes = [a * d, a, b * a, b, m * bs, m]
+        shapes = [(a, d), (a,), (b, a), (b,), (m, bs), (m,)]
         out, o = {}, 0
         for name, sz, sh in zip(["W1", "b1", "W2", "b2", "W3", "b3"], sizes, shapes):
             out[name] = flat[o:o + sz].view(*sh)
             o += sz
         return out
 
-    def forward(self, x, stream=None):
+    def _codes(self, codes, n):
+        if self.code_bits == 0:
+            return None
+        if codes is None:
+            raise ValueError("this router takes the points' codes as input")
+        _dev(codes, torch.int64, "codes", 2)
+        if codes.shape[0] != n or codes.shape[1] * 64 != self.code_bits:
+            raise ValueError(f"codes: expected [{n}, {self.code_bits // 64}]")
+        return codes
+
+    def forward(self, x, codes=None, stream=None):
         _dev(x, torch.bfloat16, "x", 2)
+        c = self._codes(codes, x.shape[0])
         z = torch.empty(x.shape[0], self.m, dtype=torch.float32, device=x.device)
-        _check(lib().bdg_router_forward(self._h, _ptr(x), x.shape[0], _ptr(z), _stream(stream)))
+        _check(lib().bdg_router_forward(self._h, _ptr(x), _ptr(c), x.shape[0], _ptr(z),
+                                        _stream(stream)))
         return z
 
-    def train_step(self, x, labels, lr: float, apply_update: bool = True, stream=None):
+    def train_step(self, x, labels, lr: float, apply_update: bool = True, codes=None,
+                   exclude=None, stream=None):
+        """exclude: optional int32 [B], a partition per row left out of its softmax."""
         _dev(x, torch.bfloat16, "x", 2)
         _dev(labels, torch.int32, "labels", 2)
-        _check(lib().bdg_router_train_step(self._h, _ptr(x), _ptr(labels), labels.shape[1],
-                                           x.shape[0], float(lr), int(apply_update),
-                                           _stream(stream)))
+        c = self._codes(codes, x.shape[0])
+        if exclude is not None:
+            _dev(exclude, torch.int32, "exclude", 1)
+        _check(lib().bdg_router_train_step(self._h, _ptr(x), _ptr(c), _ptr(labels),
+                                           labels.shape[1], _ptr(exclude), x.shape[0], float(lr),
+                                           int(apply_update), _stream(stream)))
         return self.loss
 
-    def route(self, x, home, P: int, stream=None):
+    def route(self, x, home, P: int, codes=None, stream=None):
         _dev(x, torch.bfloat16, "x", 2)
         _dev(home, torch.int32, "home", 1)
+        c = self._codes(codes, x.shape[0])
         routes = torch.empty(x.shape[0], P, dtype=torch.int32, device=x.device)
-        _check(lib().bdg_router_route(self._h, _ptr(x), x.shape[0], _ptr(home), P, _ptr(routes),
-                                      _stream(stream)))
+        _check(lib().bdg_router_route(self._h, _ptr(x), _ptr(c), x.shape[0], _ptr(home), P,
+                                      _ptr(routes), _stream(stream)))
         return routes
 
     def free(self):

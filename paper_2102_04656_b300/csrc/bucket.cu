@@ -304,6 +304,7 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
                          int t, int tile_v, void* mem, bdg_csr* c, cudaStream_t st) {
   if (m > kMaxSortM)
     return bdg_set_error(BDG_EUNSUPPORTED, "m = %d partitions exceeds %d", m, kMaxSortM);
+  bdg_prof_scope prof("bucket", st);
   char* p = (char*)mem;
   const size_t ts = t > 1 ? (size_t)(t - 1) : 1;
   c->home_off = (int32_t*)p;   p += al((m + 1) * 4);

@@ -144,39 +144,37 @@ struct bdg_knn_args {
 // running list R[0..k) of the same point (global memory): R becomes the k
 // smallest keys of both. The valid keys of R and L are distinct (they come from
 // disjoint home sets), so every key's rank is its index plus the number of
-// smaller keys in the other list.
-__device__ __forceinline__ int bdg_lower_bound(const uint64_t* a, int n, uint64_t x) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
+// smaller keys in the other list. Keys of L at or above `bound` (the caller's
+// copy of R[k - 1], or pad) cannot enter; a row without any key below it leaves
+// R untouched, without reading it. k <= 128.
 __device__ __forceinline__ void bdg_warp_merge_running(uint64_t* R, const uint64_t* L, int len,
-                                                       int k, uint64_t pad, int lane) {
-  const int nr = bdg_lower_bound(R, k, pad);
-  const int nl = bdg_lower_bound(L, len, pad);
-  uint64_t rv[4], lv[4];
-  int rp[4], lp[4];
+                                                       int k, uint64_t pad, uint64_t bound,
+                                                       int lane) {
+  const uint64_t lim = bound < pad ? bound : pad;
+  if (!(len > 0 && L[0] < lim)) return;  // L is sorted: nothing can enter
+  uint64_t rv[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int j = lane + 32 * q;
-    rp[q] = k;
-    lp[q] = k;
-    rv[q] = 0;
-    lv[q] = 0;
-    if (j < nr) { rv[q] = R[j]; rp[q] = j + bdg_lower_bound(L, nl, rv[q]); }
-    if (j < nl) { lv[q] = L[j]; lp[q] = j + bdg_lower_bound(R, nr, lv[q]); }
+    rv[q] = j < k ? R[j] : pad;
   }
-  __syncwarp();
+  int rc[4] = {0, 0, 0, 0};  // new keys below each running key
+  for (int i = 0; i < len; ++i) {
+    const uint64_t x = L[i];  // the same for every lane
+    if (x >= lim) break;
+    int below = 0;            // running keys below x
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      rc[q] += (x < rv[q]);
+      below += __popc(__ballot_sync(0xffffffffu, rv[q] < x));
+    }
+    if (lane == (i & 31) && i + below < k) R[i + below] = x;
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (rp[q] < k) R[rp[q]] = rv[q];
-    if (lp[q] < k) R[lp[q]] = lv[q];
+    const int j = lane + 32 * q;
+    if (j < k && rc[q] > 0 && j + rc[q] < k) R[j + rc[q]] = rv[q];
   }
-  const int total = nr + nl < k ? nr + nl : k;
-  for (int j = total + lane; j < k; j += 32) R[j] = pad;
   __syncwarp();
 }
 // knn_tc.cu: tensor-core (tcgen05, FP8 +-1) Reduce 1 for 256/512-bit codes and k <= 64.
@@ -213,3 +211,8 @@ bdg_status bdg_launch_rerank(const float* feats, int64_t N, int D, const float* 
                              const int32_t* cand, int64_t nq, int R, int k, int32_t* out_ids,
                              float* out_d2, cudaStream_t st);
 int bdg_knn_tile_visitors(int W);
+// BF16 tcgen05 GEMM with row strides for the mask and the output (gemm_tc.cu)
+bdg_status bdg_gemm_bf16_ld(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                            const float* bias, const void* mask, int32_t ldm, int32_t relu,
+                            float* out_f32, void* out_bf16, int32_t ldo, float* colsum,
+                            int32_t* err, cudaStream_t st);

@@ -28,10 +28,12 @@ struct GemmArgs {
   const __nv_bfloat16* B;  // [N][K]
   int M, N, K;
   const float* bias;       // [N] or NULL
-  const __nv_bfloat16* mask;  // [M][N] or NULL: multiply by (mask > 0)
+  const __nv_bfloat16* mask;  // [M][ldm] or NULL: multiply by (mask > 0)
+  int ldm;                 // row stride of mask (elements)
   int relu;
-  float* out_f32;          // [M][N] or NULL
-  __nv_bfloat16* out_bf16; // [M][N] or NULL
+  float* out_f32;          // [M][ldo] or NULL
+  __nv_bfloat16* out_bf16; // [M][ldo] or NULL
+  int ldo;                 // row stride of the output (elements)
   float* colsum;           // [N] or NULL: += column sums of the result (before rounding)
   int32_t* err;
 };
@@ -162,19 +164,19 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
           if (g.bias && col < g.N) x += g.bias[col];
           if (g.relu) x = fmaxf(x, 0.f);
           if (g.mask && row < g.M && col < g.N &&
-              !(__bfloat162float(g.mask[(int64_t)row * g.N + col]) > 0.f))
+              !(__bfloat162float(g.mask[(int64_t)row * g.ldm + col]) > 0.f))
             x = 0.f;
           f[j] = (row < g.M && col < g.N) ? x : 0.f;
         }
         if (row < g.M) {
           if (g.out_f32) {
             for (int j = 0; j < 32; ++j)
-              if (n0 + c0 + j < g.N) g.out_f32[(int64_t)row * g.N + n0 + c0 + j] = f[j];
+              if (n0 + c0 + j < g.N) g.out_f32[(int64_t)row * g.ldo + n0 + c0 + j] = f[j];
           }
           if (g.out_bf16) {
             for (int j = 0; j < 32; ++j)
               if (n0 + c0 + j < g.N)
-                g.out_bf16[(int64_t)row * g.N + n0 + c0 + j] = __float2bfloat16_rn(f[j]);
+                g.out_bf16[(int64_t)row * g.ldo + n0 + c0 + j] = __float2bfloat16_rn(f[j]);
           }
         }
         if (g.colsum) {  // column sums over this warp's 32 rows, one atomic per column
@@ -198,16 +200,18 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
 
 size_t bdg_gemm_smem_bytes() { return (size_t)kStages * 2 * kSlab + 256; }
 
-// C = epilogue(A * B^T); see GemmArgs. K % 8 == 0 (16-byte rows).
-extern "C" bdg_status bdg_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
-                                    const float* bias, const void* mask, int32_t relu,
-                                    float* out_f32, void* out_bf16, float* colsum, int32_t* err,
-                                    void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  if (M <= 0 || N <= 0 || K <= 0 || (K & 7))
-    return bdg_set_error(BDG_EINVAL, "gemm: M=%d N=%d K=%d (K %% 8 == 0)", M, N, K);
+// C = epilogue(A * B^T) with row strides for the mask and the output; see GemmArgs.
+// K % 8 == 0 (16-byte rows); ldm, ldo >= N.
+bdg_status bdg_gemm_bf16_ld(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                            const float* bias, const void* mask, int32_t ldm, int32_t relu,
+                            float* out_f32, void* out_bf16, int32_t ldo, float* colsum,
+                            int32_t* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0 || (K & 7) || ldm < N || ldo < N)
+    return bdg_set_error(BDG_EINVAL, "gemm: M=%d N=%d K=%d ldm=%d ldo=%d (K %% 8 == 0)", M, N,
+                         K, ldm, ldo);
   GemmArgs g{(const __nv_bfloat16*)A, (const __nv_bfloat16*)B, M, N, K, bias,
-             (const __nv_bfloat16*)mask, relu, out_f32, (__nv_bfloat16*)out_bf16, colsum, err};
+             (const __nv_bfloat16*)mask, ldm, relu, out_f32, (__nv_bfloat16*)out_bf16, ldo,
+             colsum, err};
   const size_t smem = bdg_gemm_smem_bytes();
   BDG_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
@@ -217,4 +221,13 @@ extern "C" bdg_status bdg_gemm_bf16(const void* A, const void* B, int32_t M, int
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   return BDG_OK;
+}
+
+// C = epilogue(A * B^T) with contiguous rows; see GemmArgs. K % 8 == 0 (16-byte rows).
+extern "C" bdg_status bdg_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                                    const float* bias, const void* mask, int32_t relu,
+                                    float* out_f32, void* out_bf16, float* colsum, int32_t* err,
+                                    void* stream) {
+  return bdg_gemm_bf16_ld(A, B, M, N, K, bias, mask, N, relu, out_f32, out_bf16, N, colsum, err,
+                          (cudaStream_t)stream);
 }

@@ -241,7 +241,7 @@ knn_popc_kernel(bdg_knn_args a) {
         uint64_t* out = a.partial + (int64_t)id * k;
         for (int j = lane; j < k; j += 32) out[j] = j < len ? L[j] : pad;
       } else {
-        bdg_warp_merge_running(a.partial + (int64_t)id * k, L, len, k, pad, lane);
+        bdg_warp_merge_running(a.partial + (int64_t)id * k, L, len, k, pad, pad, lane);
       }
     }
     __syncthreads();
@@ -259,7 +259,7 @@ bdg_status launch_w(const bdg_knn_args& a, cudaStream_t st) {
                                                              kThreads, smem));
   if (per_sm < 1) return bdg_set_error(BDG_EUNSUPPORTED, "knn kernel does not fit (k=%d)", a.k);
   const int grid = bdg_num_sms() * per_sm;
-  bdg_prof_scope prof("knn", st);
+  bdg_prof_scope prof(a.fixflag ? "knn_fixup" : "knn", st);
   knn_popc_kernel<W><<<grid, kThreads, smem, st>>>(a);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();

@@ -17,13 +17,11 @@
 //     dot products of its row and appends the values under its threshold as
 //     words (d << 21 | home position) to a per-row candidate list in shared
 //     memory. The homes of a partition are stored in ascending id order, so
-//     word order is (d, id) order. An exact per-row histogram of the listed
-//     distances (d < 256) lowers the threshold to the k-th smallest distance
-//     seen so far after every 16 values; it only tightens, so every final
-//     neighbour is kept. When a row's list is nearly full, the warp compacts
-//     all its rows together against their thresholds (with an exact word
-//     threshold if ties at the k-th distance fill the list); a row whose list
-//     still overflows is flagged and recomputed by the popcount kernel.
+//     word order is (d, id) order. When a row's list is nearly full, the warp
+//     compacts all its rows together: the threshold of each row becomes its
+//     exact k-th smallest distance so far (binary search over its list), or its
+//     exact k-th smallest word when ties at that distance fill the list. The
+//     threshold only tightens, so every final neighbour is kept.
 // At the end of the item each warp selects, row by row, the k smallest
 // (d, id) keys among the candidates inside the final threshold (bitonic sort
 // of at most 128 keys) and writes the row's partial list.
@@ -39,11 +37,13 @@ namespace {
 constexpr int kM = 128;         // visitors per item (TMEM lanes)
 constexpr int kNT = 64;         // homes per tile (TMEM columns per accumulator)
 constexpr int kStages = 2;
-constexpr int kCap = 124;       // candidate slots per row
+constexpr int kCap = 188;       // candidate slots per row
 constexpr int kHalf = 16;       // compaction is checked every 16 columns
-constexpr int kHB = 256;        // exact distance histogram over d in [0, 256)
 constexpr int kSortN = 128;     // keys sorted per row at selection
-constexpr int kCandStride = kM + 1;  // words between candidate slots (odd: no bank conflicts)
+// words between a row's candidate slots: slot c of row r is word c * kM + r, so
+// the 32 lanes of a warp (32 rows) always touch 32 different banks, whatever
+// slot each row is at
+constexpr int kCandStride = kM;
 constexpr int kThreads = 192;   // warps 0-3 epilogue, warp 4 producer, warp 5 MMA
 constexpr uint32_t kPolls = 1u << 20;
 constexpr int kPosBits = 21;    // home position bits in a candidate word
@@ -52,18 +52,15 @@ constexpr uint32_t kPosMask = (1u << kPosBits) - 1;
 template <int W>
 struct TcCfg {
   static constexpr int KB = 64 * W;               // bytes of one expanded code
-  static constexpr int NB = kHB;                   // distance histogram bins (width 1)
   static constexpr uint32_t A_BYTES = kM * KB;
   static constexpr uint32_t B_BYTES = kNT * KB;
-  static constexpr uint32_t HIST_BYTES = ((NB * kM) + 15) & ~15u;
   static constexpr uint32_t CAND_BYTES = ((kCap * kCandStride * 4) + 15) & ~15u;
   static constexpr uint32_t OFF_B = A_BYTES;
-  static constexpr uint32_t OFF_HIST = OFF_B + kStages * B_BYTES;
-  static constexpr uint32_t OFF_CAND = OFF_HIST + HIST_BYTES;
+  static constexpr uint32_t OFF_CAND = OFF_B + kStages * B_BYTES;
   static constexpr uint32_t OFF_SORT = OFF_CAND + CAND_BYTES;     // 4 warps x 128 keys
   static constexpr uint32_t OFF_BAR = OFF_SORT + 4 * kSortN * 8;
   static constexpr uint32_t SMEM = OFF_BAR + 256;
-  static_assert(OFF_B % 16 == 0 && OFF_HIST % 16 == 0 && OFF_CAND % 16 == 0 &&
+  static_assert(OFF_B % 16 == 0 && OFF_CAND % 16 == 0 &&
                     OFF_SORT % 16 == 0 && OFF_BAR % 16 == 0,
                 "shared-memory regions must be 16-byte aligned");
   static_assert(SMEM <= 232448, "shared memory per block exceeds 227 KB");
@@ -138,31 +135,61 @@ __device__ __forceinline__ uint32_t cidx(int c, int r) {  // candidate slot c of
   return (uint32_t)(c * kCandStride + r);
 }
 
-// Keep the row's candidates below thr_w, in order; the histogram of listed
-// distances (d < kHB) loses the dropped ones. Returns the new count.
-__device__ __forceinline__ int compact_row(uint32_t* crow, int cnt, uint32_t thr_w,
-                                           uint8_t* hist, int r) {
+// Keep the row's candidates below thr_w, in order. Returns the new count.
+__device__ __forceinline__ int compact_row(uint32_t* crow, int cnt, uint32_t thr_w) {
   int w = 0;
   for (int x = 0; x < cnt; ++x) {
     const uint32_t e = crow[x * kCandStride];
-    if (e < thr_w) {
-      crow[(w++) * kCandStride] = e;
-    } else {
-      const uint32_t d = e >> kPosBits;
-      if (d < (uint32_t)kHB) hist[d * kM + r] = (uint8_t)(hist[d * kM + r] - 1);
-    }
+    if (e < thr_w) crow[(w++) * kCandStride] = e;
   }
   return w;
+}
+
+// Exact compaction of one row's list (every listed word is below thr_w): once it
+// holds need_k words, the bound becomes the need_k-th smallest distance (binary
+// search over the list) and the words above it are dropped; if ties at that
+// distance still leave more than `limit` words, the need_k-th smallest word
+// itself becomes the bound, leaving exactly need_k. Returns the new count.
+__device__ __forceinline__ int compact_exact(uint32_t* crow, int cnt, uint32_t& thr_w, int need_k,
+                                             int bits, int limit) {
+  if (cnt < need_k) return cnt;
+  int lo = 0, hi = min((int)((thr_w - 1u) >> kPosBits), bits);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    int c2 = 0;
+    for (int x = 0; x < cnt; ++x) c2 += ((int)(crow[x * kCandStride] >> kPosBits) <= mid);
+    if (c2 >= need_k) hi = mid; else lo = mid + 1;
+  }
+  thr_w = min(thr_w, (uint32_t)(lo + 1) << kPosBits);
+  cnt = compact_row(crow, cnt, thr_w);
+  if (cnt > limit) {
+    int c_lt = 0;
+    for (int x = 0; x < cnt; ++x) c_lt += ((int)(crow[x * kCandStride] >> kPosBits) < lo);
+    const int want = need_k - c_lt - 1;  // rank among the words at distance lo
+    uint32_t wk = thr_w - 1u;
+    for (int x = 0; x < cnt; ++x) {
+      const uint32_t e = crow[x * kCandStride];
+      if ((int)(e >> kPosBits) != lo) continue;
+      int below = 0;
+      for (int y = 0; y < cnt; ++y) {
+        const uint32_t f = crow[y * kCandStride];
+        below += (f < e && (int)(f >> kPosBits) == lo);
+      }
+      if (below == want) wk = e;
+    }
+    thr_w = wk + 1u;
+    cnt = compact_row(crow, cnt, thr_w);
+  }
+  return cnt;
 }
 
 template <int W>
 __global__ void __launch_bounds__(kThreads, 1)
 knn_tc_kernel(bdg_knn_tc_args ta) {
   using C = TcCfg<W>;
-  constexpr int KB = C::KB, NB = C::NB;
+  constexpr int KB = C::KB;
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t* sA = sm;
-  uint8_t* hist = sm + C::OFF_HIST;
   uint32_t* cand = reinterpret_cast<uint32_t*>(sm + C::OFF_CAND);
   uint64_t* sortbuf = reinterpret_cast<uint64_t*>(sm + C::OFF_SORT);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
@@ -246,7 +273,6 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       *reinterpret_cast<uint4*>(sA + cm_off<KB>(r, q * 16)) =
           expand16((uint32_t)(word >> (16 * (q & 3))) & 0xFFFFu);
     }
-    for (int x = tid; x < NB * kM / 4; x += kThreads) reinterpret_cast<uint32_t*>(hist)[x] = 0u;
     tc05::fence_proxy_async();
     __syncthreads();
 
@@ -296,16 +322,21 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       // v is one of its own partition's homes: its self pair (d = 0) is counted
       // like any other value and dropped at selection, so k + 1 values are needed
       const int need_k = k + ((live && c.visit_slot[v0 + r] == 0) ? 1 : 0);
-      uint32_t thr_w = live ? 0xFFFFFFFFu : 0u;  // accept word < thr_w
-      if (live && a.home_kth != nullptr) {  // sub-round: the running k-th key bounds d
-        const uint64_t kth = a.home_kth[(int64_t)c.visit_ids[v0 + r] * k + (k - 1)];
+      // accept word < thr_w; (bits + 1) << 21 accepts every real distance and no
+      // missing home of a ragged tile (those read as d = bits + 1)
+      uint32_t thr_w = live ? (uint32_t)(bits + 1) << kPosBits : 0u;
+      uint64_t kth = BDG_KEY_INF;  // sub-round: the running list's k-th key
+      if (live && a.home_kth != nullptr) {  // it bounds d, and no key above it can enter
+        kth = a.home_kth[(int64_t)c.visit_ids[v0 + r] * k + (k - 1)];
         if (kth < bdg_pad_key(bits)) thr_w = (uint32_t)(bdg_key_d(kth) + 1) << kPosBits;
       }
       int cnt = 0;   // entries in the row's candidate list
-      int cle = 0;   // entries with word < thr_w (every value seen below thr_w is listed)
       bool overflow = false;
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-      const float hbits = 0.5f * (float)bits;  // d = (bits - dot) / 2 = dot * -0.5 + bits / 2
+      // d = (bits - dot) / 2; adding 2^23 places the integer d in the low mantissa
+      // bits of the FP32 result (exact: |dot| <= 1024), and multiplying those bits
+      // by 2^21 (mod 2^32) leaves d << 21: the word is one FFMA and one IMAD
+      const float hmagic = 0.5f * (float)bits + 8388608.0f;
       uint32_t* crow = cand + r;
       for (int j = 0; j < ntiles; ++j) {
         const uint32_t gg = g + j, b = gg & 1;
@@ -325,112 +356,60 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         if (lane == 0) tc05::mbar_arrive(&tempty[b]);
         const uint32_t pos0 = (uint32_t)(j * kNT);
         const int nvalid = min(kNT, nh - j * kNT);
+        if (nvalid < kNT) {  // ragged last tile: missing homes read as d = bits + 1
+          const uint32_t padv = __float_as_uint(-(float)(bits + 2));
+#pragma unroll
+          for (int cc = 0; cc < kNT; ++cc)
+            if (cc >= nvalid) v[cc] = padv;
+        }
 #pragma unroll
         for (int half = 0; half < kNT / kHalf; ++half) {
           // compaction, taken by the whole warp at once as soon as one row's list
           // could not take another 16 values (lanes compacting one by one would
           // serialise the warp)
           if (__any_sync(0xffffffffu, cnt > kCap - kHalf)) {
-            int td = (int)((thr_w - 1u) >> kPosBits);
-            if (cle >= need_k && td >= kHB) {
-              // outside the histogram: binary search of the k-th distance over the list
-              int lo = 0, hi = min(td, bits);
-              while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                int c2 = 0;
-                for (int x = 0; x < cnt; ++x) {
-                  const uint32_t e = crow[x * kCandStride];
-                  c2 += (e < thr_w && (int)(e >> kPosBits) <= mid);
-                }
-                if (c2 >= need_k) hi = mid; else lo = mid + 1;
-              }
-              thr_w = min(thr_w, (uint32_t)(lo + 1) << kPosBits);
+            cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kCap - kHalf);
+            if (cnt > kCap - kHalf) {  // cannot happen (need_k <= 65); kept as a guard:
+              overflow = true;         // the popcount kernel redoes this row
+              thr_w = 0u;
+              cnt = 0;
             }
-            cnt = compact_row(crow, cnt, thr_w, hist, r);
-            cle = cnt;
-            if (cnt > kCap - kHalf) {
-              // heavy ties at the k-th distance: the exact need_k-th smallest word
-              // becomes the threshold, leaving exactly need_k entries
-              td = (int)((thr_w - 1u) >> kPosBits);
-              int c_lt = 0;
-              for (int x = 0; x < cnt; ++x)
-                c_lt += ((int)(crow[x * kCandStride] >> kPosBits) < td);
-              const int want = need_k - c_lt - 1;  // rank among the entries at td
-              uint32_t wk = thr_w - 1u;
-              for (int x = 0; x < cnt; ++x) {
-                const uint32_t e = crow[x * kCandStride];
-                if ((int)(e >> kPosBits) != td) continue;
-                int below = 0;
-                for (int y = 0; y < cnt; ++y) {
-                  const uint32_t f = crow[y * kCandStride];
-                  below += (f < e && (int)(f >> kPosBits) == td);
-                }
-                if (below == want) wk = e;
-              }
-              thr_w = wk + 1u;
-              cnt = compact_row(crow, cnt, thr_w, hist, r);
-              cle = cnt;
-            }
-            if (cnt > kCap - kHalf) {  // still full: the popcount kernel redoes this row
-              overflow = true;
-              thr_w = 0u;  // accept nothing more
-              cnt = 0;     // (the row's list is no longer used)
-            }
+          }
+          // skip the 16 values when no row of the warp can take one of them: a value
+          // can enter only if its distance is at most td, the bound's distance part
+          {
+            const int tdh = (int)((thr_w - 1u) >> kPosBits);
+            const float lim = thr_w ? (float)(bits - 2 * tdh) : 3.0e38f;
+            float f[kHalf];
+#pragma unroll
+            for (int c2 = 0; c2 < kHalf; ++c2) f[c2] = __uint_as_float(v[half * kHalf + c2]);
+            const float m0 = fmaxf(fmaxf(f[0], f[1]), fmaxf(f[2], f[3]));
+            const float m1 = fmaxf(fmaxf(f[4], f[5]), fmaxf(f[6], f[7]));
+            const float m2 = fmaxf(fmaxf(f[8], f[9]), fmaxf(f[10], f[11]));
+            const float m3 = fmaxf(fmaxf(f[12], f[13]), fmaxf(f[14], f[15]));
+            if (!__any_sync(0xffffffffu, fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) >= lim)) continue;
           }
           // branch-free append: every value is written at the running slot, only
           // words below the threshold advance it
-          const int c_before = cnt;
-          uint32_t* wp = crow + cnt * kCandStride;
+          uint32_t* const wp0 = crow + cnt * kCandStride;
+          uint32_t* wp = wp0;
           const uint32_t posq = pos0 + (uint32_t)(half * kHalf);
-          if (nvalid == kNT) {
 #pragma unroll
-            for (int c2 = 0; c2 < kHalf; ++c2) {
-              const float dot = __uint_as_float(v[half * kHalf + c2]);
-              const uint32_t d = (uint32_t)__float2int_rz(fmaf(dot, -0.5f, hbits));
-              const uint32_t word = d * (1u << kPosBits) + (posq + c2);
-              *wp = word;
-              wp += (word < thr_w) ? kCandStride : 0;
-            }
-          } else {
-#pragma unroll
-            for (int c2 = 0; c2 < kHalf; ++c2) {
-              const int cc = half * kHalf + c2;
-              const float dot = __uint_as_float(v[cc]);
-              const uint32_t d = (uint32_t)__float2int_rz(fmaf(dot, -0.5f, hbits));
-              const uint32_t word = d * (1u << kPosBits) + (posq + c2);
-              *wp = word;
-              wp += (word < thr_w && cc < nvalid) ? kCandStride : 0;
-            }
+          for (int c2 = 0; c2 < kHalf; ++c2) {
+            const float dot = __uint_as_float(v[half * kHalf + c2]);
+            const uint32_t fb = __float_as_uint(fmaf(dot, -0.5f, hmagic));
+            const uint32_t word = fb * (1u << kPosBits) + (posq + c2);
+            *wp = word;
+            wp += (word < thr_w) ? kCandStride : 0;
           }
-          cnt = (int)((wp - crow) / kCandStride);
-          if (cnt > c_before) {
-            cle += cnt - c_before;
-            for (int x = c_before; x < cnt; ++x) {
-              const uint32_t d = crow[x * kCandStride] >> kPosBits;
-              if (d > (uint32_t)bits) {  // cannot happen for +-1 operands
-                atomicExch(ta.err, 5);
-                continue;
-              }
-              if (d < (uint32_t)kHB) hist[d * kM + r] = (uint8_t)(hist[d * kM + r] + 1);
-            }
-            // lower the bound one distance at a time while need_k listed words
-            // stay below it; every listed word at the bound's distance is below
-            // the bound, so hist counts them exactly
-            int td = (int)((thr_w - 1u) >> kPosBits);
-            while (td > 0 && td < kHB) {
-              const int h = hist[td * kM + r];
-              if (cle - h < need_k) break;
-              cle -= h;
-              thr_w = (uint32_t)td << kPosBits;
-              --td;
-            }
-          }
+          cnt += (int)((wp - wp0) / kCandStride);
         }
       }
-      // ---- final compaction: only candidates inside the final threshold remain
-      if (!overflow) {
-        cnt = compact_row(crow, cnt, thr_w, hist, r);
-        if (cnt > kSortN) overflow = true;  // cannot happen: cnt <= kCap
+      // ---- final compaction: a list longer than the sort takes is cut to its k
+      // best words
+      if (__any_sync(0xffffffffu, cnt > kSortN)) {
+        if (cnt > kSortN) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kSortN);
+        if (cnt > kSortN) overflow = true;  // cannot happen; the popcount kernel would redo it
       }
       // ---- selection: k smallest (d, id) among candidates inside the threshold
       uint64_t* sb = sortbuf + warp * 128;
@@ -440,6 +419,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         const int n_r = __shfl_sync(0xffffffffu, cnt, rr);
         const uint32_t tb = __shfl_sync(0xffffffffu, thr_w, rr);
         const int ovf = __shfl_sync(0xffffffffu, overflow ? 1 : 0, rr);
+        const uint64_t kb = __shfl_sync(0xffffffffu, kth, rr);
         if (row >= nv) continue;
         const int32_t vid = c.visit_ids[v0 + row];
         if (vid < 0) {  // an invalid id: its row (written by position) is padding
@@ -456,6 +436,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           if (lane == 0) ta.fixflag[v0 + row] = 1;
           continue;
         }
+        if (a.merge_running && n_r == 0) continue;  // nothing to merge
         if (n_r <= 32) {
           // few candidates: one key per lane, bitonic sort across the warp in registers
           uint64_t key = BDG_KEY_INF;
@@ -467,6 +448,9 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
               if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
             }
           }
+          // a sub-round key above the running k-th cannot enter: a row left
+          // without keys is done
+          if (a.merge_running && !__any_sync(0xffffffffu, key < kb)) continue;
 #pragma unroll
           for (int k2 = 2; k2 <= 32; k2 <<= 1) {
 #pragma unroll
@@ -524,7 +508,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           uint64_t* out = a.partial + (int64_t)vid * k;
           for (int j2 = lane; j2 < k; j2 += 32) out[j2] = sb[j2] < pad ? sb[j2] : pad;
         } else {
-          bdg_warp_merge_running(a.partial + (int64_t)vid * k, sb, k, k, pad, lane);
+          bdg_warp_merge_running(a.partial + (int64_t)vid * k, sb, k, k, pad, kb, lane);
         }
         __syncwarp();
       }
@@ -555,6 +539,7 @@ bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
   if (expand) {  // expanded home operand (rows are bounded by N + 64 m)
     const int64_t max_rows = a.N + 64LL * a.m;
     const int64_t nthreads = ((max_rows + 7) / 8) * 8 * (4 * W);
+    bdg_prof_scope prof("expand", st);
     expand_homes_kernel<W><<<bdg_cdiv(nthreads, 256), 256, 0, st>>>(
         a.csr.home_codes, a.csr.home_off, a.csr.eoff, a.m, max_rows, ta.hexp);
     BDG_CUDA_TRY(cudaGetLastError());

@@ -5,7 +5,11 @@
 // keeps that nearest centre as the home and replaces the other t - 1 probes by
 // the partitions where the point's neighbours are predicted to live.
 //
-//   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2), z = h2 W3^T + b3
+//   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2), z = [h2 | s] W3^T + b3
+// where s in {-1, +1}^cb is the point's code (cb = 0: no code input). Through
+// the code columns of W3 the logits can carry the Hamming prior of the method's
+// own routing: with W3 = [0 | c_p / 2] and b3 = 0, z_p = bits / 2 - d(y, c_p),
+// whose top-P order is exactly the nearest-centre order (ties by p).
 //   loss = -(1/B) sum_i sum_p q_ip log softmax(z_i)_p,
 //   q_ip = #{labels of i equal to p} / #{valid labels of i}
 // (a row without a valid label contributes neither loss nor gradient)
@@ -25,6 +29,8 @@
 
 struct bdg_router {
   int d_in, h1, h2, m;
+  int cb;            // code bits appended to h2 as +-1 inputs of the last layer (0 = none)
+  int h2s;           // h2 + cb: row length of the last layer's input
   int64_t n_params;
   float* w;          // fp32 master, packed W1 b1 W2 b2 W3 b3
   float* grad;       // same layout: gradients of the last training step
@@ -34,7 +40,7 @@ struct bdg_router {
   int64_t step;
   int32_t* err;
   float* loss;       // device scalar: loss of the last step
-  // training workspace for batches up to cap_b rows
+  // training workspace for batches up to cap_b rows (h2 rows are h2s long)
   int cap_b;
   void* ws;
   size_t ws_bytes;
@@ -47,14 +53,15 @@ inline size_t al(size_t b) { return (b + 255) & ~size_t(255); }
 struct Offs {
   int64_t W1, b1, W2, b2, W3, b3, n;
 };
-Offs param_offsets(int d_in, int h1, int h2, int m) {
+// W3 is m x h2s (h2s = h2 + cb)
+Offs param_offsets(int d_in, int h1, int h2, int h2s, int m) {
   Offs o;
   o.W1 = 0;
   o.b1 = o.W1 + (int64_t)h1 * d_in;
   o.W2 = o.b1 + h1;
   o.b2 = o.W2 + (int64_t)h2 * h1;
   o.W3 = o.b2 + h2;
-  o.b3 = o.W3 + (int64_t)m * h2;
+  o.b3 = o.W3 + (int64_t)m * h2s;
   o.n = o.b3 + m;
   return o;
 }
@@ -81,17 +88,34 @@ __global__ void transpose_bf16(const __nv_bfloat16* __restrict__ in, int rows, i
   }
 }
 
+// out[i][col0 + b] = +1 if bit b of code i is set, else -1 (BF16), for i < rows
+__global__ void code_pm_bf16(const uint64_t* __restrict__ codes, int64_t rows, int W,
+                             __nv_bfloat16* __restrict__ out, int ld, int col0) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bits = 64 * W;
+  if (x >= rows * bits) return;
+  const int64_t i = x / bits;
+  const int b = (int)(x - i * bits);
+  const uint64_t w = codes[i * W + (b >> 6)];
+  out[i * ld + col0 + b] = __float2bfloat16_rn(((w >> (b & 63)) & 1ull) ? 1.f : -1.f);
+}
+
 // Softmax cross-entropy against the neighbour-partition targets, one block per
-// row: dz = (softmax(z) - q) / B as FP32 and BF16, loss accumulated.
+// row: dz = (softmax(z) - q) / B as FP32 and BF16, loss accumulated. With
+// `exclude`, partition exclude[i] is left out of row i's softmax (it gets
+// probability 0 and gradient 0; its labels are ignored).
 __global__ void __launch_bounds__(256)
 softmax_ce(const float* __restrict__ z, int m, int B, const int32_t* __restrict__ labels, int kt,
-           float* __restrict__ dz32, __nv_bfloat16* __restrict__ dz16, float* __restrict__ loss) {
+           const int32_t* __restrict__ exclude, float* __restrict__ dz32,
+           __nv_bfloat16* __restrict__ dz16, float* __restrict__ loss) {
   const int i = blockIdx.x;
   const float* zr = z + (int64_t)i * m;
+  const int ex = exclude ? exclude[i] : -1;
   __shared__ float red[32];
   __shared__ float s_max, s_sum;
   float mx = -INFINITY;
-  for (int p = threadIdx.x; p < m; p += blockDim.x) mx = fmaxf(mx, zr[p]);
+  for (int p = threadIdx.x; p < m; p += blockDim.x)
+    if (p != ex) mx = fmaxf(mx, zr[p]);
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
@@ -103,7 +127,8 @@ softmax_ce(const float* __restrict__ z, int m, int B, const int32_t* __restrict_
   __syncthreads();
   const float zmax = s_max;
   float sum = 0.f;
-  for (int p = threadIdx.x; p < m; p += blockDim.x) sum += expf(zr[p] - zmax);
+  for (int p = threadIdx.x; p < m; p += blockDim.x)
+    if (p != ex) sum += expf(zr[p] - zmax);
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
@@ -117,7 +142,7 @@ softmax_ce(const float* __restrict__ z, int m, int B, const int32_t* __restrict_
   const float lse = zmax + logf(s_sum);
   const int32_t* lab = labels + (int64_t)i * kt;
   int nval = 0;  // labels inside [0, m): the row's target is their empirical distribution
-  for (int j = 0; j < kt; ++j) nval += (lab[j] >= 0 && lab[j] < m);
+  for (int j = 0; j < kt; ++j) nval += (lab[j] >= 0 && lab[j] < m && lab[j] != ex);
   const float inv_b = 1.f / (float)B;
   float* dzr = dz32 + (int64_t)i * m;
   if (nval == 0) {  // no target: the row contributes neither loss nor gradient
@@ -128,11 +153,12 @@ softmax_ce(const float* __restrict__ z, int m, int B, const int32_t* __restrict_
     return;
   }
   const float inv_k = 1.f / (float)nval;
-  for (int p = threadIdx.x; p < m; p += blockDim.x) dzr[p] = expf(zr[p] - lse) * inv_b;
+  for (int p = threadIdx.x; p < m; p += blockDim.x)
+    dzr[p] = p == ex ? 0.f : expf(zr[p] - lse) * inv_b;
   __syncthreads();
   for (int j = threadIdx.x; j < kt; j += blockDim.x) {
     const int32_t p = lab[j];
-    if (p >= 0 && p < m) atomicAdd(&dzr[p], -inv_k * inv_b);  // - q_ip / B
+    if (p >= 0 && p < m && p != ex) atomicAdd(&dzr[p], -inv_k * inv_b);  // - q_ip / B
   }
   __syncthreads();
   for (int p = threadIdx.x; p < m; p += blockDim.x)
@@ -140,7 +166,7 @@ softmax_ce(const float* __restrict__ z, int m, int B, const int32_t* __restrict_
   if (threadIdx.x == 0) {
     float l = 0.f;
     for (int j = 0; j < kt; ++j)
-      if (lab[j] >= 0 && lab[j] < m) l -= inv_k * (zr[lab[j]] - lse);
+      if (lab[j] >= 0 && lab[j] < m && lab[j] != ex) l -= inv_k * (zr[lab[j]] - lse);
     atomicAdd(loss, l * inv_b);
   }
 }
@@ -228,7 +254,7 @@ __global__ void topp_kernel(const float* __restrict__ z, int rows, int m,
 
 extern "C" {
 
-bdg_status bdg_router_create(int32_t d_in, int32_t h1, int32_t h2, int32_t m,
+bdg_status bdg_router_create(int32_t d_in, int32_t h1, int32_t h2, int32_t m, int32_t code_bits,
                              const float* init_params, int32_t max_batch, bdg_router** out) {
   if (!out) return bdg_set_error(BDG_EINVAL, "router_create: out is NULL");
   *out = nullptr;
@@ -237,17 +263,22 @@ bdg_status bdg_router_create(int32_t d_in, int32_t h1, int32_t h2, int32_t m,
     return bdg_set_error(BDG_EINVAL,
                          "router_create: sizes must be multiples of 8 (d_in=%d h1=%d h2=%d m=%d "
                          "max_batch=%d) and init_params given", d_in, h1, h2, m, max_batch);
-  const Offs o = param_offsets(d_in, h1, h2, m);
+  if (code_bits < 0 || code_bits > 1024 || (code_bits & 63))
+    return bdg_set_error(BDG_EINVAL, "router_create: code_bits = %d (0 or 64..1024, multiple of 64)",
+                         code_bits);
+  const int h2s = h2 + code_bits;
+  const Offs o = param_offsets(d_in, h1, h2, h2s, m);
   bdg_router* r = new bdg_router();
   r->d_in = d_in; r->h1 = h1; r->h2 = h2; r->m = m; r->n_params = o.n; r->cap_b = max_batch;
-  const int64_t nw = (int64_t)h1 * d_in + (int64_t)h2 * h1 + (int64_t)m * h2;
+  r->cb = code_bits; r->h2s = h2s;
+  const int64_t nw = (int64_t)h1 * d_in + (int64_t)h2 * h1 + (int64_t)m * h2s;
   const int64_t B = max_batch;
-  // workspace: h1, h2 (bf16), z (f32), dz32, dz16, transposes, dh1, dh2, label copy
-  r->ws_bytes = al(B * h1 * 2) + al(B * h2 * 2) + al(B * m * 4) * 2 + al(B * m * 2) +
-                al(B * m * 2) /* dzT */ + al(B * h2 * 2) * 2 /* h2T, dh2 */ +
+  // workspace: h1, [h2 | s] (bf16), z (f32), dz32, dz16, transposes, dh1, dh2
+  r->ws_bytes = al(B * h1 * 2) + al(B * h2s * 2) + al(B * m * 4) * 2 + al(B * m * 2) +
+                al(B * m * 2) /* dzT */ + al(B * h2s * 2) /* h2T */ + al(B * h2 * 2) /* dh2 */ +
                 al(B * h1 * 2) * 2 /* h1T, dh1 */ + al(B * d_in * 2) /* xT */ +
                 al(B * h2 * 2) /* dh2T */ + al(B * h1 * 2) /* dh1T */ +
-                al((int64_t)h2 * m * 2) /* W3T */ + al((int64_t)h1 * h2 * 2) /* W2T */;
+                al((int64_t)h2s * m * 2) /* W3T */ + al((int64_t)h1 * h2 * 2) /* W2T */;
   cudaError_t e = cudaSuccess;
   e = e == cudaSuccess ? cudaMalloc(&r->w, o.n * 4) : e;
   e = e == cudaSuccess ? cudaMalloc(&r->grad, o.n * 4) : e;
@@ -272,8 +303,8 @@ bdg_status bdg_router_create(int32_t d_in, int32_t h1, int32_t h2, int32_t m,
   f32_to_bf16<<<bdg_cdiv((int64_t)h1 * d_in, 256), 256>>>(r->w + o.W1, r->wb, (int64_t)h1 * d_in);
   f32_to_bf16<<<bdg_cdiv((int64_t)h2 * h1, 256), 256>>>(r->w + o.W2, r->wb + (int64_t)h1 * d_in,
                                                          (int64_t)h2 * h1);
-  f32_to_bf16<<<bdg_cdiv((int64_t)m * h2, 256), 256>>>(
-      r->w + o.W3, r->wb + (int64_t)h1 * d_in + (int64_t)h2 * h1, (int64_t)m * h2);
+  f32_to_bf16<<<bdg_cdiv((int64_t)m * h2s, 256), 256>>>(
+      r->w + o.W3, r->wb + (int64_t)h1 * d_in + (int64_t)h2 * h1, (int64_t)m * h2s);
   bdg_note_launch(3);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     bdg_router_free(r);
@@ -301,57 +332,68 @@ bdg_status bdg_router_info(const bdg_router* r, float** params, float** grads, i
   return BDG_OK;
 }
 
-// Forward pass into caller-provided buffers (h1, h2 bf16 may be NULL -> workspace).
-static bdg_status router_fwd(bdg_router* r, const void* x, int B, float* z, void* h1b, void* h2b,
-                             cudaStream_t st) {
-  const Offs o = param_offsets(r->d_in, r->h1, r->h2, r->m);
+// Forward pass into caller-provided buffers: h1b [B][h1], h2b [B][h2s] (h2, then
+// the +-1 code), z [B][m].
+static bdg_status router_fwd(bdg_router* r, const void* x, const uint64_t* codes, int B, float* z,
+                             void* h1b, void* h2b, cudaStream_t st) {
+  const Offs o = param_offsets(r->d_in, r->h1, r->h2, r->h2s, r->m);
   const __nv_bfloat16* W1 = r->wb;
   const __nv_bfloat16* W2 = W1 + (int64_t)r->h1 * r->d_in;
   const __nv_bfloat16* W3 = W2 + (int64_t)r->h2 * r->h1;
-  BDG_TRY(bdg_gemm_bf16(x, W1, B, r->h1, r->d_in, r->w + o.b1, nullptr, 1, nullptr, h1b, nullptr,
-                        r->err, (void*)st));
-  BDG_TRY(bdg_gemm_bf16(h1b, W2, B, r->h2, r->h1, r->w + o.b2, nullptr, 1, nullptr, h2b, nullptr,
-                        r->err, (void*)st));
-  BDG_TRY(bdg_gemm_bf16(h2b, W3, B, r->m, r->h2, r->w + o.b3, nullptr, 0, z, nullptr, nullptr,
-                        r->err, (void*)st));
+  BDG_TRY(bdg_gemm_bf16_ld(x, W1, B, r->h1, r->d_in, r->w + o.b1, nullptr, r->h1, 1, nullptr,
+                           h1b, r->h1, nullptr, r->err, st));
+  BDG_TRY(bdg_gemm_bf16_ld(h1b, W2, B, r->h2, r->h1, r->w + o.b2, nullptr, r->h2, 1, nullptr,
+                           h2b, r->h2s, nullptr, r->err, st));
+  if (r->cb) {
+    const int64_t n = (int64_t)B * r->cb;
+    code_pm_bf16<<<bdg_cdiv(n, 256), 256, 0, st>>>(codes, B, r->cb / 64, (__nv_bfloat16*)h2b,
+                                                   r->h2s, r->h2);
+    BDG_CUDA_TRY(cudaGetLastError());
+    bdg_note_launch();
+  }
+  BDG_TRY(bdg_gemm_bf16_ld(h2b, W3, B, r->m, r->h2s, r->w + o.b3, nullptr, r->m, 0, z, nullptr,
+                           r->m, nullptr, r->err, st));
   return BDG_OK;
 }
 
-bdg_status bdg_router_forward(bdg_router* r, const void* x, int32_t B, float* logits,
-                              void* stream) {
-  if (!r || !x || !logits || B < 1 || B > r->cap_b)
-    return bdg_set_error(BDG_EINVAL, "router_forward: B = %d (1..%d)", B, r ? r->cap_b : 0);
+bdg_status bdg_router_forward(bdg_router* r, const void* x, const uint64_t* codes, int32_t B,
+                              float* logits, void* stream) {
+  if (!r || !x || !logits || B < 1 || B > r->cap_b || (r->cb && !codes))
+    return bdg_set_error(BDG_EINVAL, "router_forward: B = %d (1..%d)%s", B, r ? r->cap_b : 0,
+                         r && r->cb && !codes ? ", codes required" : "");
   cudaStream_t st = (cudaStream_t)stream;
   char* p = (char*)r->ws;
   void* h1b = p; p += al((int64_t)r->cap_b * r->h1 * 2);
   void* h2b = p;
-  return router_fwd(r, x, B, logits, h1b, h2b, st);
+  return router_fwd(r, x, codes, B, logits, h1b, h2b, st);
 }
 
-bdg_status bdg_router_train_step(bdg_router* r, const void* x, const int32_t* labels, int32_t kt,
+bdg_status bdg_router_train_step(bdg_router* r, const void* x, const uint64_t* codes,
+                                 const int32_t* labels, int32_t kt, const int32_t* exclude,
                                  int32_t B, float lr, int32_t apply_update, void* stream) {
-  if (!r || !x || !labels || B < 8 || B > r->cap_b || (B & 7) || kt < 1)
-    return bdg_set_error(BDG_EINVAL, "router_train_step: B = %d (8..%d, multiple of 8), kt = %d",
-                         B, r ? r->cap_b : 0, kt);
+  if (!r || !x || !labels || B < 8 || B > r->cap_b || (B & 7) || kt < 1 || (r->cb && !codes))
+    return bdg_set_error(BDG_EINVAL,
+                         "router_train_step: B = %d (8..%d, multiple of 8), kt = %d%s", B,
+                         r ? r->cap_b : 0, kt, r && r->cb && !codes ? ", codes required" : "");
   cudaStream_t st = (cudaStream_t)stream;
-  const int d = r->d_in, H1 = r->h1, H2 = r->h2, m = r->m;
+  const int d = r->d_in, H1 = r->h1, H2 = r->h2, H2S = r->h2s, m = r->m;
   const int64_t cap = r->cap_b;
-  const Offs o = param_offsets(d, H1, H2, m);
+  const Offs o = param_offsets(d, H1, H2, H2S, m);
   char* p = (char*)r->ws;
   __nv_bfloat16* h1b = (__nv_bfloat16*)p; p += al(cap * H1 * 2);
-  __nv_bfloat16* h2b = (__nv_bfloat16*)p; p += al(cap * H2 * 2);
+  __nv_bfloat16* h2b = (__nv_bfloat16*)p; p += al(cap * H2S * 2);
   float* z = (float*)p;                   p += al(cap * m * 4);
   float* dz32 = (float*)p;                p += al(cap * m * 4);
   __nv_bfloat16* dz16 = (__nv_bfloat16*)p; p += al(cap * m * 2);
   __nv_bfloat16* dzT = (__nv_bfloat16*)p;  p += al(cap * m * 2);
-  __nv_bfloat16* h2T = (__nv_bfloat16*)p;  p += al(cap * H2 * 2);
+  __nv_bfloat16* h2T = (__nv_bfloat16*)p;  p += al(cap * H2S * 2);
   __nv_bfloat16* dh2 = (__nv_bfloat16*)p;  p += al(cap * H2 * 2);
   __nv_bfloat16* h1T = (__nv_bfloat16*)p;  p += al(cap * H1 * 2);
   __nv_bfloat16* dh1 = (__nv_bfloat16*)p;  p += al(cap * H1 * 2);
   __nv_bfloat16* xT = (__nv_bfloat16*)p;   p += al(cap * d * 2);
   __nv_bfloat16* dh2T = (__nv_bfloat16*)p; p += al(cap * H2 * 2);
   __nv_bfloat16* dh1T = (__nv_bfloat16*)p; p += al(cap * H1 * 2);
-  __nv_bfloat16* W3T = (__nv_bfloat16*)p;  p += al((int64_t)H2 * m * 2);
+  __nv_bfloat16* W3T = (__nv_bfloat16*)p;  p += al((int64_t)H2S * m * 2);
   __nv_bfloat16* W2T = (__nv_bfloat16*)p;
   const __nv_bfloat16* W2 = r->wb + (int64_t)H1 * d;
   const __nv_bfloat16* W3 = W2 + (int64_t)H2 * H1;
@@ -363,20 +405,20 @@ bdg_status bdg_router_train_step(bdg_router* r, const void* x, const int32_t* la
   BDG_CUDA_TRY(cudaMemsetAsync(r->grad, 0, r->n_params * 4, st));
   BDG_CUDA_TRY(cudaMemsetAsync(r->loss, 0, 4, st));
   // forward
-  BDG_TRY(router_fwd(r, x, B, z, h1b, h2b, st));
+  BDG_TRY(router_fwd(r, x, codes, B, z, h1b, h2b, st));
   // loss and logit gradient
-  softmax_ce<<<B, 256, 0, st>>>(z, m, B, labels, kt, dz32, dz16, r->loss);
+  softmax_ce<<<B, 256, 0, st>>>(z, m, B, labels, kt, exclude, dz32, dz16, r->loss);
   bdg_note_launch();
   colsum_f32<<<bdg_cdiv(m, 256), 256, 0, st>>>(dz32, B, m, r->grad + o.b3);
   bdg_note_launch();
-  // layer 3: dW3 = dz^T h2, dh2 = (dz W3) * [h2 > 0], db2 = colsum(dh2)
+  // layer 3: dW3 = dz^T [h2 | s], dh2 = (dz W3[:, :h2]) * [h2 > 0], db2 = colsum(dh2)
   T(dz16, B, m, dzT);
-  T(h2b, B, H2, h2T);
-  T(W3, m, H2, W3T);
-  BDG_TRY(bdg_gemm_bf16(dzT, h2T, m, H2, B, nullptr, nullptr, 0, r->grad + o.W3, nullptr, nullptr,
-                        r->err, (void*)st));
-  BDG_TRY(bdg_gemm_bf16(dz16, W3T, B, H2, m, nullptr, h2b, 0, nullptr, dh2, r->grad + o.b2,
-                        r->err, (void*)st));
+  T(h2b, B, H2S, h2T);
+  T(W3, m, H2S, W3T);  // its first h2 rows are W3[:, :h2]^T
+  BDG_TRY(bdg_gemm_bf16(dzT, h2T, m, H2S, B, nullptr, nullptr, 0, r->grad + o.W3, nullptr,
+                        nullptr, r->err, (void*)st));
+  BDG_TRY(bdg_gemm_bf16_ld(dz16, W3T, B, H2, m, nullptr, h2b, H2S, 0, nullptr, dh2, H2,
+                           r->grad + o.b2, r->err, st));
   // layer 2: dW2 = dh2^T h1, dh1 = (dh2 W2) * [h1 > 0], db1 = colsum(dh1)
   T(dh2, B, H2, dh2T);
   T(h1b, B, H1, h1T);
@@ -401,28 +443,30 @@ bdg_status bdg_router_train_step(bdg_router* r, const void* x, const int32_t* la
                                                                 (int64_t)H1 * d);
     f32_to_bf16<<<bdg_cdiv((int64_t)H2 * H1, 256), 256, 0, st>>>(
         r->w + o.W2, r->wb + (int64_t)H1 * d, (int64_t)H2 * H1);
-    f32_to_bf16<<<bdg_cdiv((int64_t)m * H2, 256), 256, 0, st>>>(
-        r->w + o.W3, r->wb + (int64_t)H1 * d + (int64_t)H2 * H1, (int64_t)m * H2);
+    f32_to_bf16<<<bdg_cdiv((int64_t)m * H2S, 256), 256, 0, st>>>(
+        r->w + o.W3, r->wb + (int64_t)H1 * d + (int64_t)H2 * H1, (int64_t)m * H2S);
     bdg_note_launch(3);
   }
   BDG_CUDA_TRY(cudaGetLastError());
   return BDG_OK;
 }
 
-bdg_status bdg_router_route(bdg_router* r, const void* x, int64_t N, const int32_t* home,
-                            int32_t P, int32_t* routes, void* stream) {
-  if (!r || !x || !home || !routes || N < 0 || P < 1 || P > kMaxP + 1 || P > r->m)
-    return bdg_set_error(BDG_EINVAL, "router_route: N = %lld, P = %d (1..%d)", (long long)N, P,
-                         kMaxP + 1);
+bdg_status bdg_router_route(bdg_router* r, const void* x, const uint64_t* codes, int64_t N,
+                            const int32_t* home, int32_t P, int32_t* routes, void* stream) {
+  if (!r || !x || !home || !routes || N < 0 || P < 1 || P > kMaxP + 1 || P > r->m ||
+      (r->cb && !codes))
+    return bdg_set_error(BDG_EINVAL, "router_route: N = %lld, P = %d (1..%d)%s", (long long)N, P,
+                         kMaxP + 1, r && r->cb && !codes ? ", codes required" : "");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t cap = r->cap_b;
   char* p = (char*)r->ws;
   void* h1b = p; p += al(cap * r->h1 * 2);
-  void* h2b = p; p += al(cap * r->h2 * 2);
+  void* h2b = p; p += al(cap * r->h2s * 2);
   float* z = (float*)p;
   for (int64_t s = 0; s < N; s += cap) {
     const int B = (int)((N - s) < cap ? (N - s) : cap);
-    BDG_TRY(router_fwd(r, (const __nv_bfloat16*)x + s * r->d_in, B, z, h1b, h2b, st));
+    BDG_TRY(router_fwd(r, (const __nv_bfloat16*)x + s * r->d_in,
+                       r->cb ? codes + s * (r->cb / 64) : nullptr, B, z, h1b, h2b, st));
     topp_kernel<<<bdg_cdiv(B, 8), 256, 0, st>>>(z, B, r->m, home + s, P, routes + s * P);
     BDG_CUDA_TRY(cudaGetLastError());
     bdg_note_launch();

@@ -41,17 +41,20 @@ struct PoolSmem {
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
 
-// Returns true if id was already recorded; records it when there is room.
-__device__ __forceinline__ bool hash_seen(int32_t* h, int32_t id) {
+// Records id in the per-warp visited hash. Returns kNew if it was not there
+// (recorded now), kSeen if it was, kFull if its probe window is full (not
+// recorded: the id is re-scored and checked against the pool).
+constexpr int kNew = 0, kSeen = 1, kFull = 2;
+__device__ __forceinline__ int hash_visit(int32_t* h, int32_t id) {
   uint32_t x = (uint32_t)id * 2654435761u;
   uint32_t slot = x >> (32 - 10);  // kHash = 1024
   for (int p = 0; p < kProbe; ++p) {
     const uint32_t sidx = (slot + p) & (kHash - 1);
     const int32_t old = atomicCAS(&h[sidx], -1, id);
-    if (old == -1) return false;  // inserted now
-    if (old == id) return true;
+    if (old == -1) return kNew;
+    if (old == id) return kSeen;
   }
-  return false;  // table region full: not recorded, will be re-scored
+  return kFull;
 }
 
 template <int W, int CAPW>
@@ -105,7 +108,7 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
     if (lane == 0) {
       sm.key[0] = best;
       sm.expd[0] = 0;
-      hash_seen(sm.hash, bdg_key_id(best));
+      hash_visit(sm.hash, bdg_key_id(best));
     }
     int size = 1, hint = 0, nexp = 0;
     __syncwarp();
@@ -129,14 +132,17 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
         const int32_t nb = (b0 + lane < g.deg) ? g.ids[(int64_t)node * g.deg + b0 + lane] : -1;
         uint64_t key = BDG_KEY_INF;
         bool acc = false;
-        if (nb >= 0 && nb < g.n && !hash_seen(sm.hash, nb)) {
+        const int hv = (nb >= 0 && nb < g.n) ? hash_visit(sm.hash, nb) : kSeen;
+        if (hv != kSeen) {
           uint32_t d = 0;
 #pragma unroll
           for (int w = 0; w < W; ++w) d += __popcll(y[w] ^ g.codes[(int64_t)nb * W + w]);
           key = bdg_key(d, (uint32_t)nb);
           const uint64_t worst = sm.key[size - 1];
           acc = (size < ef) || (key < worst);
-          if (acc) {  // already in the pool?
+          // every pool entry was recorded in the hash when it entered, unless its
+          // window was full: only an id the hash could not record may be a duplicate
+          if (acc && hv == kFull) {  // already in the pool?
             int lo = 0, hi = size;
             while (lo < hi) {
               const int mid = (lo + hi) >> 1;
@@ -173,32 +179,29 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
           newpos = lane + lo;
         }
         // pool entries at or after the first new position shift right by the
-        // number of smaller new keys; entries before it stay in place
+        // number of smaller new keys; entries before it stay in place. Chunks of
+        // 32 slots move top-down, so no entry is overwritten before it is read
+        // (an entry only moves up, and the final positions are all distinct).
         const int minpos = (int)__reduce_min_sync(0xffffffffu, (unsigned)newpos);
-        uint64_t pk[CAPW];
-        uint8_t pf[CAPW];
-        int pp[CAPW];
-#pragma unroll
-        for (int r = 0; r < CAPW; ++r) {
-          const int j = r * 32 + lane;
-          pp[r] = CAP;
-          pk[r] = 0;
-          pf[r] = 0;
+        for (int base = (size - 1) & ~31; base >= (minpos & ~31); base -= 32) {
+          const int j = base + lane;
+          uint64_t pk = 0;
+          uint8_t pf = 0;
+          int pp = CAP;
           if (j >= minpos && j < size) {
-            pk[r] = sm.key[j];
-            pf[r] = sm.expd[j];
+            pk = sm.key[j];
+            pf = sm.expd[j];
             int lo = 0, hi = na;
             while (lo < hi) {
               const int mid = (lo + hi) >> 1;
-              if (sm.nk[mid] < pk[r]) lo = mid + 1; else hi = mid;
+              if (sm.nk[mid] < pk) lo = mid + 1; else hi = mid;
             }
-            pp[r] = j + lo;
+            pp = j + lo;
           }
+          __syncwarp();
+          if (pp < ef) { sm.key[pp] = pk; sm.expd[pp] = pf; }
+          __syncwarp();
         }
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < CAPW; ++r)
-          if (pp[r] < ef) { sm.key[pp[r]] = pk[r]; sm.expd[pp[r]] = pf[r]; }
         if (newpos < ef) { sm.key[newpos] = v; sm.expd[newpos] = 0; }
         size = min(ef, size + na);
         hint = min(hint, minpos);

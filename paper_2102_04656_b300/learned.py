@@ -8,6 +8,11 @@ the home partition of each neighbour; the router learns to put probability on
 the partitions where a point's neighbours live. Routes keep the nearest centre
 as the home (slot 0) so the home sets H_p are the same as with exhaustive
 routing; only the other P - 1 probed partitions come from the network.
+
+With the code input (``prior_params``), the last layer also sees the point's
+code as +-1 and starts with the centres in its code columns and zeros
+elsewhere: the untrained router routes exactly like the nearest-centre rule,
+and training moves it from there towards where the neighbours actually live.
 """
 from __future__ import annotations
 
@@ -16,7 +21,7 @@ import dataclasses
 import numpy as np
 import torch
 
-from . import Router, build_graph
+from . import Router, build_graph, knn_rows
 
 
 @dataclasses.dataclass
@@ -26,6 +31,33 @@ class TrainConfig:
     epochs: int = 4
     lr: float = 1e-3
     k_labels: int = 32
+
+
+def prior_params(base_flat, d_in: int, h1: int, h2: int, m: int, centres):
+    """Packed router parameters with a code input of the last layer: W1, b1, W2,
+    b2 from ``base_flat`` (a packed d_in -> h1 -> h2 -> m vector), W3 =
+    [0 | (2 c_p - 1) / 2] with c_p the bits of centre p, b3 = 0. The logits are
+    then bits / 2 - d(y, c_p). centres: int64 [m, W] packed codes."""
+    W = centres.shape[1]
+    bits = 64 * W
+    n12 = h1 * d_in + h1 + h2 * h1 + h2
+    shifts = torch.arange(64, device=centres.device, dtype=torch.int64)
+    cb = ((centres[:, :, None] >> shifts) & 1).reshape(m, bits).to(torch.float32)
+    w3 = torch.cat([torch.zeros(m, h2, device=centres.device), cb - 0.5], dim=1)
+    return torch.cat([base_flat[:n12].to(centres.device, torch.float32), w3.reshape(-1),
+                      torch.zeros(m, device=centres.device)]).contiguous()
+
+
+def neighbour_labels_full(codes, rows, home, k: int, skip_home: bool = True):
+    """Home partitions of the exact k nearest neighbours, over all N points, of
+    the sample points ``rows`` (int32 [S]): int32 [S, k]. -1 marks a neighbour
+    living in the point's own home partition (with skip_home)."""
+    ids, _ = knn_rows(codes, rows, k)
+    ids = ids.long()
+    lab = torch.where(ids >= 0, home[ids.clamp(min=0)], torch.full_like(ids, -1))
+    if skip_home:
+        lab = torch.where(lab == home[rows.long()][:, None], torch.full_like(lab, -1), lab)
+    return lab.to(torch.int32).contiguous()
 
 
 def neighbour_labels(codes_sample, home_sample, k: int, entry=None, skip_home: bool = True):
@@ -46,25 +78,32 @@ def neighbour_labels(codes_sample, home_sample, k: int, entry=None, skip_home: b
 
 
 def train_router(feats_bf16, labels, m: int, init_params, cfg: TrainConfig, seed: int,
-                 log=None) -> Router:
+                 log=None, codes=None, home=None) -> Router:
     """Train a router on (features, labels) with Adam for cfg.epochs epochs of
-    shuffled batches (seeded order). Returns the trained Router."""
+    shuffled batches (seeded order). With ``codes`` (int64 [S, W]) the last
+    layer also takes the codes (init_params then holds W3 [m, h2 + 64 W], e.g.
+    from prior_params). With ``home`` (int32 [S]) each row's home partition,
+    probed anyway, is left out of its softmax. Returns the trained Router."""
     S, d = feats_bf16.shape
     h1, h2 = cfg.hidden
     B = min(cfg.batch, S - S % 8)
-    r = Router(init_params, d, h1, h2, m, max_batch=max(B, 8))
+    cbits = 0 if codes is None else 64 * codes.shape[1]
+    r = Router(init_params, d, h1, h2, m, max_batch=max(B, 8), code_bits=cbits)
     rng = np.random.default_rng(seed)
     for ep in range(cfg.epochs):
         order = torch.from_numpy(rng.permutation(S)).to(feats_bf16.device)
         last = None
         for s in range(0, S - B + 1, B):
             idx = order[s:s + B]
-            last = r.train_step(feats_bf16[idx].contiguous(), labels[idx].contiguous(), cfg.lr)
+            cx = None if codes is None else codes[idx].contiguous()
+            hx = None if home is None else home[idx].to(torch.int32).contiguous()
+            last = r.train_step(feats_bf16[idx].contiguous(), labels[idx].contiguous(), cfg.lr,
+                                codes=cx, exclude=hx)
         if log is not None and last is not None:
             log(ep, float(last.item()))
     return r
 
 
-def learned_routes(router: Router, feats_bf16, home, P: int):
+def learned_routes(router: Router, feats_bf16, home, P: int, codes=None):
     """int32 [N, P]: home first, then the router's P - 1 best other partitions."""
-    return router.route(feats_bf16, home.to(torch.int32).contiguous(), P)
+    return router.route(feats_bf16, home.to(torch.int32).contiguous(), P, codes=codes)

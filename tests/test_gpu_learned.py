@@ -3,7 +3,9 @@
 Same data, same Bk-means centres, same home partitions, same number P of probed
 partitions per point: the divide-and-conquer graph built with the nearest-centre
 probes of Section 3.2 against the graph built with the router's probes (home +
-P - 1 learned picks). Recall@k of both is judged against exact brute-force rows
+P - 1 learned picks). The router's last layer also takes the code as +-1 and
+starts at the nearest-centre logits, so training starts from the method's own
+routing. Recall@k of both is judged against exact brute-force rows
 (bdg_knn_rows) on sampled points; the router must not lose recall, and it must
 gain at the smaller P. The exact rows themselves are checked against the CPU
 oracle on a few points."""
@@ -45,15 +47,18 @@ def test_learned_router_gains_over_nearest_centre_probes(bdg):
     home = bdg.route(codes, cent, 1)[0][:, 0].contiguous()
     xb = feats.to(torch.bfloat16).contiguous()
 
-    # training data: exact neighbours within a seeded sample, their home partitions
+    # training data: the exact neighbours (over all points) of a seeded sample,
+    # their home partitions
     S = 40_000
     tr = torch.from_numpy(datagen.sample_ids(n, S, spec.seed + 5)).cuda()
-    labels = learned.neighbour_labels(codes[tr].contiguous(), home[tr].contiguous(), k)
-    init = torch.from_numpy(datagen.router_init(128, 256, 256, m, spec.seed + 5)).cuda()
+    labels = learned.neighbour_labels_full(codes, tr.to(torch.int32), home, k)
+    base = torch.from_numpy(datagen.router_init(128, 256, 256, m, spec.seed + 5)).cuda()
+    init = learned.prior_params(base, 128, 256, 256, m, cent)
     cfg = learned.TrainConfig(hidden=(256, 256), batch=2048, epochs=6, lr=1e-3)
     losses = []
     router = learned.train_router(xb[tr].contiguous(), labels, m, init, cfg, seed=spec.seed + 5,
-                                  log=lambda ep, l: losses.append(l))
+                                  log=lambda ep, l: losses.append(l), codes=codes[tr].contiguous(),
+                                  home=home[tr].contiguous())
     assert losses[-1] < losses[0]
 
     # judge rows
@@ -68,7 +73,7 @@ def test_learned_router_gains_over_nearest_centre_probes(bdg):
     for P in (2, 4):
         r_ex, _ = bdg.route(codes, cent, P)
         g_ex = bdg.build_graph(codes, k, m=m, t=P, routes=r_ex, entry=entry)
-        r_ln = learned.learned_routes(router, xb, home, P)
+        r_ln = learned.learned_routes(router, xb, home, P, codes=codes)
         assert torch.equal(r_ln[:, 0], home)
         g_ln = bdg.build_graph(codes, k, m=m, t=P, routes=r_ln, entry=entry)
         res[P] = (_recall(g_ex, ex_ids, ex_d, rows), _recall(g_ln, ex_ids, ex_d, rows))

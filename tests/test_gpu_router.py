@@ -149,3 +149,63 @@ def test_router_route_top_p(bdg):
             kth = np.sort(zz)[::-1][P - 2]
             tol = 1e-2 * np.abs(z_o[i]).max()
             assert np.all(zz[got] >= kth - tol)
+
+
+def _rand_codes(n, bits, seed):
+    c = datagen.random_codes(n, bits, seed)
+    return c, c.numpy().view(np.uint64)
+
+
+def test_router_code_input_forward_and_gradients(bdg):
+    """Last layer over [h2 | code as +-1], one partition per row left out of the
+    softmax: forward, loss and gradients against the oracle."""
+    d, h1, h2, m, B, kt, bits = 64, 32, 48, 40, 256, 12, 128
+    flat, params = _net(21, d, h1, h2, m)
+    rng = np.random.default_rng(22)
+    params["W3"] = rng.uniform(-0.1, 0.1, (m, h2 + bits))
+    o = np.cumsum([0, h1 * d, h1, h2 * h1, h2])
+    flat = np.concatenate([flat[:o[-1]], params["W3"].reshape(-1), params["b3"]]).astype(np.float32)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):  # the oracle sees the fp32 values
+        params[k] = params[k].astype(np.float32).astype(np.float64)
+    r = bdg.Router(torch.from_numpy(flat).cuda(), d, h1, h2, m, max_batch=256, code_bits=bits)
+    x, lab = _batch(B, d, m, kt, 23)
+    ct, cu = _rand_codes(B, bits, 24)
+    s = omlp.code_pm(cu, bits)
+    xb, cd = _bf16(x).cuda(), ct.cuda()
+    z = r.forward(xb, codes=cd).cpu().numpy()
+    z_o, _ = omlp.forward(params, x, bf16=True, s=s)
+    assert np.abs(z - z_o).max() <= 1e-2 * np.abs(z_o).max()
+    ex = np.random.default_rng(25).integers(0, m, B).astype(np.int32)
+    lab[::5, 0] = ex[::5]  # labels naming the left-out partition are ignored
+    r.train_step(xb, torch.from_numpy(lab).cuda(), lr=0.0, apply_update=False, codes=cd,
+                 exclude=torch.from_numpy(ex).cuda())
+    torch.cuda.synchronize()
+    loss_o, g_o, _ = omlp.loss_and_grads(params, x, omlp.label_targets(lab, m, exclude=ex),
+                                         bf16=True, s=s, exclude=ex)
+    assert abs(float(r.loss.item()) - loss_o) <= 1e-3 * abs(loss_o)
+    g = r.unpack(r.grads.cpu())
+    for name in ["W1", "b1", "W2", "b2", "W3", "b3"]:
+        a, b_ = g[name].double().numpy(), g_o[name]
+        rel = np.linalg.norm(a - b_) / (np.linalg.norm(b_) + 1e-30)
+        assert rel <= 2e-2, (name, rel)
+    assert int(r.err.item()) == 0
+
+
+def test_prior_router_routes_like_nearest_centres(bdg):
+    """Untrained router with prior_params: its routes equal the oracle's
+    nearest-centre routes exactly (home = nearest centre, then by (d, c))."""
+    import oracle
+    from paper_2102_04656_b300 import learned
+    d, h1, h2, m, N, P, bits = 64, 32, 32, 96, 3000, 6, 256
+    flat, _ = _net(31, d, h1, h2, m)
+    ct, cu = _rand_codes(N, bits, 32)
+    cent_t, cent_u = _rand_codes(m, bits, 33)
+    cent_t[7] = cent_t[50]  # duplicate centres: ties broken by index
+    cent_u = cent_t.numpy().view(np.uint64)
+    init = learned.prior_params(torch.from_numpy(flat).cuda(), d, h1, h2, m, cent_t.cuda())
+    r = bdg.Router(init, d, h1, h2, m, max_batch=1024, code_bits=bits)  # 3 chunks
+    want, _ = oracle.route(cu, cent_u, P)
+    x = _bf16(np.random.default_rng(34).standard_normal((N, d))).cuda()
+    got = learned.learned_routes(r, x, torch.from_numpy(want[:, 0].copy()).cuda(), P,
+                                 codes=ct.cuda()).cpu().numpy()
+    assert np.array_equal(got, want)

@@ -84,3 +84,81 @@ def test_rows_without_target_have_no_gradient():
     # the two target-less rows change nothing but the 1/B normalisation
     for name in g:
         assert np.allclose(g[name] * 3, g1[name], rtol=1e-12, atol=1e-14)
+
+
+def test_code_input_gradients_match_finite_differences():
+    rng = np.random.default_rng(5)
+    p = _params(rng)
+    cb = 3
+    p["W3"] = rng.standard_normal((4, 5 + cb)) * 0.5
+    x = rng.standard_normal((6, 6))
+    s = np.where(rng.random((6, cb)) < 0.5, 1.0, -1.0)
+    q = rng.random((6, 4))
+    q /= q.sum(1, keepdims=True)
+    _, g, _ = mlp.loss_and_grads(p, x, q, bf16=False, s=s)
+    eps = 1e-6
+    for name, w in p.items():
+        flat = w.reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 8)):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp, _, _ = mlp.loss_and_grads(p, x, q, bf16=False, s=s)
+            flat[idx] = old - eps
+            lm, _, _ = mlp.loss_and_grads(p, x, q, bf16=False, s=s)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - g[name].reshape(-1)[idx]) < 1e-6 * max(1.0, abs(fd)), name
+
+
+def test_prior_weights_give_nearest_centre_routing(oracle_lib):
+    """W3 = [0 | c_p / 2], b3 = 0: logits are bits/2 - Hamming distance (checked by a
+    per-bit loop), and their top-t by (-z, p) is the C oracle's nearest-centre route."""
+    rng = np.random.default_rng(6)
+    n, m, bits, h = 40, 24, 128, 8
+    codes = rng.integers(0, 2**63, size=(n, bits // 64), dtype=np.int64).view(np.uint64)
+    cent = rng.integers(0, 2**63, size=(m, bits // 64), dtype=np.int64).view(np.uint64)
+    cent[5] = cent[9]  # duplicate centres: equal logits, order by index
+    s, cs = mlp.code_pm(codes, bits), mlp.code_pm(cent, bits)
+    p = _params(rng, d_in=6, h=h, m=m)
+    p["W3"] = np.concatenate([np.zeros((m, h)), cs / 2], axis=1)
+    p["b3"] = np.zeros(m)
+    z, _ = mlp.forward(p, rng.standard_normal((n, 6)), bf16=True, s=s)
+    for i in range(0, n, 7):
+        for c in range(m):
+            d = sum(((int(codes[i, b // 64]) >> (b % 64)) & 1) != ((int(cent[c, b // 64]) >> (b % 64)) & 1)
+                    for b in range(bits))
+            assert z[i, c] == bits / 2 - d
+    routes, _ = oracle_lib.route(codes, cent, 5)
+    assert np.array_equal(mlp.topp(z, 5), routes)
+
+
+def test_excluded_partition_is_left_out_of_the_softmax():
+    """Leaving partition e out equals the plain loss of the network whose logit e
+    is removed: checked against a hand-built softmax over the other columns and
+    by finite differences."""
+    rng = np.random.default_rng(7)
+    p = _params(rng, m=5)
+    x = rng.standard_normal((4, 6))
+    ex = np.array([0, 3, 3, 1])
+    lab = np.array([[0, 1, 2], [3, 3, 4], [1, -1, 3], [0, 2, 2]])
+    q = mlp.label_targets(lab, 5, exclude=ex)
+    assert np.allclose(q[1], [0, 0, 0, 0, 1]) and np.allclose(q[2], [0, 1, 0, 0, 0])
+    loss, g, z = mlp.loss_and_grads(p, x, q, bf16=False, exclude=ex)
+    want = 0.0
+    for i in range(4):
+        keep = [c for c in range(5) if c != ex[i]]
+        lse = np.log(np.exp(z[i, keep]).sum())
+        want -= sum(q[i, c] * (z[i, c] - lse) for c in keep)
+    assert abs(loss - want / 4) < 1e-12
+    eps = 1e-6
+    for name in ("W3", "b3", "W1"):
+        flat = p[name].reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 5)):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp, _, _ = mlp.loss_and_grads(p, x, q, bf16=False, exclude=ex)
+            flat[idx] = old - eps
+            lm, _, _ = mlp.loss_and_grads(p, x, q, bf16=False, exclude=ex)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - g[name].reshape(-1)[idx]) < 1e-6 * max(1.0, abs(fd)), name
