@@ -29,6 +29,7 @@ namespace {
 constexpr int kWarps = 4;
 constexpr int kHash = 1024;  // visited-id hash slots per warp
 constexpr int kProbe = 8;
+constexpr int kSmallBatch = 8;  // accepted keys ranked by counting instead of a sort
 
 template <int CAPW>
 struct PoolSmem {
@@ -111,25 +112,41 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
       hash_visit(sm.hash, bdg_key_id(best));
     }
     int size = 1, hint = 0, nexp = 0;
+    // speculation: while a node is expanded, the neighbour list of the next
+    // unexpanded pool entry is loaded (and its codes prefetched); it is used if
+    // that entry is still the one expanded next
+    int32_t spec_node = -1, spec_nb = -1;
     __syncwarp();
 
     for (;;) {
-      // first unexpanded slot at or after `hint`
-      int slot = -1;
+      // first unexpanded slot at or after `hint`, and the one after it
+      int slot = -1, slot2 = -1;
       for (int b = hint & ~31; b < size; b += 32) {
         const int j = b + lane;
-        const unsigned m = __ballot_sync(0xffffffffu, j < size && !sm.expd[j]);
-        if (m) { slot = b + __ffs(m) - 1; break; }
+        unsigned m = __ballot_sync(0xffffffffu, j < size && !sm.expd[j]);
+        if (slot < 0 && m) {
+          slot = b + __ffs(m) - 1;
+          m &= m - 1;
+        }
+        if (slot >= 0 && m) { slot2 = b + __ffs(m) - 1; break; }
       }
       if (slot < 0) break;
       hint = slot + 1;
       const uint64_t ck = sm.key[slot];
+      const int32_t node2 = slot2 >= 0 ? bdg_key_id(sm.key[slot2]) : -1;
       __syncwarp();
       if (lane == 0) sm.expd[slot] = 1;
       ++nexp;
       const int32_t node = bdg_key_id(ck);
+      const bool use_spec = node == spec_node;
+      const int32_t cur_spec_nb = spec_nb;
+      if (g.deg <= 32) {  // load the next candidate's list now; its codes are prefetched below
+        spec_node = node2;
+        spec_nb = (node2 >= 0 && lane < g.deg) ? g.ids[(int64_t)node2 * g.deg + lane] : -1;
+      }
       for (int b0 = 0; b0 < g.deg; b0 += 32) {
-        const int32_t nb = (b0 + lane < g.deg) ? g.ids[(int64_t)node * g.deg + b0 + lane] : -1;
+        const int32_t nb = use_spec ? cur_spec_nb
+                         : (b0 + lane < g.deg) ? g.ids[(int64_t)node * g.deg + b0 + lane] : -1;
         uint64_t key = BDG_KEY_INF;
         bool acc = false;
         const int hv = (nb >= 0 && nb < g.n) ? hash_visit(sm.hash, nb) : kSeen;
@@ -154,20 +171,34 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
         const unsigned am = __ballot_sync(0xffffffffu, acc);
         if (am == 0) continue;
         const int na = __popc(am);
-        // sort accepted keys ascending across the warp (rejected = +inf)
-        uint64_t v = acc ? key : BDG_KEY_INF;
-#pragma unroll
-        for (int k2 = 2; k2 <= 32; k2 <<= 1) {
-#pragma unroll
-          for (int j = k2 >> 1; j > 0; j >>= 1) {
-            const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
-            const bool up = (lane & k2) == 0;
-            const bool low = (lane & j) == 0;
-            v = (low == up) ? umin64(v, o) : umax64(v, o);
+        uint64_t v;
+        if (na <= kSmallBatch) {
+          // few accepted keys: each finds its rank by comparing with the others
+          int rank = 0;
+          for (unsigned mm = am; mm; mm &= mm - 1) {
+            const int src = __ffs(mm) - 1;
+            const uint64_t o = __shfl_sync(0xffffffffu, key, src);
+            rank += (o < key) || (o == key && src < lane);  // an id listed twice
           }
+          if (acc) sm.nk[rank] = key;
+          __syncwarp();
+          v = lane < na ? sm.nk[lane] : BDG_KEY_INF;
+        } else {
+          // sort accepted keys ascending across the warp (rejected = +inf)
+          v = acc ? key : BDG_KEY_INF;
+#pragma unroll
+          for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+#pragma unroll
+            for (int j = k2 >> 1; j > 0; j >>= 1) {
+              const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
+              const bool up = (lane & k2) == 0;
+              const bool low = (lane & j) == 0;
+              v = (low == up) ? umin64(v, o) : umax64(v, o);
+            }
+          }
+          sm.nk[lane] = v;
+          __syncwarp();
         }
-        sm.nk[lane] = v;
-        __syncwarp();
         // new key positions: own rank + rank in the pool
         int newpos = CAP;
         if (lane < na) {
@@ -191,10 +222,15 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
           if (j >= minpos && j < size) {
             pk = sm.key[j];
             pf = sm.expd[j];
-            int lo = 0, hi = na;
-            while (lo < hi) {
-              const int mid = (lo + hi) >> 1;
-              if (sm.nk[mid] < pk) lo = mid + 1; else hi = mid;
+            int lo = 0;
+            if (na <= kSmallBatch) {
+              for (int i = 0; i < na; ++i) lo += (sm.nk[i] < pk);
+            } else {
+              int hi = na;
+              while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sm.nk[mid] < pk) lo = mid + 1; else hi = mid;
+              }
             }
             pp = j + lo;
           }
@@ -207,6 +243,9 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
         hint = min(hint, minpos);
         __syncwarp();
       }
+      // codes of the speculated next list: into L2 while the pool is scanned
+      if (spec_nb >= 0 && spec_nb < g.n)
+        asm volatile("prefetch.L2 [%0];" ::"l"(g.codes + (int64_t)spec_nb * W));
     }
     const int keep = min(size, R);
     for (int r = lane; r < R; r += 32) {
