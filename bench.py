@@ -299,6 +299,36 @@ def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
     ef_s = ef[qs].cpu().numpy()
     rec_by_ef = {int(e): float(hits[ef_s == e].sum()) / max(1, (ef_s == e).sum() * topk)
                  for e in w["efs"]}
+    # search quality: the same queries answered by an exhaustive Hamming scan
+    # (top R by distance over all N codes, ties in any order; torch +-1 matmul,
+    # exact integers in FP32) followed by the same FP32 re-rank; recall@10 of
+    # the graph search's answers against those
+    bits = spec.bits
+    shifts = torch.arange(64, device=device, dtype=torch.int64)
+
+    def pm(c):  # packed codes -> +-1 float32
+        return (((c[:, :, None] >> shifts) & 1).reshape(c.shape[0], bits).float() * 2 - 1)
+
+    qpm = pm(qcodes[qs])
+    bestk = torch.full((qs.numel(), R), float("inf"), device=device)
+    besti = torch.zeros((qs.numel(), R), dtype=torch.int64, device=device)
+    for s0 in range(0, n, 1 << 20):
+        e0 = min(n, s0 + (1 << 20))
+        dh = (bits - qpm @ pm(codes[s0:e0]).T) * 0.5  # Hamming distances, exact
+        v, i = torch.topk(dh, R, dim=1, largest=False, sorted=True)
+        cat_v = torch.cat([bestk, v], 1)
+        cat_i = torch.cat([besti, i + s0], 1)
+        o = torch.topk(cat_v, R, dim=1, largest=False).indices
+        bestk, besti = torch.gather(cat_v, 1, o), torch.gather(cat_i, 1, o)
+    # re-rank the exhaustive candidates with the library's FP32 re-rank
+    bf_ids, _ = bdg.rerank(feats, qfeats[qs].contiguous(), besti.to(torch.int32).contiguous(), topk)
+    got_s = ids[qs].long().cpu().numpy()
+    bf = bf_ids.long().cpu().numpy()
+    hits_bf = np.array([len(set(a.tolist()) & set(b.tolist())) for a, b in zip(got_s, bf)])
+    rec_vs_bf = float(hits_bf.sum()) / (qs.numel() * topk)
+    hits_bfx = np.array([len(set(a.tolist()) & set(b.tolist()))
+                         for a, b in zip(bf, best_i.cpu().numpy())])
+    rec_bf_exact = float(hits_bfx.sum()) / (qs.numel() * topk)
     # algorithmic bytes of the search kernel: per expansion a 4*deg-byte id list and
     # one 32-byte code per scored neighbour (upper bound: every neighbour scored)
     _, _, ex = bdg.search(g, qcodes, ef, R, ef_max=max(w["efs"]), expansions=True)
@@ -311,6 +341,8 @@ def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
         "ef_mix": list(w["efs"]), "R": R, "topk": topk, "graph_build": {"m": m, "t": t,
                                                                          "seconds": build_s},
         "qps": nq / (ms / 1000.0), "ms_per_batch": ms, "recall@10_vs_exact_fp32": rec,
+        "recall@10_vs_exhaustive_hamming_rerank": rec_vs_bf,
+        "exhaustive_hamming_rerank_recall@10_vs_exact_fp32": rec_bf_exact,
         "recall@10_by_ef": rec_by_ef, "entry_sample": n_entry,
         "recall_queries": int(qs.numel()), "search_kernel_ms": search_ms,
         "rerank_kernel_ms": rerank_ms, "expansions_mean": exp_total / nq,

@@ -22,9 +22,11 @@
 //     exact k-th smallest distance so far (binary search over its list), or its
 //     exact k-th smallest word when ties at that distance fill the list. The
 //     threshold only tightens, so every final neighbour is kept.
-// At the end of the item each warp selects, row by row, the k smallest
-// (d, id) keys among the candidates inside the final threshold (bitonic sort
-// of at most 128 keys) and writes the row's partial list.
+// At the end of an item, in round A (and in a single-round build) each thread
+// cuts its row's list to its k + 1 best words, ranks them by counting and
+// writes its row without the self pair; in the sub-rounds each warp sorts, row
+// by row, the few candidates below the running list's k-th key and merges them
+// into that list.
 //
 // Every mbarrier wait is bounded; a wait that gives up sets the device error
 // word and the CTA drains (waits for its own copies and MMAs, bounded) and
@@ -39,7 +41,11 @@ constexpr int kNT = 64;         // homes per tile (TMEM columns per accumulator)
 constexpr int kStages = 2;
 constexpr int kCap = 188;       // candidate slots per row
 constexpr int kHalf = 16;       // compaction is checked every 16 columns
-constexpr int kSortN = 128;     // keys sorted per row at selection
+constexpr int kSortN = 128;     // keys sorted per row at selection (sub-rounds)
+constexpr int kOutSlot = 96;    // first slot of a row's ranked words (round A / one round)
+constexpr int kNeedMax = 65;    // k + 1 for the largest k the kernel takes
+static_assert(kOutSlot >= kNeedMax && kOutSlot + kNeedMax <= kCap,
+              "ranked words need k + 1 free slots after the list");
 // words between a row's candidate slots: slot c of row r is word c * kM + r, so
 // the 32 lanes of a warp (32 rows) always touch 32 different banks, whatever
 // slot each row is at
@@ -138,6 +144,7 @@ __device__ __forceinline__ uint32_t cidx(int c, int r) {  // candidate slot c of
 // Keep the row's candidates below thr_w, in order. Returns the new count.
 __device__ __forceinline__ int compact_row(uint32_t* crow, int cnt, uint32_t thr_w) {
   int w = 0;
+#pragma unroll 8
   for (int x = 0; x < cnt; ++x) {
     const uint32_t e = crow[x * kCandStride];
     if (e < thr_w) crow[(w++) * kCandStride] = e;
@@ -145,37 +152,49 @@ __device__ __forceinline__ int compact_row(uint32_t* crow, int cnt, uint32_t thr
   return w;
 }
 
-// Exact compaction of one row's list (every listed word is below thr_w): once it
-// holds need_k words, the bound becomes the need_k-th smallest distance (binary
-// search over the list) and the words above it are dropped; if ties at that
-// distance still leave more than `limit` words, the need_k-th smallest word
-// itself becomes the bound, leaving exactly need_k. Returns the new count.
+// Number of listed words with distance <= dm.
+__device__ __forceinline__ int count_le(const uint32_t* crow, int cnt, int dm) {
+  int c2 = 0;
+#pragma unroll 8
+  for (int x = 0; x < cnt; ++x) c2 += ((int)(crow[x * kCandStride] >> kPosBits) <= dm);
+  return c2;
+}
+
+// Exact compaction of one row's list. Every listed word is below thr_w, and the
+// list is in position order (words are appended by increasing position and
+// compaction keeps their order). Once it holds need_k words, the bound becomes
+// the need_k-th smallest distance and the words above it are dropped; if ties
+// at that distance still leave more than `limit` words, the need_k-th smallest
+// word itself becomes the bound, leaving exactly need_k. Returns the new count.
 __device__ __forceinline__ int compact_exact(uint32_t* crow, int cnt, uint32_t& thr_w, int need_k,
                                              int bits, int limit) {
   if (cnt < need_k) return cnt;
-  int lo = 0, hi = min((int)((thr_w - 1u) >> kPosBits), bits);
+  // the k-th distance: binary search over [0, td], td the bound's distance;
+  // between compactions it usually drops by a few units, so [td - 7, td] is
+  // tried first
+  const int td = min((int)((thr_w - 1u) >> kPosBits), bits);
+  int lo = 0, hi = td;
+  if (td >= 8) {
+    if (count_le(crow, cnt, td - 8) >= need_k) hi = td - 8; else lo = td - 7;
+  }
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    int c2 = 0;
-    for (int x = 0; x < cnt; ++x) c2 += ((int)(crow[x * kCandStride] >> kPosBits) <= mid);
-    if (c2 >= need_k) hi = mid; else lo = mid + 1;
+    if (count_le(crow, cnt, mid) >= need_k) hi = mid; else lo = mid + 1;
   }
   thr_w = min(thr_w, (uint32_t)(lo + 1) << kPosBits);
   cnt = compact_row(crow, cnt, thr_w);
   if (cnt > limit) {
+    // words at distance lo are in position order: the bound is the
+    // (need_k - #{d < lo})-th of them
     int c_lt = 0;
+#pragma unroll 8
     for (int x = 0; x < cnt; ++x) c_lt += ((int)(crow[x * kCandStride] >> kPosBits) < lo);
-    const int want = need_k - c_lt - 1;  // rank among the words at distance lo
+    const int want = need_k - c_lt;  // 1-based rank among the words at distance lo
     uint32_t wk = thr_w - 1u;
+    int seen = 0;
     for (int x = 0; x < cnt; ++x) {
       const uint32_t e = crow[x * kCandStride];
-      if ((int)(e >> kPosBits) != lo) continue;
-      int below = 0;
-      for (int y = 0; y < cnt; ++y) {
-        const uint32_t f = crow[y * kCandStride];
-        below += (f < e && (int)(f >> kPosBits) == lo);
-      }
-      if (below == want) wk = e;
+      if ((int)(e >> kPosBits) == lo && ++seen == want) { wk = e; break; }
     }
     thr_w = wk + 1u;
     cnt = compact_row(crow, cnt, thr_w);
@@ -405,112 +424,177 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           cnt += (int)((wp - wp0) / kCandStride);
         }
       }
-      // ---- final compaction: a list longer than the sort takes is cut to its k
-      // best words
-      if (__any_sync(0xffffffffu, cnt > kSortN)) {
-        if (cnt > kSortN) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kSortN);
-        if (cnt > kSortN) overflow = true;  // cannot happen; the popcount kernel would redo it
-      }
-      // ---- selection: k smallest (d, id) among candidates inside the threshold
-      uint64_t* sb = sortbuf + warp * 128;
       const uint64_t pad = bdg_pad_key(bits);
-      for (int rr = 0; rr < 32; ++rr) {
-        const int row = warp * 32 + rr;
-        const int n_r = __shfl_sync(0xffffffffu, cnt, rr);
-        const uint32_t tb = __shfl_sync(0xffffffffu, thr_w, rr);
-        const int ovf = __shfl_sync(0xffffffffu, overflow ? 1 : 0, rr);
-        const uint64_t kb = __shfl_sync(0xffffffffu, kth, rr);
-        if (row >= nv) continue;
-        const int32_t vid = c.visit_ids[v0 + row];
-        if (vid < 0) {  // an invalid id: its row (written by position) is padding
-          if (a.t == 1 && a.out_by_pos) {
-            const int64_t orow = (int64_t)(tile * kM + row);
-            for (int j2 = lane; j2 < k; j2 += 32) {
-              a.out_ids[orow * k + j2] = -1;
-              a.out_dist[orow * k + j2] = bits + 1;
-            }
-          }
-          continue;
+      if (!a.merge_running) {
+        // ---- round A or a single round. Each thread cuts its row's list to
+        // exactly its need_k best words, ranks them by counting (word order is
+        // (d, id) order) into slots kOutSlot.., and looks up their ids into
+        // slots 0..; then each warp writes its 32 rows, coalesced, without the
+        // self pair.
+        if (__any_sync(0xffffffffu, !overflow && cnt > need_k)) {
+          if (!overflow && cnt > need_k) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, need_k);
         }
-        if (ovf) {  // recomputed by the popcount kernel
-          if (lane == 0) ta.fixflag[v0 + row] = 1;
-          continue;
+        if (cnt > need_k) overflow = true;  // cannot happen; the popcount kernel would redo it
+        const int32_t myvid = r < nv ? c.visit_ids[v0 + r] : -1;
+        int self_j = kNeedMax;  // sorted index of the self pair (none: kNeedMax)
+        if (!overflow) {
+          uint32_t wv[kNeedMax];  // the row's words in registers (missing ones: never below)
+#pragma unroll
+          for (int j = 0; j < kNeedMax; ++j) wv[j] = j < cnt ? crow[j * kCandStride] : 0xFFFFFFFFu;
+          for (int i = 0; i < cnt; ++i) {
+            const uint32_t wi = crow[i * kCandStride];
+            int rank = 0;
+#pragma unroll
+            for (int j = 0; j < kNeedMax; ++j) rank += (wv[j] < wi);
+            crow[(kOutSlot + rank) * kCandStride] = wi;
+          }
+          for (int j0 = 0; j0 < cnt; j0 += 8) {
+            int32_t h8[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {  // eight id loads in flight
+              const int j = j0 + q;
+              h8[q] = j < cnt ? c.home_ids[h0 + (int)(crow[(kOutSlot + j) * kCandStride] & kPosMask)]
+                              : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int j = j0 + q;
+              if (j < cnt) {
+                crow[j * kCandStride] = (uint32_t)h8[q];
+                if (h8[q] == myvid && self_j == kNeedMax) self_j = j;
+              }
+            }
+          }
         }
-        if (a.merge_running && n_r == 0) continue;  // nothing to merge
-        if (n_r <= 32) {
-          // few candidates: one key per lane, bitonic sort across the warp in registers
-          uint64_t key = BDG_KEY_INF;
-          if (lane < n_r) {
-            const uint32_t e = cand[cidx(lane, row)];
-            const int d = (int)(e >> kPosBits);
-            if (e < tb) {
-              const int32_t hid = c.home_ids[h0 + (int)(e & kPosMask)];
-              if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
+        __syncwarp();
+        for (int rr = 0; rr < 32; ++rr) {
+          const int row = warp * 32 + rr;
+          const int n_r = __shfl_sync(0xffffffffu, cnt, rr);
+          const int sj = __shfl_sync(0xffffffffu, self_j, rr);
+          const int ovf = __shfl_sync(0xffffffffu, overflow ? 1 : 0, rr);
+          const int32_t vid = __shfl_sync(0xffffffffu, myvid, rr);
+          if (row >= nv) continue;
+          const int64_t orow = a.out_by_pos ? (int64_t)(tile * kM + row) : (int64_t)vid;
+          if (vid < 0) {  // an invalid id: its row (written by position) is padding
+            if (a.t == 1 && a.out_by_pos) {
+              for (int j2 = lane; j2 < k; j2 += 32) {
+                a.out_ids[orow * k + j2] = -1;
+                a.out_dist[orow * k + j2] = bits + 1;
+              }
+            }
+            continue;
+          }
+          if (ovf) {  // recomputed by the popcount kernel
+            if (lane == 0) ta.fixflag[v0 + row] = 1;
+            continue;
+          }
+          const int n_out = min(k, n_r - (sj < n_r ? 1 : 0));
+          for (int o = lane; o < k; o += 32) {
+            if (o < n_out) {
+              const int e = o + (o >= sj ? 1 : 0);  // sorted index, the self pair skipped
+              const int32_t hid = (int32_t)cand[cidx(e, row)];
+              const uint32_t d = cand[cidx(kOutSlot + e, row)] >> kPosBits;
+              if (a.t == 1) {
+                a.out_ids[orow * k + o] = hid;
+                a.out_dist[orow * k + o] = (int32_t)d;
+              } else {
+                a.partial[(int64_t)vid * k + o] = bdg_key(d, (uint32_t)hid);
+              }
+            } else {  // fewer than k candidates: padding
+              if (a.t == 1) {
+                a.out_ids[orow * k + o] = -1;
+                a.out_dist[orow * k + o] = bits + 1;
+              } else {
+                a.partial[(int64_t)vid * k + o] = pad;
+              }
             }
           }
-          // a sub-round key above the running k-th cannot enter: a row left
-          // without keys is done
-          if (a.merge_running && !__any_sync(0xffffffffu, key < kb)) continue;
-#pragma unroll
-          for (int k2 = 2; k2 <= 32; k2 <<= 1) {
-#pragma unroll
-            for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
-              const uint64_t o = __shfl_xor_sync(0xffffffffu, key, j2);
-              const bool up = (lane & k2) == 0, low = (lane & j2) == 0;
-              key = (low == up) ? (key < o ? key : o) : (key < o ? o : key);
-            }
+        }
+      } else {
+        // ---- sub-round: a list longer than the sort takes is cut to its k best words
+        if (__any_sync(0xffffffffu, cnt > kSortN)) {
+          if (cnt > kSortN) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kSortN);
+          if (cnt > kSortN) overflow = true;  // cannot happen; the popcount kernel would redo it
+        }
+        // ---- selection: k smallest (d, id) among candidates inside the threshold
+        uint64_t* sb = sortbuf + warp * 128;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int row = warp * 32 + rr;
+          const int n_r = __shfl_sync(0xffffffffu, cnt, rr);
+          const uint32_t tb = __shfl_sync(0xffffffffu, thr_w, rr);
+          const int ovf = __shfl_sync(0xffffffffu, overflow ? 1 : 0, rr);
+          const uint64_t kb = __shfl_sync(0xffffffffu, kth, rr);
+          if (row >= nv) continue;
+          const int32_t vid = c.visit_ids[v0 + row];
+          if (vid < 0) continue;  // an invalid id
+          if (ovf) {  // recomputed by the popcount kernel
+            if (lane == 0) ta.fixflag[v0 + row] = 1;
+            continue;
           }
-          sb[lane] = key;
-          sb[lane + 32] = BDG_KEY_INF;
-          sb[lane + 64] = BDG_KEY_INF;
-          sb[lane + 96] = BDG_KEY_INF;
-          __syncwarp();
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int x = lane + 32 * q;
+          if (n_r == 0) continue;  // nothing to merge
+          if (n_r <= 32) {
+            // few candidates: one key per lane, bitonic sort across the warp in registers
             uint64_t key = BDG_KEY_INF;
-            if (x < n_r) {
-              const uint32_t e = cand[cidx(x, row)];
+            if (lane < n_r) {
+              const uint32_t e = cand[cidx(lane, row)];
               const int d = (int)(e >> kPosBits);
               if (e < tb) {
                 const int32_t hid = c.home_ids[h0 + (int)(e & kPosMask)];
                 if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
               }
             }
-            sb[x] = key;
-          }
-          __syncwarp();
-          // bitonic sort of 128 keys, ascending
-          for (int size = 2; size <= 128; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-#pragma unroll
-              for (int q = 0; q < 2; ++q) {
-                const int i = lane + 32 * q;                           // pair index 0..63
-                const int lo2 = (i / stride) * (2 * stride) + (i % stride);
-                const int hi2 = lo2 + stride;
-                const bool up = (lo2 & size) == 0;
-                const uint64_t x0 = sb[lo2], x1 = sb[hi2];
-                if ((x0 > x1) == up) { sb[lo2] = x1; sb[hi2] = x0; }
+            // a sub-round key above the running k-th cannot enter: a row left
+            // without keys is done
+            if (!__any_sync(0xffffffffu, key < kb)) continue;
+  #pragma unroll
+            for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+  #pragma unroll
+              for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+                const uint64_t o = __shfl_xor_sync(0xffffffffu, key, j2);
+                const bool up = (lane & k2) == 0, low = (lane & j2) == 0;
+                key = (low == up) ? (key < o ? key : o) : (key < o ? o : key);
               }
-              __syncwarp();
+            }
+            sb[lane] = key;
+            sb[lane + 32] = BDG_KEY_INF;
+            sb[lane + 64] = BDG_KEY_INF;
+            sb[lane + 96] = BDG_KEY_INF;
+            __syncwarp();
+          } else {
+  #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int x = lane + 32 * q;
+              uint64_t key = BDG_KEY_INF;
+              if (x < n_r) {
+                const uint32_t e = cand[cidx(x, row)];
+                const int d = (int)(e >> kPosBits);
+                if (e < tb) {
+                  const int32_t hid = c.home_ids[h0 + (int)(e & kPosMask)];
+                  if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
+                }
+              }
+              sb[x] = key;
+            }
+            __syncwarp();
+            // bitonic sort of 128 keys, ascending
+            for (int size = 2; size <= 128; size <<= 1) {
+              for (int stride = size >> 1; stride > 0; stride >>= 1) {
+  #pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                  const int i = lane + 32 * q;                           // pair index 0..63
+                  const int lo2 = (i / stride) * (2 * stride) + (i % stride);
+                  const int hi2 = lo2 + stride;
+                  const bool up = (lo2 & size) == 0;
+                  const uint64_t x0 = sb[lo2], x1 = sb[hi2];
+                  if ((x0 > x1) == up) { sb[lo2] = x1; sb[hi2] = x0; }
+                }
+                __syncwarp();
+              }
             }
           }
-        }
-        if (a.t == 1) {
-          const int64_t orow = a.out_by_pos ? (int64_t)(tile * kM + row) : (int64_t)vid;
-          for (int j2 = lane; j2 < k; j2 += 32) {
-            const uint64_t key = sb[j2] < pad ? sb[j2] : pad;
-            a.out_ids[orow * k + j2] = key < pad ? bdg_key_id(key) : -1;
-            a.out_dist[orow * k + j2] = bdg_key_d(key);
-          }
-        } else if (!a.merge_running) {  // round A: the running list starts as this row
-          uint64_t* out = a.partial + (int64_t)vid * k;
-          for (int j2 = lane; j2 < k; j2 += 32) out[j2] = sb[j2] < pad ? sb[j2] : pad;
-        } else {
           bdg_warp_merge_running(a.partial + (int64_t)vid * k, sb, k, k, pad, kb, lane);
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
     g += ntiles;
