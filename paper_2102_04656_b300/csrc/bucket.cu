@@ -154,9 +154,12 @@ plan_kernel(int m, int t, int tile_v, int32_t* __restrict__ hcnt, int32_t* __res
   // --- offsets of the 64-row-padded expanded home operand (tensor path)
   {
     int32_t s = 0;
-    for (int p = b; p < e; ++p) s += (hcnt[p] + 63) & ~63;
+    for (int p = b; p < e; ++p) s += (hcnt[p] + BDG_TC_TILE - 1) & ~(BDG_TC_TILE - 1);
     int32_t run = block_exclusive_scan(s, warp_tot, &total);
-    for (int p = b; p < e; ++p) { eoff[p] = run; run += (hcnt[p] + 63) & ~63; }
+    for (int p = b; p < e; ++p) {
+      eoff[p] = run;
+      run += (hcnt[p] + BDG_TC_TILE - 1) & ~(BDG_TC_TILE - 1);
+    }
     if (threadIdx.x == 0) eoff[m] = total;
     __syncthreads();
   }
@@ -247,7 +250,7 @@ __global__ void rows_plan_kernel(int64_t N, const int32_t* __restrict__ rows, in
     visit_off[0] = 0; visit_off[1] = (int32_t)nrows;
     part_order[0] = 0;
     item_off[0] = 0; item_off[1] = (int32_t)((nrows + tile_v - 1) / tile_v);
-    eoff[0] = 0; eoff[1] = (int32_t)((N + 63) & ~63LL);
+    eoff[0] = 0; eoff[1] = (int32_t)((N + BDG_TC_TILE - 1) & ~(int64_t)(BDG_TC_TILE - 1));
   }
 }
 

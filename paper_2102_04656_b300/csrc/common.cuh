@@ -178,6 +178,9 @@ __device__ __forceinline__ void bdg_warp_merge_running(uint64_t* R, const uint64
   __syncwarp();
 }
 // knn_tc.cu: tensor-core (tcgen05, FP8 +-1) Reduce 1 for 256/512-bit codes and k <= 64.
+// homes per tensor-core tile: each partition's expanded home operand is padded
+// to a multiple of this many rows
+constexpr int BDG_TC_TILE = 128;
 struct bdg_knn_tc_args {
   bdg_knn_args base;
   uint8_t* hexp;          // expanded home operand, eoff[m] rows x bits bytes

@@ -2,19 +2,23 @@
 //
 // Hamming distance as a +-1 dot product: with s = 2y - 1 in {-1, +1}^bits,
 // <s_a, s_b> = bits - 2 d(a, b). Codes become FP8 E4M3 +-1.0 and one
-// tcgen05.mma kind::f8f6f4 (M = 128 visitors x N = 64 homes x K = 32 bits)
+// tcgen05.mma kind::f8f6f4 (M = 128 visitors x N = 128 homes x K = 32 bits)
 // accumulates in FP32 in tensor memory; every partial sum is an integer of
 // magnitude <= 1024, so the result is exact.
 //
-// Work item = (partition p, 128 visitors of V_p). Roles inside a CTA:
-//   * producer (one thread): streams 64-home tiles of the pre-expanded home
-//     operand of p from HBM/L2 into a 2-stage shared-memory ring with
+// Work item = (partition p, 128 visitors of V_p). The visitors' codes are the
+// A operand: each epilogue thread writes its visitor's code, expanded to E4M3,
+// into its tensor-memory lane, and the MMAs read A from there (shared memory
+// holds only the home tiles, so its bandwidth serves B alone). Roles:
+//   * producer (one thread): streams 128-home tiles of the pre-expanded home
+//     operand of p from HBM/L2 into a shared-memory ring (2 stages of 64 KB at
+//     512 bits, 4 at 256) with
 //     cp.async.bulk (TMA bulk copies completing on mbarriers);
-//   * MMA issuer (one thread): K / 32 MMAs per tile into one of two TMEM
-//     accumulators (64 columns each), then tcgen05.commit frees the stage and
+//   * MMA issuer (one thread): K / 32 MMAs per tile into one of three TMEM
+//     accumulators (128 columns each), then tcgen05.commit frees the stage and
 //     hands the accumulator to the epilogue;
-//   * epilogue (4 warps, one thread per visitor row = TMEM lane): reads the 64
-//     dot products of its row and appends the values under its threshold as
+//   * epilogue (4 warps, one thread per visitor row = TMEM lane): reads its
+//     row's dot products, 64 at a time, and appends the values under its threshold as
 //     words (d << 21 | home position) to a per-row candidate list in shared
 //     memory. The homes of a partition are stored in ascending id order, so
 //     word order is (d, id) order. When a row's list is nearly full, the warp
@@ -37,8 +41,9 @@
 namespace {
 
 constexpr int kM = 128;         // visitors per item (TMEM lanes)
-constexpr int kNT = 64;         // homes per tile (TMEM columns per accumulator)
-constexpr int kStages = 2;
+constexpr int kNT = BDG_TC_TILE;  // homes per tile (TMEM columns per accumulator)
+constexpr int kSub = 64;        // columns the epilogue reads from TMEM at a time
+constexpr int kMaxStages = 4;   // home-tile ring in shared memory (2 stages of 64 KB at 512 bits)
 constexpr int kCap = 188;       // candidate slots per row
 constexpr int kHalf = 16;       // compaction is checked every 16 columns
 constexpr int kSortN = 128;     // keys sorted per row at selection (sub-rounds)
@@ -55,14 +60,18 @@ constexpr uint32_t kPolls = 1u << 20;
 constexpr int kPosBits = 21;    // home position bits in a candidate word
 constexpr uint32_t kPosMask = (1u << kPosBits) - 1;
 
+constexpr int kAcc = 3;                  // accumulators: the MMAs run up to 2 tiles ahead
+constexpr uint32_t kAccCols = kAcc * kNT;  // accumulators in TMEM columns [0, 384)
+constexpr uint32_t kTmemCols = 512;        // + the visitors' operand in [384, 384 + KB / 4)
+
 template <int W>
 struct TcCfg {
   static constexpr int KB = 64 * W;               // bytes of one expanded code
-  static constexpr uint32_t A_BYTES = kM * KB;
   static constexpr uint32_t B_BYTES = kNT * KB;
+  static constexpr int STAGES = W >= 8 ? 2 : kMaxStages;
   static constexpr uint32_t CAND_BYTES = ((kCap * kCandStride * 4) + 15) & ~15u;
-  static constexpr uint32_t OFF_B = A_BYTES;
-  static constexpr uint32_t OFF_CAND = OFF_B + kStages * B_BYTES;
+  static constexpr uint32_t OFF_B = 0;
+  static constexpr uint32_t OFF_CAND = OFF_B + STAGES * B_BYTES;
   static constexpr uint32_t OFF_SORT = OFF_CAND + CAND_BYTES;     // 4 warps x 128 keys
   static constexpr uint32_t OFF_BAR = OFF_SORT + 4 * kSortN * 8;
   static constexpr uint32_t SMEM = OFF_BAR + 256;
@@ -70,13 +79,8 @@ struct TcCfg {
                     OFF_SORT % 16 == 0 && OFF_BAR % 16 == 0,
                 "shared-memory regions must be 16-byte aligned");
   static_assert(SMEM <= 232448, "shared memory per block exceeds 227 KB");
+  static_assert(kAccCols + KB / 4 <= kTmemCols, "visitor operand does not fit in TMEM");
 };
-
-// offset of (row r, byte kb) in a K-major no-swizzle operand whose rows are KB bytes
-template <int KB>
-__device__ __forceinline__ uint32_t cm_off(int r, int kb) {
-  return (uint32_t)((r >> 3) * (KB * 8) + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
-}
 
 // 16 code bits -> 16 bytes of E4M3 (+1.0 = 0x38 for a set bit, -1.0 = 0xB8 otherwise)
 __device__ __forceinline__ uint4 expand16(uint32_t bits16) {
@@ -105,7 +109,7 @@ __device__ __forceinline__ void arrive_expect_tx(uint64_t* bar, uint32_t bytes) 
       : "memory");
 }
 
-// Expanded home operand: row e of the 64-padded order of partition p holds
+// Expanded home operand: row e of the 128-padded order of partition p holds
 // home_codes[home_off[p] + (e - eoff[p])] (zeros past |H_p|) as KB bytes of
 // E4M3 in the K-major core-matrix layout (8-row groups of KB * 8 bytes).
 template <int W>
@@ -208,18 +212,18 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   using C = TcCfg<W>;
   constexpr int KB = C::KB;
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint8_t* sA = sm;
   uint32_t* cand = reinterpret_cast<uint32_t*>(sm + C::OFF_CAND);
   uint64_t* sortbuf = reinterpret_cast<uint64_t*>(sm + C::OFF_SORT);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
-  uint64_t* full = bars;            // [2]
-  uint64_t* empty = bars + 2;       // [2]
-  uint64_t* tfull = bars + 4;       // [2]
-  uint64_t* tempty = bars + 6;      // [2]
-  uint64_t* drain = bars + 8;       // MMA drain at exit
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
-  int32_t* s_item = reinterpret_cast<int32_t*>(bars + 10);
-  volatile int32_t* s_abort = reinterpret_cast<int32_t*>(bars + 11);
+  constexpr int kStages = C::STAGES;
+  uint64_t* full = bars;                  // [kStages]
+  uint64_t* empty = bars + kMaxStages;    // [kStages]
+  uint64_t* tfull = bars + 2 * kMaxStages;  // [kAcc]
+  uint64_t* tempty = tfull + kAcc;        // [kAcc]
+  uint64_t* drain = tempty + kAcc;        // MMA drain at exit
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  int32_t* s_item = reinterpret_cast<int32_t*>(drain + 2);
+  volatile int32_t* s_abort = reinterpret_cast<int32_t*>(drain + 3);
 
   const bdg_knn_args& a = ta.base;
   const bdg_csr& c = a.csr;
@@ -227,11 +231,13 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   const int m = a.m, k = a.k, bits = a.bits;
   const int32_t total_items = c.item_off[m];
 
-  if (warp == 0) tc05::tmem_alloc(tmem_slot, 128);
+  if (warp == 0) tc05::tmem_alloc(tmem_slot, kTmemCols);
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kStages; ++i) {
       tc05::mbar_init(&full[i], 1);
       tc05::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < kAcc; ++i) {
       tc05::mbar_init(&tfull[i], 1);
       tc05::mbar_init(&tempty[i], 4);
     }
@@ -271,35 +277,36 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       continue;
     }
 
-    // ---- A operand: the item's visitor codes (staged in the candidate area,
-    // which is free between items) expanded to E4M3 +-1 by all threads
-    uint64_t* vwords = reinterpret_cast<uint64_t*>(cand);
-    for (int x = tid; x < kM * W; x += kThreads) {
-      const int r = x / W, w = x - r * W;
-      uint64_t word = 0ull;
-      if (r < nv) {
-        const int32_t vid = c.visit_ids[v0 + r];
-        if (vid >= 0) word = a.codes[(int64_t)vid * W + w];
+    // ---- A operand: each epilogue thread writes its visitor's code, as E4M3
+    // +-1 (+1 for a set bit), into its TMEM lane: column c holds code bits
+    // 4c .. 4c + 3, one byte each (the layout tcgen05.mma reads A from TMEM in)
+    if (warp < 4) {
+      const int r = tid;
+      uint64_t cw[W];
+      const int32_t vid = r < nv ? c.visit_ids[v0 + r] : -1;
+#pragma unroll
+      for (int w = 0; w < W; ++w) cw[w] = vid >= 0 ? a.codes[(int64_t)vid * W + w] : 0ull;
+#pragma unroll
+      for (int ch = 0; ch < W / 2; ++ch) {  // 32 columns = 128 code bits per store
+        uint32_t col[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const uint64_t word = cw[2 * ch + (q >> 4)];
+          const uint32_t nib = (uint32_t)(word >> (4 * (q & 15))) & 0xFu;
+          col[q] = vid >= 0 ? 0xB8B8B8B8u ^ (((nib * 0x00204081u) & 0x01010101u) << 7) : 0u;
+        }
+        tc05::st32(tmem + ((uint32_t)(32 * warp) << 16) + kAccCols + 32 * ch, col);
       }
-      vwords[x] = word;
+      tc05::wait_st();
     }
-    __syncthreads();
-    for (int x = tid; x < kM * 4 * W; x += kThreads) {
-      const int rr = x & 7, rest = x >> 3;
-      const int q = rest % (4 * W), grp = rest / (4 * W);
-      const int r = grp * 8 + rr;
-      const uint64_t word = vwords[r * W + (q >> 2)];
-      *reinterpret_cast<uint4*>(sA + cm_off<KB>(r, q * 16)) =
-          expand16((uint32_t)(word >> (16 * (q & 3))) & 0xFFFFu);
-    }
-    tc05::fence_proxy_async();
+    tc05::fence_before();
     __syncthreads();
 
     if (warp == 4) {
       // ---------------- producer
       if (lane == 0) {
         for (int j = 0; j < ntiles && !*s_abort; ++j) {
-          const uint32_t gg = g + j, st = gg & 1, use = gg >> 1;
+          const uint32_t gg = g + j, st = gg % kStages, use = gg / kStages;
           if (use > 0 && !tc05::mbar_wait(&empty[st], (use - 1) & 1, kPolls)) {
             atomicExch(ta.err, 1); *s_abort = 1; break;
           }
@@ -312,20 +319,19 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
     } else if (warp == 5) {
       // ---------------- MMA issuer
       if (lane == 0) {
-        const uint32_t a0 = tc05::smem_u32(sA);
+        const uint32_t a0 = tmem + kAccCols;  // visitors' operand (TMEM columns)
         for (int j = 0; j < ntiles && !*s_abort; ++j) {
-          const uint32_t gg = g + j, st = gg & 1, b = gg & 1;
-          if (!tc05::mbar_wait(&full[st], (gg >> 1) & 1, kPolls) ||
-              (gg >= 2 && !tc05::mbar_wait(&tempty[b], ((gg >> 1) - 1) & 1, kPolls))) {
+          const uint32_t gg = g + j, st = gg % kStages, b = gg % kAcc;
+          if (!tc05::mbar_wait(&full[st], (gg / kStages) & 1, kPolls) ||
+              (gg >= kAcc && !tc05::mbar_wait(&tempty[b], ((gg / kAcc) - 1) & 1, kPolls))) {
             atomicExch(ta.err, 2); *s_abort = 1; break;
           }
           tc05::fence_after();
           const uint32_t b0 = tc05::smem_u32(sm + C::OFF_B + st * C::B_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < KB / 32; ++kk) {
-            const uint64_t ad = tc05::sdesc(a0 + kk * 256, 128, KB * 8);
+          for (int kk = 0; kk < KB / 32; ++kk) {  // K = 32 per MMA: 8 TMEM columns of A
             const uint64_t bd = tc05::sdesc(b0 + kk * 256, 128, KB * 8);
-            tc05::mma_f8(tmem + b * kNT, ad, bd, id_mma, kk > 0 ? 1u : 0u);
+            tc05::mma_f8_ts(tmem + b * kNT, a0 + kk * 8, bd, id_mma, kk > 0 ? 1u : 0u);
           }
           tc05::commit(&empty[st]);
           tc05::commit(&tfull[b]);
@@ -358,70 +364,77 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       const float hmagic = 0.5f * (float)bits + 8388608.0f;
       uint32_t* crow = cand + r;
       for (int j = 0; j < ntiles; ++j) {
-        const uint32_t gg = g + j, b = gg & 1;
-        bool ok = !*s_abort && tc05::mbar_wait(&tfull[b], (gg >> 1) & 1, kPolls);
+        const uint32_t gg = g + j, b = gg % kAcc;
+        bool ok = !*s_abort && tc05::mbar_wait(&tfull[b], (gg / kAcc) & 1, kPolls);
         ok = __all_sync(0xffffffffu, ok);  // the warp leaves together
         if (!ok) {
           if (lane == 0) { atomicExch(ta.err, 3); *s_abort = 1; }
           break;
         }
         tc05::fence_after();
-        uint32_t v[64];
-        tc05::ld32(tmem + lane_base + b * kNT, *reinterpret_cast<uint32_t(*)[32]>(&v[0]));
-        tc05::ld32(tmem + lane_base + b * kNT + 32, *reinterpret_cast<uint32_t(*)[32]>(&v[32]));
-        tc05::wait_ld();
-        tc05::fence_before();
-        __syncwarp();
-        if (lane == 0) tc05::mbar_arrive(&tempty[b]);
-        const uint32_t pos0 = (uint32_t)(j * kNT);
-        const int nvalid = min(kNT, nh - j * kNT);
-        if (nvalid < kNT) {  // ragged last tile: missing homes read as d = bits + 1
-          const uint32_t padv = __float_as_uint(-(float)(bits + 2));
-#pragma unroll
-          for (int cc = 0; cc < kNT; ++cc)
-            if (cc >= nvalid) v[cc] = padv;
-        }
-#pragma unroll
-        for (int half = 0; half < kNT / kHalf; ++half) {
-          // compaction, taken by the whole warp at once as soon as one row's list
-          // could not take another 16 values (lanes compacting one by one would
-          // serialise the warp)
-          if (__any_sync(0xffffffffu, cnt > kCap - kHalf)) {
-            cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kCap - kHalf);
-            if (cnt > kCap - kHalf) {  // cannot happen (need_k <= 65); kept as a guard:
-              overflow = true;         // the popcount kernel redoes this row
-              thr_w = 0u;
-              cnt = 0;
+#pragma unroll 1
+        for (int sub = 0; sub < kNT / kSub; ++sub) {  // 64 columns at a time
+          uint32_t v[kSub];
+          const uint32_t tcol = tmem + lane_base + b * kNT + sub * kSub;
+          tc05::ld32(tcol, *reinterpret_cast<uint32_t(*)[32]>(&v[0]));
+          tc05::ld32(tcol + 32, *reinterpret_cast<uint32_t(*)[32]>(&v[32]));
+          tc05::wait_ld();
+          if (sub == kNT / kSub - 1) {  // the accumulator is read: hand it back
+            tc05::fence_before();
+            __syncwarp();
+            if (lane == 0) tc05::mbar_arrive(&tempty[b]);
+          }
+          const uint32_t pos0 = (uint32_t)(j * kNT + sub * kSub);
+          const int nvalid = min(kSub, nh - (int)pos0);
+          if (nvalid <= 0) continue;  // past the partition's last home
+          if (nvalid < kSub) {  // ragged last columns: missing homes read as d = bits + 1
+            const uint32_t padv = __float_as_uint(-(float)(bits + 2));
+  #pragma unroll
+            for (int cc = 0; cc < kSub; ++cc)
+              if (cc >= nvalid) v[cc] = padv;
+          }
+  #pragma unroll
+          for (int half = 0; half < kSub / kHalf; ++half) {
+            // compaction, taken by the whole warp at once as soon as one row's list
+            // could not take another 16 values (lanes compacting one by one would
+            // serialise the warp)
+            if (__any_sync(0xffffffffu, cnt > kCap - kHalf)) {
+              cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kCap - kHalf);
+              if (cnt > kCap - kHalf) {  // cannot happen (need_k <= 65); kept as a guard:
+                overflow = true;         // the popcount kernel redoes this row
+                thr_w = 0u;
+                cnt = 0;
+              }
             }
+            // skip the 16 values when no row of the warp can take one of them: a value
+            // can enter only if its distance is at most td, the bound's distance part
+            {
+              const int tdh = (int)((thr_w - 1u) >> kPosBits);
+              const float lim = thr_w ? (float)(bits - 2 * tdh) : 3.0e38f;
+              float f[kHalf];
+  #pragma unroll
+              for (int c2 = 0; c2 < kHalf; ++c2) f[c2] = __uint_as_float(v[half * kHalf + c2]);
+              const float m0 = fmaxf(fmaxf(f[0], f[1]), fmaxf(f[2], f[3]));
+              const float m1 = fmaxf(fmaxf(f[4], f[5]), fmaxf(f[6], f[7]));
+              const float m2 = fmaxf(fmaxf(f[8], f[9]), fmaxf(f[10], f[11]));
+              const float m3 = fmaxf(fmaxf(f[12], f[13]), fmaxf(f[14], f[15]));
+              if (!__any_sync(0xffffffffu, fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) >= lim)) continue;
+            }
+            // branch-free append: every value is written at the running slot, only
+            // words below the threshold advance it
+            uint32_t* const wp0 = crow + cnt * kCandStride;
+            uint32_t* wp = wp0;
+            const uint32_t posq = pos0 + (uint32_t)(half * kHalf);
+  #pragma unroll
+            for (int c2 = 0; c2 < kHalf; ++c2) {
+              const float dot = __uint_as_float(v[half * kHalf + c2]);
+              const uint32_t fb = __float_as_uint(fmaf(dot, -0.5f, hmagic));
+              const uint32_t word = fb * (1u << kPosBits) + (posq + c2);
+              *wp = word;
+              wp += (word < thr_w) ? kCandStride : 0;
+            }
+            cnt += (int)((wp - wp0) / kCandStride);
           }
-          // skip the 16 values when no row of the warp can take one of them: a value
-          // can enter only if its distance is at most td, the bound's distance part
-          {
-            const int tdh = (int)((thr_w - 1u) >> kPosBits);
-            const float lim = thr_w ? (float)(bits - 2 * tdh) : 3.0e38f;
-            float f[kHalf];
-#pragma unroll
-            for (int c2 = 0; c2 < kHalf; ++c2) f[c2] = __uint_as_float(v[half * kHalf + c2]);
-            const float m0 = fmaxf(fmaxf(f[0], f[1]), fmaxf(f[2], f[3]));
-            const float m1 = fmaxf(fmaxf(f[4], f[5]), fmaxf(f[6], f[7]));
-            const float m2 = fmaxf(fmaxf(f[8], f[9]), fmaxf(f[10], f[11]));
-            const float m3 = fmaxf(fmaxf(f[12], f[13]), fmaxf(f[14], f[15]));
-            if (!__any_sync(0xffffffffu, fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) >= lim)) continue;
-          }
-          // branch-free append: every value is written at the running slot, only
-          // words below the threshold advance it
-          uint32_t* const wp0 = crow + cnt * kCandStride;
-          uint32_t* wp = wp0;
-          const uint32_t posq = pos0 + (uint32_t)(half * kHalf);
-#pragma unroll
-          for (int c2 = 0; c2 < kHalf; ++c2) {
-            const float dot = __uint_as_float(v[half * kHalf + c2]);
-            const uint32_t fb = __float_as_uint(fmaf(dot, -0.5f, hmagic));
-            const uint32_t word = fb * (1u << kPosBits) + (posq + c2);
-            *wp = word;
-            wp += (word < thr_w) ? kCandStride : 0;
-          }
-          cnt += (int)((wp - wp0) / kCandStride);
         }
       }
       const uint64_t pad = bdg_pad_key(bits);
@@ -608,20 +621,20 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   }
   if (warp == 4 && lane == 0 && *s_abort) {
     // copies issued but possibly never consumed: wait for their completion
-    for (uint32_t gg = (nprod > 2 ? nprod - 2 : 0); gg < nprod; ++gg)
-      tc05::mbar_wait(&full[gg & 1], (gg >> 1) & 1, kPolls);
+    for (uint32_t gg = (nprod > kStages ? nprod - kStages : 0); gg < nprod; ++gg)
+      tc05::mbar_wait(&full[gg % kStages], (gg / kStages) & 1, kPolls);
   }
   tc05::fence_before();
   __syncthreads();
-  if (warp == 0) tc05::tmem_dealloc(tmem, 128);
+  if (warp == 0) tc05::tmem_dealloc(tmem, kTmemCols);
 }
 
 template <int W>
 bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
   using C = TcCfg<W>;
   const bdg_knn_args& a = ta.base;
-  if (expand) {  // expanded home operand (rows are bounded by N + 64 m)
-    const int64_t max_rows = a.N + 64LL * a.m;
+  if (expand) {  // expanded home operand (rows are bounded by N + BDG_TC_TILE m)
+    const int64_t max_rows = a.N + (int64_t)BDG_TC_TILE * a.m;
     const int64_t nthreads = ((max_rows + 7) / 8) * 8 * (4 * W);
     bdg_prof_scope prof("expand", st);
     expand_homes_kernel<W><<<bdg_cdiv(nthreads, 256), 256, 0, st>>>(
@@ -650,7 +663,7 @@ bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
 bool bdg_knn_tc_supported(int W, int k) { return (W == 4 || W == 8) && k >= 1 && k <= 64; }
 
 size_t bdg_knn_tc_hexp_bytes(int64_t N, int m, int W) {
-  return (size_t)(N + 64LL * m) * 64 * W;
+  return (size_t)(N + (int64_t)BDG_TC_TILE * m) * 64 * W;
 }
 
 bdg_status bdg_launch_knn_tc(const bdg_knn_tc_args& a, int W, bool expand, cudaStream_t st) {
