@@ -343,7 +343,8 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       // a partition are stored in ascending id order, so word order is exactly
       // (d, id) order: the row keeps an exact threshold on words.
       const int r = tid;
-      const bool live = r < nv && c.visit_ids[v0 + r] >= 0;
+      const int32_t myvid = r < nv ? c.visit_ids[v0 + r] : -1;  // this row's point
+      const bool live = myvid >= 0;
       // v is one of its own partition's homes: its self pair (d = 0) is counted
       // like any other value and dropped at selection, so k + 1 values are needed
       const int need_k = k + ((live && c.visit_slot[v0 + r] == 0) ? 1 : 0);
@@ -352,7 +353,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       uint32_t thr_w = live ? (uint32_t)(bits + 1) << kPosBits : 0u;
       uint64_t kth = BDG_KEY_INF;  // sub-round: the running list's k-th key
       if (live && a.home_kth != nullptr) {  // it bounds d, and no key above it can enter
-        kth = a.home_kth[(int64_t)c.visit_ids[v0 + r] * k + (k - 1)];
+        kth = a.home_kth[(int64_t)myvid * k + (k - 1)];
         if (kth < bdg_pad_key(bits)) thr_w = (uint32_t)(bdg_key_d(kth) + 1) << kPosBits;
       }
       int cnt = 0;   // entries in the row's candidate list
@@ -448,7 +449,6 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           if (!overflow && cnt > need_k) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, need_k);
         }
         if (cnt > need_k) overflow = true;  // cannot happen; the popcount kernel would redo it
-        const int32_t myvid = r < nv ? c.visit_ids[v0 + r] : -1;
         int self_j = kNeedMax;  // sorted index of the self pair (none: kNeedMax)
         if (!overflow) {
           uint32_t wv[kNeedMax];  // the row's words in registers (missing ones: never below)
@@ -524,88 +524,91 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           }
         }
       } else {
-        // ---- sub-round: a list longer than the sort takes is cut to its k best words
-        if (__any_sync(0xffffffffu, cnt > kSortN)) {
-          if (cnt > kSortN) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kSortN);
-          if (cnt > kSortN) overflow = true;  // cannot happen; the popcount kernel would redo it
+        // ---- sub-round. Each thread cuts its row's list to its k best words and
+        // turns them into keys (d, id), dropping those at or above the running
+        // list's k-th key (they cannot enter); then each warp sorts, row by row,
+        // the few surviving keys and merges them into the running list.
+        if (__any_sync(0xffffffffu, !overflow && cnt > need_k)) {
+          if (!overflow && cnt > need_k) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, need_k);
         }
-        // ---- selection: k smallest (d, id) among candidates inside the threshold
+        if (cnt > need_k) overflow = true;  // cannot happen; the popcount kernel would redo it
+        if (!overflow) {
+          int w = 0;
+          for (int j0 = 0; j0 < cnt; j0 += 8) {
+            uint32_t w8[8];
+            int32_t h8[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {  // eight id loads in flight
+              const int j = j0 + q;
+              w8[q] = j < cnt ? crow[j * kCandStride] : 0u;
+              h8[q] = j < cnt ? c.home_ids[h0 + (int)(w8[q] & kPosMask)] : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              if (j0 + q >= cnt || h8[q] == myvid) continue;
+              if (bdg_key(w8[q] >> kPosBits, (uint32_t)h8[q]) >= kth) continue;
+              crow[w * kCandStride] = w8[q];
+              crow[(kOutSlot + w) * kCandStride] = (uint32_t)h8[q];
+              ++w;
+            }
+          }
+          cnt = w;
+        }
+        __syncwarp();
         uint64_t* sb = sortbuf + warp * 128;
         for (int rr = 0; rr < 32; ++rr) {
           const int row = warp * 32 + rr;
           const int n_r = __shfl_sync(0xffffffffu, cnt, rr);
-          const uint32_t tb = __shfl_sync(0xffffffffu, thr_w, rr);
           const int ovf = __shfl_sync(0xffffffffu, overflow ? 1 : 0, rr);
           const uint64_t kb = __shfl_sync(0xffffffffu, kth, rr);
-          if (row >= nv) continue;
-          const int32_t vid = c.visit_ids[v0 + row];
-          if (vid < 0) continue;  // an invalid id
+          const int32_t vid = __shfl_sync(0xffffffffu, myvid, rr);
+          if (row >= nv || vid < 0) continue;  // no row, or an invalid id
           if (ovf) {  // recomputed by the popcount kernel
             if (lane == 0) ta.fixflag[v0 + row] = 1;
             continue;
           }
-          if (n_r == 0) continue;  // nothing to merge
-          if (n_r <= 32) {
-            // few candidates: one key per lane, bitonic sort across the warp in registers
+          if (n_r == 0) continue;  // nothing enters the running list
+          // keys ascending: n_r <= 32 by one bitonic sort across the warp in
+          // registers, else (n_r <= 64) two such sorts merged by ranks
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int x = lane + 32 * q;
             uint64_t key = BDG_KEY_INF;
-            if (lane < n_r) {
-              const uint32_t e = cand[cidx(lane, row)];
-              const int d = (int)(e >> kPosBits);
-              if (e < tb) {
-                const int32_t hid = c.home_ids[h0 + (int)(e & kPosMask)];
-                if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
-              }
-            }
-            // a sub-round key above the running k-th cannot enter: a row left
-            // without keys is done
-            if (!__any_sync(0xffffffffu, key < kb)) continue;
-  #pragma unroll
+            if (x < n_r)
+              key = bdg_key(cand[cidx(x, row)] >> kPosBits, cand[cidx(kOutSlot + x, row)]);
+            if (q == 1 && n_r <= 32) break;
+#pragma unroll
             for (int k2 = 2; k2 <= 32; k2 <<= 1) {
-  #pragma unroll
+#pragma unroll
               for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
                 const uint64_t o = __shfl_xor_sync(0xffffffffu, key, j2);
                 const bool up = (lane & k2) == 0, low = (lane & j2) == 0;
                 key = (low == up) ? (key < o ? key : o) : (key < o ? o : key);
               }
             }
-            sb[lane] = key;
-            sb[lane + 32] = BDG_KEY_INF;
-            sb[lane + 64] = BDG_KEY_INF;
-            sb[lane + 96] = BDG_KEY_INF;
-            __syncwarp();
-          } else {
-  #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int x = lane + 32 * q;
-              uint64_t key = BDG_KEY_INF;
-              if (x < n_r) {
-                const uint32_t e = cand[cidx(x, row)];
-                const int d = (int)(e >> kPosBits);
-                if (e < tb) {
-                  const int32_t hid = c.home_ids[h0 + (int)(e & kPosMask)];
-                  if (hid != vid) key = bdg_key((uint32_t)d, (uint32_t)hid);
-                }
-              }
-              sb[x] = key;
-            }
-            __syncwarp();
-            // bitonic sort of 128 keys, ascending
-            for (int size = 2; size <= 128; size <<= 1) {
-              for (int stride = size >> 1; stride > 0; stride >>= 1) {
-  #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                  const int i = lane + 32 * q;                           // pair index 0..63
-                  const int lo2 = (i / stride) * (2 * stride) + (i % stride);
-                  const int hi2 = lo2 + stride;
-                  const bool up = (lo2 & size) == 0;
-                  const uint64_t x0 = sb[lo2], x1 = sb[hi2];
-                  if ((x0 > x1) == up) { sb[lo2] = x1; sb[hi2] = x0; }
-                }
-                __syncwarp();
-              }
-            }
+            sb[32 * q + lane] = key;
           }
-          bdg_warp_merge_running(a.partial + (int64_t)vid * k, sb, k, k, pad, kb, lane);
+          __syncwarp();
+          if (n_r > 32) {  // merge the two sorted halves by ranks
+            const uint64_t x0 = sb[lane], x1 = sb[32 + lane];
+            int lo = 0, hi = 32;  // rank of x0 among the second half
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (sb[32 + mid] < x0) lo = mid + 1; else hi = mid;
+            }
+            int lo1 = 0, hi1 = 32;  // rank of x1 among the first half
+            while (lo1 < hi1) {
+              const int mid = (lo1 + hi1) >> 1;
+              if (sb[mid] < x1) lo1 = mid + 1; else hi1 = mid;
+            }
+            __syncwarp();
+            sb[64 + lane + lo] = x0;
+            sb[64 + lane + lo1] = x1;
+            __syncwarp();
+            bdg_warp_merge_running(a.partial + (int64_t)vid * k, sb + 64, n_r, k, pad, kb, lane);
+          } else {
+            bdg_warp_merge_running(a.partial + (int64_t)vid * k, sb, n_r, k, pad, kb, lane);
+          }
           __syncwarp();
         }
       }
