@@ -68,11 +68,53 @@ def test_exact_knn_bit_exact(bdg, bits, n, k, kernel):
 
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_exact_knn_all_equal_codes(bdg, kernel):
-    # every pair ties at d = 0: the tensor path overflows its candidate lists and
-    # hands every row to the popcount recomputation
+    # every pair ties at d = 0: the k nearest are the k smallest other ids, which
+    # the tensor path finds by its word-level (distance, position) bound
     c = torch.zeros(300, 4, dtype=torch.int64)
     g, _ = _build_exact(bdg, c.cuda(), 32, kernel=kernel)
     ids_o, dist_o = oracle.knn_exact(_np(c), 32)
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("bits,k,m,t", [(512, 64, 1, 1), (256, 32, 1, 1), (512, 64, 8, 3),
+                                        (256, 32, 12, 4)])
+def test_heavy_ties_bit_exact(bdg, bits, k, m, t, kernel):
+    """Codes drawn from 40 distinct values: every row meets long runs of equal
+    distances, so the lists keep filling with ties at the k-th distance."""
+    n = 6000
+    base = datagen.random_codes(40, bits, seed=bits + k)
+    pick = np.random.default_rng(bits * 7 + m).integers(0, 40, n)
+    c = base[torch.from_numpy(pick)]
+    entry = torch.from_numpy(_entry(n, 64, 3)).cuda()
+    if m == 1:
+        g = bdg.build_graph(c.cuda(), k, m=1, t=1, entry=entry, kernel=kernel)
+        ids_o, dist_o = oracle.knn_exact(_np(c), k)
+    else:
+        sample = datagen.sample_ids(n, 64 * m, 4)
+        g = bdg.build_graph(c.cuda(), k, m=m, t=t, bk_sample=torch.from_numpy(sample).cuda(),
+                            bk_iters=4, entry=entry, kernel=kernel)
+        cent, _, _ = oracle.bkmeans(_np(c), sample, m, 4)
+        r, _ = oracle.route(_np(c), cent, t)
+        ids_o, dist_o = oracle.knn_partitioned(_np(c), r, k)
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_many_small_partitions_256b(bdg, kernel):
+    """Partitions of ~100 homes (many ragged tiles) with four probes per point."""
+    spec = datagen.MixtureSpec(30000, 64, 500, 256, seed=31)
+    c = datagen.make_codes(spec)
+    n, m, t, k = spec.n, 300, 4, 32
+    sample = datagen.sample_ids(n, 64 * m, 5)
+    entry = torch.from_numpy(_entry(n, 64, 6)).cuda()
+    g = bdg.build_graph(c.cuda(), k, m=m, t=t, bk_sample=torch.from_numpy(sample).cuda(),
+                        bk_iters=4, entry=entry, kernel=kernel)
+    cent, _, _ = oracle.bkmeans(_np(c), sample, m, 4)
+    r, _ = oracle.route(_np(c), cent, t)
+    ids_o, dist_o = oracle.knn_partitioned(_np(c), r, k)
     assert np.array_equal(g.ids.cpu().numpy(), ids_o)
     assert np.array_equal(g.dists.cpu().numpy(), dist_o)
 
