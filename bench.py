@@ -171,7 +171,7 @@ def _traffic_record(name, source):
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if vals.get("kernel_source_sha256_16") != h or "dram_bytes_per_launch_full" not in vals:
         return None
-    return float(vals["dram_bytes_per_launch_full"])
+    return float(vals["dram_bytes_per_launch_full"].split()[0])
 
 
 def _pairs_from_routes(routes):
@@ -441,8 +441,9 @@ def _learned_bench(bdg, device, kernel, n=10_000_000, lr=1e-3, lr_epochs=4):
     torch.cuda.synchronize()
     out["setup_s"] = time.perf_counter() - t0
     # training data: the exact neighbours (over all N points) of a seeded sample
-    # of 1M points, as the home partitions they live in (home itself left out)
-    S = min(n, 1_000_000)
+    # (1M points; 200k beyond 20M points, where the exact rows cost N per row),
+    # as the home partitions they live in (home itself left out)
+    S = min(n, 1_000_000 if n <= 20_000_000 else 200_000)
     tr = torch.from_numpy(datagen.sample_ids(n, S, spec.seed + 5)).to(device)
     t0 = time.perf_counter()
     labels = learned.neighbour_labels_full(codes, tr.to(torch.int32), home, k)
@@ -645,6 +646,7 @@ def run_ours(a):
     if not a.no_learned and ws == 1:
         learned_res = _learned_bench(bdg, device, "popc" if kernel_used == "popc" else "auto",
                                      n=a.learned_n, lr=a.learned_lr, lr_epochs=a.learned_epochs)
+        print("learned_routing: " + json.dumps(learned_res), file=sys.stderr, flush=True)
 
     if rank != 0:
         if ws > 1:

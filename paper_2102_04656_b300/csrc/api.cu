@@ -293,7 +293,7 @@ bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_
   c->b_routes = c->need_routes || m == 1 ? al((size_t)N * t * 4) : 0;
   c->b_cent = c->need_bk ? al((size_t)m * W * 8) : 0;
   c->b_bk = c->need_bk ? al(bdg_bkmeans_scratch_bytes(P->bk_sample_size, m, W)) : 0;
-  c->b_csr = al(bdg_csr_bytes(N, m, t, W));
+  c->b_csr = al(bdg_csr_bytes(N, m, t, W, c->tile_v));
   c->b_part = t > 1 ? al((size_t)N * k * 8) : 0;  // running k-lists
   c->b_hexp = c->tc_ok ? al(bdg_knn_tc_hexp_bytes(N, m, W)) : 0;
   c->b_fix = c->tc_ok ? al((size_t)N * t) + al(64) : 0;
@@ -604,7 +604,7 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
   keep_pool_cached();
   const bool use_tc = bdg_knn_tc_supported(W, k) && N < (1 << 21) && bdg_tc_default();
   Scratch sc;
-  const size_t b = al(bdg_csr_rows_bytes(N, nrows));
+  const size_t b = al(bdg_csr_rows_bytes(N, nrows, tile_v));
   const size_t b_hexp = use_tc ? al(bdg_knn_tc_hexp_bytes(N, 1, W)) : 0;
   const size_t b_fix = use_tc ? al((size_t)nrows) + al(64) : 0;
   BDG_TRY(sc.alloc(b + b_hexp + b_fix, st));

@@ -256,8 +256,9 @@ __global__ void rows_plan_kernel(int64_t N, const int32_t* __restrict__ rows, in
 
 }  // namespace
 
-size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows) {
-  return al(2 * 4) * 4 + al(N * 4) + al(nrows * 4) + al(nrows) + al(4) + al(8 * 4);
+size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows, int tile_v) {
+  return al(2 * 4) * 4 + al(N * 4) + al(nrows * 4) + al(nrows) + al(4) + al(8 * 4) +
+         al((size_t)((nrows + tile_v - 1) / tile_v + 1) * 4);
 }
 
 bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* rows,
@@ -271,13 +272,17 @@ bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* r
   c->visit_ids = (int32_t*)p;  p += al(nrows * 4);
   c->visit_slot = (int8_t*)p;  p += al(nrows);
   c->part_order = (int32_t*)p; p += al(4);
-  c->counters = (int32_t*)p;
+  c->counters = (int32_t*)p;   p += al(8 * 4);
+  c->item_lo_a = (int32_t*)p;  // one partition: every item's rank is 0
+  c->item_lo = c->item_lo_a;
+  c->item_stride = 0;
   c->home_codes = const_cast<uint64_t*>(codes);  // identity order: read the codes in place
   c->item_off_a = c->item_off;
   c->slot_zero = c->visit_slot;
   c->m = 1;
   c->t = 1;
   BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, 8 * 4, st));
+  BDG_CUDA_TRY(cudaMemsetAsync(c->item_lo_a, 0, ((nrows + tile_v - 1) / tile_v + 1) * 4, st));
   const int64_t n = N > nrows ? N : nrows;
   rows_plan_kernel<<<bdg_cdiv(n, 256), 256, 0, st>>>(N, rows, nrows, tile_v, c->home_off,
                                                      c->home_ids, c->visit_off, c->visit_ids,
@@ -295,12 +300,25 @@ int bdg_home_block(int64_t N, int m) {
   return (int)bp;
 }
 
-size_t bdg_csr_bytes(int64_t N, int m, int t, int W) {
+// item_lo[item] = r for r's items: one thread per (round, partition rank r)
+__global__ void item_table_kernel(int m, int rounds, const int32_t* __restrict__ item_off_a,
+                                  const int32_t* __restrict__ item_off, int64_t stride,
+                                  int32_t* __restrict__ item_lo_a, int32_t* __restrict__ item_lo) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (int64_t)rounds * m) return;
+  const int round = (int)(x / m), r = (int)(x - (int64_t)round * m);
+  const int32_t* io = round == 0 ? item_off_a : item_off + (size_t)(round - 1) * (m + 1);
+  int32_t* out = round == 0 ? item_lo_a : item_lo + (size_t)(round - 1) * stride;
+  for (int32_t it = io[r]; it < io[r + 1]; ++it) out[it] = r;
+}
+
+size_t bdg_csr_bytes(int64_t N, int m, int t, int W, int tile_v) {
   const size_t ts = t > 1 ? (size_t)(t - 1) : 1;
   const size_t blk = (size_t)((N + bdg_home_block(N, m) - 1) / bdg_home_block(N, m)) * m * 4;
+  const size_t stride = (size_t)bdg_csr_item_stride(N, m, tile_v);
   return al((m + 1) * 4) * 3 + al(ts * (m + 1) * 4) * 2 + al(N * 4) + al(N * W * 8) +
          al(N * t * 4) + al(N * t) + al(m * 4) + al(bdg_csr_counter_words(m, t) * 4) + al(N) +
-         al(blk);
+         al(blk) + al(stride * 4) + al(ts * stride * 4);
 }
 
 bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
@@ -323,6 +341,9 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   c->slot_zero = (int8_t*)p;   p += al(N);
   c->home_blocks = (int32_t*)p;
   p += al((size_t)((N + bdg_home_block(N, m) - 1) / bdg_home_block(N, m)) * m * 4);
+  c->item_stride = bdg_csr_item_stride(N, m, tile_v);
+  c->item_lo_a = (int32_t*)p;  p += al((size_t)c->item_stride * 4);
+  c->item_lo = (int32_t*)p;    p += al(ts * (size_t)c->item_stride * 4);
   c->counters = (int32_t*)p;
   int32_t* hcnt = c->counters;
   int32_t* vcnt = c->counters + m;
@@ -361,6 +382,10 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   plan_kernel<<<1, kScanThreads, smem, st>>>(m, t, tile_v, hcnt, vcnt, c->home_off, c->visit_off,
                                              c->part_order, c->item_off, c->eoff,
                                              c->item_off_a);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  item_table_kernel<<<bdg_cdiv((int64_t)t * m, 128), 128, 0, st>>>(
+      m, t, c->item_off_a, c->item_off, c->item_stride, c->item_lo_a, c->item_lo);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   home_place<<<nblk, 32, sm_m, st>>>(routes, N, t, m, bp, bcnt, c->home_off, c->home_ids);

@@ -90,8 +90,17 @@ struct bdg_csr {
   int32_t* item_off_a; // [m + 1]  work items of round A in part_order order
   int8_t* slot_zero;   // [N]      zeros: the route slot of every round-A visit
   int32_t* home_blocks;// [blocks][m] scratch of the stable home placement
+  // item -> its partition's rank in part_order (the r with item_off[r] <= item <
+  // item_off[r + 1]): round A at item_lo_a, sub-round s at item_lo + (s - 1) * item_stride
+  int32_t* item_lo_a;
+  int32_t* item_lo;
+  int64_t item_stride;
   int m, t;
 };
+// items of one round are at most ceil(visits / tile_v) + m <= N / tile_v + m + 1
+inline int64_t bdg_csr_item_stride(int64_t N, int m, int tile_v) {
+  return (N + tile_v - 1) / tile_v + m + 1;
+}
 int bdg_home_block(int64_t N, int m);
 // The visits of slot s >= 1 form sub-round s: visit_off / item_off hold t - 1
 // consecutive [m + 1] arrays (positions are absolute in visit_ids).
@@ -100,6 +109,7 @@ inline bdg_csr bdg_csr_subround(const bdg_csr& c, int s) {
   bdg_csr v = c;
   v.visit_off = c.visit_off + (size_t)(s - 1) * (c.m + 1);
   v.item_off = c.item_off + (size_t)(s - 1) * (c.m + 1);
+  v.item_lo = c.item_lo + (size_t)(s - 1) * c.item_stride;
   return v;
 }
 // The CSR view of round A (visitors = homes).
@@ -109,14 +119,15 @@ inline bdg_csr bdg_csr_round_a(const bdg_csr& c) {
   a.visit_ids = c.home_ids;
   a.visit_slot = c.slot_zero;
   a.item_off = c.item_off_a;
+  a.item_lo = c.item_lo_a;
   return a;
 }
-size_t bdg_csr_bytes(int64_t N, int m, int t, int W);
+size_t bdg_csr_bytes(int64_t N, int m, int t, int W, int tile_v);
 bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
                          int t, int tile_v, void* mem, bdg_csr* csr, cudaStream_t st);
 // one partition: every point is a home (identity order, codes used in place);
 // the visitors are the given rows
-size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows);
+size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows, int tile_v);
 bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* rows,
                               int64_t nrows, int tile_v, void* mem, bdg_csr* csr, cudaStream_t st);
 // knn_popc.cu

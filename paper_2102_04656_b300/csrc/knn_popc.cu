@@ -141,12 +141,7 @@ knn_popc_kernel(bdg_knn_args a) {
     __syncthreads();
     const int item = *s.item;
     if (item >= total_items) break;
-    // partition rank r with item_off[r] <= item < item_off[r + 1]
-    int lo = 0, hi = m;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (c.item_off[mid] <= item) lo = mid; else hi = mid;
-    }
+    const int lo = c.item_lo[item];  // rank of the item's partition in part_order
     const int p = c.part_order[lo];
     const int tile = item - c.item_off[lo];
     const int h0 = c.home_off[p];

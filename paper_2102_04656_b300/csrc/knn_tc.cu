@@ -259,11 +259,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
     __syncthreads();
     const int item = *s_item;
     if (item >= total_items || *s_abort) break;
-    int lo = 0, hi = m;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (c.item_off[mid] <= item) lo = mid; else hi = mid;
-    }
+    const int lo = c.item_lo[item];  // rank of the item's partition in part_order
     const int p = c.part_order[lo];
     const int tile = item - c.item_off[lo];
     const int v0 = c.visit_off[p] + tile * kM;
