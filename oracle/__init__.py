@@ -128,6 +128,20 @@ def knn_partitioned(codes, routes, k: int, qidx=None):
     return ids, dist
 
 
+def propagate(codes, ids_in, k: int | None = None):
+    """One round of neighbourhood propagation (Section 3.3): (ids, dists) int32 [n, k]."""
+    c = _codes(codes)
+    n, w = c.shape
+    g = np.ascontiguousarray(ids_in, np.int32)
+    k = g.shape[1] if k is None else k
+    assert g.shape == (n, k)
+    ids = np.empty((n, k), np.int32)
+    dist = np.empty((n, k), np.int32)
+    _load().or_propagate(_p(c), ctypes.c_int64(n), ctypes.c_int32(w), _p(g), ctypes.c_int32(k),
+                         _p(ids), _p(dist))
+    return ids, dist
+
+
 def search(codes, graph, entry, queries, ef, R: int):
     """Best-first search: (ids int32 [nq, R], dists int32 [nq, R], counters int64 [nq, 2])."""
     c = _codes(codes)

@@ -16,8 +16,8 @@
  *
  * Parity status per function (pins live in tests/test_oracle_*.py):
  *   or_hamming, or_knn_exact, or_bkmeans, or_route, or_knn_partitioned,
- *   or_search, or_rerank_f32/_f64 -- pinned (brute force, invariants,
- *   closed forms, hand-worked fixtures).
+ *   or_search, or_rerank_f32/_f64, or_propagate -- pinned (brute force,
+ *   invariants, closed forms, hand-worked fixtures).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -182,6 +182,44 @@ void or_knn_partitioned(const uint64_t* codes, int64_t n, int32_t W, const int32
       }
       qsort(keys, (size_t)c, sizeof(uint64_t), cmp_u64);
       emit_topk(keys, c, k, bits, out_ids + q * k, out_dist + q * k);
+    }
+    free(keys);
+  }
+}
+
+/* One round of neighbourhood propagation (Section 3.3): every point x is
+ * compared with the neighbours of its neighbours (the "second floor"), and its
+ * new list is the first k of sort over (d, id) of its current list together
+ * with those candidates:
+ *   G'(x) = first k of sort_{(d, id)} ( G(x) u { y in G(z) : z in G(x), y != x } ),
+ * every id counted once; ids -1 (padding) are ignored. All rows read the input
+ * graph G (ids [n][k], distances recomputed from the codes), none reads G'.
+ * The propagation filter of Section 3.6 (3) only drops candidates that cannot
+ * enter the first k, so it is not applied here. */
+void or_propagate(const uint64_t* codes, int64_t n, int32_t W, const int32_t* ids_in, int32_t k,
+                  int32_t* out_ids, int32_t* out_dist) {
+  const int32_t bits = 64 * W;
+#pragma omp parallel
+  {
+    uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(k + (int64_t)k * k + 1));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t x = 0; x < n; ++x) {
+      int64_t c = 0;
+      for (int32_t a = 0; a < k; ++a) {
+        const int32_t z = ids_in[x * k + a];
+        if (z < 0 || z >= n) continue;
+        if (z != x) keys[c++] = KEY(or_hamming(codes + x * W, codes + (int64_t)z * W, W), z);
+        for (int32_t b2 = 0; b2 < k; ++b2) {
+          const int32_t y = ids_in[(int64_t)z * k + b2];
+          if (y < 0 || y >= n || y == x) continue;
+          keys[c++] = KEY(or_hamming(codes + x * W, codes + (int64_t)y * W, W), y);
+        }
+      }
+      qsort(keys, (size_t)c, sizeof(uint64_t), cmp_u64);
+      int64_t u = 0;  /* every id once */
+      for (int64_t i = 0; i < c; ++i)
+        if (u == 0 || keys[i] != keys[u - 1]) keys[u++] = keys[i];
+      emit_topk(keys, u, k, bits, out_ids + x * k, out_dist + x * k);
     }
     free(keys);
   }

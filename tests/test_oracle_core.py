@@ -298,3 +298,71 @@ def test_recall_definitions(oracle_lib):
     ed = np.array([[1, 2, 2, 2]])
     assert oracle_lib.recall_tie_aware(np.array([[1, 2, 2, 2]]), ed) == 1.0
     assert oracle_lib.recall_tie_aware(np.array([[1, 2, 3, 3]]), ed) == 0.5
+
+
+# ---------------------------------------------------------------- propagation
+def _read_propagate_golden():
+    with open(os.path.join(GOLDEN, "propagate_tiny.txt")) as f:
+        lines = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+    codes = np.array([[int(x, 16)] for x in lines[0].split()], dtype=np.uint64)
+    n = codes.shape[0]
+    g_in = np.array([[int(v) for v in ln.split(":")[1].split()] for ln in lines[1:1 + n]],
+                    dtype=np.int32)
+    want_ids, want_d = [], []
+    for ln in lines[1 + n:1 + 2 * n]:
+        pairs = [p.split(",") for p in ln.split(":")[1].split()]
+        want_ids.append([int(a) for a, _ in pairs])
+        want_d.append([int(b) for _, b in pairs])
+    return codes, g_in, np.array(want_ids, np.int32), np.array(want_d, np.int32)
+
+
+def test_propagate_hand_worked_fixture(oracle_lib):
+    codes, g_in, want_ids, want_d = _read_propagate_golden()
+    ids, d = oracle_lib.propagate(codes, g_in)
+    assert np.array_equal(ids, want_ids)
+    assert np.array_equal(d, want_d)
+
+
+def test_propagate_brute_force_with_padding(oracle_lib):
+    """Against a direct set enumeration, on random graphs with padding and self ids."""
+    rng = np.random.default_rng(12)
+    n, k, bits = 70, 5, 128
+    c = _rand_codes(n, bits, 21)
+    b = _bits(c, bits)
+    g = rng.integers(0, n, (n, k)).astype(np.int32)
+    g[rng.random((n, k)) < 0.15] = -1
+    g[3, 0] = 3  # a point listed as its own neighbour is not a candidate of itself
+    ids, d = oracle_lib.propagate(c, g)
+    for x in range(n):
+        cand = {int(z) for z in g[x] if z >= 0 and z != x}
+        for z in g[x]:
+            if z >= 0:
+                cand |= {int(y) for y in g[z] if y >= 0 and y != x}
+        keys = sorted((int((b[x] != b[y]).sum()), y) for y in cand)[:k]
+        want_i = [y for _, y in keys] + [-1] * (k - len(keys))
+        want_d = [dd for dd, _ in keys] + [bits + 1] * (k - len(keys))
+        assert ids[x].tolist() == want_i and d[x].tolist() == want_d, x
+
+
+def test_propagate_keeps_the_exact_graph_and_improves_rows(oracle_lib):
+    """The exact graph is a fixed point; on an approximate graph no row's k-th key
+    grows, and every row is drawn from its old list and its second floor."""
+    spec = datagen.MixtureSpec(1500, 32, 12, 256, seed=44)
+    c = datagen.make_codes(spec).numpy().view(np.uint64)
+    k = 8
+    ex_i, ex_d = oracle_lib.knn_exact(c, k)
+    ids, d = oracle_lib.propagate(c, ex_i)
+    assert np.array_equal(ids, ex_i) and np.array_equal(d, ex_d)
+    cent, _, _ = oracle_lib.bkmeans(c, np.arange(0, 1500, 3, dtype=np.int64), 20, 4)
+    r, _ = oracle_lib.route(c, cent, 2)  # two probes: lists reach into neighbouring partitions
+    ap_i, ap_d = oracle_lib.knn_partitioned(c, r, k)
+    ids, d = oracle_lib.propagate(c, ap_i)
+    key = lambda dd, ii: dd.astype(np.int64) * (1 << 32) + (ii.astype(np.int64) & 0xffffffff)
+    assert (key(d[:, -1], ids[:, -1]) <= key(ap_d[:, -1], ap_i[:, -1])).all()
+    assert (d[:, -1] < ap_d[:, -1]).any()  # the round found better neighbours somewhere
+    for x in range(0, 1500, 97):
+        pool = set(ap_i[x].tolist())
+        for z in ap_i[x]:
+            if z >= 0:
+                pool |= set(ap_i[z].tolist())
+        assert set(ids[x].tolist()) <= pool
