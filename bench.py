@@ -57,6 +57,7 @@ def _args():
                     help="long-link entry sample size of the search graph")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-routing leg")
+    ap.add_argument("--no-propagate", action="store_true", help="skip the propagation leg")
     ap.add_argument("--learned-n", type=int, default=10_000_000,
                     help="points of the learned-routing leg (the workload's full size is 100M)")
     ap.add_argument("--learned-lr", type=float, default=3e-4, help="router learning rate")
@@ -197,6 +198,51 @@ def _recall(bdg, g, codes, k, rows_n, seed):
     for a, b in zip(gi_c, ex_c):
         inter += len(set(a.tolist()) & set(b.tolist()))
     return tie, inter / (rows_n * k)
+
+
+def _propagate_bench(bdg, codes, k, m, sample, bk_iters, entry, kernel, rows_n, t_main):
+    """Neighbourhood propagation (Section 3.3) on the bench workload: a cheaper
+    divide-and-conquer build (t = 2 probes) followed by one propagation round,
+    against the t = 5 build of the headline, recall judged on the same exact rows."""
+    L = bdg.lib()
+    out = {"base_t": 2, "rounds": 1}
+    g = bdg.build_graph(codes, k, m=m, t=2, bk_sample=sample, bk_iters=bk_iters, entry=entry,
+                        kernel=kernel)
+    g.free()  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g = bdg.build_graph(codes, k, m=m, t=2, bk_sample=sample, bk_iters=bk_iters, entry=entry,
+                        kernel=kernel)
+    e1.record()
+    torch.cuda.synchronize()
+    out["base_build_ms"] = e0.elapsed_time(e1)
+    out["base_recall_tie_aware"], _ = _recall(bdg, g, codes, k, rows_n, 1009)
+    p = bdg.propagate(g, 1)
+    p.free()  # warm-up
+    torch.cuda.synchronize()
+    L.bdg_profile_reset()
+    L.bdg_profile_enable(1)
+    e0.record()
+    p = bdg.propagate(g, 1)
+    e1.record()
+    L.bdg_profile_enable(0)
+    torch.cuda.synchronize()
+    tot, nl = ctypes.c_double(), ctypes.c_int64()
+    L.bdg_profile_read(b"propagate", ctypes.byref(tot), ctypes.byref(nl))
+    out["propagate_ms"] = e0.elapsed_time(e1)
+    out["propagate_kernel_ms"] = tot.value
+    out["after_recall_tie_aware"], _ = _recall(bdg, p, codes, k, rows_n, 1009)
+    n = codes.shape[0]
+    out["points_per_s"] = n / (out["propagate_ms"] / 1e3)
+    # upper bound of the kernel's bytes: k first-floor rows of k ids, and one code
+    # per second-floor candidate, for every point
+    W = codes.shape[1]
+    out["bytes_upper_bound_gbs"] = n * k * k * (4 + 8 * W) / (tot.value / 1e3) / 1e9
+    out["vs"] = f"t = {t_main} build of the headline (see value / recall)"
+    p.free()
+    g.free()
+    return out
 
 
 def _build_inputs(w, device, seed_shift=0):
@@ -642,6 +688,12 @@ def run_ours(a):
         if not a.no_serve:
             serve = _serve_bench(bdg, ctx, a.serve_seconds)
 
+    prop_res = None
+    if not a.no_propagate and ws == 1:
+        prop_res = _propagate_bench(bdg, codes, k, m, sample, w["bk_iters"], entry, kernel_used,
+                                    a.recall_rows, t)
+        print("propagation: " + json.dumps(prop_res), file=sys.stderr, flush=True)
+
     learned_res = None
     if not a.no_learned and ws == 1:
         learned_res = _learned_bench(bdg, device, "popc" if kernel_used == "popc" else "auto",
@@ -710,6 +762,8 @@ def run_ours(a):
         line["search"] = search
     if serve is not None:
         line["serving"] = serve
+    if prop_res is not None:
+        line["propagation"] = prop_res
     if learned_res is not None:
         line["learned_routing"] = learned_res
     if ws == 1 and not a.no_cpu:

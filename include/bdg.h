@@ -177,6 +177,18 @@ void bdg_build_plan_free(bdg_build_plan* plan);
 bdg_status bdg_graph_info(const bdg_graph* g, const int32_t** ids, const int32_t** dists,
                           int64_t* n, int32_t* k, int32_t* bits);
 
+/* Neighbourhood propagation (Section 3.3, with the propagation filter of
+ * Section 3.6 (3)): `rounds` synchronous rounds, each replacing every row by
+ *   G'(x) = first k of sort_{(d, id)} ( G(x) u { y in G(z) : z in G(x), y != x } ),
+ * every id once (the neighbours of the neighbours are the "second floor"). Reads
+ * g's rows, which must be sorted by (distance, id) with padding last (every
+ * graph this library builds or loads is), and writes a new graph *out (same k,
+ * entry sample and borrowed codes; free it with bdg_graph_free). k <= 128.
+ * Asynchronous on `stream`; BDG_EINVAL for rounds < 1, BDG_EUNSUPPORTED for
+ * k > 128, BDG_ENOMEM if the rows (and, for rounds > 1, one scratch pair) do
+ * not fit the memory budget. */
+bdg_status bdg_graph_propagate(const bdg_graph* g, int32_t rounds, void* stream, bdg_graph** out);
+
 /* Save to / load from a file: header {magic "BDG1", version, N, bits, k, n_entry}
  * followed by ids, dists and entry ids (little-endian int32). Synchronous.
  * load borrows `codes` ([N][W], device) for later searches. */

@@ -241,6 +241,17 @@ def build_graph(codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample
     return Graph(h.value, codes)
 
 
+def propagate(g: Graph, rounds: int = 1, stream=None) -> Graph:
+    """Neighbourhood propagation (see bdg_graph_propagate): a new Graph."""
+    L = lib()
+    if not getattr(L, "_prop_sigs", False):
+        L.bdg_graph_propagate.argtypes = [_c_void_p, _i32, _c_void_p, ctypes.POINTER(_c_void_p)]
+        L._prop_sigs = True
+    h = ctypes.c_void_p()
+    _check(L.bdg_graph_propagate(g._h, int(rounds), _stream(stream), ctypes.byref(h)))
+    return Graph(h.value, g.codes)
+
+
 def load_graph(path: str, codes) -> Graph:
     codes, _ = _codes(codes)
     h = ctypes.c_void_p()

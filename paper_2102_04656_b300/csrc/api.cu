@@ -667,6 +667,57 @@ bdg_status bdg_graph_save(const bdg_graph* g, const char* path) {
   return ok ? BDG_OK : bdg_set_error(BDG_EINVAL, "save: write to %s failed", path);
 }
 
+bdg_status bdg_graph_propagate(const bdg_graph* g, int32_t rounds, void* stream,
+                               bdg_graph** out) {
+  if (!out) return bdg_set_error(BDG_EINVAL, "propagate: out is NULL");
+  *out = nullptr;
+  if (!g || rounds < 1)
+    return bdg_set_error(BDG_EINVAL, "propagate: graph %p, rounds = %d (>= 1)", (const void*)g,
+                         rounds);
+  if (g->k > bdg_propagate_max_k())
+    return bdg_set_error(BDG_EUNSUPPORTED, "propagate: k = %d (at most %d)", g->k,
+                         bdg_propagate_max_k());
+  cudaStream_t st = (cudaStream_t)stream;
+  keep_pool_cached();
+  bdg_graph* h = new bdg_graph();
+  h->n = g->n; h->k = g->k; h->bits = g->bits; h->W = g->W; h->n_entry = g->n_entry;
+  h->codes = g->codes;
+  const size_t rows = (size_t)g->n * g->k * 4;
+  bdg_status s = dalloc((void**)&h->ids, rows);
+  if (s == BDG_OK) s = dalloc((void**)&h->dists, rows);
+  if (s == BDG_OK) s = dalloc((void**)&h->entry, (size_t)g->n_entry * 4);
+  if (s == BDG_OK) s = dalloc((void**)&h->entry_codes, (size_t)g->n_entry * g->W * 8);
+  if (s != BDG_OK) { bdg_graph_free(h); return s; }
+  // rounds alternate between the output rows and one scratch pair, ending in the output
+  Scratch sc;
+  if (rounds > 1) s = sc.alloc(2 * rows, st);
+  if (s != BDG_OK) { bdg_graph_free(h); return s; }
+  int32_t* ping_ids = rounds > 1 ? (int32_t*)sc.p : nullptr;
+  int32_t* ping_d = rounds > 1 ? (int32_t*)((char*)sc.p + rows) : nullptr;
+  const int32_t* in_ids = g->ids;
+  const int32_t* in_d = g->dists;
+  for (int r = 0; r < rounds; ++r) {
+    // the last round writes the output, the one before it the scratch pair, and so on
+    const bool to_out = ((rounds - 1 - r) & 1) == 0;
+    int32_t* o_ids = to_out ? h->ids : ping_ids;
+    int32_t* o_d = to_out ? h->dists : ping_d;
+    s = bdg_launch_propagate(g->codes, g->n, g->W, g->k, in_ids, in_d, o_ids, o_d, st);
+    if (s != BDG_OK) { bdg_graph_free(h); return s; }
+    in_ids = o_ids;
+    in_d = o_d;
+  }
+  if (cudaMemcpyAsync(h->entry, g->entry, (size_t)g->n_entry * 4, cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h->entry_codes, g->entry_codes, (size_t)g->n_entry * g->W * 8,
+                      cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    bdg_graph_free(h);
+    return bdg_set_error(BDG_ECUDA, "propagate: entry copy failed");
+  }
+  *out = h;
+  return BDG_OK;
+}
+
 bdg_status bdg_graph_load(const char* path, const uint64_t* codes, bdg_graph** out) {
   if (!path || !codes || !out) return bdg_set_error(BDG_EINVAL, "load: null argument");
   *out = nullptr;

@@ -221,6 +221,11 @@ struct bdg_graph_view {
 bdg_status bdg_launch_search(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
                              const int32_t* ef, int ef_max, int R, int32_t* out_ids,
                              int32_t* out_dist, int32_t* expansions, cudaStream_t st);
+// propagate.cu: one round of neighbourhood propagation, ids/dists [n][k] -> new rows
+int bdg_propagate_max_k();
+bdg_status bdg_launch_propagate(const uint64_t* codes, int64_t n, int W, int k,
+                                const int32_t* ids_in, const int32_t* dist_in, int32_t* ids_out,
+                                int32_t* dist_out, cudaStream_t st);
 bdg_status bdg_launch_rerank(const float* feats, int64_t N, int D, const float* qfeats,
                              const int32_t* cand, int64_t nq, int R, int k, int32_t* out_ids,
                              float* out_d2, cudaStream_t st);

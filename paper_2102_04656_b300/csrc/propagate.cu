@@ -1,0 +1,194 @@
+// propagate.cu -- neighbourhood propagation (Section 3.3) with the propagation
+// filter of Section 3.6 (3), one round per launch.
+//
+// For every point x, its new list is the first k by (d, id) of its current list
+// and the neighbours of its neighbours (the "second floor"), every id once; all
+// rows read the input graph and write a new one. One warp per point:
+//   * the current list is kept sorted in shared memory (its k-th key is the
+//     filter: a candidate whose key is not below it cannot enter and is
+//     dropped as soon as its distance is known);
+//   * each first-floor neighbour's list is read 32 ids at a time, one id per
+//     lane; a per-warp hash of the ids already seen skips repeats (the second
+//     floor overlaps heavily) before the candidate's code is gathered;
+//   * the keys that pass the filter are ranked across the warp and merged into
+//     the list by ranks.
+// The result does not depend on the order candidates are met in: the filter
+// bound only tightens and is never below the final k-th key.
+#include "common.cuh"
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kMaxK = 128;
+constexpr int kHash = 1024;  // seen-id slots per warp
+constexpr int kProbe = 8;
+constexpr int kNew = 0, kSeen = 1, kFull = 2;
+
+struct WarpSmem {
+  uint64_t list[kMaxK];  // current list, sorted, `size` valid keys
+  uint64_t nk[32];       // accepted keys of one batch, sorted
+  int32_t hash[kHash];
+};
+
+__device__ __forceinline__ int hash_visit(int32_t* h, int32_t id) {
+  const uint32_t slot = ((uint32_t)id * 2654435761u) >> (32 - 10);  // kHash = 1024
+  for (int p = 0; p < kProbe; ++p) {
+    const uint32_t s = (slot + p) & (kHash - 1);
+    const int32_t old = atomicCAS(&h[s], -1, id);
+    if (old == -1) return kNew;
+    if (old == id) return kSeen;
+  }
+  return kFull;  // window full: not recorded (checked against the list instead)
+}
+
+// Is key in the sorted list[0, size)?
+__device__ __forceinline__ bool in_list(const uint64_t* list, int size, uint64_t key) {
+  int lo = 0, hi = size;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (list[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo < size && list[lo] == key;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kWarps * 32)
+propagate_kernel(const uint64_t* __restrict__ codes, int64_t n, int k, int bits,
+                 const int32_t* __restrict__ ids_in, const int32_t* __restrict__ dist_in,
+                 int32_t* __restrict__ ids_out, int32_t* __restrict__ dist_out) {
+  extern __shared__ __align__(16) char prop_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpSmem& sm = reinterpret_cast<WarpSmem*>(prop_smem)[warp];
+  const uint64_t pad = bdg_pad_key(bits);
+  for (int64_t x = (int64_t)blockIdx.x * kWarps + warp; x < n; x += (int64_t)gridDim.x * kWarps) {
+    uint64_t cx[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) cx[w] = codes[x * W + w];
+    for (int i = lane; i < kHash; i += 32) sm.hash[i] = -1;
+    __syncwarp();
+    // the current list: the input row (sorted by (d, id), padding last)
+    int size = 0;
+    for (int a0 = 0; a0 < k; a0 += 32) {
+      const int a = a0 + lane;
+      uint64_t key = BDG_KEY_INF;
+      if (a < k) {
+        const int32_t z = ids_in[x * k + a];
+        if (z >= 0 && z < n && z != x) {
+          key = bdg_key((uint32_t)dist_in[x * k + a], (uint32_t)z);
+          hash_visit(sm.hash, z);
+        }
+      }
+      const unsigned ok = __ballot_sync(0xffffffffu, key != BDG_KEY_INF);
+      if (key != BDG_KEY_INF) sm.list[size + __popc(ok & ((1u << lane) - 1))] = key;
+      size += __popc(ok);
+    }
+    __syncwarp();
+    uint64_t kth = size == k ? sm.list[k - 1] : BDG_KEY_INF;
+    // the second floor
+    for (int a = 0; a < k; ++a) {
+      const int32_t z = ids_in[x * k + a];
+      if (z < 0 || z >= n) continue;
+      for (int b0 = 0; b0 < k; b0 += 32) {
+        const int32_t y = (b0 + lane < k) ? ids_in[(int64_t)z * k + b0 + lane] : -1;
+        uint64_t key = BDG_KEY_INF;
+        bool acc = false;
+        if (y >= 0 && y < n && y != x) {
+          const int hv = hash_visit(sm.hash, y);
+          if (hv != kSeen) {
+            uint32_t d = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) d += __popcll(cx[w] ^ codes[(int64_t)y * W + w]);
+            key = bdg_key(d, (uint32_t)y);
+            acc = key < kth;  // the propagation filter
+            if (acc && hv == kFull) acc = !in_list(sm.list, size, key);
+          }
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, acc);
+        if (am == 0) continue;
+        const int na = __popc(am);
+        // rank the accepted keys (ids of one row are distinct) and store them sorted
+        int rank = 0;
+        for (unsigned mm = am; mm; mm &= mm - 1) {
+          const uint64_t o = __shfl_sync(0xffffffffu, key, __ffs(mm) - 1);
+          rank += (o < key);
+        }
+        if (acc) sm.nk[rank] = key;
+        __syncwarp();
+        // merge by ranks into the list, keeping the first k
+        uint64_t lv[kMaxK / 32];
+        int lp[kMaxK / 32];
+#pragma unroll
+        for (int q = 0; q < kMaxK / 32; ++q) {
+          const int j = lane + 32 * q;
+          lp[q] = kMaxK;
+          lv[q] = 0;
+          if (j < size) {
+            lv[q] = sm.list[j];
+            int c = 0;
+            for (int i = 0; i < na; ++i) c += (sm.nk[i] < lv[q]);
+            lp[q] = j + c;
+          }
+        }
+        uint64_t nv = 0;
+        int np = kMaxK;
+        if (lane < na) {
+          nv = sm.nk[lane];
+          int lo = 0, hi = size;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.list[mid] < nv) lo = mid + 1; else hi = mid;
+          }
+          np = lane + lo;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kMaxK / 32; ++q)
+          if (lp[q] < k) sm.list[lp[q]] = lv[q];
+        if (np < k) sm.list[np] = nv;
+        size = min(k, size + na);
+        __syncwarp();
+        kth = size == k ? sm.list[k - 1] : BDG_KEY_INF;
+      }
+    }
+    // write the new row
+    for (int j = lane; j < k; j += 32) {
+      const uint64_t key = j < size ? sm.list[j] : pad;
+      ids_out[x * k + j] = j < size ? bdg_key_id(key) : -1;
+      dist_out[x * k + j] = bdg_key_d(key);
+    }
+    __syncwarp();
+  }
+}
+
+template <int W>
+bdg_status launch_w(const uint64_t* codes, int64_t n, int k, int bits, const int32_t* ids_in,
+                    const int32_t* dist_in, int32_t* ids_out, int32_t* dist_out,
+                    cudaStream_t st) {
+  const size_t smem = sizeof(WarpSmem) * kWarps;
+  BDG_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<W>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  BDG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, propagate_kernel<W>,
+                                                             kWarps * 32, smem));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t need = (n + kWarps - 1) / kWarps;
+  const int64_t cap = (int64_t)bdg_num_sms() * per_sm;
+  const int grid = (int)(need < cap ? need : cap);
+  bdg_prof_scope prof("propagate", st);
+  propagate_kernel<W><<<grid, kWarps * 32, smem, st>>>(codes, n, k, bits, ids_in, dist_in,
+                                                        ids_out, dist_out);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
+
+}  // namespace
+
+int bdg_propagate_max_k() { return kMaxK; }
+
+bdg_status bdg_launch_propagate(const uint64_t* codes, int64_t n, int W, int k,
+                                const int32_t* ids_in, const int32_t* dist_in, int32_t* ids_out,
+                                int32_t* dist_out, cudaStream_t st) {
+  if (n == 0) return BDG_OK;
+  BDG_DISPATCH_W(W, launch_w, codes, n, k, 64 * W, ids_in, dist_in, ids_out, dist_out, st);
+}

@@ -389,3 +389,34 @@ def test_build_plan_replays_bit_exact(bdg, kernel, tmp_path, monkeypatch):
     ids2, _ = oracle.knn_partitioned(_np(c2.cpu()), r2, 64)
     assert np.array_equal(plan.graph.ids.cpu().numpy(), ids2)
     plan.free()
+
+
+# ------------------------------------------------------------------ neighbourhood propagation
+@pytest.mark.parametrize("bits,n,m,t,k,rounds", [(512, 20000, 16, 2, 32, 1), (256, 12000, 30, 2, 64, 2),
+                                                 (128, 5000, 8, 1, 16, 1), (64, 3000, 6, 2, 100, 1)])
+def test_propagate_bit_exact(bdg, bits, n, m, t, k, rounds):
+    spec = datagen.MixtureSpec(n, 64, 40, bits, seed=bits + n + k)
+    c = datagen.make_codes(spec)
+    sample = datagen.sample_ids(n, min(n, 64 * m), 7)
+    entry = torch.from_numpy(_entry(n, 64, 8)).cuda()
+    g = bdg.build_graph(c.cuda(), k, m=m, t=t, bk_sample=torch.from_numpy(sample).cuda(),
+                        bk_iters=4, entry=entry)
+    base = g.ids.cpu().numpy()
+    p = bdg.propagate(g, rounds)
+    torch.cuda.synchronize()
+    ids_o = base
+    for _ in range(rounds):
+        ids_o, dist_o = oracle.propagate(_np(c), ids_o)
+    assert np.array_equal(p.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(p.dists.cpu().numpy(), dist_o)
+    assert np.array_equal(g.ids.cpu().numpy(), base)  # the input graph is untouched
+
+
+def test_propagate_padded_rows(bdg):
+    """A graph with more neighbours asked for than exist (padding rows)."""
+    c = datagen.random_codes(40, 256, seed=77)
+    g, _ = _build_exact(bdg, c.cuda(), 39)
+    p = bdg.propagate(g, 1)
+    ids_o, dist_o = oracle.propagate(_np(c), g.ids.cpu().numpy())
+    assert np.array_equal(p.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(p.dists.cpu().numpy(), dist_o)
