@@ -7,9 +7,10 @@
 //   * the current list is kept sorted in shared memory (its k-th key is the
 //     filter: a candidate whose key is not below it cannot enter and is
 //     dropped as soon as its distance is known);
-//   * each first-floor neighbour's list is read 32 ids at a time, one id per
-//     lane; a per-warp hash of the ids already seen skips repeats (the second
-//     floor overlaps heavily) before the candidate's code is gathered;
+//   * each first-floor neighbour's list is read whole (up to four ids per
+//     lane) while the next one's is loading; a per-warp hash of the ids already
+//     seen skips repeats (the second floor overlaps heavily) before the
+//     candidates' codes are gathered, all at once;
 //   * the keys that pass the filter are ranked across the warp and merged into
 //     the list by ranks.
 // The result does not depend on the order candidates are met in: the filter
@@ -84,49 +85,76 @@ propagate_kernel(const uint64_t* __restrict__ codes, int64_t n, int k, int bits,
     }
     __syncwarp();
     uint64_t kth = size == k ? sm.list[k - 1] : BDG_KEY_INF;
-    // the second floor
-    for (int a = 0; a < k; ++a) {
-      const int32_t z = ids_in[x * k + a];
-      if (z < 0 || z >= n) continue;
-      for (int b0 = 0; b0 < k; b0 += 32) {
-        const int32_t y = (b0 + lane < k) ? ids_in[(int64_t)z * k + b0 + lane] : -1;
-        uint64_t key = BDG_KEY_INF;
-        bool acc = false;
-        if (y >= 0 && y < n && y != x) {
-          const int hv = hash_visit(sm.hash, y);
-          if (hv != kSeen) {
-            uint32_t d = 0;
+    // the second floor: a neighbour's whole list is read at once (up to four ids
+    // per lane) while the next neighbour's list is already on its way, and all
+    // of its new candidates' codes are gathered before any of them is merged
+    constexpr int kB = kMaxK / 32;
+    const int nb = (k + 31) >> 5;
+    int32_t ynext[kB];
+    {
+      const int32_t z0 = ids_in[x * k];
 #pragma unroll
-            for (int w = 0; w < W; ++w) d += __popcll(cx[w] ^ codes[(int64_t)y * W + w]);
-            key = bdg_key(d, (uint32_t)y);
-            acc = key < kth;  // the propagation filter
-            if (acc && hv == kFull) acc = !in_list(sm.list, size, key);
-          }
+      for (int q = 0; q < kB; ++q)
+        ynext[q] = (z0 >= 0 && z0 < n && q < nb && q * 32 + lane < k)
+                       ? ids_in[(int64_t)z0 * k + q * 32 + lane] : -1;
+    }
+    for (int a = 0; a < k; ++a) {
+      int32_t y[kB];
+#pragma unroll
+      for (int q = 0; q < kB; ++q) y[q] = ynext[q];
+      if (a + 1 < k) {  // the next neighbour's list
+        const int32_t zn = ids_in[x * k + a + 1];
+#pragma unroll
+        for (int q = 0; q < kB; ++q)
+          ynext[q] = (zn >= 0 && zn < n && q < nb && q * 32 + lane < k)
+                         ? ids_in[(int64_t)zn * k + q * 32 + lane] : -1;
+      }
+      uint64_t key[kB];
+      int hv[kB];
+#pragma unroll
+      for (int q = 0; q < kB; ++q) {
+        key[q] = BDG_KEY_INF;
+        hv[q] = kSeen;
+        if (y[q] >= 0 && y[q] < n && y[q] != x) hv[q] = hash_visit(sm.hash, y[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < kB; ++q) {
+        if (hv[q] != kSeen) {
+          uint32_t d = 0;
+#pragma unroll
+          for (int w = 0; w < W; ++w) d += __popcll(cx[w] ^ codes[(int64_t)y[q] * W + w]);
+          key[q] = bdg_key(d, (uint32_t)y[q]);
         }
+      }
+#pragma unroll
+      for (int q = 0; q < kB; ++q) {
+        if (q >= nb) break;
+        bool acc = key[q] < kth;  // the propagation filter
+        if (acc && hv[q] == kFull) acc = !in_list(sm.list, size, key[q]);
         const unsigned am = __ballot_sync(0xffffffffu, acc);
         if (am == 0) continue;
         const int na = __popc(am);
         // rank the accepted keys (ids of one row are distinct) and store them sorted
         int rank = 0;
         for (unsigned mm = am; mm; mm &= mm - 1) {
-          const uint64_t o = __shfl_sync(0xffffffffu, key, __ffs(mm) - 1);
-          rank += (o < key);
+          const uint64_t o = __shfl_sync(0xffffffffu, key[q], __ffs(mm) - 1);
+          rank += (o < key[q]);
         }
-        if (acc) sm.nk[rank] = key;
+        if (acc) sm.nk[rank] = key[q];
         __syncwarp();
         // merge by ranks into the list, keeping the first k
-        uint64_t lv[kMaxK / 32];
-        int lp[kMaxK / 32];
+        uint64_t lv[kB];
+        int lp[kB];
 #pragma unroll
-        for (int q = 0; q < kMaxK / 32; ++q) {
-          const int j = lane + 32 * q;
-          lp[q] = kMaxK;
-          lv[q] = 0;
+        for (int r = 0; r < kB; ++r) {
+          const int j = lane + 32 * r;
+          lp[r] = kMaxK;
+          lv[r] = 0;
           if (j < size) {
-            lv[q] = sm.list[j];
+            lv[r] = sm.list[j];
             int c = 0;
-            for (int i = 0; i < na; ++i) c += (sm.nk[i] < lv[q]);
-            lp[q] = j + c;
+            for (int i = 0; i < na; ++i) c += (sm.nk[i] < lv[r]);
+            lp[r] = j + c;
           }
         }
         uint64_t nv = 0;
@@ -142,8 +170,8 @@ propagate_kernel(const uint64_t* __restrict__ codes, int64_t n, int k, int bits,
         }
         __syncwarp();
 #pragma unroll
-        for (int q = 0; q < kMaxK / 32; ++q)
-          if (lp[q] < k) sm.list[lp[q]] = lv[q];
+        for (int r = 0; r < kB; ++r)
+          if (lp[r] < k) sm.list[lp[r]] = lv[r];
         if (np < k) sm.list[np] = nv;
         size = min(k, size + na);
         __syncwarp();
