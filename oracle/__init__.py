@@ -113,8 +113,21 @@ def route(codes, centroids, t: int):
     return r, d
 
 
+def routes_coarse(routes, m: int, coarse_num: int):
+    """The coarse_num rule of Section 3.2 applied to t-nearest-centre routes
+    [n, t]: (routes with the dropped slots set to -1, home counts int32 [m])."""
+    rt = np.ascontiguousarray(routes, np.int32)
+    n, t = rt.shape
+    out = np.empty_like(rt)
+    cnt = np.empty(m, np.int32)
+    _load().or_routes_coarse(_p(rt), ctypes.c_int64(n), ctypes.c_int32(t), ctypes.c_int32(m),
+                             ctypes.c_int64(coarse_num), _p(out), _p(cnt))
+    return out, cnt
+
+
 def knn_partitioned(codes, routes, k: int, qidx=None):
-    """Divide-and-conquer graph rows of points qidx given routes [n, t] (slot 0 = home)."""
+    """Divide-and-conquer graph rows of points qidx given routes [n, t] (slot 0 =
+    home; a slot holding -1 probes nothing)."""
     c = _codes(codes)
     n, w = c.shape
     rt = np.ascontiguousarray(routes, np.int32)

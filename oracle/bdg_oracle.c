@@ -15,8 +15,8 @@
  *   - rows with fewer than k candidates are padded with (d = bits + 1, id = -1).
  *
  * Parity status per function (pins live in tests/test_oracle_*.py):
- *   or_hamming, or_knn_exact, or_bkmeans, or_route, or_knn_partitioned,
- *   or_search, or_rerank_f32/_f64, or_propagate -- pinned (brute force,
+ *   or_hamming, or_knn_exact, or_bkmeans, or_route, or_routes_coarse,
+ *   or_knn_partitioned, or_search, or_rerank_f32/_f64, or_propagate -- pinned (brute force,
  *   invariants, closed forms, hand-worked fixtures).
  */
 #include <stdint.h>
@@ -154,6 +154,34 @@ void or_route(const uint64_t* codes, int64_t n, int32_t W, const uint64_t* centr
   }
 }
 
+/* The coarse_num rule of Section 3.2: the number of nearest centres a point is
+ * mapped to varies so that the points held by its centres add up to a fixed
+ * total. Given each point's t nearest centres in order (routes [n][t], slot 0
+ * the home) and the home counts |H_p| = #{ j : routes[j][0] = p }, point i keeps
+ * slot 0 and keeps slot s >= 1 while the centres before it hold fewer than
+ * coarse_num points:
+ *   keep(i, s)  <=>  s = 0  or  sum_{s' < s} |H_{routes[i][s']}| < coarse_num,
+ * i.e. the shortest prefix holding at least coarse_num points (all t slots
+ * when even they hold fewer). Dropped slots become -1. home_count receives
+ * |H_p| for p in [0, m). */
+void or_routes_coarse(const int32_t* routes, int64_t n, int32_t t, int32_t m,
+                      int64_t coarse_num, int32_t* out, int32_t* home_count) {
+  for (int32_t p = 0; p < m; ++p) home_count[p] = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const int32_t h = routes[j * t];
+    if (h >= 0 && h < m) home_count[h] += 1;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t held = 0;  /* points in the centres kept so far */
+    for (int32_t s = 0; s < t; ++s) {
+      const int32_t p = routes[i * t + s];
+      const int keep = (s == 0) || (held < coarse_num);
+      out[i * t + s] = keep ? p : -1;
+      if (keep && p >= 0 && p < m) held += home_count[p];
+    }
+  }
+}
+
 /* Single-pass divide-and-conquer graph of Section 3.2, as a plain definition:
  *   home(j) = routes[j][0],   C(i) = { j != i : home(j) in T(i) },
  *   G(i)    = first k of sort over (d(i, j), j) for j in C(i).
@@ -176,7 +204,7 @@ void or_knn_partitioned(const uint64_t* codes, int64_t n, int32_t W, const int32
         if (j == i) continue;
         const int32_t hj = routes[j * t];
         int in_t = 0;
-        for (int32_t s = 0; s < t; ++s) in_t |= (routes[i * t + s] == hj);
+        for (int32_t s = 0; s < t; ++s) in_t |= (hj >= 0 && routes[i * t + s] == hj);
         if (!in_t) continue;
         keys[c++] = KEY(or_hamming(codes + i * W, codes + j * W, W), j);
       }

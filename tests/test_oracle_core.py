@@ -366,3 +366,95 @@ def test_propagate_keeps_the_exact_graph_and_improves_rows(oracle_lib):
             if z >= 0:
                 pool |= set(ap_i[z].tolist())
         assert set(ids[x].tolist()) <= pool
+
+
+# ---------------------------------------------------------------- coarse_num
+def _read_coarse_golden():
+    with open(os.path.join(GOLDEN, "routes_coarse_tiny.txt")) as f:
+        lines = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+    routes, counts, cases, cur = [], None, {}, None
+    for ln in lines:
+        if ln.startswith("counts:"):
+            counts = np.array([int(v) for v in ln.split(":")[1].split()], np.int32)
+        elif ln.startswith("coarse"):
+            cur = int(ln.split()[1])
+            cases[cur] = []
+        elif cur is None:
+            routes.append([int(v) for v in ln.split(":")[1].split()])
+        else:
+            cases[cur].append([int(v) for v in ln.split(":")[1].split()])
+    return (np.array(routes, np.int32), counts,
+            {c: np.array(r, np.int32) for c, r in cases.items()})
+
+
+def test_routes_coarse_hand_worked_fixture(oracle_lib):
+    routes, counts, cases = _read_coarse_golden()
+    for coarse, want in cases.items():
+        got, cnt = oracle_lib.routes_coarse(routes, 4, coarse)
+        assert np.array_equal(cnt, counts)
+        assert np.array_equal(got, want), coarse
+
+
+def _random_routes(n, m, t, seed):
+    rng = np.random.default_rng(seed)
+    sizes = rng.zipf(1.6, m).astype(np.float64)  # skewed partition sizes
+    home = rng.choice(m, n, p=sizes / sizes.sum()).astype(np.int32)
+    r = np.empty((n, t), np.int32)
+    for i in range(n):
+        others = rng.permutation(np.setdiff1d(np.arange(m), [home[i]]))[:t - 1]
+        r[i, 0], r[i, 1:] = home[i], others
+    return r
+
+
+def test_routes_coarse_invariants(oracle_lib):
+    """Kept slots form a prefix; the prefix before the last kept slot holds fewer
+    than coarse_num points; a cut prefix holds at least coarse_num; the home
+    counts are the histogram of slot 0; coarse_num <= 1 keeps only the home and
+    coarse_num > n keeps everything; more coarse_num never keeps fewer slots."""
+    n, m, t = 3000, 40, 7
+    r = _random_routes(n, m, t, 5)
+    hist = np.bincount(r[:, 0], minlength=m)
+    prev = None
+    for coarse in (0, 1, 50, 120, 300, 800, n + 1):
+        got, cnt = oracle_lib.routes_coarse(r, m, coarse)
+        assert np.array_equal(cnt, hist)
+        kept = got >= 0
+        assert kept[:, 0].all()
+        assert np.array_equal(got[kept], r[kept])
+        nk = kept.sum(1)
+        assert np.array_equal(kept, np.arange(t)[None, :] < nk[:, None])  # a prefix
+        held = np.cumsum(hist[r], axis=1)  # points held by the first s + 1 slots
+        before_last = np.where(nk > 1, held[np.arange(n), np.maximum(nk - 2, 0)], 0)
+        assert (before_last[nk > 1] < coarse).all()
+        cut = nk < t
+        assert (held[np.arange(n), nk - 1][cut] >= coarse).all()
+        if coarse <= 1:
+            assert (nk == 1).all()
+        if coarse > n:
+            assert (nk == t).all()
+        if prev is not None:
+            assert (nk >= prev).all()
+        prev = nk
+
+
+def test_partitioned_unused_slots_probe_nothing(oracle_lib):
+    """A -1 slot contributes no neighbours: the rows equal those of the routes
+    with every -1 slot replaced by the home (a repeat adds no candidate), and a
+    direct set enumeration."""
+    n, m, t, k, bits = 400, 12, 4, 6, 128
+    c = _rand_codes(n, bits, 31)
+    r = _random_routes(n, m, t, 6)
+    got_r, _ = oracle_lib.routes_coarse(r, m, 60)
+    assert (got_r < 0).any() and (got_r[:, 1] >= 0).any()
+    filled = np.where(got_r >= 0, got_r, got_r[:, :1])
+    ids, d = oracle_lib.knn_partitioned(c, got_r, k)
+    ids2, d2 = oracle_lib.knn_partitioned(c, filled, k)
+    assert np.array_equal(ids, ids2) and np.array_equal(d, d2)
+    bitsm = _bits(c, bits)
+    for i in range(0, n, 37):
+        parts = set(int(p) for p in got_r[i] if p >= 0)
+        cand = [(int((bitsm[i] != bitsm[j]).sum()), j) for j in range(n)
+                if j != i and int(r[j, 0]) in parts]
+        cand.sort()
+        want = cand[:k] + [(bits + 1, -1)] * max(0, k - len(cand))
+        assert [j for _, j in want] == list(ids[i]) and [dd for dd, _ in want] == list(d[i])
