@@ -5,7 +5,9 @@ from the paper (Zhao et al., "Large-Scale Visual Search with Binary Distributed
 Graph at Alibaba"): Hamming distance and k-NN lists (Section 3), Bk-means
 (Section 3.2, Eq. 1-2), nearest-centre routing and the single-pass
 divide-and-conquer graph (Section 3.2), best-first search with a long-link entry
-sample (Section 3.5), the real-valued re-rank (Section 3.5), recall (Eq. 3) and
+sample (Section 3.5), the real-valued re-rank (Section 3.5), the coarse_num
+rule (Section 3.2), neighbourhood propagation (Section 3.3), occlusion pruning
+(Section 3.4), recall (Eq. 3) and
 the MLP router's forward/backward (``oracle.mlp``; the paper has no router).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg may
@@ -152,6 +154,21 @@ def propagate(codes, ids_in, k: int | None = None):
     dist = np.empty((n, k), np.int32)
     _load().or_propagate(_p(c), ctypes.c_int64(n), ctypes.c_int32(w), _p(g), ctypes.c_int32(k),
                          _p(ids), _p(dist))
+    return ids, dist
+
+
+def prune(codes, ids_in, L: int):
+    """Occlusion pruning of Section 3.4 (FANNG's rule) of every row to at most L
+    edges: (ids, dists) int32 [n, L]."""
+    c = _codes(codes)
+    n, w = c.shape
+    g = np.ascontiguousarray(ids_in, np.int32)
+    assert g.shape[0] == n
+    k = g.shape[1]
+    ids = np.empty((n, L), np.int32)
+    dist = np.empty((n, L), np.int32)
+    _load().or_prune(_p(c), ctypes.c_int64(n), ctypes.c_int32(w), _p(g), ctypes.c_int32(k),
+                     ctypes.c_int32(L), _p(ids), _p(dist))
     return ids, dist
 
 

@@ -16,7 +16,8 @@
  *
  * Parity status per function (pins live in tests/test_oracle_*.py):
  *   or_hamming, or_knn_exact, or_bkmeans, or_route, or_routes_coarse,
- *   or_knn_partitioned, or_search, or_rerank_f32/_f64, or_propagate -- pinned (brute force,
+ *   or_knn_partitioned, or_search, or_rerank_f32/_f64, or_propagate, or_prune
+ *   -- pinned (brute force,
  *   invariants, closed forms, hand-worked fixtures).
  */
 #include <stdint.h>
@@ -212,6 +213,52 @@ void or_knn_partitioned(const uint64_t* codes, int64_t n, int32_t W, const int32
       emit_topk(keys, c, k, bits, out_ids + q * k, out_dist + q * k);
     }
     free(keys);
+  }
+}
+
+/* Graph pruning of Section 3.4, after the occlusion rule of FANNG (Harwood and
+ * Drummond, CVPR 2016). The candidates of point x are the ids listed in its row
+ * (ids outside [0, n), x itself and repeats dropped), taken in order of
+ * (d(x, y), y). A candidate y is kept unless a neighbour z kept before it lies
+ * closer to y than x does:
+ *   keep(y)  <=>  no kept z with d(z, y) < d(x, y),
+ * and at most L are kept (the walk stops there). The row is written in kept
+ * order (which is (d, id) order), padded to L with (-1, bits + 1). */
+void or_prune(const uint64_t* codes, int64_t n, int32_t W, const int32_t* ids_in, int32_t k,
+              int32_t L, int32_t* out_ids, int32_t* out_dist) {
+  const int32_t bits = 64 * W;
+#pragma omp parallel
+  {
+    uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(k + 1));
+    int32_t* kept = (int32_t*)malloc(sizeof(int32_t) * (size_t)(L + 1));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t x = 0; x < n; ++x) {
+      int64_t c = 0;
+      for (int32_t a = 0; a < k; ++a) {
+        const int32_t y = ids_in[x * k + a];
+        if (y < 0 || y >= n || y == x) continue;
+        int seen = 0;
+        for (int64_t b = 0; b < c; ++b) seen |= (KEY_ID(keys[b]) == y);
+        if (!seen) keys[c++] = KEY(or_hamming(codes + x * W, codes + (int64_t)y * W, W), y);
+      }
+      qsort(keys, (size_t)c, sizeof(uint64_t), cmp_u64);
+      int32_t nk = 0;
+      for (int64_t b = 0; b < c && nk < L; ++b) {
+        const int32_t y = KEY_ID(keys[b]), dxy = KEY_D(keys[b]);
+        int occluded = 0;
+        for (int32_t e = 0; e < nk && !occluded; ++e)
+          occluded = or_hamming(codes + (int64_t)kept[e] * W, codes + (int64_t)y * W, W) < dxy;
+        if (!occluded) {
+          kept[nk] = y;
+          out_ids[x * L + nk] = y;
+          out_dist[x * L + nk] = dxy;
+          ++nk;
+        }
+      }
+      for (int32_t r = nk; r < L; ++r) { out_ids[x * L + r] = -1; out_dist[x * L + r] = bits + 1; }
+    }
+    free(keys);
+    free(kept);
   }
 }
 

@@ -458,3 +458,89 @@ def test_partitioned_unused_slots_probe_nothing(oracle_lib):
         cand.sort()
         want = cand[:k] + [(bits + 1, -1)] * max(0, k - len(cand))
         assert [j for _, j in want] == list(ids[i]) and [dd for dd, _ in want] == list(d[i])
+
+
+# ---------------------------------------------------------------- pruning
+def _read_prune_golden():
+    with open(os.path.join(GOLDEN, "prune_tiny.txt")) as f:
+        lines = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+    codes = np.array([[int(x, 16)] for x in lines[0].split()], dtype=np.uint64)
+    n = codes.shape[0]
+    g_in = np.array([[int(v) for v in ln.split(":")[1].split()] for ln in lines[1:1 + n]],
+                    dtype=np.int32)
+    cases, i = {}, 1 + n
+    while i < len(lines):
+        L = int(lines[i].split()[1])
+        rows = [[p.split(",") for p in ln.split(":")[1].split()] for ln in lines[i + 1:i + 1 + n]]
+        cases[L] = (np.array([[int(a) for a, _ in r] for r in rows], np.int32),
+                    np.array([[int(b) for _, b in r] for r in rows], np.int32))
+        i += 1 + n
+    return codes, g_in, cases
+
+
+def test_prune_hand_worked_fixture(oracle_lib):
+    codes, g_in, cases = _read_prune_golden()
+    assert set(cases) == {4, 2}
+    for L, (want_ids, want_d) in cases.items():
+        ids, d = oracle_lib.prune(codes, g_in, L)
+        assert np.array_equal(ids, want_ids), L
+        assert np.array_equal(d, want_d), L
+
+
+def test_prune_line_keeps_the_two_sides(oracle_lib):
+    """Codes with i ones (d(i, j) = |i - j|) and complete rows: every interior
+    point keeps exactly its two line neighbours, the ends keep one."""
+    n = 40
+    codes = np.array([[(1 << i) - 1] for i in range(n)], dtype=np.uint64)
+    g = np.array([[j for j in range(n) if j != i] for i in range(n)], np.int32)
+    ids, d = oracle_lib.prune(codes, g, 8)
+    for i in range(n):
+        want = [i - 1, i + 1] if 0 < i < n - 1 else ([1] if i == 0 else [n - 2])
+        got = [int(v) for v in ids[i] if v >= 0]
+        assert got == want, i
+        assert (d[i, :len(want)] == 1).all() and (d[i, len(want):] == 65).all()
+
+
+def test_prune_equal_codes_keep_first_L_by_id(oracle_lib):
+    """All codes equal: every distance is 0 and nothing is strictly closer, so
+    the first L candidates by id are kept."""
+    n, k, L = 30, 12, 7
+    codes = np.full((n, 2), 0x5A5A, dtype=np.uint64)
+    rng = np.random.default_rng(3)
+    g = np.stack([rng.permutation(np.setdiff1d(np.arange(n), [i]))[:k] for i in range(n)]
+                 ).astype(np.int32)
+    ids, d = oracle_lib.prune(codes, g, L)
+    for i in range(n):
+        assert list(ids[i]) == sorted(g[i])[:L]
+    assert (d == 0).all()
+
+
+@pytest.mark.parametrize("bits,n,k,L", [(64, 300, 20, 10), (256, 200, 32, 32), (128, 150, 16, 3)])
+def test_prune_characterisation(oracle_lib, bits, n, k, L):
+    """On random rows (with -1, self ids and repeats): the kept ids are a
+    subsequence of the distinct candidates in (d, id) order; no kept id is
+    occluded by one kept before it; every candidate skipped before the walk
+    stopped has an occluder kept before it; the walk stops only at L kept."""
+    c = _rand_codes(n, bits, 41 + n)
+    rng = np.random.default_rng(n)
+    g = rng.integers(-1, n, (n, k)).astype(np.int32)
+    g[::7, 0] = np.arange(0, n, 7)  # self ids
+    g[:, 1] = g[:, 2]  # repeats
+    ids, d = oracle_lib.prune(c, g, L)
+    b = _bits(c, bits)
+    dist = lambda i, j: int((b[i] != b[j]).sum())
+    for x in range(n):
+        cand = sorted({(dist(x, int(y)), int(y)) for y in g[x] if 0 <= y < n and y != x})
+        kept = [int(v) for v in ids[x] if v >= 0]
+        assert all(v == -1 for v in ids[x][len(kept):])
+        pos = [cand.index((dist(x, y), y)) for y in kept]
+        assert pos == sorted(pos) and len(set(kept)) == len(kept)
+        for a, y in enumerate(kept):
+            assert d[x, a] == dist(x, y)
+            assert all(dist(z, y) >= dist(x, y) for z in kept[:a])
+        last = pos[-1] if len(kept) == L else len(cand) - 1
+        for j, (dxy, y) in enumerate(cand[:last + 1]):
+            if y in kept:
+                continue
+            before = [z for z, p in zip(kept, pos) if p < j]
+            assert any(dist(z, y) < dxy for z in before), (x, y)
