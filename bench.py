@@ -58,6 +58,8 @@ def _args():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-routing leg")
     ap.add_argument("--no-propagate", action="store_true", help="skip the propagation leg")
+    ap.add_argument("--no-coarse", action="store_true", help="skip the coarse_num leg")
+    ap.add_argument("--no-prune", action="store_true", help="skip the pruning leg")
     ap.add_argument("--learned-n", type=int, default=10_000_000,
                     help="points of the learned-routing leg (the workload's full size is 100M)")
     ap.add_argument("--learned-lr", type=float, default=3e-4, help="router learning rate")
@@ -251,6 +253,93 @@ def _propagate_bench(bdg, codes, k, m, sample, bk_iters, entry, kernel, rows_n, 
     return out
 
 
+def _coarse_bench(bdg, codes, k, m, sample, bk_iters, entry, kernel, rows_n, t_main):
+    """The coarse_num rule of Section 3.2 on the bench workload: up to t_max = 8
+    nearest centres per point, cut where they hold coarse_num = t_main * N / m
+    points (as many as t_main average partitions), against the fixed-t build of
+    the headline; recall judged on the same exact rows."""
+    n = codes.shape[0]
+    t_max, coarse = 8, int(round(t_main * n / m))
+    out = {"t_max": t_max, "coarse_num": coarse}
+    cent, _ = bdg.bkmeans(codes, sample, m, bk_iters)
+    for name, tt, cn in (("fixed", t_main, 0), ("coarse", t_max, coarse)):
+        r, _ = bdg.route(codes, cent, tt)
+        if cn:
+            bdg.routes_coarse(r, m, cn)
+        kept = (r >= 0).sum(1).double()
+        hc = torch.bincount(r[:, 0].long(), minlength=m).double()
+        held = torch.where(r >= 0, hc[r.clamp(min=0).long()], torch.zeros_like(r, dtype=torch.float64)).sum(1)
+        out[name] = {"t": tt, "mean_probes": float(kept.mean().item()),
+                     "mean_candidates": float(held.mean().item()),
+                     "candidates_p99_over_mean": float(torch.quantile(held[::97], 0.99).item()
+                                                        / held.mean().item())}
+        del r
+    for name, tt, cn in (("fixed", t_main, 0), ("coarse", t_max, coarse)):
+        g = bdg.build_graph(codes, k, m=m, t=tt, bk_sample=sample, bk_iters=bk_iters,
+                            entry=entry, kernel=kernel, coarse_num=cn)
+        g.free()  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g = bdg.build_graph(codes, k, m=m, t=tt, bk_sample=sample, bk_iters=bk_iters,
+                            entry=entry, kernel=kernel, coarse_num=cn)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name]["build_ms"] = e0.elapsed_time(e1)
+        out[name]["recall_tie_aware"], _ = _recall(bdg, g, codes, k, rows_n, 1009)
+        g.free()
+    return out
+
+
+def _prune_bench(bdg, ctx, steps=3):
+    """Occlusion pruning (Section 3.4) of the search graph to at most L = degree
+    edges, and the search + re-rank on the pruned graph (same queries, ef mix and
+    R) against the unpruned one."""
+    g, k = ctx["graph"], ctx["graph"].k
+    L = bdg.lib()
+    p = bdg.prune(g, k)
+    p.free()  # warm-up
+    torch.cuda.synchronize()
+    L.bdg_profile_reset()
+    L.bdg_profile_enable(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    p = bdg.prune(g, k)
+    e1.record()
+    L.bdg_profile_enable(0)
+    torch.cuda.synchronize()
+    tot, nl = ctypes.c_double(), ctypes.c_int64()
+    L.bdg_profile_read(b"prune", ctypes.byref(tot), ctypes.byref(nl))
+    n, W = g.ids.shape[0], ctx["qcodes"].shape[1]
+    kept = (p.ids >= 0).sum(1).double()
+    # algorithmic bytes per point: the row, the candidates' codes, the own code, the new row
+    per_pt = 4 * k + 8 * W * k + 8 * W + 8 * k
+    out = {"L": k, "prune_ms": e0.elapsed_time(e1), "prune_kernel_ms": tot.value,
+           "mean_degree_after": float(kept.mean().item()),
+           "algorithmic_gbs": n * per_pt / (tot.value / 1e3) / 1e9}
+    ef = ctx["ef"]
+    for _ in range(2):
+        bdg.search_rerank(p, ctx["qcodes"], ctx["qfeats"], ctx["feats"], ef, ctx["R"],
+                          ctx["topk"], ef_max=ctx["ef_max"])
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for s in range(steps):
+        ev[s][0].record()
+        ids, _ = bdg.search_rerank(p, ctx["qcodes"], ctx["qfeats"], ctx["feats"], ef, ctx["R"],
+                                   ctx["topk"], ef_max=ctx["ef_max"])
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    got = ids[ctx["gt_q"]].long().cpu().numpy()
+    gt = ctx["gt_ids"].cpu().numpy()
+    hits = sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(got, gt))
+    out["pruned_qps"] = ctx["qcodes"].shape[0] / (ms / 1e3)
+    out["pruned_recall@10_vs_exact_fp32"] = hits / gt.size
+    p.free()
+    return out
+
+
 def _build_inputs(w, device, seed_shift=0):
     spec = w["spec"]
     if seed_shift:
@@ -386,7 +475,7 @@ def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
     _, _, ex = bdg.search(g, qcodes, ef, R, ef_max=max(w["efs"]), expansions=True)
     exp_total = float(ex.double().sum().item())
     bytes_search = exp_total * (4 * k + k * 8 * (spec.bits // 64))
-    ctx = {"graph": g, "qcodes": qcodes, "qfeats": qfeats, "feats": feats, "R": R,
+    ctx = {"graph": g, "qcodes": qcodes, "qfeats": qfeats, "feats": feats, "R": R, "ef": ef,
            "topk": topk, "ef_max": max(w["efs"]), "gt_q": qs, "gt_ids": best_i}
     return ctx, {
         "workload": SEARCH_WORKLOAD, "N": n, "bits": spec.bits, "degree": k, "nq": nq,
@@ -693,12 +782,21 @@ def run_ours(a):
                                     "popc" if kernel_used == "popc" else "auto")
         if not a.no_serve:
             serve = _serve_bench(bdg, ctx, a.serve_seconds)
+        if not a.no_prune:
+            search["prune"] = _prune_bench(bdg, ctx)
+            print("prune: " + json.dumps(search["prune"]), file=sys.stderr, flush=True)
 
     prop_res = None
     if not a.no_propagate and ws == 1:
         prop_res = _propagate_bench(bdg, codes, k, m, sample, w["bk_iters"], entry, kernel_used,
                                     a.recall_rows, t)
         print("propagation: " + json.dumps(prop_res), file=sys.stderr, flush=True)
+
+    coarse_res = None
+    if not a.no_coarse and ws == 1:
+        coarse_res = _coarse_bench(bdg, codes, k, m, sample, w["bk_iters"], entry, kernel_used,
+                                   a.recall_rows, t)
+        print("coarse_num: " + json.dumps(coarse_res), file=sys.stderr, flush=True)
 
     learned_res = None
     if not a.no_learned and ws == 1:
@@ -770,6 +868,8 @@ def run_ours(a):
         line["serving"] = serve
     if prop_res is not None:
         line["propagation"] = prop_res
+    if coarse_res is not None:
+        line["coarse_num"] = coarse_res
     if learned_res is not None:
         line["learned_routing"] = learned_res
     if ws == 1 and not a.no_cpu:

@@ -73,6 +73,20 @@ void bdg_profile_reset(void);
 bdg_status bdg_route(const uint64_t* codes, int64_t n, int32_t bits, const uint64_t* centroids,
                      int32_t m, int32_t t, int32_t* routes, int32_t* rdist, void* stream);
 
+/* The coarse_num rule of Section 3.2: the number of nearest centres a point is
+ * mapped to varies so that the points held by its centres add up to a fixed
+ * total. routes: [n][t] int32, in place, each row the point's t nearest
+ * centres in order (slot 0 = home, as bdg_route writes them). home_count:
+ * out [m] int32, |H_p| = #{ j : routes[j][0] = p } (caller-owned device
+ * memory). Point i keeps slot 0 and keeps slot s >= 1 while the centres before
+ * it hold fewer than coarse_num points (sum of home_count over slots < s);
+ * later slots become -1 (the build then probes nothing there). So each point
+ * keeps the shortest prefix of its centres holding at least coarse_num
+ * points, or all t. Slots outside [0, m) hold no points. Requires
+ * 1 <= t <= 16, m >= 1, coarse_num >= 0; BDG_EINVAL otherwise. */
+bdg_status bdg_routes_coarse(int32_t* routes, int64_t n, int32_t t, int32_t m, int64_t coarse_num,
+                             int32_t* home_count, void* stream);
+
 /* Bk-means of Section 3.2 (objective Eq. 1, update Eq. 2) on the down-sample
  * codes[sample[0..S)]: centres start as the codes of sample[0..m); each of
  * `iters` iterations assigns every sample point to its nearest centre by
@@ -128,6 +142,10 @@ typedef struct bdg_partitions {
   int32_t tile_visitors;      /* work-item size in visitors: 0 (= 128) or 128 */
   int32_t kernel;             /* Reduce-1 kernel: 0 = auto (tensor cores for 256/512-bit
                                  codes and k <= 64, else popcount), 1 = popcount, 2 = tensor */
+  int64_t coarse_num;         /* 0: every point probes its t nearest centres. > 0: the
+                                 library's routes are cut by the coarse_num rule of
+                                 Section 3.2 (see bdg_routes_coarse), t being the most a
+                                 point may probe; needs routes == NULL */
 } bdg_partitions;
 
 typedef struct bdg_graph bdg_graph; /* opaque; owns ids/dists/entry, borrows codes */
@@ -188,6 +206,18 @@ bdg_status bdg_graph_info(const bdg_graph* g, const int32_t** ids, const int32_t
  * k > 128, BDG_ENOMEM if the rows (and, for rounds > 1, one scratch pair) do
  * not fit the memory budget. */
 bdg_status bdg_graph_propagate(const bdg_graph* g, int32_t rounds, void* stream, bdg_graph** out);
+
+/* Graph pruning of Section 3.4, after FANNG's occlusion rule (Harwood and
+ * Drummond, CVPR 2016): the neighbours y of x listed in g's row (ids outside
+ * [0, N), x itself and repeats dropped) are taken in (d(x, y), y) order, with
+ * distances recomputed from the codes; y is kept unless a neighbour z kept
+ * before it has d(z, y) < d(x, y) (an equal distance does not occlude), and at
+ * most L are kept. Writes a new graph *out with k = L (rows in kept order,
+ * padded with id -1, distance bits + 1; same entry sample and borrowed codes;
+ * free it with bdg_graph_free). Asynchronous on `stream`. BDG_EINVAL unless
+ * 1 <= L <= min(g's k, 64); BDG_EUNSUPPORTED for g's k > 128; BDG_ENOMEM if the
+ * new rows do not fit the memory budget. */
+bdg_status bdg_graph_prune(const bdg_graph* g, int32_t L, void* stream, bdg_graph** out);
 
 /* Save to / load from a file: header {magic "BDG1", version, N, bits, k, n_entry}
  * followed by ids, dists and entry ids (little-endian int32). Synchronous.

@@ -37,6 +37,7 @@ class _Partitions(ctypes.Structure):
         ("m", _i32), ("t", _i32), ("centroids", _c_void_p), ("bk_sample", _c_void_p),
         ("bk_sample_size", _i64), ("bk_iters", _i32), ("routes", _c_void_p),
         ("entry", _c_void_p), ("n_entry", _i32), ("tile_visitors", _i32), ("kernel", _i32),
+        ("coarse_num", _i64),
     ]
 
 
@@ -53,6 +54,7 @@ def lib():
         L.bdg_set_memory_budget.argtypes = [ctypes.c_uint64]
         L.bdg_route.argtypes = [_c_void_p, _i64, _i32, _c_void_p, _i32, _i32, _c_void_p,
                                 _c_void_p, _c_void_p]
+        L.bdg_routes_coarse.argtypes = [_c_void_p, _i64, _i32, _i32, _i64, _c_void_p, _c_void_p]
         L.bdg_bkmeans.argtypes = [_c_void_p, _i64, _i32, _c_void_p, _i64, _i32, _i32, _c_void_p,
                                   _c_void_p, _c_void_p]
         L.bdg_build_graph.argtypes = [_c_void_p, _i64, _i32, _i32, ctypes.POINTER(_Partitions),
@@ -132,6 +134,17 @@ def route(codes, centroids, t: int, stream=None):
     _check(lib().bdg_route(_ptr(codes), n, bits, _ptr(centroids), m, t, _ptr(routes),
                            _ptr(rdist), _stream(stream)))
     return routes, rdist
+
+
+def routes_coarse(routes, m: int, coarse_num: int, stream=None):
+    """The coarse_num rule of Section 3.2 (bdg_routes_coarse) on routes int32
+    [n, t], in place: the slots a point does not need become -1. Returns the
+    home counts int32 [m]."""
+    _dev(routes, torch.int32, "routes", 2)
+    cnt = torch.empty(m, dtype=torch.int32, device=routes.device)
+    _check(lib().bdg_routes_coarse(_ptr(routes), routes.shape[0], routes.shape[1], m, coarse_num,
+                                   _ptr(cnt), _stream(stream)))
+    return cnt
 
 
 def knn_rows(codes, rows, k: int, stream=None):
@@ -215,10 +228,12 @@ KERNELS = {"auto": 0, "popc": 1, "tc": 2}
 
 def build_graph(codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample=None,
                 bk_iters: int = 8, routes=None, entry=None, tile_visitors: int = 0,
-                kernel: str = "auto", stream=None) -> Graph:
+                kernel: str = "auto", coarse_num: int = 0, stream=None) -> Graph:
     """Single-pass divide-and-conquer k-NN graph (exact when m == 1).
 
-    kernel: "auto", "popc" (XOR + POPC) or "tc" (tcgen05 FP8 +-1 tensor cores)."""
+    kernel: "auto", "popc" (XOR + POPC) or "tc" (tcgen05 FP8 +-1 tensor cores).
+    coarse_num > 0: each point probes the shortest prefix of its t nearest
+    centres holding at least coarse_num points (Section 3.2)."""
     codes, bits = _codes(codes)
     if entry is None:
         raise ValueError("entry (long-link sample ids, int32 CUDA tensor) is required")
@@ -235,6 +250,7 @@ def build_graph(codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample
     P.n_entry = entry.numel()
     P.tile_visitors = tile_visitors
     P.kernel = KERNELS[kernel]
+    P.coarse_num = coarse_num
     h = ctypes.c_void_p()
     _check(lib().bdg_build_graph(_ptr(codes), codes.shape[0], bits, k, ctypes.byref(P),
                                  _stream(stream), ctypes.byref(h)))
@@ -249,6 +265,17 @@ def propagate(g: Graph, rounds: int = 1, stream=None) -> Graph:
         L._prop_sigs = True
     h = ctypes.c_void_p()
     _check(L.bdg_graph_propagate(g._h, int(rounds), _stream(stream), ctypes.byref(h)))
+    return Graph(h.value, g.codes)
+
+
+def prune(g: Graph, L: int, stream=None) -> Graph:
+    """Occlusion pruning to at most L edges per point (see bdg_graph_prune): a new Graph."""
+    lb = lib()
+    if not getattr(lb, "_prune_sigs", False):
+        lb.bdg_graph_prune.argtypes = [_c_void_p, _i32, _c_void_p, ctypes.POINTER(_c_void_p)]
+        lb._prune_sigs = True
+    h = ctypes.c_void_p()
+    _check(lb.bdg_graph_prune(g._h, int(L), _stream(stream), ctypes.byref(h)))
     return Graph(h.value, g.codes)
 
 
@@ -513,7 +540,8 @@ class BuildPlan:
     kernel. Arrays passed here are re-read by every run and must stay alive."""
 
     def __init__(self, codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample=None,
-                 bk_iters: int = 8, routes=None, entry=None, kernel: str = "auto", stream=None):
+                 bk_iters: int = 8, routes=None, entry=None, kernel: str = "auto",
+                 coarse_num: int = 0, stream=None):
         L = lib()
         if not getattr(L, "_plan_sigs", False):
             L.bdg_build_plan_create.argtypes = [_c_void_p, _i64, _i32, _i32,
@@ -542,6 +570,7 @@ class BuildPlan:
         P.n_entry = entry.numel()
         P.tile_visitors = 0
         P.kernel = KERNELS[kernel]
+        P.coarse_num = coarse_num
         h = ctypes.c_void_p()
         _check(L.bdg_build_plan_create(_ptr(codes), codes.shape[0], bits, k, ctypes.byref(P),
                                        _stream(stream), ctypes.byref(h)))

@@ -228,6 +228,16 @@ bdg_status bdg_route(const uint64_t* codes, int64_t n, int32_t bits, const uint6
   return bdg_launch_route(codes, n, bits / 64, centroids, m, t, routes, rdist, (cudaStream_t)stream);
 }
 
+bdg_status bdg_routes_coarse(int32_t* routes, int64_t n, int32_t t, int32_t m, int64_t coarse_num,
+                             int32_t* home_count, void* stream) {
+  if (n < 0 || m < 1 || t < 1 || t > 16 || coarse_num < 0)
+    return bdg_set_error(BDG_EINVAL, "routes_coarse: n=%lld m=%d t=%d coarse_num=%lld",
+                         (long long)n, m, t, (long long)coarse_num);
+  if (!home_count || (n > 0 && !routes))
+    return bdg_set_error(BDG_EINVAL, "routes_coarse: null pointer");
+  return bdg_launch_routes_coarse(routes, n, t, m, coarse_num, home_count, (cudaStream_t)stream);
+}
+
 bdg_status bdg_bkmeans(const uint64_t* codes, int64_t n, int32_t bits, const int64_t* sample,
                        int64_t S, int32_t m, int32_t iters, uint64_t* centroids, int64_t* loss,
                        void* stream) {
@@ -255,7 +265,8 @@ namespace {
 struct BuildCfg {
   int W, m, t, tile_v;
   bool need_routes, need_bk, use_tc, tc_ok;
-  size_t b_routes, b_cent, b_bk, b_csr, b_part, b_hexp, b_fix, total;
+  int64_t coarse;
+  size_t b_routes, b_cent, b_bk, b_csr, b_part, b_hexp, b_fix, b_cnt, total;
 };
 
 bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
@@ -274,6 +285,11 @@ bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_
   c->W = bits / 64; c->m = m; c->t = t;
   c->need_routes = (P->routes == nullptr) && m > 1;
   c->need_bk = c->need_routes && P->centroids == nullptr;
+  if (P->coarse_num < 0 || (P->coarse_num > 0 && P->routes != nullptr))
+    return bdg_set_error(BDG_EINVAL, "build: coarse_num = %lld needs library routing "
+                         "(routes == NULL; cut given routes with bdg_routes_coarse)",
+                         (long long)P->coarse_num);
+  c->coarse = c->need_routes ? P->coarse_num : 0;
   if (c->need_bk && (!P->bk_sample || P->bk_sample_size < m || P->bk_iters < 0))
     return bdg_set_error(BDG_EINVAL, "build: Bk-means needs bk_sample with >= m ids");
   if (P->tile_visitors != 0 && P->tile_visitors != bdg_knn_tile_visitors(c->W))
@@ -297,7 +313,9 @@ bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_
   c->b_part = t > 1 ? al((size_t)N * k * 8) : 0;  // running k-lists
   c->b_hexp = c->tc_ok ? al(bdg_knn_tc_hexp_bytes(N, m, W)) : 0;
   c->b_fix = c->tc_ok ? al((size_t)N * t) + al(64) : 0;
-  c->total = c->b_routes + c->b_cent + c->b_bk + c->b_csr + c->b_part + c->b_hexp + c->b_fix;
+  c->b_cnt = c->coarse > 0 ? al((size_t)m * 4) : 0;
+  c->total = c->b_routes + c->b_cent + c->b_bk + c->b_csr + c->b_part + c->b_hexp + c->b_fix +
+             c->b_cnt;
   return BDG_OK;
 }
 
@@ -333,6 +351,8 @@ bdg_status build_enqueue(const BuildCfg& c, bool use_tc, bdg_graph* g, const uin
   p += c.b_hexp;
   int8_t* fixflag = c.b_fix ? (int8_t*)p : nullptr;
   int32_t* tc_err = c.b_fix ? (int32_t*)(p + al((size_t)N * t)) : nullptr;
+  p += c.b_fix;
+  int32_t* home_count = c.b_cnt ? (int32_t*)p : nullptr;
 
   BDG_CUDA_TRY(cudaMemcpyAsync(g->entry, P->entry, (size_t)P->n_entry * 4,
                                cudaMemcpyDeviceToDevice, st));
@@ -344,6 +364,8 @@ bdg_status build_enqueue(const BuildCfg& c, bool use_tc, bdg_graph* g, const uin
       BDG_TRY(bdg_launch_bkmeans(codes, N, W, P->bk_sample, P->bk_sample_size, m, P->bk_iters,
                                  cent, nullptr, bk, c.b_bk, st));
     BDG_TRY(bdg_launch_route(codes, N, W, cent, m, t, routes, nullptr, st));
+    if (c.coarse > 0)
+      BDG_TRY(bdg_launch_routes_coarse(routes, N, t, m, c.coarse, home_count, st));
   }
   if (t > 1) {  // running lists start empty (a point without a valid home keeps none)
     BDG_CUDA_TRY(cudaMemsetAsync(partial, 0xff, (size_t)N * k * 8, st));
@@ -435,8 +457,8 @@ std::string tune_key(int64_t N, int32_t bits, int32_t k, const bdg_partitions* P
   char buf[512];
   std::string name(prop.name);
   for (auto& ch : name) if (ch == ' ') ch = '_';
-  snprintf(buf, sizeof(buf), "%s|bits=%d|k=%d|N=%lld|m=%d|t=%d", name.c_str(), bits, k,
-           (long long)N, P->m, P->t);
+  snprintf(buf, sizeof(buf), "%s|bits=%d|k=%d|N=%lld|m=%d|t=%d|coarse=%lld", name.c_str(), bits,
+           k, (long long)N, P->m, P->t, (long long)P->coarse_num);
   return buf;
 }
 
@@ -713,6 +735,41 @@ bdg_status bdg_graph_propagate(const bdg_graph* g, int32_t rounds, void* stream,
     cudaGetLastError();
     bdg_graph_free(h);
     return bdg_set_error(BDG_ECUDA, "propagate: entry copy failed");
+  }
+  *out = h;
+  return BDG_OK;
+}
+
+bdg_status bdg_graph_prune(const bdg_graph* g, int32_t L, void* stream, bdg_graph** out) {
+  if (!out) return bdg_set_error(BDG_EINVAL, "prune: out is NULL");
+  *out = nullptr;
+  if (!g) return bdg_set_error(BDG_EINVAL, "prune: graph is NULL");
+  if (g->k > bdg_prune_max_k())
+    return bdg_set_error(BDG_EUNSUPPORTED, "prune: k = %d (at most %d)", g->k,
+                         bdg_prune_max_k());
+  if (L < 1 || L > g->k || L > bdg_prune_max_l())
+    return bdg_set_error(BDG_EINVAL, "prune: L = %d (need 1 <= L <= min(k = %d, %d))", L, g->k,
+                         bdg_prune_max_l());
+  cudaStream_t st = (cudaStream_t)stream;
+  keep_pool_cached();
+  bdg_graph* h = new bdg_graph();
+  h->n = g->n; h->k = L; h->bits = g->bits; h->W = g->W; h->n_entry = g->n_entry;
+  h->codes = g->codes;
+  const size_t rows = (size_t)g->n * L * 4;
+  bdg_status s = dalloc((void**)&h->ids, rows);
+  if (s == BDG_OK) s = dalloc((void**)&h->dists, rows);
+  if (s == BDG_OK) s = dalloc((void**)&h->entry, (size_t)g->n_entry * 4);
+  if (s == BDG_OK) s = dalloc((void**)&h->entry_codes, (size_t)g->n_entry * g->W * 8);
+  if (s == BDG_OK)
+    s = bdg_launch_prune(g->codes, g->n, g->W, g->k, L, g->ids, h->ids, h->dists, st);
+  if (s != BDG_OK) { bdg_graph_free(h); return s; }
+  if (cudaMemcpyAsync(h->entry, g->entry, (size_t)g->n_entry * 4, cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h->entry_codes, g->entry_codes, (size_t)g->n_entry * g->W * 8,
+                      cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    bdg_graph_free(h);
+    return bdg_set_error(BDG_ECUDA, "prune: entry copy failed");
   }
   *out = h;
   return BDG_OK;

@@ -68,6 +68,8 @@ struct bdg_prof_scope {
 // route.cu
 bdg_status bdg_launch_route(const uint64_t* codes, int64_t n, int W, const uint64_t* cent,
                             int m, int t, int32_t* routes, int32_t* rdist, cudaStream_t st);
+bdg_status bdg_launch_routes_coarse(int32_t* routes, int64_t n, int t, int m, int64_t coarse,
+                                    int32_t* home_count, cudaStream_t st);
 bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int64_t* sample,
                               int64_t S, int m, int iters, uint64_t* cent, int64_t* loss,
                               void* scratch, size_t scratch_bytes, cudaStream_t st);
@@ -226,6 +228,12 @@ int bdg_propagate_max_k();
 bdg_status bdg_launch_propagate(const uint64_t* codes, int64_t n, int W, int k,
                                 const int32_t* ids_in, const int32_t* dist_in, int32_t* ids_out,
                                 int32_t* dist_out, cudaStream_t st);
+// prune.cu: occlusion pruning, ids [n][k] -> ids/dists [n][L]
+int bdg_prune_max_k();
+int bdg_prune_max_l();
+bdg_status bdg_launch_prune(const uint64_t* codes, int64_t n, int W, int k, int L,
+                            const int32_t* ids_in, int32_t* ids_out, int32_t* dist_out,
+                            cudaStream_t st);
 bdg_status bdg_launch_rerank(const float* feats, int64_t N, int D, const float* qfeats,
                              const int32_t* cand, int64_t nq, int R, int k, int32_t* out_ids,
                              float* out_d2, cudaStream_t st);

@@ -137,11 +137,78 @@ __global__ void bk_update(uint64_t* __restrict__ cent, int m, int W,
   cent[x] = v;
 }
 
+// ---- coarse_num (Section 3.2): a point keeps its home and further nearest
+// centres only while the centres kept so far hold fewer than coarse_num points.
+// Pass 1 counts the homes |H_p| (block-local shared-memory histogram when m
+// fits, flushed with one global atomic per non-empty bin); pass 2 trims each
+// row in place, one thread per point (the row is read whole before any write).
+constexpr int kHistThreads = 512;
+constexpr int kHistSmemBins = 12288;  // 48 KB of int32 bins
+
+__global__ void __launch_bounds__(kHistThreads)
+home_hist_kernel(const int32_t* __restrict__ routes, int64_t n, int t, int m,
+                 int32_t* __restrict__ cnt) {
+  extern __shared__ int32_t hb[];
+  const bool local = m <= kHistSmemBins;
+  if (local)
+    for (int p = threadIdx.x; p < m; p += kHistThreads) hb[p] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * kHistThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kHistThreads) {
+    const int32_t h = routes[i * t];
+    if (h >= 0 && h < m) atomicAdd(local ? &hb[h] : &cnt[h], 1);
+  }
+  if (!local) return;
+  __syncthreads();
+  for (int p = threadIdx.x; p < m; p += kHistThreads)
+    if (hb[p] != 0) atomicAdd(&cnt[p], hb[p]);
+}
+
+template <int MAXT>
+__global__ void coarse_trim_kernel(int32_t* __restrict__ routes, int64_t n, int t, int m,
+                                   int64_t coarse, const int32_t* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t r[MAXT];
+#pragma unroll
+  for (int s = 0; s < MAXT; ++s) r[s] = s < t ? routes[i * t + s] : -1;
+  int64_t held = 0;
+#pragma unroll
+  for (int s = 0; s < MAXT; ++s) {
+    if (s >= t) break;
+    const bool keep = s == 0 || held < coarse;
+    if (keep && r[s] >= 0 && r[s] < m) held += cnt[r[s]];
+    if (!keep) routes[i * t + s] = -1;
+  }
+}
+
 }  // namespace
 
 bdg_status bdg_launch_route(const uint64_t* codes, int64_t n, int W, const uint64_t* cent, int m,
                             int t, int32_t* routes, int32_t* rdist, cudaStream_t st) {
   BDG_DISPATCH_W(W, route_w, codes, n, cent, m, t, routes, rdist, nullptr, st);
+}
+
+bdg_status bdg_launch_routes_coarse(int32_t* routes, int64_t n, int t, int m, int64_t coarse,
+                                    int32_t* home_count, cudaStream_t st) {
+  BDG_CUDA_TRY(cudaMemsetAsync(home_count, 0, (size_t)m * 4, st));
+  if (n == 0) return BDG_OK;
+  const size_t smem = m <= kHistSmemBins ? (size_t)m * 4 : 0;
+  if (smem > 48 * 1024)
+    BDG_CUDA_TRY(cudaFuncSetAttribute(home_hist_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t need = bdg_cdiv(n, kHistThreads);
+  const int64_t cap = (int64_t)bdg_num_sms() * 2;
+  const int grid = (int)(need < cap ? need : cap);
+  bdg_prof_scope prof("routes_coarse", st);
+  home_hist_kernel<<<grid, kHistThreads, smem, st>>>(routes, n, t, m, home_count);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  coarse_trim_kernel<16><<<(int)bdg_cdiv(n, 256), 256, 0, st>>>(routes, n, t, m, coarse,
+                                                                home_count);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
 }
 
 size_t bdg_bkmeans_scratch_bytes(int64_t S, int m, int W) {

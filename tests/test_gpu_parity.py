@@ -391,6 +391,82 @@ def test_build_plan_replays_bit_exact(bdg, kernel, tmp_path, monkeypatch):
     plan.free()
 
 
+# ------------------------------------------------------------------ coarse_num (Section 3.2)
+def _skewed_routes(n, m, t, seed):
+    """Routes with Zipf-skewed homes and random further slots (repeats allowed:
+    the rule only sums the counts of the slots it keeps)."""
+    rng = np.random.default_rng(seed)
+    w = rng.zipf(1.5, m).astype(np.float64)
+    r = rng.integers(0, m, (n, t)).astype(np.int32)
+    if n:
+        r[:, 0] = rng.choice(m, n, p=w / w.sum())
+    return r
+
+
+@pytest.mark.parametrize("n,m,t,coarse", [(5000, 40, 7, 300), (20000, 13000, 5, 4),
+                                          (3000, 64, 1, 10), (0, 8, 3, 5), (4000, 30, 16, 0),
+                                          (4000, 30, 4, 10 ** 12), (100003, 256, 8, 2500)])
+def test_routes_coarse_bit_exact(bdg, n, m, t, coarse):
+    r = _skewed_routes(n, m, t, seed=n + m)
+    rt = torch.from_numpy(r).cuda()
+    cnt = bdg.routes_coarse(rt, m, coarse)
+    r_o, cnt_o = oracle.routes_coarse(r, m, coarse)
+    assert np.array_equal(cnt.cpu().numpy(), cnt_o)
+    assert np.array_equal(rt.cpu().numpy(), r_o)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("bits,n,m,t,k,coarse", [(512, 20000, 16, 6, 64, 3500),
+                                                 (256, 9000, 40, 8, 32, 700),
+                                                 (128, 5000, 64, 4, 8, 150)])
+def test_partitioned_build_coarse_num_bit_exact(bdg, bits, n, m, t, k, coarse, kernel):
+    if kernel == "tc" and not _tc_ok(bits, k):
+        pytest.skip("tensor path: 256/512-bit codes and k <= 64")
+    spec = datagen.MixtureSpec(n, 64, 48, bits, seed=n + m + 1)
+    c = datagen.make_codes(spec)
+    sample = datagen.sample_ids(n, min(n, 64 * m), seed=3)
+    entry = torch.from_numpy(_entry(n, 64, 4)).cuda()
+    g = bdg.build_graph(c.cuda(), k, m=m, t=t, bk_sample=torch.from_numpy(sample).cuda(),
+                        bk_iters=8, entry=entry, kernel=kernel, coarse_num=coarse)
+    cent_o, _, _ = oracle.bkmeans(_np(c), sample, m, 8)
+    r_o, _ = oracle.route(_np(c), cent_o, t)
+    rc_o, _ = oracle.routes_coarse(r_o, m, coarse)
+    kept = (rc_o >= 0).sum(1)
+    assert kept.min() < kept.max()  # the number of probed partitions varies
+    ids_o, dist_o = oracle.knn_partitioned(_np(c), rc_o, k)
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+def test_build_plan_coarse_num_bit_exact(bdg, tmp_path, monkeypatch):
+    monkeypatch.setenv("BDG_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    spec = datagen.MixtureSpec(12000, 64, 48, 512, seed=516)
+    c = datagen.make_codes(spec).cuda()
+    sample = torch.from_numpy(datagen.sample_ids(spec.n, 1024, 3)).cuda()
+    entry = torch.from_numpy(_entry(spec.n, 64, 4)).cuda()
+    plan = bdg.BuildPlan(c, 64, m=16, t=5, bk_sample=sample, bk_iters=6, entry=entry,
+                         coarse_num=2000)
+    cent_o, _, _ = oracle.bkmeans(_np(c.cpu()), sample.cpu().numpy(), 16, 6)
+    r_o, _ = oracle.route(_np(c.cpu()), cent_o, 5)
+    rc_o, _ = oracle.routes_coarse(r_o, 16, 2000)
+    ids_o, dist_o = oracle.knn_partitioned(_np(c.cpu()), rc_o, 64)
+    for _ in range(2):
+        plan.run()
+        torch.cuda.synchronize()
+        assert np.array_equal(plan.graph.ids.cpu().numpy(), ids_o)
+        assert np.array_equal(plan.graph.dists.cpu().numpy(), dist_o)
+    plan.free()
+
+
+def test_coarse_num_rejects_given_routes(bdg):
+    c = datagen.random_codes(500, 256, seed=2).cuda()
+    r = torch.zeros(500, 2, dtype=torch.int32, device="cuda")
+    r[:, 1] = 1
+    entry = torch.from_numpy(_entry(500, 16, 1)).cuda()
+    with pytest.raises(bdg.BDGError):
+        bdg.build_graph(c, 8, m=2, t=2, routes=r, entry=entry, coarse_num=100)
+
+
 # ------------------------------------------------------------------ neighbourhood propagation
 @pytest.mark.parametrize("bits,n,m,t,k,rounds", [(512, 20000, 16, 2, 32, 1), (256, 12000, 30, 2, 64, 2),
                                                  (128, 5000, 8, 1, 16, 1), (64, 3000, 6, 2, 100, 1)])
@@ -420,3 +496,69 @@ def test_propagate_padded_rows(bdg):
     ids_o, dist_o = oracle.propagate(_np(c), g.ids.cpu().numpy())
     assert np.array_equal(p.ids.cpu().numpy(), ids_o)
     assert np.array_equal(p.dists.cpu().numpy(), dist_o)
+
+
+# ------------------------------------------------------------------ pruning (Section 3.4)
+@pytest.mark.parametrize("bits,n,m,t,k,L", [(512, 20000, 16, 3, 64, 50), (256, 12000, 30, 2, 32, 32),
+                                            (256, 12000, 30, 2, 32, 1), (1024, 3000, 1, 1, 128, 64),
+                                            (64, 5000, 8, 2, 16, 7)])
+def test_prune_bit_exact(bdg, bits, n, m, t, k, L):
+    spec = datagen.MixtureSpec(n, 64, 40, bits, seed=bits + n + k + L)
+    c = datagen.make_codes(spec)
+    sample = datagen.sample_ids(n, min(n, 64 * m), 7)
+    entry = torch.from_numpy(_entry(n, 64, 8)).cuda()
+    g = bdg.build_graph(c.cuda(), k, m=m, t=t, bk_sample=torch.from_numpy(sample).cuda(),
+                        bk_iters=4, entry=entry)
+    base = g.ids.cpu().numpy()
+    p = bdg.prune(g, L)
+    ids_o, dist_o = oracle.prune(_np(c), base, L)
+    assert p.ids.shape == (n, L)
+    assert np.array_equal(p.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(p.dists.cpu().numpy(), dist_o)
+    assert np.array_equal(g.ids.cpu().numpy(), base)  # the input graph is untouched
+    if L >= 32:
+        assert (ids_o < 0).any()  # occlusion removed edges
+
+
+def test_prune_adversarial_rows(bdg, tmp_path):
+    """Loaded rows in no order, with -1, out-of-range ids, self ids and repeats;
+    all-equal codes (nothing occludes)."""
+    n, k, bits = 3000, 48, 256
+    rng = np.random.default_rng(4)
+    for codes in (datagen.random_codes(n, bits, seed=5),
+                  torch.full((n, bits // 64), 0x1234, dtype=torch.int64)):
+        ids = rng.integers(-3, n + 5, (n, k)).astype(np.int32)
+        ids[::5, 3] = np.arange(0, n, 5)
+        ids[:, 7] = ids[:, 9]
+        ids[100] = -1
+        path = str(tmp_path / "adv.bdg")
+        _write_graph(path, ids, bits, np.arange(16))
+        g = bdg.load_graph(path, codes.cuda())
+        for L in (40, 5):
+            p = bdg.prune(g, L)
+            ids_o, dist_o = oracle.prune(_np(codes), ids, L)
+            assert np.array_equal(p.ids.cpu().numpy(), ids_o)
+            assert np.array_equal(p.dists.cpu().numpy(), dist_o)
+
+
+def test_prune_rejects_bad_L(bdg):
+    c = datagen.random_codes(500, 256, seed=2).cuda()
+    g, _ = _build_exact(bdg, c, 8)
+    for L in (0, 9):
+        with pytest.raises(bdg.BDGError):
+            bdg.prune(g, L)
+
+
+def test_prune_then_search_bit_exact(bdg):
+    """The pruned graph (padded rows) searched: equal to the oracle's search on it."""
+    spec = datagen.MixtureSpec(8000, 64, 40, 256, seed=91)
+    c = datagen.make_codes(spec)
+    g, entry = _build_exact(bdg, c.cuda(), 32)
+    p = bdg.prune(g, 24)
+    q = datagen.random_codes(64, 256, seed=92)
+    ef = torch.full((64,), 64, dtype=torch.int32).cuda()
+    ids, dist = bdg.search(p, q.cuda(), ef, 40)
+    ids_o, dist_o, _ = oracle.search(_np(c), p.ids.cpu().numpy(), entry.cpu().numpy(), _np(q),
+                                     np.full(64, 64), 40)
+    assert np.array_equal(ids.cpu().numpy(), ids_o)
+    assert np.array_equal(dist.cpu().numpy(), dist_o)
