@@ -191,6 +191,40 @@ def search(codes, graph, entry, queries, ef, R: int):
     return ids, dist, cnt
 
 
+def shard_offsets(n: int, S: int) -> np.ndarray:
+    """Contiguous shards of Section 3.4: shard s holds points [off[s], off[s+1])
+    with off[s] = floor(s * n / S)."""
+    return np.array([(s * n) // S for s in range(S + 1)], np.int64)
+
+
+def search_sharded(codes, graphs, entries, queries, ef, R: int):
+    """Search over a multi-shard index (Sections 3.4 and 4): every shard s (its
+    points codes[off[s]:off[s+1]], its own graph with local ids and its own
+    entry sample) answers the query with ``search``; local ids become global
+    (+ off[s]); the answer is the first min(ef, R) of all shards' keys by
+    (d, global id), padded to R with (-1, bits + 1).
+    Returns (ids, dists) int32 [nq, R]."""
+    c = _codes(codes)
+    S = len(graphs)
+    off = shard_offsets(c.shape[0], S)
+    qc = _codes(queries)
+    nq, bits = qc.shape[0], 64 * c.shape[1]
+    efa = np.broadcast_to(np.asarray(ef, np.int64), (nq,))
+    parts = []
+    for s in range(S):
+        ids_s, d_s, _ = search(c[off[s]:off[s + 1]], graphs[s], entries[s], qc, ef, R)
+        parts.append((np.where(ids_s >= 0, ids_s + off[s], -1), d_s))
+    out_ids = np.full((nq, R), -1, np.int32)
+    out_d = np.full((nq, R), bits + 1, np.int32)
+    for q in range(nq):
+        keys = [(int(d_s[q, r]), int(ids_s[q, r])) for ids_s, d_s in parts
+                for r in range(R) if ids_s[q, r] >= 0]
+        keys.sort()
+        for r, (d, i) in enumerate(keys[:max(0, min(int(efa[q]), R))]):
+            out_ids[q, r], out_d[q, r] = i, d
+    return out_ids, out_d
+
+
 def rerank(feats, qfeats, cand, k: int, precision: str = "f32"):
     """Re-rank candidates cand [nq, R] by squared L2: (ids int32 [nq, k], d [nq, k])."""
     f = np.ascontiguousarray(feats, np.float32)

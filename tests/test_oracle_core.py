@@ -544,3 +544,47 @@ def test_prune_characterisation(oracle_lib, bits, n, k, L):
                 continue
             before = [z for z, p in zip(kept, pos) if p < j]
             assert any(dist(z, y) < dxy for z in before), (x, y)
+
+
+# ---------------------------------------------------------------- multi-shard search
+def test_shard_offsets_cover_contiguously(oracle_lib):
+    for n, S in ((10, 3), (1000, 7), (5, 5), (8, 1)):
+        off = oracle_lib.shard_offsets(n, S)
+        assert off[0] == 0 and off[-1] == n and (np.diff(off) >= n // S).all()
+        assert (np.diff(off) <= -(-n // S)).all()
+
+
+def test_search_sharded_one_shard_is_search(oracle_lib):
+    n, bits = 300, 128
+    c = _rand_codes(n, bits, 91)
+    rng = np.random.default_rng(9)
+    g = np.array([rng.permutation(np.setdiff1d(np.arange(n), [i]))[:12] for i in range(n)],
+                 np.int32)
+    e = np.array([0, 100, 200], np.int32)
+    q = _rand_codes(20, bits, 92)
+    ef = np.array([5, 40] * 10)
+    a_ids, a_d, _ = oracle_lib.search(c, g, e, q, ef, 30)
+    b_ids, b_d = oracle_lib.search_sharded(c, [g], [e], q, ef, 30)
+    assert np.array_equal(a_ids, b_ids) and np.array_equal(a_d, b_d)
+
+
+def test_search_sharded_complete_shards_equal_brute_force(oracle_lib):
+    """Complete graph per shard and ef >= shard size: each shard returns its
+    exact first keys, so the merged answer is the exact first R over all n."""
+    n, bits, S, R = 150, 256, 4, 25
+    c = _rand_codes(n, bits, 93)
+    c[77] = c[12]  # a duplicate code across shards: ties by global id
+    off = oracle_lib.shard_offsets(n, S)
+    graphs, entries = [], []
+    for s in range(S):
+        ns = int(off[s + 1] - off[s])
+        graphs.append(np.array([[j for j in range(ns) if j != i] for i in range(ns)], np.int32))
+        entries.append(np.array([0], np.int32))
+    q = np.concatenate([_rand_codes(9, bits, 94), c[12:13]])
+    ids, d = oracle_lib.search_sharded(c, graphs, entries, q, n, R)
+    full = (_bits(q, bits)[:, None, :] != _bits(c, bits)[None, :, :]).sum(2)
+    for i in range(q.shape[0]):
+        order = np.lexsort((np.arange(n), full[i]))[:R]
+        assert list(ids[i]) == list(order)
+        assert list(d[i]) == [int(full[i, o]) for o in order]
+    assert list(ids[-1][:2]) == [12, 77]
