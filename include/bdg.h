@@ -219,6 +219,33 @@ bdg_status bdg_graph_propagate(const bdg_graph* g, int32_t rounds, void* stream,
  * new rows do not fit the memory budget. */
 bdg_status bdg_graph_prune(const bdg_graph* g, int32_t L, void* stream, bdg_graph** out);
 
+/* Multi-shard build of Section 3.4: the points are split into S contiguous
+ * shards, shard s holding points [off[s], off[s+1]) with off[s] = floor(s N / S),
+ * and each shard gets its own divide-and-conquer graph over its points only
+ * (local ids 0 .. n_s - 1), as bdg_build_graph builds it. The binary centres do
+ * not depend on the shard, so Bk-means runs once, on the whole data (with
+ * partitions->bk_sample, global ids), unless partitions->centroids is given;
+ * every shard is routed with the same centres. partitions->entry holds S
+ * consecutive samples of n_entry LOCAL ids, one per shard; partitions->routes,
+ * when given, is the [N][t] array for all points (shard s reads its rows).
+ * out: host array of S handles, each a graph that borrows codes + off[s] * W;
+ * free each with bdg_graph_free (on failure none is returned). 1 <= S <= 32;
+ * every shard needs k < n_s. */
+bdg_status bdg_build_sharded(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
+                             const bdg_partitions* partitions, int32_t S, void* stream,
+                             bdg_graph** out);
+
+/* Search over a multi-shard index (Sections 3.4 and 4): each of the S shard
+ * graphs (shards[s] holding global ids off[s] .. off[s] + n_s - 1, off[s] the
+ * sum of the earlier shards' sizes) answers every query as bdg_search does; the
+ * answers are merged into the first min(ef[q], R) pairs by (distance, global
+ * id), padded to R with (-1, bits + 1). All shards must have the queries' bits.
+ * out_ids/out_dist: [nq][R] global ids and distances. Scratch of S * nq * R * 8
+ * bytes is taken from the memory budget. 1 <= S <= 32, S * R <= 6144. */
+bdg_status bdg_search_sharded(const bdg_graph* const* shards, int32_t S, const uint64_t* queries,
+                              int64_t nq, const int32_t* ef, int32_t ef_max, int32_t R,
+                              int32_t* out_ids, int32_t* out_dist, void* stream);
+
 /* Save to / load from a file: header {magic "BDG1", version, N, bits, k, n_entry}
  * followed by ids, dists and entry ids (little-endian int32). Synchronous.
  * load borrows `codes` ([N][W], device) for later searches. */

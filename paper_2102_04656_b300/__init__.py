@@ -302,6 +302,65 @@ def search(g: Graph, queries, ef, R: int, ef_max: int | None = None, expansions:
     return (ids, dist, ex) if expansions else (ids, dist)
 
 
+def _shard_sigs(lb):
+    if not getattr(lb, "_shard_sigs", False):
+        lb.bdg_build_sharded.argtypes = [_c_void_p, _i64, _i32, _i32, ctypes.POINTER(_Partitions),
+                                         _i32, _c_void_p, ctypes.POINTER(_c_void_p)]
+        lb.bdg_search_sharded.argtypes = [ctypes.POINTER(_c_void_p), _i32, _c_void_p, _i64,
+                                          _c_void_p, _i32, _i32, _c_void_p, _c_void_p, _c_void_p]
+        lb._shard_sigs = True
+    return lb
+
+
+def shard_offsets(n: int, S: int) -> list:
+    """Shard s of a multi-shard build holds points [off[s], off[s+1])."""
+    return [(s * n) // S for s in range(S + 1)]
+
+
+def build_sharded(codes, k: int, S: int, entries, m: int = 1, t: int = 1, centroids=None,
+                  bk_sample=None, bk_iters: int = 8, kernel: str = "auto", coarse_num: int = 0,
+                  stream=None) -> list:
+    """Multi-shard build (bdg_build_sharded): S graphs over contiguous shards,
+    Bk-means once. entries: int32 [S, n_entry] local entry ids per shard."""
+    codes, bits = _codes(codes)
+    _dev(entries, torch.int32, "entries", 2)
+    if entries.shape[0] != S:
+        raise ValueError("entries must hold one sample per shard")
+    P = _Partitions()
+    P.m, P.t = m, t
+    P.centroids = None if centroids is None else _codes(centroids, "centroids")[0].data_ptr()
+    P.bk_sample = None if bk_sample is None else _dev(bk_sample, torch.int64, "bk_sample",
+                                                      1).data_ptr()
+    P.bk_sample_size = 0 if bk_sample is None else bk_sample.numel()
+    P.bk_iters = bk_iters
+    P.routes = None
+    P.entry = entries.data_ptr()
+    P.n_entry = entries.shape[1]
+    P.tile_visitors = 0
+    P.kernel = KERNELS[kernel]
+    P.coarse_num = coarse_num
+    hs = (_c_void_p * S)()
+    _check(_shard_sigs(lib()).bdg_build_sharded(_ptr(codes), codes.shape[0], bits, k,
+                                                ctypes.byref(P), S, _stream(stream), hs))
+    off = shard_offsets(codes.shape[0], S)
+    return [Graph(hs[s], codes[off[s]:off[s + 1]]) for s in range(S)]
+
+
+def search_sharded(graphs, queries, ef, R: int, ef_max: int, stream=None):
+    """Search over a multi-shard index (bdg_search_sharded): (ids, dists) int32
+    [nq, R] with global ids (shard s's ids offset by the earlier shards' sizes)."""
+    queries, _ = _codes(queries, "queries")
+    _dev(ef, torch.int32, "ef", 1)
+    nq = queries.shape[0]
+    ids = torch.empty(nq, R, dtype=torch.int32, device=queries.device)
+    dist = torch.empty(nq, R, dtype=torch.int32, device=queries.device)
+    hs = (_c_void_p * len(graphs))(*[g.handle for g in graphs])
+    _check(_shard_sigs(lib()).bdg_search_sharded(hs, len(graphs), _ptr(queries), nq, _ptr(ef),
+                                                 ef_max, R, _ptr(ids), _ptr(dist),
+                                                 _stream(stream)))
+    return ids, dist
+
+
 def rerank(feats, qfeats, cand, k: int, stream=None):
     """FP32 squared-L2 re-rank of candidates: (ids int32 [nq, k], d2 float32 [nq, k])."""
     _dev(feats, torch.float32, "feats", 2)

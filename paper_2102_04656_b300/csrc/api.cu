@@ -827,6 +827,94 @@ bdg_status bdg_search(const bdg_graph* g, const uint64_t* queries, int64_t nq, c
                            (cudaStream_t)stream);
 }
 
+bdg_status bdg_build_sharded(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
+                             const bdg_partitions* P, int32_t S, void* stream, bdg_graph** out) {
+  if (!out || !P || !codes) return bdg_set_error(BDG_EINVAL, "build_sharded: null argument");
+  if (S < 1 || S > BDG_MAX_SHARDS)
+    return bdg_set_error(BDG_EINVAL, "build_sharded: S = %d (1 .. %d)", S, BDG_MAX_SHARDS);
+  for (int s = 0; s < S; ++s) out[s] = nullptr;
+  BDG_TRY(check_bits(bits));
+  if (N < 2 || N >= (int64_t(1) << 31))
+    return bdg_set_error(BDG_EINVAL, "build_sharded: N = %lld", (long long)N);
+  if (!P->entry || P->n_entry < 1)
+    return bdg_set_error(BDG_EINVAL, "build_sharded: an entry sample per shard is required");
+  const int W = bits / 64;
+  for (int s = 0; s < S; ++s) {
+    const int64_t ns = (int64_t)(s + 1) * N / S - (int64_t)s * N / S;
+    if (k >= ns)
+      return bdg_set_error(BDG_EINVAL, "build_sharded: shard %d holds %lld points (k = %d)", s,
+                           (long long)ns, k);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  keep_pool_cached();
+  // the centres, once, over the whole data
+  Scratch sc;
+  const uint64_t* cent = P->centroids;
+  if (P->m > 1 && !cent && !P->routes) {
+    if (!P->bk_sample || P->bk_sample_size < P->m || P->bk_iters < 0)
+      return bdg_set_error(BDG_EINVAL, "build_sharded: Bk-means needs bk_sample with >= m ids");
+    BDG_TRY(sc.alloc(al((size_t)P->m * W * 8), st));
+    BDG_TRY(bdg_bkmeans(codes, N, bits, P->bk_sample, P->bk_sample_size, P->m, P->bk_iters,
+                        (uint64_t*)sc.p, nullptr, stream));
+    cent = (const uint64_t*)sc.p;
+  }
+  for (int s = 0; s < S; ++s) {
+    const int64_t o = (int64_t)s * N / S, ns = (int64_t)(s + 1) * N / S - o;
+    bdg_partitions Ps = *P;
+    Ps.centroids = cent;
+    Ps.entry = P->entry + (size_t)s * P->n_entry;
+    Ps.routes = P->routes ? P->routes + (size_t)o * P->t : nullptr;
+    const bdg_status r = bdg_build_graph(codes + (size_t)o * W, ns, bits, k, &Ps, stream, &out[s]);
+    if (r != BDG_OK) {
+      for (int u = 0; u <= s; ++u) {
+        if (out[u]) bdg_graph_free(out[u]);
+        out[u] = nullptr;
+      }
+      return r;
+    }
+  }
+  return BDG_OK;
+}
+
+bdg_status bdg_search_sharded(const bdg_graph* const* shards, int32_t S, const uint64_t* queries,
+                              int64_t nq, const int32_t* ef, int32_t ef_max, int32_t R,
+                              int32_t* out_ids, int32_t* out_dist, void* stream) {
+  if (!shards || S < 1 || S > BDG_MAX_SHARDS || R < 1 || S * R > 6144)
+    return bdg_set_error(BDG_EINVAL, "search_sharded: S = %d, R = %d (1 <= S <= %d, S R <= 6144)",
+                         S, R, BDG_MAX_SHARDS);
+  if (nq < 0 || ef_max < 1 || ef_max > 1024)
+    return bdg_set_error(BDG_EINVAL, "search_sharded: nq=%lld ef_max=%d", (long long)nq, ef_max);
+  if (nq > 0 && (!queries || !ef || !out_ids || !out_dist))
+    return bdg_set_error(BDG_EINVAL, "search_sharded: null pointer");
+  bdg_shard_offsets off{};
+  int64_t o = 0;
+  for (int s = 0; s < S; ++s) {
+    if (!shards[s]) return bdg_set_error(BDG_EINVAL, "search_sharded: shard %d is NULL", s);
+    if (shards[s]->bits != shards[0]->bits)
+      return bdg_set_error(BDG_EINVAL, "search_sharded: shards of different code widths");
+    off.off[s] = o;
+    o += shards[s]->n;
+  }
+  if (o >= (int64_t(1) << 31))
+    return bdg_set_error(BDG_EINVAL, "search_sharded: %lld points in all (< 2^31)", (long long)o);
+  if (nq == 0) return BDG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  keep_pool_cached();
+  const size_t part = (size_t)nq * R * 4;
+  Scratch sc;
+  BDG_TRY(sc.alloc(2 * al(part * S), st));
+  int32_t* ids = (int32_t*)sc.p;
+  int32_t* dist = (int32_t*)((char*)sc.p + al(part * S));
+  for (int s = 0; s < S; ++s) {
+    const bdg_graph* g = shards[s];
+    bdg_graph_view v{g->codes, g->ids, g->entry, g->entry_codes, g->n, g->k, g->bits, g->n_entry};
+    BDG_TRY(bdg_launch_search(v, queries, nq, ef, ef_max, R, ids + (size_t)s * nq * R,
+                              dist + (size_t)s * nq * R, nullptr, st));
+  }
+  return bdg_launch_shard_merge(ids, dist, S, nq, R, off, ef, ef_max, shards[0]->bits, out_ids,
+                                out_dist, st);
+}
+
 bdg_status bdg_rerank(const float* feats, int64_t N, int32_t D, const float* qfeats,
                       const int32_t* cand, int64_t nq, int32_t R, int32_t k, int32_t* out_ids,
                       float* out_d2, void* stream) {

@@ -223,6 +223,16 @@ struct bdg_graph_view {
 bdg_status bdg_launch_search(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
                              const int32_t* ef, int ef_max, int R, int32_t* out_ids,
                              int32_t* out_dist, int32_t* expansions, cudaStream_t st);
+// shard.cu: merge of per-shard search answers into one (global ids)
+#define BDG_MAX_SHARDS 32
+struct bdg_shard_offsets {
+  int64_t off[BDG_MAX_SHARDS];  // global id of each shard's local id 0
+};
+size_t bdg_shard_merge_smem(int S, int R);
+bdg_status bdg_launch_shard_merge(const int32_t* ids, const int32_t* dist, int S, int64_t nq,
+                                  int R, const bdg_shard_offsets& off, const int32_t* ef,
+                                  int ef_max, int bits, int32_t* out_ids, int32_t* out_dist,
+                                  cudaStream_t st);
 // propagate.cu: one round of neighbourhood propagation, ids/dists [n][k] -> new rows
 int bdg_propagate_max_k();
 bdg_status bdg_launch_propagate(const uint64_t* codes, int64_t n, int W, int k,

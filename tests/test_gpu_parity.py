@@ -562,3 +562,68 @@ def test_prune_then_search_bit_exact(bdg):
                                      np.full(64, 64), 40)
     assert np.array_equal(ids.cpu().numpy(), ids_o)
     assert np.array_equal(dist.cpu().numpy(), dist_o)
+
+
+# ------------------------------------------------------------------ multi-shard (Section 3.4)
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("bits,n,S,m,t,k", [(512, 20003, 4, 16, 3, 32), (256, 9001, 3, 1, 1, 16),
+                                            (128, 6000, 7, 12, 2, 8)])
+def test_build_and_search_sharded_bit_exact(bdg, bits, n, S, m, t, k, kernel):
+    if kernel == "tc" and not _tc_ok(bits, k):
+        pytest.skip("tensor path: 256/512-bit codes and k <= 64")
+    spec = datagen.MixtureSpec(n, 64, 48, bits, seed=n + S)
+    c = datagen.make_codes(spec)
+    cn = _np(c)
+    off = oracle.shard_offsets(n, S)
+    assert list(off) == bdg.shard_offsets(n, S)
+    sample = datagen.sample_ids(n, min(n, 64 * m), seed=3)
+    entries = np.stack([_entry(int(off[s + 1] - off[s]), 32, 10 + s) for s in range(S)])
+    graphs = bdg.build_sharded(c.cuda(), k, S, torch.from_numpy(entries).cuda(), m=m, t=t,
+                               bk_sample=torch.from_numpy(sample).cuda(), bk_iters=6,
+                               kernel=kernel)
+    cent_o = oracle.bkmeans(cn, sample, m, 6)[0] if m > 1 else None
+    for s in range(S):
+        sl = cn[off[s]:off[s + 1]]
+        if m > 1:
+            r_o, _ = oracle.route(sl, cent_o, t)
+            ids_o, dist_o = oracle.knn_partitioned(sl, r_o, k)
+        else:
+            ids_o, dist_o = oracle.knn_exact(sl, k)
+        assert np.array_equal(graphs[s].ids.cpu().numpy(), ids_o), s
+        assert np.array_equal(graphs[s].dists.cpu().numpy(), dist_o), s
+    q = datagen.make_codes(spec, n=300, seed_offset=2)
+    efs = np.array([16, 64, 100, 7] * 75, np.int32)
+    R = 40
+    ids, dist = bdg.search_sharded(graphs, q.cuda(), torch.from_numpy(efs).cuda(), R, ef_max=100)
+    ids_o, dist_o = oracle.search_sharded(cn, [g.ids.cpu().numpy() for g in graphs],
+                                          list(entries), _np(q), efs, R)
+    assert np.array_equal(ids.cpu().numpy(), ids_o)
+    assert np.array_equal(dist.cpu().numpy(), dist_o)
+    for g in graphs:
+        g.free()
+
+
+def test_search_sharded_one_shard_equals_search(bdg):
+    c = datagen.random_codes(5000, 256, seed=21).cuda()
+    g, _ = _build_exact(bdg, c, 16)
+    q = datagen.random_codes(200, 256, seed=22).cuda()
+    ef = torch.tensor([3, 50, 0, 65] * 50, dtype=torch.int32).cuda()  # 0 and 65: invalid rows
+    a_ids, a_d = bdg.search(g, q, ef, 30, ef_max=64)
+    b_ids, b_d = bdg.search_sharded([g], q, ef, 30, ef_max=64)
+    assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d)
+
+
+def test_sharded_argument_errors(bdg):
+    c = datagen.random_codes(400, 256, seed=23).cuda()
+    e = torch.zeros(2, 4, dtype=torch.int32).cuda()
+    with pytest.raises(bdg.BDGError):
+        bdg.build_sharded(c, 8, 0, e[:0])
+    with pytest.raises(bdg.BDGError):
+        bdg.build_sharded(c, 250, 2, e)  # k >= shard size
+    g, _ = _build_exact(bdg, c, 8)
+    q = c[:4]
+    ef = torch.full((4,), 8, dtype=torch.int32).cuda()
+    with pytest.raises(bdg.BDGError):
+        bdg.search_sharded([g] * 33, q, ef, 8, ef_max=8)
+    with pytest.raises(bdg.BDGError):
+        bdg.search_sharded([g] * 7, q, ef, 1000, ef_max=8)  # S R > 6144
