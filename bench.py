@@ -60,6 +60,7 @@ def _args():
     ap.add_argument("--no-propagate", action="store_true", help="skip the propagation leg")
     ap.add_argument("--no-coarse", action="store_true", help="skip the coarse_num leg")
     ap.add_argument("--no-prune", action="store_true", help="skip the pruning leg")
+    ap.add_argument("--no-shards", action="store_true", help="skip the multi-shard leg")
     ap.add_argument("--learned-n", type=int, default=10_000_000,
                     help="points of the learned-routing leg (the workload's full size is 100M)")
     ap.add_argument("--learned-lr", type=float, default=3e-4, help="router learning rate")
@@ -340,6 +341,51 @@ def _prune_bench(bdg, ctx, steps=3):
     return out
 
 
+def _shard_bench(bdg, ctx, S=4, steps=3):
+    """Multi-shard index (Sections 3.4 and 4) of the search workload: S
+    contiguous shards built with one Bk-means (bdg_build_sharded), searched
+    shard by shard and merged (bdg_search_sharded), then the same FP32 re-rank;
+    against the single graph of the search leg."""
+    codes, b = ctx["codes"], ctx["build"]
+    n = codes.shape[0]
+    off = bdg.shard_offsets(n, S)
+    entries = torch.stack([torch.from_numpy(datagen.sample_ids(
+        off[s + 1] - off[s], b["n_entry"], b["seed"] + 4 + s).astype(np.int32))
+        for s in range(S)]).to(codes.device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    graphs = bdg.build_sharded(codes, ctx["graph"].k, S, entries, m=b["m"], t=b["t"],
+                               bk_sample=b["sample"], bk_iters=8, kernel=b["kernel"])
+    torch.cuda.synchronize()
+    out = {"shards": S, "build_seconds": time.perf_counter() - t0,
+           "single_build_seconds": b["seconds"]}
+    ef, R, topk = ctx["ef"], ctx["R"], ctx["topk"]
+
+    def step():
+        cand, _ = bdg.search_sharded(graphs, ctx["qcodes"], ef, R, ef_max=ctx["ef_max"])
+        return bdg.rerank(ctx["feats"], ctx["qfeats"], cand, topk)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for s in range(steps):
+        ev[s][0].record()
+        ids, _ = step()
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(e) for a, e in ev) / steps
+    got = ids[ctx["gt_q"]].long().cpu().numpy()
+    gt = ctx["gt_ids"].cpu().numpy()
+    hits = sum(len(set(a.tolist()) & set(e.tolist())) for a, e in zip(got, gt))
+    out["qps"] = ctx["qcodes"].shape[0] / (ms / 1e3)
+    out["recall@10_vs_exact_fp32"] = hits / gt.size
+    for g in graphs:
+        g.free()
+    return out
+
+
 def _build_inputs(w, device, seed_shift=0):
     spec = w["spec"]
     if seed_shift:
@@ -476,7 +522,9 @@ def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
     exp_total = float(ex.double().sum().item())
     bytes_search = exp_total * (4 * k + k * 8 * (spec.bits // 64))
     ctx = {"graph": g, "qcodes": qcodes, "qfeats": qfeats, "feats": feats, "R": R, "ef": ef,
-           "topk": topk, "ef_max": max(w["efs"]), "gt_q": qs, "gt_ids": best_i}
+           "topk": topk, "ef_max": max(w["efs"]), "gt_q": qs, "gt_ids": best_i, "codes": codes,
+           "build": {"m": m, "t": t, "sample": sample, "n_entry": n_entry, "kernel": kernel,
+                     "seconds": build_s, "seed": spec.seed}}
     return ctx, {
         "workload": SEARCH_WORKLOAD, "N": n, "bits": spec.bits, "degree": k, "nq": nq,
         "ef_mix": list(w["efs"]), "R": R, "topk": topk, "graph_build": {"m": m, "t": t,
@@ -785,6 +833,9 @@ def run_ours(a):
         if not a.no_prune:
             search["prune"] = _prune_bench(bdg, ctx)
             print("prune: " + json.dumps(search["prune"]), file=sys.stderr, flush=True)
+        if not a.no_shards:
+            search["sharded"] = _shard_bench(bdg, ctx)
+            print("sharded: " + json.dumps(search["sharded"]), file=sys.stderr, flush=True)
 
     prop_res = None
     if not a.no_propagate and ws == 1:

@@ -557,7 +557,7 @@ def test_prune_then_search_bit_exact(bdg):
     p = bdg.prune(g, 24)
     q = datagen.random_codes(64, 256, seed=92)
     ef = torch.full((64,), 64, dtype=torch.int32).cuda()
-    ids, dist = bdg.search(p, q.cuda(), ef, 40)
+    ids, dist = bdg.search(p, q.cuda(), ef, 40, ef_max=64)
     ids_o, dist_o, _ = oracle.search(_np(c), p.ids.cpu().numpy(), entry.cpu().numpy(), _np(q),
                                      np.full(64, 64), 40)
     assert np.array_equal(ids.cpu().numpy(), ids_o)
