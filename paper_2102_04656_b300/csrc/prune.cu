@@ -1,19 +1,22 @@
 // prune.cu -- graph pruning of Section 3.4 after FANNG's occlusion rule
-// (Harwood and Drummond, CVPR 2016), one warp per point.
+// (Harwood and Drummond, CVPR 2016).
 //
 // The candidates of x are the ids of its row (invalid ids, x itself and repeats
 // dropped) in (d(x, y), y) order; y is kept unless a neighbour z kept before it
-// is strictly closer to y than x is, and at most L are kept. Per warp:
-//   * every lane loads the codes of up to four candidates (16-byte loads) into
-//     shared memory (rows padded by one word against bank conflicts) and forms
-//     its key (d(x, y), y);
-//   * ranks by counting give each first occurrence of a key its position in
-//     (d, id) order (repeats of an id share the key and only the first is
-//     placed; positions left empty by them are skipped);
-//   * a warp-uniform walk takes the candidates in that order; each lane tests
-//     one or two of the kept neighbours (d(z, y) against d(x, y)) and one ballot
-//     decides. Only kept neighbours are tested, so a row costs at most
-//     k * L distances, not k^2 / 2.
+// is strictly closer to y than x is, and at most L are kept.
+//
+// A group of G lanes handles one point (32 / G points per warp; G grows with the
+// code width so that the per-point shared memory stays small):
+//   * the group loads the row, the candidates' codes (16-byte loads) into
+//     shared memory (rows padded by one word against bank conflicts) and their
+//     keys (d(x, y), y);
+//   * a row already in strict (d, id) order (every row this library builds) is
+//     walked as it is; any other row is ranked by counting (repeats of an id
+//     share the key and only the first is placed);
+//   * the walk takes the candidates in order, all groups of the warp in step;
+//     each lane of a group tests every G-th kept neighbour (d(z, y) against
+//     d(x, y)) and one ballot decides. Only kept neighbours are tested, so a row
+//     costs at most k * L distances.
 // Bytes: the row (4 k), the candidates' codes (8 W k, random rows), the own
 // code and the pruned row out (8 L): bound by the code gathers.
 #include "common.cuh"
@@ -25,107 +28,135 @@ constexpr int kMaxK = 128;
 constexpr int kMaxL = 64;
 
 template <int W>
-struct PruneSmem {
-  static constexpr int kRow = W + 1;  // padded code row (u64 words)
-  uint64_t codes[kMaxK * kRow];
-  uint64_t keys[kMaxK];
-  int16_t order[kMaxK];
-  int16_t kept[kMaxL];
+struct PruneCfg {
+  static constexpr int G = W <= 4 ? 8 : (W <= 8 ? 16 : 32);  // lanes per point
+  static constexpr int kPts = 32 / G;                           // points per warp
+  static constexpr int kRow = W + 1;                            // padded code row (words)
 };
+
+// Shared memory of one point, in 8-byte words: codes [kc][W + 1], keys [kc],
+// then walk order [kc] and kept slots [L] as int16 (kc = k rounded up to even).
+__host__ __device__ inline size_t point_words(int k, int W, int L) {
+  const int kc = (k + 1) & ~1;
+  return (size_t)kc * (W + 1) + kc + (kc + L + 3) / 4;
+}
 
 template <int W>
 __global__ void __launch_bounds__(kWarps * 32)
 prune_kernel(const uint64_t* __restrict__ codes, int64_t n, int k, int L, int bits,
              const int32_t* __restrict__ ids_in, int32_t* __restrict__ ids_out,
              int32_t* __restrict__ dist_out) {
-  using Sm = PruneSmem<W>;
-  constexpr int kRow = Sm::kRow;
-  extern __shared__ __align__(16) char prune_smem[];
+  using C = PruneCfg<W>;
+  constexpr int G = C::G, kPts = C::kPts, kRow = C::kRow;
+  extern __shared__ __align__(16) uint64_t prune_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Sm& sm = reinterpret_cast<Sm*>(prune_smem)[warp];
-  constexpr int kB = kMaxK / 32;
-  const int nb = (k + 31) >> 5;
-  for (int64_t x = (int64_t)blockIdx.x * kWarps + warp; x < n; x += (int64_t)gridDim.x * kWarps) {
+  const int grp = lane / G, lg = lane % G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  const int kc = (k + 1) & ~1;
+  uint64_t* pcodes = prune_smem + ((size_t)warp * kPts + grp) * point_words(k, W, L);
+  uint64_t* pkeys = pcodes + (size_t)kc * kRow;
+  int16_t* porder = reinterpret_cast<int16_t*>(pkeys + kc);
+  int16_t* pkept = porder + kc;
+  const int64_t stride = (int64_t)gridDim.x * kWarps * kPts;
+  for (int64_t x0 = ((int64_t)blockIdx.x * kWarps + warp) * kPts; x0 < n; x0 += stride) {
+    const int64_t x = x0 + grp;
+    const bool live = x < n;
     uint64_t cx[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) cx[w] = codes[x * W + w];
+    for (int w = 0; w < W; ++w) cx[w] = live ? codes[x * W + w] : 0;
     // candidates: codes into shared memory, keys (d, id)
-    uint64_t key[kB];
+    for (int a = lg; a < k; a += G) {
+      uint64_t key = BDG_KEY_INF;
+      const int32_t y = live ? ids_in[x * k + a] : -1;
+      if (y >= 0 && y < n && y != x) {
+        uint64_t v[W];
+        if constexpr (W % 2 == 0) {  // 16-byte loads of the code row
+          const ulonglong2* src = reinterpret_cast<const ulonglong2*>(codes + (int64_t)y * W);
 #pragma unroll
-    for (int q = 0; q < kB; ++q) {
-      key[q] = BDG_KEY_INF;
-      const int a = q * 32 + lane;
-      if (q < nb && a < k) {
-        const int32_t y = ids_in[x * k + a];
-        if (y >= 0 && y < n && y != x) {
-          uint64_t v[W];
-          if constexpr (W % 2 == 0) {  // 16-byte loads of the code row
-            const ulonglong2* src = reinterpret_cast<const ulonglong2*>(codes + (int64_t)y * W);
-#pragma unroll
-            for (int w = 0; w < W / 2; ++w) {
-              const ulonglong2 u = src[w];
-              v[2 * w] = u.x;
-              v[2 * w + 1] = u.y;
-            }
-          } else {
-#pragma unroll
-            for (int w = 0; w < W; ++w) v[w] = codes[(int64_t)y * W + w];
+          for (int w = 0; w < W / 2; ++w) {
+            const ulonglong2 u = src[w];
+            v[2 * w] = u.x;
+            v[2 * w + 1] = u.y;
           }
-          uint32_t d = 0;
+        } else {
 #pragma unroll
-          for (int w = 0; w < W; ++w) {
-            sm.codes[a * kRow + w] = v[w];
-            d += __popcll(v[w] ^ cx[w]);
-          }
-          key[q] = bdg_key(d, (uint32_t)y);
+          for (int w = 0; w < W; ++w) v[w] = codes[(int64_t)y * W + w];
         }
-        sm.keys[a] = key[q];
-        sm.order[a] = -1;
-      }
-    }
-    __syncwarp();
-    // position in (d, id) order = number of smaller keys; a repeat of an earlier
-    // key is not placed
-#pragma unroll
-    for (int q = 0; q < kB; ++q) {
-      const int a = q * 32 + lane;
-      if (q < nb && a < k && key[q] != BDG_KEY_INF) {
-        int rank = 0;
-        bool dup = false;
-        for (int b = 0; b < k; ++b) {
-          const uint64_t o = sm.keys[b];
-          rank += o < key[q];
-          dup |= (o == key[q]) & (b < a);
-        }
-        if (!dup) sm.order[rank] = (int16_t)a;
-      }
-    }
-    __syncwarp();
-    // the walk
-    int nk = 0;
-    for (int r = 0; r < k && nk < L; ++r) {
-      const int a = sm.order[r];
-      if (a < 0) continue;
-      const uint32_t dxy = bdg_key_d(sm.keys[a]);
-      bool occ = false;
-      for (int e = lane; e < nk; e += 32) {
-        const int z = sm.kept[e];
         uint32_t d = 0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) d += __popcll(sm.codes[z * kRow + w] ^ sm.codes[a * kRow + w]);
-        occ |= d < dxy;
+        for (int w = 0; w < W; ++w) {
+          pcodes[a * kRow + w] = v[w];
+          d += __popcll(v[w] ^ cx[w]);
+        }
+        key = bdg_key(d, (uint32_t)y);
       }
-      if (__ballot_sync(0xffffffffu, occ) == 0) {
-        if (lane == 0) sm.kept[nk] = (int16_t)a;
-        ++nk;
-        __syncwarp();
-      }
+      pkeys[a] = key;
     }
     __syncwarp();
-    for (int e = lane; e < L; e += 32) {
-      const uint64_t kk = e < nk ? sm.keys[sm.kept[e]] : 0;
-      ids_out[x * L + e] = e < nk ? (int32_t)bdg_key_id(kk) : -1;
-      dist_out[x * L + e] = e < nk ? (int32_t)bdg_key_d(kk) : bits + 1;
+    // is the row already in strict (d, id) order, padding last?
+    bool in_order = true;
+    for (int a = lg; a < k; a += G) {
+      const uint64_t key = pkeys[a];
+      in_order &= key == BDG_KEY_INF || a == 0 || pkeys[a - 1] < key;
+      porder[a] = -1;
+    }
+    for (int e = lg; e < L; e += G) pkept[e] = 0;  // every slot index below stays in range
+    const bool sorted = (__ballot_sync(0xffffffffu, !in_order) & gmask) == 0;
+    __syncwarp();
+    // walk order: the row itself, or positions by counting (a repeat of an
+    // earlier key is not placed)
+    for (int a = lg; a < k; a += G) {
+      const uint64_t key = pkeys[a];
+      if (key == BDG_KEY_INF) continue;
+      if (sorted) {
+        porder[a] = (int16_t)a;
+        continue;
+      }
+      int rank = 0;
+      bool dup = false;
+      for (int b = 0; b < k; ++b) {
+        const uint64_t o = pkeys[b];
+        rank += o < key;
+        dup |= (o == key) & (b < a);
+      }
+      if (!dup) porder[rank] = (int16_t)a;
+    }
+    __syncwarp();
+    // the walk, every group of the warp in step
+    int nk = 0;
+    for (int r = 0; r < k; ++r) {
+      const int a = porder[r];
+      const bool act = a >= 0 && nk < L;
+      const int as = a < 0 ? 0 : a;  // an in-range slot even where it is not used
+      bool occ = false;
+      if (act) {
+        const uint32_t dxy = bdg_key_d(pkeys[as]);
+        uint64_t yv[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) yv[w] = pcodes[as * kRow + w];
+        for (int e = lg; e < nk; e += G) {
+          const int z = pkept[e];
+          uint32_t d = 0;
+#pragma unroll
+          for (int w = 0; w < W; ++w) d += __popcll(pcodes[z * kRow + w] ^ yv[w]);
+          occ |= d < dxy;
+        }
+      }
+      // every lane takes part in the ballot, whatever its group is doing
+      const unsigned bal = __ballot_sync(0xffffffffu, occ);
+      const bool keep = act && (bal & gmask) == 0;
+      if (keep) {
+        if (lg == 0) pkept[nk] = (int16_t)a;
+        ++nk;
+      }
+      __syncwarp();
+    }
+    if (live) {
+      for (int e = lg; e < L; e += G) {
+        const uint64_t kk = pkeys[e < nk ? pkept[e] : 0];
+        ids_out[x * L + e] = e < nk ? (int32_t)bdg_key_id(kk) : -1;
+        dist_out[x * L + e] = e < nk ? (int32_t)bdg_key_d(kk) : bits + 1;
+      }
     }
     __syncwarp();
   }
@@ -135,14 +166,15 @@ template <int W>
 bdg_status launch_w(const uint64_t* codes, int64_t n, int k, int L, int bits,
                     const int32_t* ids_in, int32_t* ids_out, int32_t* dist_out,
                     cudaStream_t st) {
-  const size_t smem = sizeof(PruneSmem<W>) * kWarps;
+  const size_t smem = point_words(k, W, L) * 8 * PruneCfg<W>::kPts * kWarps;
   BDG_CUDA_TRY(cudaFuncSetAttribute(prune_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   int per_sm = 0;
   BDG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_kernel<W>,
                                                              kWarps * 32, smem));
   if (per_sm < 1) per_sm = 1;
-  const int64_t need = (n + kWarps - 1) / kWarps;
+  const int64_t per_block = (int64_t)kWarps * PruneCfg<W>::kPts;
+  const int64_t need = (n + per_block - 1) / per_block;
   const int64_t cap = (int64_t)bdg_num_sms() * per_sm;
   const int grid = (int)(need < cap ? need : cap);
   bdg_prof_scope prof("prune", st);
