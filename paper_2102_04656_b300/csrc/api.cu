@@ -716,6 +716,11 @@ bdg_status bdg_graph_propagate(const bdg_graph* g, int32_t rounds, void* stream,
   if (s != BDG_OK) { bdg_graph_free(h); return s; }
   int32_t* ping_ids = rounds > 1 ? (int32_t*)sc.p : nullptr;
   int32_t* ping_d = rounds > 1 ? (int32_t*)((char*)sc.p + rows) : nullptr;
+  Scratch so;  // processing order of the points
+  int32_t* perm = nullptr;
+  s = so.alloc(bdg_propagate_order_bytes(g->n), st);
+  if (s == BDG_OK) s = bdg_launch_propagate_order(g->codes, g->n, g->W, so.p, &perm, st);
+  if (s != BDG_OK) { bdg_graph_free(h); return s; }
   const int32_t* in_ids = g->ids;
   const int32_t* in_d = g->dists;
   for (int r = 0; r < rounds; ++r) {
@@ -723,7 +728,7 @@ bdg_status bdg_graph_propagate(const bdg_graph* g, int32_t rounds, void* stream,
     const bool to_out = ((rounds - 1 - r) & 1) == 0;
     int32_t* o_ids = to_out ? h->ids : ping_ids;
     int32_t* o_d = to_out ? h->dists : ping_d;
-    s = bdg_launch_propagate(g->codes, g->n, g->W, g->k, in_ids, in_d, o_ids, o_d, st);
+    s = bdg_launch_propagate(g->codes, g->n, g->W, g->k, perm, in_ids, in_d, o_ids, o_d, st);
     if (s != BDG_OK) { bdg_graph_free(h); return s; }
     in_ids = o_ids;
     in_d = o_d;

@@ -235,9 +235,14 @@ bdg_status bdg_launch_shard_merge(const int32_t* ids, const int32_t* dist, int S
                                   cudaStream_t st);
 // propagate.cu: one round of neighbourhood propagation, ids/dists [n][k] -> new rows
 int bdg_propagate_max_k();
+// processing order of the points (perm [n], in scratch of bdg_propagate_order_bytes)
+size_t bdg_propagate_order_bytes(int64_t n);
+bdg_status bdg_launch_propagate_order(const uint64_t* codes, int64_t n, int W, void* scratch,
+                                      int32_t** perm, cudaStream_t st);
 bdg_status bdg_launch_propagate(const uint64_t* codes, int64_t n, int W, int k,
-                                const int32_t* ids_in, const int32_t* dist_in, int32_t* ids_out,
-                                int32_t* dist_out, cudaStream_t st);
+                                const int32_t* perm, const int32_t* ids_in,
+                                const int32_t* dist_in, int32_t* ids_out, int32_t* dist_out,
+                                cudaStream_t st);
 // prune.cu: occlusion pruning, ids [n][k] -> ids/dists [n][L]
 int bdg_prune_max_k();
 int bdg_prune_max_l();

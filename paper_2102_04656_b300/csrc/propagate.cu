@@ -14,7 +14,10 @@
 //   * the keys that pass the filter are ranked across the warp and merged into
 //     the list by ranks.
 // The result does not depend on the order candidates are met in: the filter
-// bound only tightens and is never below the final k-th key.
+// bound only tightens and is never below the final k-th key. Nor does it depend
+// on the order points are processed in, so points go grouped by 16 bits of
+// their code (a counting sort): points processed at the same time then tend to
+// be neighbours, their second floors overlap and the code gathers hit L2.
 #include "common.cuh"
 
 namespace {
@@ -52,16 +55,71 @@ __device__ __forceinline__ bool in_list(const uint64_t* list, int size, uint64_t
   return lo < size && list[lo] == key;
 }
 
+// ---- processing order: counting sort of the points by 16 code bits
+constexpr int kOrderBins = 1 << 16;
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ uint32_t order_key(const uint64_t* codes, int64_t x, int W) {
+  return (uint32_t)(codes[x * W] & (kOrderBins - 1));
+}
+
+__global__ void order_hist(const uint64_t* __restrict__ codes, int64_t n, int W,
+                           int32_t* __restrict__ cnt) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[order_key(codes, x, W)], 1);
+}
+
+// exclusive prefix sums of the kOrderBins counts, in place (one block)
+__global__ void __launch_bounds__(kScanThreads) order_scan(int32_t* __restrict__ cnt) {
+  constexpr int kPer = kOrderBins / kScanThreads;
+  __shared__ int32_t wsum[kScanThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  int32_t s = 0;
+  for (int i = 0; i < kPer; ++i) s += cnt[t * kPer + i];
+  int32_t incl = s;  // inclusive scan over the warp
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[wp] = incl;
+  __syncthreads();
+  if (wp == 0) {
+    int32_t w = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t v = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += v;
+    }
+    wsum[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  int32_t run = incl - s + (wp > 0 ? wsum[wp - 1] : 0);
+  for (int i = 0; i < kPer; ++i) {
+    const int32_t c = cnt[t * kPer + i];
+    cnt[t * kPer + i] = run;
+    run += c;
+  }
+}
+
+__global__ void order_scatter(const uint64_t* __restrict__ codes, int64_t n, int W,
+                              int32_t* __restrict__ cur, int32_t* __restrict__ perm) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x)
+    perm[atomicAdd(&cur[order_key(codes, x, W)], 1)] = (int32_t)x;
+}
+
 template <int W>
 __global__ void __launch_bounds__(kWarps * 32)
 propagate_kernel(const uint64_t* __restrict__ codes, int64_t n, int k, int bits,
-                 const int32_t* __restrict__ ids_in, const int32_t* __restrict__ dist_in,
-                 int32_t* __restrict__ ids_out, int32_t* __restrict__ dist_out) {
+                 const int32_t* __restrict__ perm, const int32_t* __restrict__ ids_in,
+                 const int32_t* __restrict__ dist_in, int32_t* __restrict__ ids_out,
+                 int32_t* __restrict__ dist_out) {
   extern __shared__ __align__(16) char prop_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(prop_smem)[warp];
   const uint64_t pad = bdg_pad_key(bits);
-  for (int64_t x = (int64_t)blockIdx.x * kWarps + warp; x < n; x += (int64_t)gridDim.x * kWarps) {
+  for (int64_t i = (int64_t)blockIdx.x * kWarps + warp; i < n; i += (int64_t)gridDim.x * kWarps) {
+    const int64_t x = perm[i];
     uint64_t cx[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) cx[w] = codes[x * W + w];
@@ -189,9 +247,9 @@ propagate_kernel(const uint64_t* __restrict__ codes, int64_t n, int k, int bits,
 }
 
 template <int W>
-bdg_status launch_w(const uint64_t* codes, int64_t n, int k, int bits, const int32_t* ids_in,
-                    const int32_t* dist_in, int32_t* ids_out, int32_t* dist_out,
-                    cudaStream_t st) {
+bdg_status launch_w(const uint64_t* codes, int64_t n, int k, int bits, const int32_t* perm,
+                    const int32_t* ids_in, const int32_t* dist_in, int32_t* ids_out,
+                    int32_t* dist_out, cudaStream_t st) {
   const size_t smem = sizeof(WarpSmem) * kWarps;
   BDG_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<W>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -203,8 +261,8 @@ bdg_status launch_w(const uint64_t* codes, int64_t n, int k, int bits, const int
   const int64_t cap = (int64_t)bdg_num_sms() * per_sm;
   const int grid = (int)(need < cap ? need : cap);
   bdg_prof_scope prof("propagate", st);
-  propagate_kernel<W><<<grid, kWarps * 32, smem, st>>>(codes, n, k, bits, ids_in, dist_in,
-                                                        ids_out, dist_out);
+  propagate_kernel<W><<<grid, kWarps * 32, smem, st>>>(codes, n, k, bits, perm, ids_in,
+                                                        dist_in, ids_out, dist_out);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   return BDG_OK;
@@ -214,9 +272,31 @@ bdg_status launch_w(const uint64_t* codes, int64_t n, int k, int bits, const int
 
 int bdg_propagate_max_k() { return kMaxK; }
 
-bdg_status bdg_launch_propagate(const uint64_t* codes, int64_t n, int W, int k,
-                                const int32_t* ids_in, const int32_t* dist_in, int32_t* ids_out,
-                                int32_t* dist_out, cudaStream_t st) {
+size_t bdg_propagate_order_bytes(int64_t n) { return (size_t)kOrderBins * 4 + (size_t)n * 4; }
+
+bdg_status bdg_launch_propagate_order(const uint64_t* codes, int64_t n, int W, void* scratch,
+                                      int32_t** perm, cudaStream_t st) {
+  int32_t* cnt = (int32_t*)scratch;
+  *perm = cnt + kOrderBins;
+  BDG_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)kOrderBins * 4, st));
   if (n == 0) return BDG_OK;
-  BDG_DISPATCH_W(W, launch_w, codes, n, k, 64 * W, ids_in, dist_in, ids_out, dist_out, st);
+  const int64_t blocks = bdg_cdiv(n, 256), cap = (int64_t)bdg_num_sms() * 8;
+  const int grid = (int)(blocks < cap ? blocks : cap);
+  order_hist<<<grid, 256, 0, st>>>(codes, n, W, cnt);
+  BDG_CUDA_TRY(cudaGetLastError());
+  order_scan<<<1, kScanThreads, 0, st>>>(cnt);
+  BDG_CUDA_TRY(cudaGetLastError());
+  order_scatter<<<grid, 256, 0, st>>>(codes, n, W, cnt, *perm);
+  BDG_CUDA_TRY(cudaGetLastError());
+  for (int i = 0; i < 3; ++i) bdg_note_launch();
+  return BDG_OK;
+}
+
+bdg_status bdg_launch_propagate(const uint64_t* codes, int64_t n, int W, int k,
+                                const int32_t* perm, const int32_t* ids_in,
+                                const int32_t* dist_in, int32_t* ids_out, int32_t* dist_out,
+                                cudaStream_t st) {
+  if (n == 0) return BDG_OK;
+  BDG_DISPATCH_W(W, launch_w, codes, n, k, 64 * W, perm, ids_in, dist_in, ids_out, dist_out,
+                 st);
 }
