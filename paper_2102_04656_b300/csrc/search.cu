@@ -27,7 +27,9 @@
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kHash = 1024;  // visited-id hash slots per warp
+// visited-id hash slots per warp: a small table leaves room for more warps per SM,
+// which hides more gather latency than the re-scores it causes cost
+constexpr int kHash = 256;
 constexpr int kProbe = 8;
 constexpr int kSmallBatch = 8;  // accepted keys ranked by counting instead of a sort
 
@@ -48,7 +50,7 @@ __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < 
 constexpr int kNew = 0, kSeen = 1, kFull = 2;
 __device__ __forceinline__ int hash_visit(int32_t* h, int32_t id) {
   uint32_t x = (uint32_t)id * 2654435761u;
-  uint32_t slot = x >> (32 - 10);  // kHash = 1024
+  uint32_t slot = x >> (32 - 8);  // kHash = 256
   for (int p = 0; p < kProbe; ++p) {
     const uint32_t sidx = (slot + p) & (kHash - 1);
     const int32_t old = atomicCAS(&h[sidx], -1, id);
