@@ -29,7 +29,10 @@ constexpr int kMaxL = 64;
 
 template <int W>
 struct PruneCfg {
-  static constexpr int G = W <= 4 ? 8 : (W <= 8 ? 16 : 32);  // lanes per point
+  // lanes per point, measured: 16 up to 512-bit codes (10M x 256-bit, k = 32: 4, 8, 16,
+  // 32 lanes took 26.7, 21.2, 19.8, 34.1 ms; 2M x 512-bit, k = 64: 8, 16, 32 took 22.6,
+  // 17.8, 19.3 ms), 32 above
+  static constexpr int G = W <= 8 ? 16 : 32;
   static constexpr int kPts = 32 / G;                           // points per warp
   static constexpr int kRow = W + 1;                            // padded code row (words)
 };
