@@ -246,6 +246,18 @@ bdg_status bdg_search_sharded(const bdg_graph* const* shards, int32_t S, const u
                               int64_t nq, const int32_t* ef, int32_t ef_max, int32_t R,
                               int32_t* out_ids, int32_t* out_dist, void* stream);
 
+/* (Not in the paper) a search layout that trades device memory for latency:
+ * stores, next to the graph's rows, the codes of every row's neighbours
+ * ([N][k][W] words, N * k * bits / 8 bytes: 10 GB for 10M points, k = 32,
+ * 256-bit codes), so that bdg_search reads a node's neighbour codes as one
+ * contiguous block whose address is known as soon as the node is chosen,
+ * instead of one random code per neighbour after its id has arrived. Results
+ * are unchanged. The copy reflects the graph and codes at the time of the call
+ * (call again after changing the codes is not supported: build a new graph).
+ * Owned by the graph, freed with it; a second call does nothing. Asynchronous
+ * on `stream`; BDG_ENOMEM if the copy does not fit the memory budget. */
+bdg_status bdg_graph_pack_codes(bdg_graph* g, void* stream);
+
 /* Save to / load from a file: header {magic "BDG1", version, N, bits, k, n_entry}
  * followed by ids, dists and entry ids (little-endian int32). Synchronous.
  * load borrows `codes` ([N][W], device) for later searches. */

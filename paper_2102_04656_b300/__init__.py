@@ -268,6 +268,17 @@ def propagate(g: Graph, rounds: int = 1, stream=None) -> Graph:
     return Graph(h.value, g.codes)
 
 
+def pack_codes(g: Graph, stream=None) -> Graph:
+    """Store the neighbours' codes next to the graph's rows for faster search
+    (see bdg_graph_pack_codes; N * k * bits / 8 bytes of device memory). Returns g."""
+    lb = lib()
+    if not getattr(lb, "_pack_sigs", False):
+        lb.bdg_graph_pack_codes.argtypes = [_c_void_p, _c_void_p]
+        lb._pack_sigs = True
+    _check(lb.bdg_graph_pack_codes(g.handle, _stream(stream)))
+    return g
+
+
 def prune(g: Graph, L: int, stream=None) -> Graph:
     """Occlusion pruning to at most L edges per point (see bdg_graph_prune): a new Graph."""
     lb = lib()

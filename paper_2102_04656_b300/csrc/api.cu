@@ -24,6 +24,7 @@ struct bdg_graph {
   int32_t* dists;         // [n][k]
   int32_t* entry;         // [n_entry]
   uint64_t* entry_codes;  // [n_entry][W] contiguous copy of the entry sample's codes
+  uint64_t* nbr_codes = nullptr;  // [n][k][W] neighbours' codes (bdg_graph_pack_codes), or null
 };
 
 namespace {
@@ -668,6 +669,7 @@ void bdg_graph_free(bdg_graph* g) {
   dfree(g->dists, (size_t)g->n * g->k * 4);
   dfree(g->entry, (size_t)g->n_entry * 4);
   dfree(g->entry_codes, (size_t)g->n_entry * g->W * 8);
+  if (g->nbr_codes) dfree(g->nbr_codes, (size_t)g->n * g->k * g->W * 8);
   delete g;
 }
 
@@ -780,6 +782,20 @@ bdg_status bdg_graph_prune(const bdg_graph* g, int32_t L, void* stream, bdg_grap
   return BDG_OK;
 }
 
+bdg_status bdg_graph_pack_codes(bdg_graph* g, void* stream) {
+  if (!g) return bdg_set_error(BDG_EINVAL, "pack_codes: graph is NULL");
+  if (g->nbr_codes) return BDG_OK;  // already packed
+  const size_t bytes = (size_t)g->n * g->k * g->W * 8;
+  BDG_TRY(dalloc((void**)&g->nbr_codes, bytes));
+  const bdg_status s = bdg_launch_gather_codes(g->codes, g->n, g->ids, g->n * (int64_t)g->k, g->W,
+                                               g->nbr_codes, (cudaStream_t)stream);
+  if (s != BDG_OK) {
+    dfree(g->nbr_codes, bytes);
+    g->nbr_codes = nullptr;
+  }
+  return s;
+}
+
 bdg_status bdg_graph_load(const char* path, const uint64_t* codes, bdg_graph** out) {
   if (!path || !codes || !out) return bdg_set_error(BDG_EINVAL, "load: null argument");
   *out = nullptr;
@@ -828,6 +844,7 @@ bdg_status bdg_search(const bdg_graph* g, const uint64_t* queries, int64_t nq, c
   if (nq > 0 && (!queries || !ef || !out_ids || !out_dist))
     return bdg_set_error(BDG_EINVAL, "search: null pointer");
   bdg_graph_view v{g->codes, g->ids, g->entry, g->entry_codes, g->n, g->k, g->bits, g->n_entry};
+  v.nbr_codes = g->nbr_codes;
   return bdg_launch_search(v, queries, nq, ef, ef_max, R, out_ids, out_dist, expansions,
                            (cudaStream_t)stream);
 }
@@ -913,6 +930,7 @@ bdg_status bdg_search_sharded(const bdg_graph* const* shards, int32_t S, const u
   for (int s = 0; s < S; ++s) {
     const bdg_graph* g = shards[s];
     bdg_graph_view v{g->codes, g->ids, g->entry, g->entry_codes, g->n, g->k, g->bits, g->n_entry};
+    v.nbr_codes = g->nbr_codes;
     BDG_TRY(bdg_launch_search(v, queries, nq, ef, ef_max, R, ids + (size_t)s * nq * R,
                               dist + (size_t)s * nq * R, nullptr, st));
   }

@@ -219,6 +219,7 @@ struct bdg_graph_view {
   const uint64_t* entry_codes;  // [n_entry][W] codes of the entry sample, contiguous
   int64_t n;
   int32_t deg, bits, n_entry;
+  const uint64_t* nbr_codes = nullptr;  // [n][deg][W] neighbours' codes next to the rows, or null
 };
 bdg_status bdg_launch_search(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
                              const int32_t* ef, int ef_max, int R, int32_t* out_ids,

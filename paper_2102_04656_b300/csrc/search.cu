@@ -60,7 +60,9 @@ __device__ __forceinline__ int hash_visit(int32_t* h, int32_t id) {
   return kFull;
 }
 
-template <int W, int CAPW>
+// PACKED: the neighbours' codes are read from g.nbr_codes (compiled apart so that
+// each layout gets its own register allocation)
+template <int W, int CAPW, bool PACKED>
 __global__ void __launch_bounds__(kWarps * 32)
 search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq,
               const int32_t* __restrict__ efs, int R, int32_t* __restrict__ out_ids,
@@ -149,13 +151,35 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
       for (int b0 = 0; b0 < g.deg; b0 += 32) {
         const int32_t nb = use_spec ? cur_spec_nb
                          : (b0 + lane < g.deg) ? g.ids[(int64_t)node * g.deg + b0 + lane] : -1;
+        // with the packed layout the neighbour's code sits next to the row: its
+        // address depends on the node only, so it is loaded together with the id
+        uint64_t pc[W];
+        if (PACKED && b0 + lane < g.deg) {
+          const uint64_t* src = g.nbr_codes + ((int64_t)node * g.deg + b0 + lane) * W;
+          if constexpr (W % 2 == 0) {
+#pragma unroll
+            for (int w = 0; w < W / 2; ++w) {
+              const ulonglong2 u = reinterpret_cast<const ulonglong2*>(src)[w];
+              pc[2 * w] = u.x;
+              pc[2 * w + 1] = u.y;
+            }
+          } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) pc[w] = src[w];
+          }
+        }
         uint64_t key = BDG_KEY_INF;
         bool acc = false;
         const int hv = (nb >= 0 && nb < g.n) ? hash_visit(sm.hash, nb) : kSeen;
         if (hv != kSeen) {
           uint32_t d = 0;
+          if constexpr (PACKED) {
 #pragma unroll
-          for (int w = 0; w < W; ++w) d += __popcll(y[w] ^ g.codes[(int64_t)nb * W + w]);
+            for (int w = 0; w < W; ++w) d += __popcll(y[w] ^ pc[w]);
+          } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) d += __popcll(y[w] ^ g.codes[(int64_t)nb * W + w]);
+          }
           key = bdg_key(d, (uint32_t)nb);
           const uint64_t worst = sm.key[size - 1];
           acc = (size < ef) || (key < worst);
@@ -246,8 +270,14 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
         __syncwarp();
       }
       // codes of the speculated next list: into L2 while the pool is scanned
-      if (spec_nb >= 0 && spec_nb < g.n)
-        asm volatile("prefetch.L2 [%0];" ::"l"(g.codes + (int64_t)spec_nb * W));
+      if constexpr (PACKED) {
+        if (spec_node >= 0 && lane < g.deg)
+          asm volatile("prefetch.L2 [%0];" ::"l"(g.nbr_codes +
+                                                 ((int64_t)spec_node * g.deg + lane) * W));
+      } else {
+        if (spec_nb >= 0 && spec_nb < g.n)
+          asm volatile("prefetch.L2 [%0];" ::"l"(g.codes + (int64_t)spec_nb * W));
+      }
     }
     const int keep = min(size, R);
     for (int r = lane; r < R; r += 32) {
@@ -260,26 +290,35 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
   }
 }
 
-template <int W, int CAPW>
-bdg_status launch_cap(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
+template <int W, int CAPW, bool PACKED>
+bdg_status launch_packed(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
                       const int32_t* ef, int R, int32_t* out_ids, int32_t* out_dist,
                       int32_t* expansions, cudaStream_t st) {
   const size_t smem = sizeof(PoolSmem<CAPW>) * kWarps;
-  BDG_CUDA_TRY(cudaFuncSetAttribute(search_kernel<W, CAPW>,
+  BDG_CUDA_TRY(cudaFuncSetAttribute(search_kernel<W, CAPW, PACKED>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  BDG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<W, CAPW>,
+  BDG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<W, CAPW, PACKED>,
                                                              kWarps * 32, smem));
   if (per_sm < 1) per_sm = 1;
   const int64_t need = (nq + kWarps - 1) / kWarps;
   const int64_t cap = (int64_t)bdg_num_sms() * per_sm;
   const int grid = (int)(need < cap ? need : cap);
   bdg_prof_scope prof("search", st);
-  search_kernel<W, CAPW><<<grid, kWarps * 32, smem, st>>>(g, queries, nq, ef, R, out_ids, out_dist,
+  search_kernel<W, CAPW, PACKED><<<grid, kWarps * 32, smem, st>>>(g, queries, nq, ef, R, out_ids, out_dist,
                                                        expansions);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   return BDG_OK;
+}
+
+template <int W, int CAPW>
+bdg_status launch_cap(const bdg_graph_view& g, const uint64_t* queries, int64_t nq,
+                      const int32_t* ef, int R, int32_t* out_ids, int32_t* out_dist,
+                      int32_t* expansions, cudaStream_t st) {
+  if (g.nbr_codes != nullptr)
+    return launch_packed<W, CAPW, true>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
+  return launch_packed<W, CAPW, false>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
 }
 
 template <int W>

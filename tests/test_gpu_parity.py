@@ -265,6 +265,31 @@ def test_search_bit_exact_with_expansions(bdg, efs, R):
     assert np.array_equal(ex.cpu().numpy(), cnt_o[:, 0])
 
 
+@pytest.mark.parametrize("bits,deg", [(256, 32), (512, 64), (64, 16)])
+def test_search_with_packed_codes_bit_exact(bdg, bits, deg):
+    """The packed layout (neighbour codes stored next to the rows) changes where
+    the search reads codes from, not what it finds: pools, results and expansion
+    counts equal the unpacked graph's and the oracle's, also through the
+    re-rank and the shard-merged search."""
+    spec = datagen.MixtureSpec(6000, 64, 40, bits, seed=bits + deg)
+    c = datagen.make_codes(spec)
+    g, entry = _build_exact(bdg, c.cuda(), deg)
+    q = datagen.make_codes(spec, n=300, seed_offset=2)
+    efs = np.array([16, 64, 100, 7] * 75, np.int32)
+    ef = torch.from_numpy(efs).cuda()
+    a_ids, a_d, a_ex = bdg.search(g, q.cuda(), ef, 40, ef_max=100, expansions=True)
+    bdg.pack_codes(g)
+    bdg.pack_codes(g)  # a second call does nothing
+    b_ids, b_d, b_ex = bdg.search(g, q.cuda(), ef, 40, ef_max=100, expansions=True)
+    assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d) and torch.equal(a_ex, b_ex)
+    ids_o, dist_o, cnt = oracle.search(_np(c), g.ids.cpu().numpy(), entry.cpu().numpy(), _np(q),
+                                       efs, 40)
+    assert np.array_equal(b_ids.cpu().numpy(), ids_o)
+    assert np.array_equal(b_ex.cpu().numpy(), cnt[:, 0])
+    s_ids, _ = bdg.search_sharded([g], q.cuda(), ef, 40, ef_max=100)
+    assert torch.equal(s_ids, b_ids)
+
+
 def test_search_on_loaded_adversarial_graphs(bdg, tmp_path):
     # line graph with thermometer codes + complete graph + disconnected pieces
     n = 64
