@@ -290,6 +290,35 @@ def test_search_with_packed_codes_bit_exact(bdg, bits, deg):
     assert torch.equal(s_ids, b_ids)
 
 
+def test_pack_codes_padded_rows_and_budget(bdg):
+    """Rows with padding (ids -1) search the same packed or not; a copy that does
+    not fit the memory budget is refused and leaves the graph searchable."""
+    n, bits, k = 3000, 256, 16
+    c = datagen.random_codes(n, bits, seed=61)
+    rng = np.random.default_rng(2)
+    home = rng.integers(0, 300, n)
+    routes = np.stack([home, (home + 1 + rng.integers(0, 299, n)) % 300], 1).astype(np.int32)
+    entry = torch.from_numpy(_entry(n, 32, 3)).cuda()
+    g = bdg.build_graph(c.cuda(), k, m=300, t=2, routes=torch.from_numpy(routes).cuda(),
+                        entry=entry)
+    assert (g.ids.cpu().numpy() < 0).any()  # tiny partitions leave padded rows
+    q = datagen.random_codes(100, bits, seed=62).cuda()
+    ef = torch.full((100,), 48, dtype=torch.int32).cuda()
+    a_ids, a_d = bdg.search(g, q, ef, 30, ef_max=48)
+    used = bdg.memory_in_use()
+    bdg.set_memory_budget(used + 1024)
+    try:
+        with pytest.raises(bdg.BDGError):
+            bdg.pack_codes(g)
+    finally:
+        bdg.set_memory_budget(0)
+    b_ids, _ = bdg.search(g, q, ef, 30, ef_max=48)
+    assert torch.equal(a_ids, b_ids)
+    bdg.pack_codes(g)
+    c_ids, c_d = bdg.search(g, q, ef, 30, ef_max=48)
+    assert torch.equal(a_ids, c_ids) and torch.equal(a_d, c_d)
+
+
 def test_search_on_loaded_adversarial_graphs(bdg, tmp_path):
     # line graph with thermometer codes + complete graph + disconnected pieces
     n = 64
