@@ -41,6 +41,15 @@ def _build_exact(bdg, codes_t, k, seed=5, kernel="auto"):
     return bdg.build_graph(codes_t, k, m=1, t=1, entry=entry, kernel=kernel), entry
 
 
+def _oracle_graph(cn, k, m, t, sample, bk_iters):
+    """The oracle's own graph for a build configuration (exact when m == 1)."""
+    if m == 1:
+        return oracle.knn_exact(cn, k)
+    cent, _, _ = oracle.bkmeans(cn, sample, m, bk_iters)
+    r, _ = oracle.route(cn, cent, t)
+    return oracle.knn_partitioned(cn, r, k)
+
+
 def _tc_ok(bits, k):
     return bits in (256, 512) and k <= 64
 
@@ -282,8 +291,9 @@ def test_search_with_packed_codes_bit_exact(bdg, bits, deg):
     bdg.pack_codes(g)  # a second call does nothing
     b_ids, b_d, b_ex = bdg.search(g, q.cuda(), ef, 40, ef_max=100, expansions=True)
     assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d) and torch.equal(a_ex, b_ex)
-    ids_o, dist_o, cnt = oracle.search(_np(c), g.ids.cpu().numpy(), entry.cpu().numpy(), _np(q),
-                                       efs, 40)
+    g_o, _ = oracle.knn_exact(_np(c), deg)
+    assert np.array_equal(g.ids.cpu().numpy(), g_o)
+    ids_o, dist_o, cnt = oracle.search(_np(c), g_o, entry.cpu().numpy(), _np(q), efs, 40)
     assert np.array_equal(b_ids.cpu().numpy(), ids_o)
     assert np.array_equal(b_ex.cpu().numpy(), cnt[:, 0])
     s_ids, _ = bdg.search_sharded([g], q.cuda(), ef, 40, ef_max=100)
@@ -534,7 +544,8 @@ def test_propagate_bit_exact(bdg, bits, n, m, t, k, rounds):
     base = g.ids.cpu().numpy()
     p = bdg.propagate(g, rounds)
     torch.cuda.synchronize()
-    ids_o = base
+    ids_o, _ = _oracle_graph(_np(c), k, m, t, sample, 4)
+    assert np.array_equal(base, ids_o)
     for _ in range(rounds):
         ids_o, dist_o = oracle.propagate(_np(c), ids_o)
     assert np.array_equal(p.ids.cpu().numpy(), ids_o)
@@ -547,7 +558,9 @@ def test_propagate_padded_rows(bdg):
     c = datagen.random_codes(40, 256, seed=77)
     g, _ = _build_exact(bdg, c.cuda(), 39)
     p = bdg.propagate(g, 1)
-    ids_o, dist_o = oracle.propagate(_np(c), g.ids.cpu().numpy())
+    g_o, _ = oracle.knn_exact(_np(c), 39)
+    assert np.array_equal(g.ids.cpu().numpy(), g_o)
+    ids_o, dist_o = oracle.propagate(_np(c), g_o)
     assert np.array_equal(p.ids.cpu().numpy(), ids_o)
     assert np.array_equal(p.dists.cpu().numpy(), dist_o)
 
@@ -565,7 +578,9 @@ def test_prune_bit_exact(bdg, bits, n, m, t, k, L):
                         bk_iters=4, entry=entry)
     base = g.ids.cpu().numpy()
     p = bdg.prune(g, L)
-    ids_o, dist_o = oracle.prune(_np(c), base, L)
+    g_o, _ = _oracle_graph(_np(c), k, m, t, sample, 4)
+    assert np.array_equal(base, g_o)
+    ids_o, dist_o = oracle.prune(_np(c), g_o, L)
     assert p.ids.shape == (n, L)
     assert np.array_equal(p.ids.cpu().numpy(), ids_o)
     assert np.array_equal(p.dists.cpu().numpy(), dist_o)
@@ -612,7 +627,10 @@ def test_prune_then_search_bit_exact(bdg):
     q = datagen.random_codes(64, 256, seed=92)
     ef = torch.full((64,), 64, dtype=torch.int32).cuda()
     ids, dist = bdg.search(p, q.cuda(), ef, 40, ef_max=64)
-    ids_o, dist_o, _ = oracle.search(_np(c), p.ids.cpu().numpy(), entry.cpu().numpy(), _np(q),
+    g_o, _ = oracle.knn_exact(_np(c), 32)
+    p_o, _ = oracle.prune(_np(c), g_o, 24)
+    assert np.array_equal(p.ids.cpu().numpy(), p_o)
+    ids_o, dist_o, _ = oracle.search(_np(c), p_o, entry.cpu().numpy(), _np(q),
                                      np.full(64, 64), 40)
     assert np.array_equal(ids.cpu().numpy(), ids_o)
     assert np.array_equal(dist.cpu().numpy(), dist_o)
@@ -636,6 +654,7 @@ def test_build_and_search_sharded_bit_exact(bdg, bits, n, S, m, t, k, kernel):
                                bk_sample=torch.from_numpy(sample).cuda(), bk_iters=6,
                                kernel=kernel)
     cent_o = oracle.bkmeans(cn, sample, m, 6)[0] if m > 1 else None
+    graphs_o = []
     for s in range(S):
         sl = cn[off[s]:off[s + 1]]
         if m > 1:
@@ -645,12 +664,12 @@ def test_build_and_search_sharded_bit_exact(bdg, bits, n, S, m, t, k, kernel):
             ids_o, dist_o = oracle.knn_exact(sl, k)
         assert np.array_equal(graphs[s].ids.cpu().numpy(), ids_o), s
         assert np.array_equal(graphs[s].dists.cpu().numpy(), dist_o), s
+        graphs_o.append(ids_o)
     q = datagen.make_codes(spec, n=300, seed_offset=2)
     efs = np.array([16, 64, 100, 7] * 75, np.int32)
     R = 40
     ids, dist = bdg.search_sharded(graphs, q.cuda(), torch.from_numpy(efs).cuda(), R, ef_max=100)
-    ids_o, dist_o = oracle.search_sharded(cn, [g.ids.cpu().numpy() for g in graphs],
-                                          list(entries), _np(q), efs, R)
+    ids_o, dist_o = oracle.search_sharded(cn, graphs_o, list(entries), _np(q), efs, R)
     assert np.array_equal(ids.cpu().numpy(), ids_o)
     assert np.array_equal(dist.cpu().numpy(), dist_o)
     for g in graphs:
