@@ -234,6 +234,46 @@ def test_partitioned_2m_512b_sampled_rows(bdg):
     assert np.array_equal(g.dists[torch.from_numpy(rows).cuda()].cpu().numpy(), dist_o)
 
 
+@pytest.mark.slow
+def test_search_10m_256b_properties(bdg):
+    """Full-size search workload (10M x 256-bit, degree 32, 100k queries, ef mixed
+    over {64, 128, 256, 512}, R = 100), in the configuration the bench times
+    (packed layout): properties that hold at any size, checked on sampled
+    queries — every returned distance is the Hamming distance the oracle
+    computes for that id, rows are strictly ascending by (d, id) with padding
+    last, at most min(ef, R) entries — and the packed layout gives the same
+    answers as the rows as built."""
+    w = datagen.WORKLOADS["search_10m_256b"]
+    spec = w["spec"]
+    codes = datagen.make_codes(spec, device="cuda")
+    qc = datagen.make_codes(spec, device="cuda", n=w["nq"], seed_offset=2)
+    n = spec.n
+    sample = torch.from_numpy(datagen.sample_ids(n, 64 * 1024, spec.seed + 3)).cuda()
+    entry = torch.from_numpy(datagen.sample_ids(n, 16384, spec.seed + 4).astype(np.int32)).cuda()
+    g = bdg.build_graph(codes, w["k"], m=1024, t=3, bk_sample=sample, bk_iters=8, entry=entry)
+    efs = datagen.ef_mix(w["nq"], w["efs"], spec.seed + 6)
+    ef = torch.from_numpy(efs).cuda()
+    R = 10 * w["topk"]
+    a_ids, a_d = bdg.search(g, qc, ef, R, ef_max=max(w["efs"]))
+    bdg.pack_codes(g)
+    b_ids, b_d = bdg.search(g, qc, ef, R, ef_max=max(w["efs"]))
+    assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d)
+    rows = datagen.sample_ids(w["nq"], 500, 17)
+    sel = torch.from_numpy(rows).cuda()
+    ids, d = b_ids[sel].cpu().numpy(), b_d[sel].cpu().numpy()
+    cn, qn = _np(codes.cpu()), _np(qc.cpu())
+    for r, qi in enumerate(rows):
+        valid = ids[r] >= 0
+        nv = int(valid.sum())
+        assert valid[:nv].all() and not valid[nv:].any()  # padding last
+        assert nv <= min(int(efs[qi]), R)
+        keys = [(int(dd), int(ii)) for dd, ii in zip(d[r][:nv], ids[r][:nv])]
+        assert keys == sorted(set(keys))  # strictly ascending, no repeats
+        for dd, ii in keys[:20]:
+            assert dd == oracle.hamming(qn[qi], cn[ii])
+        assert (d[r][nv:] == spec.bits + 1).all()
+
+
 @pytest.mark.parametrize("bits,k", [(512, 64), (256, 32), (128, 16), (1024, 100)])
 def test_knn_rows_bit_exact(bdg, bits, k):
     c = datagen.random_codes(6000, bits, seed=bits * 3)
