@@ -252,9 +252,9 @@ bdg_status bdg_search_sharded(const bdg_graph* const* shards, int32_t S, const u
  * 256-bit codes), so that bdg_search reads a node's neighbour codes as one
  * contiguous block whose address is known as soon as the node is chosen,
  * instead of one random code per neighbour after its id has arrived. Results
- * are unchanged. The copy reflects the graph and codes at the time of the call
- * (call again after changing the codes is not supported: build a new graph).
- * Owned by the graph, freed with it; a second call does nothing. Asynchronous
+ * are unchanged. The copy reflects the graph and the codes at the time of the
+ * call; a second call does nothing, so after changing the codes build a new
+ * graph. The copy is owned by the graph and freed with it. Asynchronous
  * on `stream`; BDG_ENOMEM if the copy does not fit the memory budget. */
 bdg_status bdg_graph_pack_codes(bdg_graph* g, void* stream);
 
