@@ -947,7 +947,10 @@ def run_ours(a):
     line = {
         "metric": METRIC, "value": _job_mpoints_per_s(n, ws, ms_max), "unit": "Mpoints/s",
         "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        # Hamming on the tensor cores: +-1 codes as FP8 E4M3, exact FP32 accumulation;
+        # on the popcount path: XOR + POPC over 64-bit words
+        "dtype": "e4m3" if kernel_used == "tc" else "u64",
         "data": "synthetic (seeded Gaussian-mixture features -> sign of random projections)",
         "config": {"workload": WORKLOAD, "N": n, "bits": spec.bits, "m": m, "t": t, "k": k,
                    "bk_sample": int(sample.numel()), "bk_iters": w["bk_iters"],
