@@ -392,17 +392,6 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           }
   #pragma unroll
           for (int half = 0; half < kSub / kHalf; ++half) {
-            // compaction, taken by the whole warp at once as soon as one row's list
-            // could not take another 16 values (lanes compacting one by one would
-            // serialise the warp)
-            if (__any_sync(0xffffffffu, cnt > kCap - kHalf)) {
-              cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kCap - kHalf);
-              if (cnt > kCap - kHalf) {  // cannot happen (need_k <= 65); kept as a guard:
-                overflow = true;         // the popcount kernel redoes this row
-                thr_w = 0u;
-                cnt = 0;
-              }
-            }
             // skip the 16 values when no row of the warp can take one of them: a value
             // can enter only if its distance is at most td, the bound's distance part
             {
@@ -416,6 +405,18 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
               const float m2 = fmaxf(fmaxf(f[8], f[9]), fmaxf(f[10], f[11]));
               const float m3 = fmaxf(fmaxf(f[12], f[13]), fmaxf(f[14], f[15]));
               if (!__any_sync(0xffffffffu, fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) >= lim)) continue;
+            }
+            // compaction, taken by the whole warp at once as soon as one row's list
+            // could not take another 16 values (lanes compacting one by one would
+            // serialise the warp); only needed before an append, so skipped groups
+            // do not pay for the check
+            if (__any_sync(0xffffffffu, cnt > kCap - kHalf)) {
+              cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kCap - kHalf);
+              if (cnt > kCap - kHalf) {  // cannot happen (need_k <= 65); kept as a guard:
+                overflow = true;         // the popcount kernel redoes this row
+                thr_w = 0u;
+                cnt = 0;
+              }
             }
             // branch-free append: every value is written at the running slot, only
             // words below the threshold advance it
