@@ -360,6 +360,13 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       // by 2^21 (mod 2^32) leaves d << 21: the word is one FFMA and one IMAD
       const float hmagic = 0.5f * (float)bits + 8388608.0f;
       uint32_t* crow = cand + r;
+      // a value can enter only if its distance is at most the threshold's distance
+      // part td, i.e. if its dot product is at least bits - 2 td: the skip test's
+      // limit, recomputed only when the threshold changes
+      auto lim_of = [bits](uint32_t t) {
+        return t ? (float)(bits - 2 * (int)((t - 1u) >> kPosBits)) : 3.0e38f;
+      };
+      float lim = lim_of(thr_w);
       for (int j = 0; j < ntiles; ++j) {
         const uint32_t gg = g + j, b = gg % kAcc;
         bool ok = !*s_abort && tc05::mbar_wait(&tfull[b], (gg / kAcc) & 1, kPolls);
@@ -395,8 +402,6 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             // skip the 16 values when no row of the warp can take one of them: a value
             // can enter only if its distance is at most td, the bound's distance part
             {
-              const int tdh = (int)((thr_w - 1u) >> kPosBits);
-              const float lim = thr_w ? (float)(bits - 2 * tdh) : 3.0e38f;
               float f[kHalf];
   #pragma unroll
               for (int c2 = 0; c2 < kHalf; ++c2) f[c2] = __uint_as_float(v[half * kHalf + c2]);
@@ -417,6 +422,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
                 thr_w = 0u;
                 cnt = 0;
               }
+              lim = lim_of(thr_w);
             }
             // branch-free append: every value is written at the running slot, only
             // words below the threshold advance it
