@@ -94,7 +94,9 @@ bdg_status bdg_routes_coarse(int32_t* routes, int64_t n, int32_t t, int32_t m, i
  * members' bits, keeping the previous bit on a tie and the previous centre
  * when the cluster is empty. centroids: out [m][W]. loss: optional out int64
  * [iters + 1], the objective after each assign step (NULL to skip).
- * Requires m <= S. */
+ * Requires m <= S. Sample ids must lie in [0, n); the kernels cannot check
+ * device-side ids before launch, so an id outside that range is read as the
+ * all-zero code (never outside `codes`) and the result is then unspecified. */
 bdg_status bdg_bkmeans(const uint64_t* codes, int64_t n, int32_t bits, const int64_t* sample,
                        int64_t S, int32_t m, int32_t iters, uint64_t* centroids, int64_t* loss,
                        void* stream);
@@ -107,19 +109,24 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
                         int64_t nrows, int32_t k, int32_t* out_ids, int32_t* out_dist,
                         void* stream);
 
-/* bdg_bkmeans without any device allocation (the paper has no counterpart: it
- * exists for callers that cannot allocate device memory -- code running while a
- * CUDA graph is captured, processes whose device memory is owned by an outside
- * manager, loops that must never reach the allocator). Same arguments and
- * results as bdg_bkmeans. Its scratch is one fixed 16 MiB array inside the
- * library, reserved on every GPU that loads the library until the process
- * exits; calls needing more (bdg_bkmeans_scratch_bytes > 16 MiB, e.g. S = 16384,
- * m = 256, 512 bits needs about 1.7 MiB) fail with BDG_EINVAL before any work.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. All calls share the one array: calls that may overlap on the GPU
- * (different streams, or different host threads) race and must be ordered by
- * the caller. No cudaMalloc/cudaFree or allocating library routine is called. */
+/* bdg_bkmeans without any device allocation (the paper has no counterpart).
+ * It is for callers that must not allocate device memory: processes whose
+ * device memory belongs to an outside manager (a framework's pool, a fixed
+ * arena set up at start-up), and loops that must never reach the allocator
+ * because an allocation there can synchronise the device or fail under memory
+ * pressure. Same arguments and results as bdg_bkmeans. Its scratch is one fixed
+ * 16 MiB array inside the library, reserved on every GPU that loads the
+ * library until the process exits; calls needing more
+ * (bdg_bkmeans_scratch_bytes > 16 MiB; S = 16384, m = 256, 512 bits needs about
+ * 1.7 MiB) fail with BDG_EINVAL before any work. The first call on a device
+ * looks up the array's device address (once per device, with that device
+ * current) and caches it for the life of the process: make that first call
+ * before any stream capture, and do not use the entry point after
+ * cudaDeviceReset (the cached address then no longer names the array). All
+ * calls share the one array, which keeps the last call's contents: calls that
+ * may overlap on the GPU (different streams, or different host threads) race
+ * and must be ordered by the caller. No cudaMalloc/cudaFree or allocating
+ * library routine is called. */
 bdg_status bdg_bkmeans_noalloc(const uint64_t* codes, int64_t n, int32_t bits,
                                const int64_t* sample, int64_t S, int32_t m, int32_t iters,
                                uint64_t* centroids, int64_t* loss, void* stream);
@@ -131,7 +138,7 @@ typedef struct bdg_partitions {
   int32_t m;                  /* number of partitions (1 = exact brute force) */
   int32_t t;                  /* partitions probed per point, home included; 1 <= t <= m, t <= 16 */
   const uint64_t* centroids;  /* [m][W] binary centres, or NULL: run Bk-means first */
-  const int64_t* bk_sample;   /* [bk_sample_size] point ids of the Bk-means down-sample */
+  const int64_t* bk_sample;   /* [bk_sample_size] point ids in [0, N) of the Bk-means down-sample */
   int64_t bk_sample_size;     /* >= m when centroids == NULL */
   int32_t bk_iters;           /* Bk-means iterations (the paper uses fewer than 10) */
   const int32_t* routes;      /* [N][t] precomputed routes (slot 0 = home), or NULL; a row

@@ -126,6 +126,13 @@ void bdg_note_launch(int n) { g_launches.fetch_add(n); }
 
 bdg_prof_scope::bdg_prof_scope(const char* name, cudaStream_t s) : slot(-1), st(s) {
   if (!g_prof_on.load()) return;
+  // events recorded into a stream capture would become graph nodes whose
+  // timings are never valid: a capturing stream is not profiled
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   for (size_t i = 0; i < g_prof.size(); ++i)
     if (g_prof[i].name == name) slot = (int)i;

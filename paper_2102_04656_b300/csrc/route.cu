@@ -95,12 +95,17 @@ bdg_status route_w(const uint64_t* codes, int64_t n, const uint64_t* cent, int m
   return BDG_OK;
 }
 
-__global__ void gather_rows(const uint64_t* __restrict__ codes, const int64_t* __restrict__ ids,
-                            int64_t S, int W, uint64_t* __restrict__ out) {
+// Sample codes codes[ids[s]]; an id outside [0, N) reads as the all-zero code
+// (the argument check cannot see device-side ids, so the kernel never reads
+// outside the codes).
+__global__ void gather_rows(const uint64_t* __restrict__ codes, int64_t N,
+                            const int64_t* __restrict__ ids, int64_t S, int W,
+                            uint64_t* __restrict__ out) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= S * W) return;
   const int64_t s = x / W;
-  out[x] = codes[ids[s] * W + (x - s * W)];
+  const int64_t id = ids[s];
+  out[x] = (id >= 0 && id < N) ? codes[id * W + (x - s * W)] : 0ull;
 }
 
 // Per-bit member counts: one warp per sample point, lanes over bits.
@@ -228,7 +233,6 @@ bdg_status bk_assign_w(const uint64_t* scodes, int64_t S, const uint64_t* cent, 
 bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int64_t* sample,
                               int64_t S, int m, int iters, uint64_t* cent, int64_t* loss,
                               void* scratch, size_t scratch_bytes, cudaStream_t st) {
-  (void)N;
   if (scratch_bytes < bdg_bkmeans_scratch_bytes(S, m, W))
     return bdg_set_error(BDG_EINVAL, "bkmeans scratch too small");
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -238,7 +242,7 @@ bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int
   int32_t* adist = (int32_t*)p;    p += al(S * 4);
   int32_t* ones = (int32_t*)p;     p += al((size_t)m * 64 * W * 4);
   int32_t* count = (int32_t*)p;
-  gather_rows<<<bdg_cdiv(S * W, 256), 256, 0, st>>>(codes, sample, S, W, scodes);
+  gather_rows<<<bdg_cdiv(S * W, 256), 256, 0, st>>>(codes, N, sample, S, W, scodes);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   // init: c_j = code of sample[j]
@@ -265,12 +269,13 @@ bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int
 }
 
 // ---------------------------------------------------------------------------
-// Allocation-free Bk-means. Some callers cannot call cudaMalloc at all: code
-// that runs while a CUDA graph is being captured, processes whose device
-// memory is owned by an external manager, or latency-critical loops that must
-// never reach the allocator. For them the Bk-means scratch lives in one
-// file-scope device array of fixed size, reserved on every GPU that loads this
-// library for as long as the process lives.
+// Allocation-free Bk-means. Some callers cannot call cudaMalloc at all:
+// processes whose device memory is owned by an external manager, or
+// latency-critical loops that must never reach the allocator (an allocation
+// can synchronise the device or fail under memory pressure). For them the
+// Bk-means scratch lives in one file-scope device array of fixed size,
+// reserved on every GPU that loads this library for as long as the process
+// lives.
 #define BDG_BK_NOALLOC_BYTES (16u << 20)
 static __device__ __align__(256) unsigned char g_bk_noalloc_scratch[BDG_BK_NOALLOC_BYTES];
 
@@ -282,7 +287,9 @@ void* g_noalloc_ptr[64] = {nullptr};
 
 // Device address of the static scratch for the current device. In host code
 // the array's name is only a host-side handle, never a device address, so it
-// is looked up once per device (with that device current) and cached.
+// is looked up once per device (with that device current) and cached for the
+// life of the process; after cudaDeviceReset the cached address is stale, which
+// the header states.
 bdg_status noalloc_scratch(void** out) {
   int dev = 0;
   BDG_CUDA_TRY(cudaGetDevice(&dev));

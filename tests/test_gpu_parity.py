@@ -160,6 +160,26 @@ def test_bkmeans_bit_exact(bdg, bits, n, m, S, iters):
     assert np.array_equal(loss.cpu().numpy(), loss_o)
 
 
+def test_bkmeans_sample_id_out_of_range_reads_zero_code(bdg):
+    """A sample id outside [0, n) cannot be checked before launch; the call
+    still returns cleanly and reads that id as the all-zero code: the centres
+    equal those of the same run on the codes with a zero row appended and the
+    bad ids pointing at it."""
+    n, bits, m, S, iters = 3000, 256, 12, 600, 4
+    c = datagen.make_codes(datagen.MixtureSpec(n, 64, 24, bits, seed=31)).cuda()
+    sample = datagen.sample_ids(n, S, seed=32)
+    bad = sample.copy()
+    bad[[5, 77, 301]] = [-3, n, 1 << 40]
+    cent, loss = bdg.bkmeans(c, torch.from_numpy(bad).cuda(), m, iters)
+    torch.cuda.synchronize()
+    c0 = torch.cat([c, torch.zeros(1, c.shape[1], dtype=c.dtype, device=c.device)])
+    fixed = sample.copy()
+    fixed[[5, 77, 301]] = n
+    cent_r, loss_r = bdg.bkmeans(c0, torch.from_numpy(fixed).cuda(), m, iters)
+    assert torch.equal(cent, cent_r)
+    assert torch.equal(loss, loss_r)
+
+
 @pytest.mark.parametrize("bits,t", [(256, 5), (512, 1), (128, 16), (64, 3)])
 def test_route_bit_exact(bdg, bits, t):
     c = datagen.random_codes(4001, bits, seed=bits)
@@ -207,31 +227,88 @@ def test_partitioned_with_given_routes_and_empty_home(bdg, kernel):
     assert np.array_equal(g.dists.cpu().numpy(), dist_o)
 
 
+_POP8 = None
+
+
+def _hamming_rows(codes, ids):
+    """Hamming distances between each row's point and its listed ids (on the
+    device; test-side arithmetic, a byte-table popcount): int32 [n, k]."""
+    global _POP8
+    if _POP8 is None:
+        _POP8 = torch.tensor([bin(b).count("1") for b in range(256)], dtype=torch.int32,
+                             device=codes.device)
+    n, k = ids.shape
+    out = torch.empty(n, k, dtype=torch.int32, device=codes.device)
+    cb = codes.view(torch.uint8).reshape(codes.shape[0], -1)
+    for s in range(0, n, 16384):
+        e = min(n, s + 16384)
+        nb = cb[ids[s:e].long().clamp(min=0)]                 # [b, k, bytes]
+        x = torch.bitwise_xor(nb, cb[s:e, None, :])
+        out[s:e] = _POP8[x.long()].sum(2).to(torch.int32)
+    return out
+
+
+def _check_rows_valid(codes, ids, dists, routes, home):
+    """Properties every row of a partitioned graph has, at any size: ids in
+    range and never the point itself, no repeats, each neighbour's home among
+    the point's probed partitions, distances equal to the Hamming distances
+    recomputed from the codes, rows ascending by (d, id)."""
+    n, k = ids.shape
+    me = torch.arange(n, device=ids.device, dtype=torch.int32)[:, None]
+    assert bool(((ids >= 0) & (ids < n)).all()), "padding or out-of-range id"
+    assert not bool((ids == me).any()), "self pair"
+    srt = torch.sort(ids, dim=1).values
+    assert not bool((srt[:, 1:] == srt[:, :-1]).any()), "repeated id"
+    nh = home[ids.long()]                                      # [n, k]
+    assert bool((nh[:, :, None] == routes[:, None, :]).any(2).all()), "id outside C(i)"
+    assert torch.equal(dists, _hamming_rows(codes, ids)), "distance != Hamming"
+    d0, d1 = dists[:, :-1], dists[:, 1:]
+    i0, i1 = ids[:, :-1], ids[:, 1:]
+    assert bool(((d0 < d1) | ((d0 == d1) & (i0 < i1))).all()), "row not ascending by (d, id)"
+
+
 @pytest.mark.slow
 def test_partitioned_2m_512b_sampled_rows(bdg):
     """Full-size partitioned workload (N = 2M, 512-bit, m = 256, t = 5, k = 64), in
-    the configuration the bench times: centres and routes compared in full, graph
-    rows on a sample the oracle computes one by one."""
+    the configuration the bench times (a build plan replayed from its CUDA graph,
+    kernel chosen by the autotuner): centres and routes compared in full; every
+    one of the 2M rows checked for the properties of a partitioned graph; 10,000
+    rows (among them members of the largest partition, the first and the last
+    point) compared with the oracle, which computes them one by one."""
     w = datagen.WORKLOADS["partitioned_2m_512b"]
     spec = w["spec"]
     c_dev = datagen.make_codes(spec, device="cuda")
     c = _np(c_dev)
     n, m, t, k = spec.n, w["m"], w["t"], w["k"]
     sample = datagen.sample_ids(n, 64 * m, spec.seed + 3)
+    sample_t = torch.from_numpy(sample).cuda()
     entry = torch.from_numpy(_entry(n, 256, spec.seed + 4)).cuda()
-    cent, _ = bdg.bkmeans(c_dev, torch.from_numpy(sample).cuda(), m, w["bk_iters"])
-    g = bdg.build_graph(c_dev, k, m=m, t=t, bk_sample=torch.from_numpy(sample).cuda(),
-                        bk_iters=w["bk_iters"], entry=entry)
+    cent, _ = bdg.bkmeans(c_dev, sample_t, m, w["bk_iters"])
+    plan = bdg.BuildPlan(c_dev, k, m=m, t=t, bk_sample=sample_t, bk_iters=w["bk_iters"],
+                         entry=entry, kernel="auto")
+    plan.run()
+    plan.run()  # a replay, as timed
+    torch.cuda.synchronize()
+    g = plan.graph
     cent_o, _, _ = oracle.bkmeans(c, sample, m, w["bk_iters"])
     assert np.array_equal(_np(cent), cent_o)
     r_gpu, _ = bdg.route(c_dev, cent, t)
     r_o, _ = oracle.route(c, cent_o, t)
     assert np.array_equal(r_gpu.cpu().numpy(), r_o)
-    rows = datagen.sample_ids(n, 300, 99)
-    rows = np.concatenate([rows, [0, n - 1]])
+    home = r_gpu[:, 0].contiguous()
+    _check_rows_valid(c_dev, g.ids, g.dists, r_gpu, home)
+    big = int(torch.bincount(home.long(), minlength=m).argmax())
+    members = torch.nonzero(home == big).flatten().cpu().numpy()
+    rng = np.random.default_rng(99)
+    rows = np.concatenate([datagen.sample_ids(n, 8000, 99),
+                           rng.choice(members, size=min(2000, members.size), replace=False),
+                           [0, n - 1]])
+    rows = np.unique(rows)
     ids_o, dist_o = oracle.knn_partitioned(c, r_o, k, rows)
-    assert np.array_equal(g.ids[torch.from_numpy(rows).cuda()].cpu().numpy(), ids_o)
-    assert np.array_equal(g.dists[torch.from_numpy(rows).cuda()].cpu().numpy(), dist_o)
+    rt = torch.from_numpy(rows).cuda()
+    assert np.array_equal(g.ids[rt].cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists[rt].cpu().numpy(), dist_o)
+    plan.free()
 
 
 @pytest.mark.slow

@@ -1,8 +1,9 @@
 """The allocation-free Bk-means entry point (bdg_bkmeans_noalloc) gives the same
 centres and objective as bdg_bkmeans, on two calls in a row through the C ABI.
 
-It exists for callers that cannot allocate device memory (graph capture,
-externally managed memory, allocator-free loops); its scratch is a fixed array
+It exists for callers that cannot allocate device memory (device memory owned
+by an outside manager, loops that must never reach the allocator); its scratch
+is a fixed array
 inside the library, so the second call also checks that nothing left over from
 the first call changes the result. This file is collected last on purpose."""
 import ctypes
