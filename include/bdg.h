@@ -87,6 +87,15 @@ bdg_status bdg_route(const uint64_t* codes, int64_t n, int32_t bits, const uint6
 bdg_status bdg_routes_coarse(int32_t* routes, int64_t n, int32_t t, int32_t m, int64_t coarse_num,
                              int32_t* home_count, void* stream);
 
+/* A distance-gap number of probes (not in the paper: the non-learned baseline
+ * of the learned router's variable number of probes, next to coarse_num). In
+ * place on t-nearest-centre routes [n][t] (device) and their distances rdist
+ * [n][t] (from bdg_route): slot s >= 1 becomes -1 when rdist[s] - rdist[0] >
+ * delta, i.e. every centre at most delta farther than the home's stays probed.
+ * Requires 1 <= t <= 16; BDG_EINVAL otherwise. */
+bdg_status bdg_routes_gap(int32_t* routes, const int32_t* rdist, int64_t n, int32_t t,
+                          int32_t delta, void* stream);
+
 /* Bk-means of Section 3.2 (objective Eq. 1, update Eq. 2) on the down-sample
  * codes[sample[0..S)]: centres start as the codes of sample[0..m); each of
  * `iters` iterations assigns every sample point to its nearest centre by
@@ -153,6 +162,11 @@ typedef struct bdg_partitions {
                                  library's routes are cut by the coarse_num rule of
                                  Section 3.2 (see bdg_routes_coarse), t being the most a
                                  point may probe; needs routes == NULL */
+  int32_t class_kernel[3];    /* Reduce-1 variant per partition size class (class 0:
+                                 |H_p| >= 4096, class 1: 512 <= |H_p| < 4096, class 2:
+                                 |H_p| < 512): 0 = follow `kernel`, 1 = popcount (64-visitor
+                                 sub-tiles), 2 = tensor (128 x 128 tiles), 3 = popcount with
+                                 32-visitor sub-tiles. Results are identical for any choice */
 } bdg_partitions;
 
 typedef struct bdg_graph bdg_graph; /* opaque; owns ids/dists/entry, borrows codes */
@@ -174,9 +188,12 @@ bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32
  * bucketing, the Reduce-1 kernel, the merge) captured once into a CUDA graph
  * over scratch and graph storage allocated once, then replayed by
  * bdg_build_plan_run (one graph launch per build). With partitions->kernel = 0
- * an autotuner times the popcount and the tensor-core Reduce-1 kernels on this
- * very workload and keeps the faster; the choice is cached per (device, bits,
- * k, N, m, t) in the file named by $BDG_AUTOTUNE_CACHE (default
+ * and no class_kernel set, an autotuner runs every Reduce-1 variant (popcount
+ * with 64- and with 32-visitor sub-tiles, tensor cores with 128 x 128 tiles) on
+ * this very workload, times each partition size class (the persistent kernels
+ * take one class's work items per launch), and keeps the fastest variant per
+ * class; the choice is cached per (device, bits, k, N, m, t) in the file named
+ * by $BDG_AUTOTUNE_CACHE (default
  * ~/.cache/bdg_autotune.txt; an unwritable cache is ignored). Every array the
  * partitions reference and the codes must stay alive and are re-read at each
  * run (their contents may change between runs; their sizes may not). Creating
@@ -195,6 +212,13 @@ bdg_status bdg_build_plan_kernel_ms(bdg_build_plan* plan, float* ms);
  * not measured). */
 bdg_status bdg_build_plan_info(const bdg_build_plan* plan, const bdg_graph** graph,
                                int32_t* kernel, float* ms_popc, float* ms_tc);
+/* The plan's Reduce-1 variant per partition size class (variant[3]: 1 popcount,
+ * 2 tensor, 3 popcount with 32-visitor sub-tiles), the classes' size bounds
+ * (size_lo[3] <= |H_p| < size_hi[3]) and, when the autotuner ran, the measured
+ * Reduce-1 ms of every variant on every class (ms[3 variants][3 classes],
+ * variant v at row v - 1; -1 = not measured). Any output pointer may be NULL. */
+bdg_status bdg_build_plan_classes(const bdg_build_plan* plan, int32_t* variant, int32_t* size_lo,
+                                  int32_t* size_hi, float* ms);
 void bdg_build_plan_free(bdg_build_plan* plan);
 
 /* Device pointers to the graph rows: ids/dists [N][k] int32, row i sorted by
@@ -380,6 +404,42 @@ bdg_status bdg_router_train_step(bdg_router* r, const void* x, const uint64_t* c
  * (when code_bits > 0), home: [N], routes: [N][P], P <= 17. */
 bdg_status bdg_router_route(bdg_router* r, const void* x, const uint64_t* codes, int64_t N,
                             const int32_t* home, int32_t P, int32_t* routes, void* stream);
+
+/* Shortlist head. The last layer evaluated only on a shortlist of Q candidate
+ * partitions per point, cand[i][0..Q) (device int32; in this library the Q
+ * nearest centres of the Map step of Section 3.2 from bdg_route, so cand[i][0]
+ * is the home; -1 = no candidate, never the home slot):
+ *   z_ij = [h2_i | s_i] . W3[cand_ij] + b3[cand_ij]   (-inf where cand_ij < 0)
+ *   loss = -(1/B) sum_i sum_j q_ij log softmax(z_i)_j,
+ *   q_ij = #{labels of i equal to cand_ij} / #{labels of i found in cand_i}
+ * (a row none of whose labels is shortlisted contributes neither loss nor
+ * gradient). The probe choice keeps the home and adds, by (-z, partition), the
+ * other shortlisted partitions whose logit is at least (largest shortlisted
+ * logit - theta), computed in FP32, at most pmax - 1 of them: a variable number
+ * of probed partitions per point, the learned counterpart of the coarse_num
+ * rule of Section 3.2. With the prior weights a (c_p - 1/2) in W3's code
+ * columns (zero elsewhere, b3 = 0) the logits are a (bits/2 - d(y, c_p)) and the
+ * rule keeps exactly the centres within theta / a of the nearest one.
+ * Q <= 16; h2 + code_bits <= 2048. */
+/* logits: [B][Q] FP32 (device). B <= max_batch. */
+bdg_status bdg_router_forward_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
+                                        const int32_t* cand, int32_t Q, int32_t B,
+                                        float* logits, void* stream);
+/* One training step of the shortlist head (forward, loss, backward through all
+ * layers, Adam when apply_update != 0). labels: [B][kt] int32 partition ids
+ * (the homes of the point's exact neighbours; -1 ignored). B % 8 == 0. */
+bdg_status bdg_router_train_step_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
+                                           const int32_t* cand, int32_t Q, const int32_t* labels,
+                                           int32_t kt, int32_t B, float lr, int32_t apply_update,
+                                           void* stream);
+/* routes: [N][pmax] int32 (device): the probe choice above, -1 after the last
+ * kept partition; logits: [N][Q] FP32 or NULL. 1 <= pmax <= Q, theta >= 0.
+ * Runs in chunks of up to 2^18 points with a stream-ordered workspace of
+ * chunk x (h1 + h2 + code_bits) BF16 values; BDG_ENOMEM if it cannot be had. */
+bdg_status bdg_router_route_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
+                                      const int32_t* cand, int32_t Q, int64_t N, float theta,
+                                      int32_t pmax, int32_t* routes, float* logits,
+                                      void* stream);
 
 /* The router's tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulation):
  *   C[M][N] = epilogue(A[M][K] * B[N][K]^T), A and B row-major with K contiguous;

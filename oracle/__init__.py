@@ -127,6 +127,19 @@ def routes_coarse(routes, m: int, coarse_num: int):
     return out, cnt
 
 
+def routes_gap(routes, rdist, delta: int):
+    """The distance-gap rule (not in the paper): t-nearest-centre routes [n, t]
+    with every slot s >= 1 whose centre lies more than delta farther than the
+    home's centre set to -1."""
+    rt = np.ascontiguousarray(routes, np.int32)
+    rd = np.ascontiguousarray(rdist, np.int32)
+    n, t = rt.shape
+    out = np.empty_like(rt)
+    _load().or_routes_gap(_p(rt), _p(rd), ctypes.c_int64(n), ctypes.c_int32(t),
+                          ctypes.c_int32(delta), _p(out))
+    return out
+
+
 def knn_partitioned(codes, routes, k: int, qidx=None):
     """Divide-and-conquer graph rows of points qidx given routes [n, t] (slot 0 =
     home; a slot holding -1 probes nothing)."""

@@ -15,7 +15,7 @@
  *   - rows with fewer than k candidates are padded with (d = bits + 1, id = -1).
  *
  * Parity status per function (pins live in tests/test_oracle_*.py):
- *   or_hamming, or_knn_exact, or_bkmeans, or_route, or_routes_coarse,
+ *   or_hamming, or_knn_exact, or_bkmeans, or_route, or_routes_coarse, or_routes_gap,
  *   or_knn_partitioned, or_search, or_rerank_f32/_f64, or_propagate, or_prune
  *   -- pinned (brute force,
  *   invariants, closed forms, hand-worked fixtures).
@@ -181,6 +181,20 @@ void or_routes_coarse(const int32_t* routes, int64_t n, int32_t t, int32_t m,
       if (keep && p >= 0 && p < m) held += home_count[p];
     }
   }
+}
+
+/* Distance-gap rule (not in the paper; a non-learned variable number of probes
+ * next to coarse_num): keep the home (slot 0) and every further slot s whose
+ * centre is at most delta farther from the point than the home's centre,
+ * rdist[s] - rdist[0] <= delta; the other slots become -1. routes, rdist:
+ * [n][t] t-nearest-centre routes and their distances. */
+void or_routes_gap(const int32_t* routes, const int32_t* rdist, int64_t n, int32_t t,
+                   int32_t delta, int32_t* out) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t s = 0; s < t; ++s) {
+      const int keep = (s == 0) || (rdist[i * t + s] - rdist[i * t] <= delta);
+      out[i * t + s] = keep ? routes[i * t + s] : -1;
+    }
 }
 
 /* Single-pass divide-and-conquer graph of Section 3.2, as a plain definition:

@@ -158,3 +158,106 @@ def neighbour_partition_targets(knn_ids, home, m):
     knn_ids = np.asarray(knn_ids)
     labels = np.where(knn_ids >= 0, np.asarray(home)[np.maximum(knn_ids, 0)], -1)
     return label_targets(labels, m)
+
+
+# ---------------------------------------------------------------------------
+# Shortlist head. The router's last layer is evaluated only on a shortlist of
+# candidate partitions per point: cand[i] = the Q nearest centres of point i in
+# the order of Section 3.2's Map step (cand[i, 0] = its home), -1 = no
+# candidate. Same parameters as above; only the softmax runs over the shortlist:
+#
+#   z_ij = [h2_i | s_i] . W3[cand_ij] + b3[cand_ij]      (j < Q, -inf where cand_ij < 0)
+#   loss = -(1/B) sum_i sum_j q_ij log softmax(z_i)_j
+#   q_ij = #{labels of i equal to cand_ij} / #{labels of i found in cand_i}
+#
+# A row none of whose labels is shortlisted has no target (no loss, no gradient).
+# The logit gradient dz stays at full precision (the CUDA path keeps it in
+# FP32); dh2 is rounded where the pipeline stores it (bf16), like the dense path.
+
+def shortlist_forward(params, x, cand, bf16=True, s=None):
+    """Shortlisted logits z [B, Q] (-inf for cand < 0) and the cache."""
+    W1, W2, W3 = (_q(params[k], bf16) for k in ("W1", "W2", "W3"))
+    b1, b2, b3 = (np.asarray(params[k], np.float64) for k in ("b1", "b2", "b3"))
+    x = _q(x, bf16)
+    h1 = _q(np.maximum(x @ W1.T + b1, 0.0), bf16)
+    h2 = _q(np.maximum(h1 @ W2.T + b2, 0.0), bf16)
+    u = h2 if s is None else np.concatenate([h2, np.asarray(s, np.float64)], axis=1)
+    cand = np.asarray(cand)
+    B, Q = cand.shape
+    z = np.full((B, Q), -np.inf)
+    for i in range(B):
+        for j in range(Q):
+            p = int(cand[i, j])
+            if p >= 0:
+                z[i, j] = u[i] @ W3[p] + b3[p]
+    return z, dict(x=x, h1=h1, h2=h2, u=u, W1=W1, W2=W2, W3=W3)
+
+
+def shortlist_targets(labels, cand):
+    """q [B, Q]: the share of row i's labels naming cand[i, j], among its labels
+    that name any shortlisted partition (zero row if none does)."""
+    labels = np.asarray(labels)
+    cand = np.asarray(cand)
+    B, Q = cand.shape
+    q = np.zeros((B, Q), np.float64)
+    for i in range(B):
+        hits = [j for lab in labels[i] for j in range(Q)
+                if cand[i, j] >= 0 and int(lab) == int(cand[i, j])]
+        for j in hits:
+            q[i, j] += 1.0 / len(hits)
+    return q
+
+
+def shortlist_loss_and_grads(params, x, cand, q, bf16=True, s=None):
+    """Mean soft-target cross-entropy over the shortlist and its gradients."""
+    z, c = shortlist_forward(params, x, cand, bf16, s)
+    cand = np.asarray(cand)
+    B, Q = z.shape
+    p = softmax(z)  # exp(-inf) = 0: a missing candidate gets probability 0
+    q = np.asarray(q, np.float64)
+    has = (q.sum(axis=1) > 0)[:, None]
+    logp = np.log(np.maximum(p, 1e-300))
+    loss = float(-np.where(q > 0, q * logp, 0.0).sum() / B)
+    dz = (p - q) / B * has
+    g = {"W3": np.zeros_like(c["W3"]), "b3": np.zeros(c["W3"].shape[0])}
+    h2n = c["h2"].shape[1]
+    dh2 = np.zeros_like(c["h2"])
+    for i in range(B):
+        for j in range(Q):
+            pj = int(cand[i, j])
+            if pj < 0:
+                continue
+            g["W3"][pj] += dz[i, j] * c["u"][i]
+            g["b3"][pj] += dz[i, j]
+            dh2[i] += dz[i, j] * c["W3"][pj, :h2n]
+    dh2 = dh2 * (c["h2"] > 0)
+    dh2q = _q(dh2, bf16)
+    g["W2"] = dh2q.T @ c["h1"]
+    g["b2"] = dh2.sum(0)
+    dh1 = (dh2q @ c["W2"]) * (c["h1"] > 0)
+    dh1q = _q(dh1, bf16)
+    g["W1"] = dh1q.T @ c["x"]
+    g["b1"] = dh1.sum(0)
+    return loss, g, z
+
+
+def shortlist_select(z, cand, theta, pmax):
+    """Partitions probed per point (int32 [B, pmax], -1 = none): slot 0 is
+    cand[i, 0] (the home, always probed); then the other shortlisted partitions
+    whose logit is within theta of the row's largest shortlisted logit, by
+    (-z, partition) ascending, at most pmax - 1 of them. The comparison is made
+    in the precision of z (float32 logits give float32 decisions)."""
+    z = np.asarray(z)
+    cand = np.asarray(cand)
+    B, Q = z.shape
+    out = np.full((B, pmax), -1, np.int32)
+    for i in range(B):
+        out[i, 0] = cand[i, 0]
+        valid = [j for j in range(Q) if cand[i, j] >= 0]
+        zmax = max(z[i, j] for j in valid)
+        thr = zmax - z.dtype.type(theta)
+        keep = [j for j in valid if j >= 1 and z[i, j] >= thr]
+        keep.sort(key=lambda j: (-z[i, j], int(cand[i, j])))
+        for r, j in enumerate(keep[:pmax - 1]):
+            out[i, 1 + r] = cand[i, j]
+    return out

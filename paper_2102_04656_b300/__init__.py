@@ -37,7 +37,7 @@ class _Partitions(ctypes.Structure):
         ("m", _i32), ("t", _i32), ("centroids", _c_void_p), ("bk_sample", _c_void_p),
         ("bk_sample_size", _i64), ("bk_iters", _i32), ("routes", _c_void_p),
         ("entry", _c_void_p), ("n_entry", _i32), ("tile_visitors", _i32), ("kernel", _i32),
-        ("coarse_num", _i64),
+        ("coarse_num", _i64), ("class_kernel", _i32 * 3),
     ]
 
 
@@ -55,6 +55,7 @@ def lib():
         L.bdg_route.argtypes = [_c_void_p, _i64, _i32, _c_void_p, _i32, _i32, _c_void_p,
                                 _c_void_p, _c_void_p]
         L.bdg_routes_coarse.argtypes = [_c_void_p, _i64, _i32, _i32, _i64, _c_void_p, _c_void_p]
+        L.bdg_routes_gap.argtypes = [_c_void_p, _c_void_p, _i64, _i32, _i32, _c_void_p]
         L.bdg_bkmeans.argtypes = [_c_void_p, _i64, _i32, _c_void_p, _i64, _i32, _i32, _c_void_p,
                                   _c_void_p, _c_void_p]
         L.bdg_build_graph.argtypes = [_c_void_p, _i64, _i32, _i32, ctypes.POINTER(_Partitions),
@@ -147,6 +148,18 @@ def routes_coarse(routes, m: int, coarse_num: int, stream=None):
     return cnt
 
 
+def routes_gap(routes, rdist, delta: int, stream=None):
+    """The distance-gap rule (bdg_routes_gap) on routes int32 [n, t], in place:
+    slots whose centre lies more than delta farther than the home's become -1."""
+    _dev(routes, torch.int32, "routes", 2)
+    _dev(rdist, torch.int32, "rdist", 2)
+    if rdist.shape != routes.shape:
+        raise ValueError("rdist must have the shape of routes")
+    _check(lib().bdg_routes_gap(_ptr(routes), _ptr(rdist), routes.shape[0], routes.shape[1],
+                                int(delta), _stream(stream)))
+    return routes
+
+
 def knn_rows(codes, rows, k: int, stream=None):
     """Exact k-NN rows of the points ``rows`` over all codes: (ids, dists) int32 [nrows, k]."""
     codes, bits = _codes(codes)
@@ -226,14 +239,20 @@ class Graph:
 KERNELS = {"auto": 0, "popc": 1, "tc": 2}
 
 
+VARIANTS = {"follow": 0, "popc": 1, "tc": 2, "popc32": 3}
+
+
 def build_graph(codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample=None,
                 bk_iters: int = 8, routes=None, entry=None, tile_visitors: int = 0,
-                kernel: str = "auto", coarse_num: int = 0, stream=None) -> Graph:
+                kernel: str = "auto", coarse_num: int = 0, class_kernel=None,
+                stream=None) -> Graph:
     """Single-pass divide-and-conquer k-NN graph (exact when m == 1).
 
     kernel: "auto", "popc" (XOR + POPC) or "tc" (tcgen05 FP8 +-1 tensor cores).
     coarse_num > 0: each point probes the shortest prefix of its t nearest
-    centres holding at least coarse_num points (Section 3.2)."""
+    centres holding at least coarse_num points (Section 3.2).
+    class_kernel: optional 3 variant names ("follow", "popc", "tc", "popc32"),
+    one per partition size class (|H_p| >= 4096, 512..4095, < 512)."""
     codes, bits = _codes(codes)
     if entry is None:
         raise ValueError("entry (long-link sample ids, int32 CUDA tensor) is required")
@@ -251,6 +270,9 @@ def build_graph(codes, k: int, m: int = 1, t: int = 1, centroids=None, bk_sample
     P.tile_visitors = tile_visitors
     P.kernel = KERNELS[kernel]
     P.coarse_num = coarse_num
+    if class_kernel is not None:
+        for i, v in enumerate(class_kernel):
+            P.class_kernel[i] = VARIANTS[v]
     h = ctypes.c_void_p()
     _check(lib().bdg_build_graph(_ptr(codes), codes.shape[0], bits, k, ctypes.byref(P),
                                  _stream(stream), ctypes.byref(h)))
@@ -423,6 +445,14 @@ def _router_sigs(L):
                                         _c_void_p, _i32, ctypes.c_float, _i32, _c_void_p]
     L.bdg_router_route.argtypes = [_c_void_p, _c_void_p, _c_void_p, _i64, _c_void_p, _i32,
                                    _c_void_p, _c_void_p]
+    L.bdg_router_forward_shortlist.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32,
+                                               _i32, _c_void_p, _c_void_p]
+    L.bdg_router_train_step_shortlist.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p,
+                                                  _i32, _c_void_p, _i32, _i32, ctypes.c_float,
+                                                  _i32, _c_void_p]
+    L.bdg_router_route_shortlist.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32,
+                                             _i64, ctypes.c_float, _i32, _c_void_p, _c_void_p,
+                                             _c_void_p]
     L._router_sigs = True
 
 
@@ -520,6 +550,55 @@ class Router:
         _check(lib().bdg_router_route(self._h, _ptr(x), _ptr(c), x.shape[0], _ptr(home), P,
                                       _ptr(routes), _stream(stream)))
         return routes
+
+    # ---- shortlist head: the last layer on each point's Q candidate partitions
+    def _cand(self, cand, n):
+        _dev(cand, torch.int32, "cand", 2)
+        if cand.shape[0] != n:
+            raise ValueError(f"cand: expected {n} rows")
+        return cand
+
+    def forward_shortlist(self, x, cand, codes=None, stream=None):
+        """Logits of the shortlisted partitions: float32 [B, Q] (-inf where cand < 0)."""
+        _dev(x, torch.bfloat16, "x", 2)
+        B = x.shape[0]
+        c = self._codes(codes, B)
+        cand = self._cand(cand, B)
+        z = torch.empty(B, cand.shape[1], dtype=torch.float32, device=x.device)
+        _check(lib().bdg_router_forward_shortlist(self._h, _ptr(x), _ptr(c), _ptr(cand),
+                                                  cand.shape[1], B, _ptr(z), _stream(stream)))
+        return z
+
+    def train_step_shortlist(self, x, cand, labels, lr: float, apply_update: bool = True,
+                             codes=None, stream=None):
+        """One step of softmax cross-entropy over each row's shortlist."""
+        _dev(x, torch.bfloat16, "x", 2)
+        _dev(labels, torch.int32, "labels", 2)
+        B = x.shape[0]
+        c = self._codes(codes, B)
+        cand = self._cand(cand, B)
+        _check(lib().bdg_router_train_step_shortlist(self._h, _ptr(x), _ptr(c), _ptr(cand),
+                                                     cand.shape[1], _ptr(labels),
+                                                     labels.shape[1], B, float(lr),
+                                                     int(apply_update), _stream(stream)))
+        return self.loss
+
+    def route_shortlist(self, x, cand, theta: float, pmax: int, codes=None, logits=False,
+                        stream=None):
+        """Probed partitions int32 [N, pmax] (-1 = none): the home cand[:, 0], then
+        the shortlisted partitions within theta of the largest shortlisted logit.
+        With logits=True also returns the float32 [N, Q] logits."""
+        _dev(x, torch.bfloat16, "x", 2)
+        N = x.shape[0]
+        c = self._codes(codes, N)
+        cand = self._cand(cand, N)
+        routes = torch.empty(N, pmax, dtype=torch.int32, device=x.device)
+        z = (torch.empty(N, cand.shape[1], dtype=torch.float32, device=x.device)
+             if logits else None)
+        _check(lib().bdg_router_route_shortlist(self._h, _ptr(x), _ptr(c), _ptr(cand),
+                                                cand.shape[1], N, float(theta), pmax,
+                                                _ptr(routes), _ptr(z), _stream(stream)))
+        return (routes, z) if logits else routes
 
     def free(self):
         if self._h is not None and self._h.value:
@@ -623,6 +702,9 @@ class BuildPlan:
                                               ctypes.POINTER(_i32),
                                               ctypes.POINTER(ctypes.c_float),
                                               ctypes.POINTER(ctypes.c_float)]
+            L.bdg_build_plan_classes.argtypes = [_c_void_p, ctypes.POINTER(_i32),
+                                                 ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                                 ctypes.POINTER(ctypes.c_float)]
             L.bdg_build_plan_free.argtypes = [_c_void_p]
             L.bdg_build_plan_free.restype = None
             L._plan_sigs = True
@@ -651,6 +733,14 @@ class BuildPlan:
                                      ctypes.byref(mt)))
         self.kernel = {1: "popc", 2: "tc"}[kern.value]
         self.tuned_ms = {"popc": mp.value, "tc": mt.value}
+        var = (_i32 * 3)()
+        lo, hi = (_i32 * 3)(), (_i32 * 3)()
+        ms = (ctypes.c_float * 9)()
+        _check(L.bdg_build_plan_classes(h, var, lo, hi, ms))
+        names = {1: "popc", 2: "tc", 3: "popc32"}
+        self.classes = [{"size_lo": lo[c], "size_hi": hi[c], "variant": names[var[c]],
+                         "tuned_ms": {names[v + 1]: round(ms[v * 3 + c], 3) for v in range(3)
+                                      if ms[v * 3 + c] >= 0}} for c in range(3)]
         self.graph = _PlanGraph(gp.value, codes, self)
 
     def run(self, stream=None):

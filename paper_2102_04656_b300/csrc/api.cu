@@ -233,7 +233,16 @@ bdg_status bdg_route(const uint64_t* codes, int64_t n, int32_t bits, const uint6
     return bdg_set_error(BDG_EINVAL, "route: n=%lld m=%d t=%d", (long long)n, m, t);
   if (n > 0 && (!codes || !centroids || !routes))
     return bdg_set_error(BDG_EINVAL, "route: null pointer");
-  return bdg_launch_route(codes, n, bits / 64, centroids, m, t, routes, rdist, (cudaStream_t)stream);
+  const int W = bits / 64;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > 0 && bdg_route_tc_ok(W, n, m, t) && bdg_tc_default()) {
+    keep_pool_cached();
+    Scratch sc;
+    const size_t b = bdg_route_tc_bytes(n, m, W, t);
+    BDG_TRY(sc.alloc(b, st));
+    return bdg_launch_route_tc(codes, n, W, centroids, m, t, routes, rdist, sc.p, b, st);
+  }
+  return bdg_launch_route(codes, n, W, centroids, m, t, routes, rdist, st);
 }
 
 bdg_status bdg_routes_coarse(int32_t* routes, int64_t n, int32_t t, int32_t m, int64_t coarse_num,
@@ -244,6 +253,14 @@ bdg_status bdg_routes_coarse(int32_t* routes, int64_t n, int32_t t, int32_t m, i
   if (!home_count || (n > 0 && !routes))
     return bdg_set_error(BDG_EINVAL, "routes_coarse: null pointer");
   return bdg_launch_routes_coarse(routes, n, t, m, coarse_num, home_count, (cudaStream_t)stream);
+}
+
+bdg_status bdg_routes_gap(int32_t* routes, const int32_t* rdist, int64_t n, int32_t t,
+                         int32_t delta, void* stream) {
+  if (n < 0 || t < 1 || t > 16)
+    return bdg_set_error(BDG_EINVAL, "routes_gap: n=%lld t=%d", (long long)n, t);
+  if (n > 0 && (!routes || !rdist)) return bdg_set_error(BDG_EINVAL, "routes_gap: null pointer");
+  return bdg_launch_routes_gap(routes, rdist, n, t, delta, (cudaStream_t)stream);
 }
 
 bdg_status bdg_bkmeans(const uint64_t* codes, int64_t n, int32_t bits, const int64_t* sample,
@@ -272,9 +289,10 @@ namespace {
 // scratch (bdg_build_graph) or captured once into a CUDA graph (build plans).
 struct BuildCfg {
   int W, m, t, tile_v;
-  bool need_routes, need_bk, use_tc, tc_ok;
+  bool need_routes, need_bk, use_tc, tc_ok, route_tc;
+  int kmap[BDG_SIZE_CLASSES];  // Reduce-1 variant (BDG_KV_*) per partition size class
   int64_t coarse;
-  size_t b_routes, b_cent, b_bk, b_csr, b_part, b_hexp, b_fix, b_cnt, total;
+  size_t b_routes, b_cent, b_bk, b_csr, b_part, b_hexp, b_fix, b_cnt, b_rtc, total;
 };
 
 bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_t k,
@@ -311,7 +329,24 @@ bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_
     return bdg_set_error(BDG_EUNSUPPORTED,
                          "build: the tensor path needs 256/512-bit codes, k <= 64 and, with "
                          "m = 1, N < 2^21");
-  c->use_tc = P->kernel == 2 || (P->kernel == 0 && c->tc_ok && bdg_tc_default());
+  for (int i = 0; i < BDG_SIZE_CLASSES; ++i) {
+    const int v = P->class_kernel[i];
+    if (v < 0 || v > 3)
+      return bdg_set_error(BDG_EINVAL, "build: class_kernel[%d] = %d (0 follow kernel, 1 popcount, "
+                           "2 tensor, 3 popcount with 32-visitor sub-tiles)", i, v);
+    if (v == BDG_KV_TC && !c->tc_ok)
+      return bdg_set_error(BDG_EUNSUPPORTED, "build: class_kernel[%d] = 2 but the tensor path "
+                           "does not apply", i);
+  }
+  if (P->kernel == 3)
+    return bdg_set_error(BDG_EINVAL, "build: kernel = 3 is a per-class choice (class_kernel)");
+  const int kdef = P->kernel == 2 || (P->kernel == 0 && c->tc_ok && bdg_tc_default())
+                       ? BDG_KV_TC : BDG_KV_POPC;
+  c->use_tc = false;
+  for (int i = 0; i < BDG_SIZE_CLASSES; ++i) {
+    c->kmap[i] = P->class_kernel[i] ? P->class_kernel[i] : kdef;
+    c->use_tc = c->use_tc || c->kmap[i] == BDG_KV_TC;
+  }
   c->tile_v = bdg_knn_tile_visitors(c->W);
   const int W = c->W;
   c->b_routes = c->need_routes || m == 1 ? al((size_t)N * t * 4) : 0;
@@ -322,8 +357,11 @@ bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_
   c->b_hexp = c->tc_ok ? al(bdg_knn_tc_hexp_bytes(N, m, W)) : 0;
   c->b_fix = c->tc_ok ? al((size_t)N * t) + al(64) : 0;
   c->b_cnt = c->coarse > 0 ? al((size_t)m * 4) : 0;
+  // library routing on the tensor cores where the codes allow it
+  c->route_tc = c->need_routes && bdg_route_tc_ok(W, N, m, t) && bdg_tc_default();
+  c->b_rtc = c->route_tc ? al(bdg_route_tc_bytes(N, m, W, t)) : 0;
   c->total = c->b_routes + c->b_cent + c->b_bk + c->b_csr + c->b_part + c->b_hexp + c->b_fix +
-             c->b_cnt;
+             c->b_cnt + c->b_rtc;
   return BDG_OK;
 }
 
@@ -341,10 +379,19 @@ bdg_status graph_alloc(const BuildCfg& c, const uint64_t* codes, int64_t N, int3
 }
 
 // Enqueue every step of the build into g using `scratch` (c.total bytes).
-bdg_status build_enqueue(const BuildCfg& c, bool use_tc, bdg_graph* g, const uint64_t* codes,
+// kmap: the Reduce-1 variant of each size class. cls_ev (optional, t x
+// BDG_SIZE_CLASSES x 2 events): each class's Reduce-1 launches of each round are
+// recorded between a pair of events, and every class gets its own launch.
+bdg_status build_enqueue(const BuildCfg& c, const int* kmap, bdg_graph* g, const uint64_t* codes,
                          int64_t N, int32_t bits, int32_t k, const bdg_partitions* P,
                          void* scratch, cudaStream_t st, cudaEvent_t ev0 = nullptr,
-                         cudaEvent_t ev1 = nullptr) {
+                         cudaEvent_t ev1 = nullptr, cudaEvent_t* cls_ev = nullptr) {
+  bool use_tc = false, uniform = true;
+  for (int i = 0; i < BDG_SIZE_CLASSES; ++i) {
+    use_tc = use_tc || kmap[i] == BDG_KV_TC;
+    uniform = uniform && kmap[i] == kmap[0];
+  }
+  const bool split = !uniform || cls_ev != nullptr;
   const int W = c.W, m = c.m, t = c.t;
   char* p = (char*)scratch;
   int32_t* routes = (int32_t*)P->routes;
@@ -361,6 +408,8 @@ bdg_status build_enqueue(const BuildCfg& c, bool use_tc, bdg_graph* g, const uin
   int32_t* tc_err = c.b_fix ? (int32_t*)(p + al((size_t)N * t)) : nullptr;
   p += c.b_fix;
   int32_t* home_count = c.b_cnt ? (int32_t*)p : nullptr;
+  p += c.b_cnt;
+  void* rtc = c.b_rtc ? (void*)p : nullptr;
 
   BDG_CUDA_TRY(cudaMemcpyAsync(g->entry, P->entry, (size_t)P->n_entry * 4,
                                cudaMemcpyDeviceToDevice, st));
@@ -371,7 +420,10 @@ bdg_status build_enqueue(const BuildCfg& c, bool use_tc, bdg_graph* g, const uin
     if (c.need_bk)
       BDG_TRY(bdg_launch_bkmeans(codes, N, W, P->bk_sample, P->bk_sample_size, m, P->bk_iters,
                                  cent, nullptr, bk, c.b_bk, st));
-    BDG_TRY(bdg_launch_route(codes, N, W, cent, m, t, routes, nullptr, st));
+    if (c.route_tc)
+      BDG_TRY(bdg_launch_route_tc(codes, N, W, cent, m, t, routes, nullptr, rtc, c.b_rtc, st));
+    else
+      BDG_TRY(bdg_launch_route(codes, N, W, cent, m, t, routes, nullptr, st));
     if (c.coarse > 0)
       BDG_TRY(bdg_launch_routes_coarse(routes, N, t, m, c.coarse, home_count, st));
   }
@@ -395,18 +447,27 @@ bdg_status build_enqueue(const BuildCfg& c, bool use_tc, bdg_graph* g, const uin
   // optional timing of the Reduce-1 step (recorded also inside a captured graph)
   if (ev0) BDG_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal));
   if (use_tc) BDG_CUDA_TRY(cudaMemsetAsync(fixflag, 0, al((size_t)N * t) + al(64), st));
+  bool expanded = false;
   for (int round = 0; round < t; ++round) {
     a.csr = round == 0 ? bdg_csr_round_a(csr) : bdg_csr_subround(csr, round);
-    a.item_counter = csr.counters + (size_t)t * m + round;
     a.home_kth = round == 0 ? nullptr : partial;
     a.merge_running = round == 0 ? 0 : 1;
-    if (use_tc) {
-      bdg_knn_tc_args ta;
-      ta.base = a; ta.hexp = hexp; ta.err = tc_err;
-      ta.fixflag = fixflag + (round == 0 ? 0 : N);  // sub-round positions are absolute
-      BDG_TRY(bdg_launch_knn_tc(ta, W, round == 0, st));
-    } else {
-      BDG_TRY(bdg_launch_knn_popc(a, W, st));
+    for (int cl = 0; cl < (split ? BDG_SIZE_CLASSES : 1); ++cl) {
+      a.size_lo = split ? kBdgClassLo[cl] : 0;
+      a.size_hi = split ? kBdgClassHi[cl] : 0x7fffffff;
+      a.item_counter = csr.counters + (size_t)t * m + (size_t)round * BDG_SIZE_CLASSES + cl;
+      cudaEvent_t* ce = cls_ev ? cls_ev + 2 * ((size_t)round * BDG_SIZE_CLASSES + cl) : nullptr;
+      if (ce) BDG_CUDA_TRY(cudaEventRecord(ce[0], st));
+      if (kmap[cl] == BDG_KV_TC) {
+        bdg_knn_tc_args ta;
+        ta.base = a; ta.hexp = hexp; ta.err = tc_err;
+        ta.fixflag = fixflag + (round == 0 ? 0 : N);  // sub-round positions are absolute
+        BDG_TRY(bdg_launch_knn_tc(ta, W, !expanded, st));
+        expanded = true;
+      } else {
+        BDG_TRY(bdg_launch_knn_popc(a, W, st, kmap[cl] == BDG_KV_POPC32));
+      }
+      if (ce) BDG_CUDA_TRY(cudaEventRecord(ce[1], st));
     }
   }
   if (ev1) BDG_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal));
@@ -434,7 +495,7 @@ bdg_status bdg_build_graph(const uint64_t* codes, int64_t N, int32_t bits, int32
   BDG_TRY(graph_alloc(c, codes, N, bits, k, P, &g));
   Scratch sc;
   bdg_status s = sc.alloc(c.total, st);
-  if (s == BDG_OK) s = build_enqueue(c, c.use_tc, g, codes, N, bits, k, P, sc.p, st);
+  if (s == BDG_OK) s = build_enqueue(c, c.kmap, g, codes, N, bits, k, P, sc.p, st);
   if (s != BDG_OK) { bdg_graph_free(g); return s; }
   *out = g;
   return BDG_OK;
@@ -449,8 +510,12 @@ struct bdg_build_plan {
   size_t scratch_bytes = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int kernel = 0;          // 1 popcount, 2 tensor
+  int kernel = 0;          // 1 popcount, 2 tensor (2 when any size class uses it)
   float ms_popc = -1.f, ms_tc = -1.f;
+  int kmap[BDG_SIZE_CLASSES] = {0, 0, 0};  // variant per size class
+  // measured Reduce-1 ms per (variant - 1, class), -1 = not measured
+  float cls_ms[3][BDG_SIZE_CLASSES] = {{-1.f, -1.f, -1.f}, {-1.f, -1.f, -1.f},
+                                       {-1.f, -1.f, -1.f}};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the Reduce-1 step of each replay
   int64_t launches = 0;    // kernels in the captured graph
 };
@@ -465,8 +530,8 @@ std::string tune_key(int64_t N, int32_t bits, int32_t k, const bdg_partitions* P
   char buf[512];
   std::string name(prop.name);
   for (auto& ch : name) if (ch == ' ') ch = '_';
-  snprintf(buf, sizeof(buf), "%s|bits=%d|k=%d|N=%lld|m=%d|t=%d|coarse=%lld", name.c_str(), bits,
-           k, (long long)N, P->m, P->t, (long long)P->coarse_num);
+  snprintf(buf, sizeof(buf), "classes2|%s|bits=%d|k=%d|N=%lld|m=%d|t=%d|coarse=%lld",
+           name.c_str(), bits, k, (long long)N, P->m, P->t, (long long)P->coarse_num);
   return buf;
 }
 
@@ -477,21 +542,30 @@ std::string tune_path() {
   return std::string(h ? h : "/tmp") + "/.cache/bdg_autotune.txt";
 }
 
-int tune_lookup(const std::string& key) {
+// The cache holds one line per key: the variant of each size class, then the
+// measured Reduce-1 ms of every (variant, class). Returns true when found.
+bool tune_lookup(const std::string& key, int* kmap) {
   FILE* f = fopen(tune_path().c_str(), "r");
-  if (!f) return 0;
-  char line[768];
-  int found = 0;
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
   while (fgets(line, sizeof(line), f)) {
     char k2[512];
-    int kern = 0;
-    if (sscanf(line, "%511s %d", k2, &kern) == 2 && key == k2) found = kern;
+    int v[BDG_SIZE_CLASSES];
+    if (sscanf(line, "%511s %d %d %d", k2, &v[0], &v[1], &v[2]) == 4 && key == k2) {
+      bool ok = true;
+      for (int i = 0; i < BDG_SIZE_CLASSES; ++i) ok = ok && v[i] >= 1 && v[i] <= 3;
+      if (ok) {
+        for (int i = 0; i < BDG_SIZE_CLASSES; ++i) kmap[i] = v[i];
+        found = true;
+      }
+    }
   }
   fclose(f);
   return found;
 }
 
-void tune_store(const std::string& key, int kern, float ms_popc, float ms_tc) {
+void tune_store(const std::string& key, const int* kmap, const float (*ms)[BDG_SIZE_CLASSES]) {
   const std::string path = tune_path();
   const size_t slash = path.rfind('/');
   if (slash != std::string::npos) {
@@ -500,27 +574,43 @@ void tune_store(const std::string& key, int kern, float ms_popc, float ms_tc) {
   }
   FILE* f = fopen(path.c_str(), "a");
   if (!f) return;  // the cache is an optimisation only
-  fprintf(f, "%s %d %.3f %.3f\n", key.c_str(), kern, ms_popc, ms_tc);
+  fprintf(f, "%s %d %d %d", key.c_str(), kmap[0], kmap[1], kmap[2]);
+  for (int v = 0; v < 3; ++v)
+    for (int c = 0; c < BDG_SIZE_CLASSES; ++c) fprintf(f, " %.3f", ms[v][c]);
+  fprintf(f, "\n");
   fclose(f);
 }
 
-float time_build(const BuildCfg& c, bool use_tc, bdg_graph* g, const uint64_t* codes, int64_t N,
-                 int32_t bits, int32_t k, const bdg_partitions* P, void* scratch,
-                 cudaStream_t st) {
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  float ms = -1.f;
-  if (build_enqueue(c, use_tc, g, codes, N, bits, k, P, scratch, st) == BDG_OK) {  // warm
-    cudaEventRecord(a, st);
-    if (build_enqueue(c, use_tc, g, codes, N, bits, k, P, scratch, st) == BDG_OK) {
-      cudaEventRecord(b, st);
-      if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+// One warm build, then one build with every size class launched on its own
+// between events: per-class Reduce-1 ms (summed over rounds) into cls_ms[c],
+// the whole Reduce-1 step's ms returned (-1 on failure).
+float time_build(const BuildCfg& c, const int* kmap, bdg_graph* g, const uint64_t* codes,
+                 int64_t N, int32_t bits, int32_t k, const bdg_partitions* P, void* scratch,
+                 cudaStream_t st, float* cls_ms) {
+  const int t = c.t;
+  std::vector<cudaEvent_t> ev((size_t)t * BDG_SIZE_CLASSES * 2);
+  for (auto& e : ev) cudaEventCreate(&e);
+  float total = -1.f;
+  if (build_enqueue(c, kmap, g, codes, N, bits, k, P, scratch, st) == BDG_OK &&
+      build_enqueue(c, kmap, g, codes, N, bits, k, P, scratch, st, nullptr, nullptr,
+                    ev.data()) == BDG_OK &&
+      cudaEventSynchronize(ev.back()) == cudaSuccess) {
+    total = 0.f;
+    for (int cl = 0; cl < BDG_SIZE_CLASSES; ++cl) {
+      float sum = 0.f;
+      for (int r = 0; r < t; ++r) {
+        float ms = 0.f;
+        const size_t x = 2 * ((size_t)r * BDG_SIZE_CLASSES + cl);
+        cudaEventElapsedTime(&ms, ev[x], ev[x + 1]);
+        sum += ms;
+      }
+      cls_ms[cl] = sum;
+      total += sum;
     }
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  return ms;
+  cudaGetLastError();
+  for (auto& e : ev) cudaEventDestroy(e);
+  return total;
 }
 
 }  // namespace
@@ -541,22 +631,43 @@ bdg_status bdg_build_plan_create(const uint64_t* codes, int64_t N, int32_t bits,
   plan->scratch_bytes = c.total;
   s = dalloc(&plan->scratch, c.total);
   if (s != BDG_OK) return fail(s);
-  // kernel choice: fixed by the caller, else measured once per device and shape
-  int kern = P->kernel == 1 ? 1 : P->kernel == 2 ? 2 : 0;
-  if (kern == 0 && !c.tc_ok) kern = 1;
-  if (kern == 0) {
+  // Reduce-1 variant per partition size class: fixed by the caller (kernel or
+  // class_kernel), else measured once per device and shape: every variant runs
+  // every class, and each class keeps its fastest variant
+  bool fixed = P->kernel != 0;
+  for (int i = 0; i < BDG_SIZE_CLASSES; ++i) fixed = fixed || P->class_kernel[i] != 0;
+  for (int i = 0; i < BDG_SIZE_CLASSES; ++i) plan->kmap[i] = c.kmap[i];
+  if (!fixed) {
     const std::string key = tune_key(N, bits, k, P);
-    kern = tune_lookup(key);
-    if (kern != 1 && kern != 2) {
-      plan->ms_popc = time_build(c, false, plan->g, codes, N, bits, k, P, plan->scratch, st);
-      plan->ms_tc = time_build(c, true, plan->g, codes, N, bits, k, P, plan->scratch, st);
-      kern = (plan->ms_tc > 0.f && (plan->ms_popc < 0.f || plan->ms_tc < plan->ms_popc)) ? 2 : 1;
-      tune_store(key, kern, plan->ms_popc, plan->ms_tc);
+    if (!tune_lookup(key, plan->kmap)) {
+      const int variants[3] = {BDG_KV_POPC, BDG_KV_TC, BDG_KV_POPC32};
+      for (int vi = 0; vi < 3; ++vi) {
+        const int v = variants[vi];
+        // the plan's scratch holds the tensor path's buffers whenever it applies
+        if (v == BDG_KV_TC && !(c.tc_ok && bdg_tc_default())) continue;
+        int km[BDG_SIZE_CLASSES] = {v, v, v};
+        const float ms = time_build(c, km, plan->g, codes, N, bits, k, P, plan->scratch, st,
+                                    plan->cls_ms[v - 1]);
+        if (v == BDG_KV_POPC) plan->ms_popc = ms;
+        if (v == BDG_KV_TC) plan->ms_tc = ms;
+      }
+      for (int cl = 0; cl < BDG_SIZE_CLASSES; ++cl) {
+        int best = 0;
+        for (int vi = 0; vi < 3; ++vi) {
+          const float ms = plan->cls_ms[variants[vi] - 1][cl];
+          if (ms < 0.f) continue;
+          if (best == 0 || ms < plan->cls_ms[best - 1][cl]) best = variants[vi];
+        }
+        plan->kmap[cl] = best ? best : c.kmap[cl];
+      }
+      tune_store(key, plan->kmap, plan->cls_ms);
     }
   }
-  plan->kernel = kern;
+  plan->kernel = BDG_KV_POPC;
+  for (int i = 0; i < BDG_SIZE_CLASSES; ++i)
+    if (plan->kmap[i] == BDG_KV_TC) plan->kernel = BDG_KV_TC;
   // warm once outside capture (lazy module loading, function attributes), then capture
-  s = build_enqueue(c, kern == 2, plan->g, codes, N, bits, k, P, plan->scratch, st);
+  s = build_enqueue(c, plan->kmap, plan->g, codes, N, bits, k, P, plan->scratch, st);
   if (s != BDG_OK) return fail(s);
   if (cudaStreamSynchronize(st) != cudaSuccess)
     return fail(bdg_set_error(BDG_ECUDA, "plan: warm-up build failed"));
@@ -567,7 +678,7 @@ bdg_status bdg_build_plan_create(const uint64_t* codes, int64_t N, int32_t bits,
   const int64_t l0 = g_launches.load();
   bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) == cudaSuccess;
   const bdg_status se =
-      ok ? build_enqueue(c, kern == 2, plan->g, codes, N, bits, k, P, plan->scratch, cap,
+      ok ? build_enqueue(c, plan->kmap, plan->g, codes, N, bits, k, P, plan->scratch, cap,
                          plan->ev0, plan->ev1)
          : BDG_OK;
   plan->launches = g_launches.load() - l0;
@@ -603,6 +714,19 @@ bdg_status bdg_build_plan_info(const bdg_build_plan* plan, const bdg_graph** gra
   if (kernel) *kernel = plan->kernel;
   if (ms_popc) *ms_popc = plan->ms_popc;
   if (ms_tc) *ms_tc = plan->ms_tc;
+  return BDG_OK;
+}
+
+bdg_status bdg_build_plan_classes(const bdg_build_plan* plan, int32_t* variant, int32_t* size_lo,
+                                  int32_t* size_hi, float* ms) {
+  if (!plan) return bdg_set_error(BDG_EINVAL, "plan is NULL");
+  for (int c = 0; c < BDG_SIZE_CLASSES; ++c) {
+    if (variant) variant[c] = plan->kmap[c];
+    if (size_lo) size_lo[c] = kBdgClassLo[c];
+    if (size_hi) size_hi[c] = kBdgClassHi[c];
+    for (int v = 0; v < 3; ++v)
+      if (ms) ms[v * BDG_SIZE_CLASSES + c] = plan->cls_ms[v][c];
+  }
   return BDG_OK;
 }
 

@@ -254,7 +254,68 @@ __global__ void rows_plan_kernel(int64_t N, const int32_t* __restrict__ rows, in
   }
 }
 
+// Routing as one partition: homes = the m centres (ids 0..m-1), visitors = all
+// n points in id order, each a visit of slot 1 (not its home set: no self pair).
+__global__ void centres_plan_kernel(int64_t n, int m, int tile_v, int32_t* __restrict__ home_off,
+                                    int32_t* __restrict__ home_ids,
+                                    int32_t* __restrict__ visit_off,
+                                    int32_t* __restrict__ visit_ids,
+                                    int8_t* __restrict__ visit_slot,
+                                    int32_t* __restrict__ part_order,
+                                    int32_t* __restrict__ item_off, int32_t* __restrict__ eoff) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < m) home_ids[x] = (int32_t)x;
+  if (x < n) {
+    visit_ids[x] = (int32_t)x;
+    visit_slot[x] = 1;
+  }
+  if (x == 0) {
+    home_off[0] = 0; home_off[1] = m;
+    visit_off[0] = 0; visit_off[1] = (int32_t)n;
+    part_order[0] = 0;
+    item_off[0] = 0; item_off[1] = (int32_t)((n + tile_v - 1) / tile_v);
+    eoff[0] = 0; eoff[1] = (m + BDG_TC_TILE - 1) & ~(BDG_TC_TILE - 1);
+  }
+}
+
 }  // namespace
+
+size_t bdg_csr_centres_bytes(int64_t n, int m, int tile_v) {
+  return al(2 * 4) * 4 + al((size_t)m * 4) + al(n * 4) + al(n) + al(4) + al(8 * 4) +
+         al((size_t)((n + tile_v - 1) / tile_v + 1) * 4);
+}
+
+bdg_status bdg_build_csr_centres(const uint64_t* cent, int m, int64_t n, int tile_v, void* mem,
+                                 bdg_csr* c, cudaStream_t st) {
+  char* p = (char*)mem;
+  c->home_off = (int32_t*)p;   p += al(2 * 4);
+  c->visit_off = (int32_t*)p;  p += al(2 * 4);
+  c->item_off = (int32_t*)p;   p += al(2 * 4);
+  c->eoff = (int32_t*)p;       p += al(2 * 4);
+  c->home_ids = (int32_t*)p;   p += al((size_t)m * 4);
+  c->visit_ids = (int32_t*)p;  p += al(n * 4);
+  c->visit_slot = (int8_t*)p;  p += al(n);
+  c->part_order = (int32_t*)p; p += al(4);
+  c->counters = (int32_t*)p;   p += al(8 * 4);
+  c->item_lo_a = (int32_t*)p;  // one partition: every item's rank is 0
+  c->item_lo = c->item_lo_a;
+  c->item_stride = 0;
+  c->home_codes = const_cast<uint64_t*>(cent);
+  c->item_off_a = c->item_off;
+  c->slot_zero = c->visit_slot;
+  c->home_blocks = nullptr;
+  c->m = 1;
+  c->t = 1;
+  BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, 8 * 4, st));
+  BDG_CUDA_TRY(cudaMemsetAsync(c->item_lo_a, 0, ((n + tile_v - 1) / tile_v + 1) * 4, st));
+  const int64_t x = n > m ? n : m;
+  centres_plan_kernel<<<bdg_cdiv(x, 256), 256, 0, st>>>(n, m, tile_v, c->home_off, c->home_ids,
+                                                        c->visit_off, c->visit_ids, c->visit_slot,
+                                                        c->part_order, c->item_off, c->eoff);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
 
 size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows, int tile_v) {
   return al(2 * 4) * 4 + al(N * 4) + al(nrows * 4) + al(nrows) + al(4) + al(8 * 4) +

@@ -21,6 +21,9 @@ __host__ __device__ __forceinline__ uint64_t bdg_pad_key(int32_t bits) {
 }
 #define BDG_KEY_INF (~0ull)
 
+// partition size classes of the Reduce-1 launches (see kBdgClassLo/Hi below)
+constexpr int BDG_SIZE_CLASSES = 3;
+
 // Host-side error plumbing (api.cu owns the thread-local message).
 bdg_status bdg_set_error(bdg_status s, const char* fmt, ...);
 #define BDG_CUDA_TRY(expr)                                                              \
@@ -70,10 +73,19 @@ bdg_status bdg_launch_route(const uint64_t* codes, int64_t n, int W, const uint6
                             int m, int t, int32_t* routes, int32_t* rdist, cudaStream_t st);
 bdg_status bdg_launch_routes_coarse(int32_t* routes, int64_t n, int t, int m, int64_t coarse,
                                     int32_t* home_count, cudaStream_t st);
+bdg_status bdg_launch_routes_gap(int32_t* routes, const int32_t* rdist, int64_t n, int t,
+                                 int delta, cudaStream_t st);
 bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int64_t* sample,
                               int64_t S, int m, int iters, uint64_t* cent, int64_t* loss,
                               void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t bdg_bkmeans_scratch_bytes(int64_t S, int m, int W);
+// routing on the tensor cores (route.cu): the t nearest centres of each point
+// as its t nearest homes in one partition whose homes are the centres
+bool bdg_route_tc_ok(int W, int64_t n, int m, int t);
+size_t bdg_route_tc_bytes(int64_t n, int m, int W, int t);
+bdg_status bdg_launch_route_tc(const uint64_t* codes, int64_t n, int W, const uint64_t* cent,
+                               int m, int t, int32_t* routes, int32_t* rdist, void* scratch,
+                               size_t scratch_bytes, cudaStream_t st);
 // bucket.cu
 struct bdg_csr {
   int32_t* home_off;   // [m + 1]
@@ -106,7 +118,11 @@ inline int64_t bdg_csr_item_stride(int64_t N, int m, int tile_v) {
 int bdg_home_block(int64_t N, int m);
 // The visits of slot s >= 1 form sub-round s: visit_off / item_off hold t - 1
 // consecutive [m + 1] arrays (positions are absolute in visit_ids).
-inline size_t bdg_csr_counter_words(int m, int t) { return (size_t)t * m + t + 8; }
+// words: per-partition cursors (t * m), one item counter per (round, size
+// class), spares
+inline size_t bdg_csr_counter_words(int m, int t) {
+  return (size_t)t * m + (size_t)t * BDG_SIZE_CLASSES + 8;
+}
 inline bdg_csr bdg_csr_subround(const bdg_csr& c, int s) {
   bdg_csr v = c;
   v.visit_off = c.visit_off + (size_t)(s - 1) * (c.m + 1);
@@ -132,6 +148,12 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
 size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows, int tile_v);
 bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* rows,
                               int64_t nrows, int tile_v, void* mem, bdg_csr* csr, cudaStream_t st);
+// one partition whose homes are the m centres (ids 0..m-1, codes `cent`) and
+// whose visitors are all n points in id order, each marked as a visit of a
+// partition that is not its home (slot 1: no self pair)
+size_t bdg_csr_centres_bytes(int64_t n, int m, int tile_v);
+bdg_status bdg_build_csr_centres(const uint64_t* cent, int m, int64_t n, int tile_v, void* mem,
+                                 bdg_csr* csr, cudaStream_t st);
 // knn_popc.cu
 struct bdg_knn_args {
   const uint64_t* codes;  // [N][W]
@@ -151,7 +173,41 @@ struct bdg_knn_args {
   // t > 1: `partial` is the running list [N][k]; round A writes it, the
   // sub-rounds merge their rows into it
   int merge_running;
+  // name the launches are timed under (bdg_profile_*); null = the kernel's own
+  const char* prof = nullptr;
+  // fix-up launch (fixflag set): a device word the flagging kernel sets non-zero
+  // when it flags any row; zero means there is nothing to recompute. NULL = always run
+  const int32_t* fix_any = nullptr;
+  // size class: the launch takes only the items of partitions with
+  // size_lo <= |H_p| < size_hi (a contiguous range of part_order, which is
+  // sorted by decreasing |H_p|)
+  int32_t size_lo = 0;
+  int32_t size_hi = 0x7fffffff;
 };
+
+// The item range [*ib, *ie) of the partitions with size_lo <= |H_p| < size_hi.
+__device__ __forceinline__ void bdg_item_range(const bdg_csr& c, int m, int32_t size_lo,
+                                               int32_t size_hi, int32_t* ib, int32_t* ie) {
+  auto first_below = [&](int32_t s) {  // first rank whose partition holds fewer than s homes
+    int lo = 0, hi = m;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      const int p = c.part_order[mid];
+      if (c.home_off[p + 1] - c.home_off[p] >= s) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+  };
+  *ib = c.item_off[first_below(size_hi)];
+  *ie = c.item_off[first_below(size_lo)];
+}
+
+// Reduce-1 kernel variants (work items of 128 visitors each): the tensor-core
+// kernel (128 x 128 tiles) and the popcount kernel walking an item in sub-tiles
+// of 64 or 32 visitors. Partition size classes (by |H_p|) each get one variant.
+enum { BDG_KV_POPC = 1, BDG_KV_TC = 2, BDG_KV_POPC32 = 3 };
+// class c holds the partitions with kBdgClassLo[c] <= |H_p| < kBdgClassHi[c]
+constexpr int32_t kBdgClassLo[BDG_SIZE_CLASSES] = {4096, 512, 0};
+constexpr int32_t kBdgClassHi[BDG_SIZE_CLASSES] = {0x7fffffff, 4096, 512};
 
 // Merge a warp's sorted row L (len keys, then anything >= pad) into the sorted
 // running list R[0..k) of the same point (global memory): R becomes the k
@@ -198,12 +254,14 @@ struct bdg_knn_tc_args {
   bdg_knn_args base;
   uint8_t* hexp;          // expanded home operand, eoff[m] rows x bits bytes
   int8_t* fixflag;        // [N * t] zeroed before launch; rows that overflow are set to 1
-  int32_t* err;           // device error word (bounded waits that gave up)
+  int32_t* err;           // device error words: err[0] bounded waits that gave up,
+                          // err[1] set when any row is flagged for the fix-up
 };
 bool bdg_knn_tc_supported(int W, int k);
 size_t bdg_knn_tc_hexp_bytes(int64_t N, int m, int W);
 bdg_status bdg_launch_knn_tc(const bdg_knn_tc_args& a, int W, bool expand, cudaStream_t st);
-bdg_status bdg_launch_knn_popc(const bdg_knn_args& a, int W, cudaStream_t st);
+bdg_status bdg_launch_knn_popc(const bdg_knn_args& a, int W, cudaStream_t st,
+                               bool narrow = false);
 // merge.cu
 bdg_status bdg_launch_finalize(const uint64_t* running, int64_t N, int k, int bits, int32_t* ids,
                                int32_t* dist, cudaStream_t st);

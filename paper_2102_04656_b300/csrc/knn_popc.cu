@@ -25,10 +25,12 @@ constexpr int kThreads = 256;  // 8 warps
 constexpr int kTH = 64;        // homes per shared-memory chunk (== candidate buffer capacity)
 constexpr int kHLanes = 16;    // threads across homes; 16 thread rows across visitors
 
-template <int W>
+// visitors per thread: 4 (64-visitor sub-tiles) up to 512-bit codes, else 2;
+// the narrow variant halves it (32- or 16-visitor sub-tiles)
+template <int W, bool NARROW>
 struct Cfg {
-  static constexpr int RV = (W <= 8) ? 4 : 2;  // visitors per thread
-  static constexpr int TV = 16 * RV;           // visitors per work item
+  static constexpr int RV = ((W <= 8) ? 4 : 2) / (NARROW ? 2 : 1);
+  static constexpr int TV = 16 * RV;           // visitors per sub-tile
 };
 
 struct Smem {
@@ -44,16 +46,16 @@ struct Smem {
   int32_t* item;   // [1]
 };
 
-template <int W>
+template <int W, bool NARROW>
 __host__ __device__ size_t smem_bytes(int k) {
-  constexpr int TV = Cfg<W>::TV;
+  constexpr int TV = Cfg<W, NARROW>::TV;
   return (size_t)TV * k * 8 + (size_t)TV * kTH * 8 + (size_t)W * kTH * 8 + TV * 8 + TV * 4 * 4 +
          kTH * 4 + 16;
 }
 
-template <int W>
+template <int W, bool NARROW>
 __device__ Smem carve(char* base, int k) {
-  constexpr int TV = Cfg<W>::TV;
+  constexpr int TV = Cfg<W, NARROW>::TV;
   Smem s;
   s.topk = (uint64_t*)base;  base += (size_t)TV * k * 8;
   s.buf = (uint64_t*)base;   base += (size_t)TV * kTH * 8;
@@ -119,28 +121,31 @@ __device__ __forceinline__ void merge_row(const Smem& s, int v, int k, int lane)
   }
 }
 
-template <int W>
+template <int W, bool NARROW>
 __global__ void __launch_bounds__(kThreads, 2)
 knn_popc_kernel(bdg_knn_args a) {
-  constexpr int RV = Cfg<W>::RV;
-  constexpr int TV = Cfg<W>::TV;
+  constexpr int RV = Cfg<W, NARROW>::RV;
+  constexpr int TV = Cfg<W, NARROW>::TV;
   extern __shared__ __align__(16) char smem_raw[];
   const int k = a.k;
-  Smem s = carve<W>(smem_raw, k);
+  Smem s = carve<W, NARROW>(smem_raw, k);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int th = tid % kHLanes;         // home lane
   const int tvg = tid / kHLanes;        // visitor row group: rows tvg*RV .. +RV
   const int m = a.m;
   const bdg_csr& c = a.csr;
-  const int32_t total_items = c.item_off[m];
+  int32_t item_begin, item_end;
+  bdg_item_range(c, m, a.size_lo, a.size_hi, &item_begin, &item_end);
   const uint64_t pad = bdg_pad_key(a.bits);
+  // a fix-up launch with nothing flagged has no work
+  if (a.fix_any != nullptr && *reinterpret_cast<const volatile int32_t*>(a.fix_any) == 0) return;
 
   for (;;) {
     __syncthreads();
-    if (tid == 0) *s.item = atomicAdd(a.item_counter, 1);
+    if (tid == 0) *s.item = item_begin + atomicAdd(a.item_counter, 1);
     __syncthreads();
     const int item = *s.item;
-    if (item >= total_items) break;
+    if (item >= item_end) break;
     const int lo = c.item_lo[item];  // rank of the item's partition in part_order
     const int p = c.part_order[lo];
     const int tile = item - c.item_off[lo];
@@ -172,11 +177,14 @@ knn_popc_kernel(bdg_knn_args a) {
     __syncthreads();
     uint64_t vc[RV][W];
     int32_t myvid[RV];
+    int32_t selfid[RV];  // the id that is the row's own point (-2: none to exclude)
     uint64_t thr[RV];
 #pragma unroll
     for (int r = 0; r < RV; ++r) {
       const int row = tvg * RV + r;
       myvid[r] = s.vid[row];
+      // only a visitor of its own home set (slot 0) can meet itself among the homes
+      selfid[r] = s.vslot[row] == 0 ? myvid[r] : -2;
       thr[r] = s.thr[row];
 #pragma unroll
       for (int w = 0; w < W; ++w)
@@ -205,7 +213,7 @@ knn_popc_kernel(bdg_knn_args a) {
 #pragma unroll
           for (int w = 0; w < W; ++w) d += __popcll(vc[r][w] ^ hw[w]);
           const uint64_t key = bdg_key(d, (uint32_t)hidv);
-          if (hidv >= 0 && key < thr[r] && hidv != myvid[r]) {
+          if (hidv >= 0 && key < thr[r] && hidv != selfid[r]) {
             const int row = tvg * RV + r;
             const int pos = atomicAdd(&s.cnt[row], 1);
             s.buf[(size_t)row * kTH + pos] = key;
@@ -244,21 +252,26 @@ knn_popc_kernel(bdg_knn_args a) {
   }
 }
 
-template <int W>
-bdg_status launch_w(const bdg_knn_args& a, cudaStream_t st) {
-  const size_t smem = smem_bytes<W>(a.k);
-  BDG_CUDA_TRY(cudaFuncSetAttribute(knn_popc_kernel<W>,
+template <int W, bool NARROW>
+bdg_status launch_v(const bdg_knn_args& a, cudaStream_t st) {
+  const size_t smem = smem_bytes<W, NARROW>(a.k);
+  BDG_CUDA_TRY(cudaFuncSetAttribute(knn_popc_kernel<W, NARROW>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  BDG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_popc_kernel<W>,
+  BDG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_popc_kernel<W, NARROW>,
                                                              kThreads, smem));
   if (per_sm < 1) return bdg_set_error(BDG_EUNSUPPORTED, "knn kernel does not fit (k=%d)", a.k);
   const int grid = bdg_num_sms() * per_sm;
-  bdg_prof_scope prof(a.fixflag ? "knn_fixup" : "knn", st);
-  knn_popc_kernel<W><<<grid, kThreads, smem, st>>>(a);
+  bdg_prof_scope prof(a.prof ? a.prof : (a.fixflag ? "knn_fixup" : "knn"), st);
+  knn_popc_kernel<W, NARROW><<<grid, kThreads, smem, st>>>(a);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   return BDG_OK;
+}
+
+template <int W>
+bdg_status launch_w(const bdg_knn_args& a, cudaStream_t st, bool narrow) {
+  return narrow ? launch_v<W, true>(a, st) : launch_v<W, false>(a, st);
 }
 
 }  // namespace
@@ -267,7 +280,7 @@ bdg_status launch_w(const bdg_knn_args& a, cudaStream_t st) {
 // tile); the popcount kernel walks an item in sub-tiles of its own size.
 int bdg_knn_tile_visitors(int W) { (void)W; return 128; }
 
-bdg_status bdg_launch_knn_popc(const bdg_knn_args& a, int W, cudaStream_t st) {
+bdg_status bdg_launch_knn_popc(const bdg_knn_args& a, int W, cudaStream_t st, bool narrow) {
   if (a.k > 128) return bdg_set_error(BDG_EUNSUPPORTED, "k = %d > 128", a.k);
-  BDG_DISPATCH_W(W, launch_w, a, st);
+  BDG_DISPATCH_W(W, launch_w, a, st, narrow);
 }

@@ -229,7 +229,8 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   const bdg_csr& c = a.csr;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m = a.m, k = a.k, bits = a.bits;
-  const int32_t total_items = c.item_off[m];
+  int32_t item_begin, item_end;
+  bdg_item_range(c, m, a.size_lo, a.size_hi, &item_begin, &item_end);
 
   if (warp == 0) tc05::tmem_alloc(tmem_slot, kTmemCols);
   if (tid == 0) {
@@ -255,10 +256,10 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
 
   for (;;) {
     __syncthreads();
-    if (tid == 0) *s_item = atomicAdd(a.item_counter, 1);
+    if (tid == 0) *s_item = item_begin + atomicAdd(a.item_counter, 1);
     __syncthreads();
     const int item = *s_item;
-    if (item >= total_items || *s_abort) break;
+    if (item >= item_end || *s_abort) break;
     const int lo = c.item_lo[item];  // rank of the item's partition in part_order
     const int p = c.part_order[lo];
     const int tile = item - c.item_off[lo];
@@ -270,6 +271,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
     const int64_t e0 = c.eoff[p];
     if (nh > (int)kPosMask) {  // positions do not fit a candidate word: popcount fixup
       for (int r = tid; r < nv; r += kThreads) ta.fixflag[v0 + r] = 1;
+      if (tid == 0) ta.err[1] = 1;
       continue;
     }
 
@@ -341,9 +343,11 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       const int r = tid;
       const int32_t myvid = r < nv ? c.visit_ids[v0 + r] : -1;  // this row's point
       const bool live = myvid >= 0;
-      // v is one of its own partition's homes: its self pair (d = 0) is counted
-      // like any other value and dropped at selection, so k + 1 values are needed
-      const int need_k = k + ((live && c.visit_slot[v0 + r] == 0) ? 1 : 0);
+      // a visitor of its own home set (slot 0) is one of the homes: its self pair
+      // (d = 0) is counted like any other value and dropped at selection, so
+      // k + 1 values are needed
+      const bool excl = live && c.visit_slot[v0 + r] == 0;
+      const int need_k = k + (excl ? 1 : 0);
       // accept word < thr_w; (bits + 1) << 21 accepts every real distance and no
       // missing home of a ragged tile (those read as d = bits + 1)
       uint32_t thr_w = live ? (uint32_t)(bits + 1) << kPosBits : 0u;
@@ -477,7 +481,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
               const int j = j0 + q;
               if (j < cnt) {
                 crow[j * kCandStride] = (uint32_t)h8[q];
-                if (h8[q] == myvid && self_j == kNeedMax) self_j = j;
+                if (excl && h8[q] == myvid && self_j == kNeedMax) self_j = j;
               }
             }
           }
@@ -501,7 +505,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             continue;
           }
           if (ovf) {  // recomputed by the popcount kernel
-            if (lane == 0) ta.fixflag[v0 + row] = 1;
+            if (lane == 0) { ta.fixflag[v0 + row] = 1; ta.err[1] = 1; }
             continue;
           }
           const int n_out = min(k, n_r - (sj < n_r ? 1 : 0));
@@ -567,7 +571,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           const int32_t vid = __shfl_sync(0xffffffffu, myvid, rr);
           if (row >= nv || vid < 0) continue;  // no row, or an invalid id
           if (ovf) {  // recomputed by the popcount kernel
-            if (lane == 0) ta.fixflag[v0 + row] = 1;
+            if (lane == 0) { ta.fixflag[v0 + row] = 1; ta.err[1] = 1; }
             continue;
           }
           if (n_r == 0) continue;  // nothing enters the running list
@@ -642,7 +646,7 @@ bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
   if (expand) {  // expanded home operand (rows are bounded by N + BDG_TC_TILE m)
     const int64_t max_rows = a.N + (int64_t)BDG_TC_TILE * a.m;
     const int64_t nthreads = ((max_rows + 7) / 8) * 8 * (4 * W);
-    bdg_prof_scope prof("expand", st);
+    bdg_prof_scope prof(a.prof ? a.prof : "expand", st);
     expand_homes_kernel<W><<<bdg_cdiv(nthreads, 256), 256, 0, st>>>(
         a.csr.home_codes, a.csr.home_off, a.csr.eoff, a.m, max_rows, ta.hexp);
     BDG_CUDA_TRY(cudaGetLastError());
@@ -652,7 +656,7 @@ bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
                                     (int)C::SMEM));
   const int grid = bdg_num_sms();
   {
-    bdg_prof_scope prof("knn", st);
+    bdg_prof_scope prof(a.prof ? a.prof : "knn", st);
     knn_tc_kernel<W><<<grid, kThreads, C::SMEM, st>>>(ta);
     BDG_CUDA_TRY(cudaGetLastError());
     bdg_note_launch();
@@ -661,6 +665,7 @@ bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
   BDG_CUDA_TRY(cudaMemsetAsync(a.item_counter, 0, sizeof(int32_t), st));
   bdg_knn_args fx = a;
   fx.fixflag = ta.fixflag;
+  fx.fix_any = ta.err + 1;
   return bdg_launch_knn_popc(fx, W, st);
 }
 

@@ -250,6 +250,224 @@ __global__ void topp_kernel(const float* __restrict__ z, int rows, int m,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Shortlist head: the last layer evaluated only on each point's shortlist of
+// Q candidate partitions (its Q nearest centres, slot 0 = its home; -1 = none):
+//   z_ij = [h2_i | s_i] . W3[cand_ij] + b3[cand_ij],
+// softmax cross-entropy over the shortlist against q_ij = the share of the
+// point's labels (homes of its exact neighbours) naming cand_ij among its labels
+// found in the shortlist, and the probe choice: the home, then the other
+// shortlisted partitions within theta of the largest shortlisted logit, by
+// (-z, partition), at most pmax - 1 of them. One warp per point; the point's
+// input row u = [h2 | s] (BF16) stays in registers, W3 rows are read from L2 in
+// 16-byte chunks (8 BF16 values), products accumulate in FP32.
+constexpr int kMaxQ = 16;
+constexpr int kUChunks = 8;  // 16-byte chunks of u per lane: rows up to 8 * 32 * 8 = 2048 values
+
+__device__ __forceinline__ float dot8(const uint4& a, const uint4& b) {
+  const __nv_bfloat162* x = reinterpret_cast<const __nv_bfloat162*>(&a);
+  const __nv_bfloat162* y = reinterpret_cast<const __nv_bfloat162*>(&b);
+  float acc = 0.f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float2 fx = __bfloat1622float2(x[e]), fy = __bfloat1622float2(y[e]);
+    acc = fmaf(fx.x, fy.x, acc);
+    acc = fmaf(fx.y, fy.y, acc);
+  }
+  return acc;
+}
+
+// z[j] of one row for j < Q (every lane ends with every value); the row's u
+// chunks are loaded into uc
+__device__ __forceinline__ void head_logits(const __nv_bfloat16* __restrict__ urow, int nch,
+                                            const __nv_bfloat16* __restrict__ W3, int h2s,
+                                            const float* __restrict__ b3,
+                                            const int32_t* __restrict__ cand, int Q, int lane,
+                                            uint4 (&uc)[kUChunks], float (&z)[kMaxQ]) {
+#pragma unroll
+  for (int q = 0; q < kUChunks; ++q) {
+    const int c = lane + 32 * q;
+    uc[q] = c < nch ? reinterpret_cast<const uint4*>(urow)[c] : make_uint4(0, 0, 0, 0);
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxQ; ++j) {
+    z[j] = -INFINITY;
+    if (j >= Q) continue;
+    const int32_t p = cand[j];
+    if (p < 0) continue;
+    const uint4* wr = reinterpret_cast<const uint4*>(W3 + (int64_t)p * h2s);
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < kUChunks; ++q) {
+      const int c = lane + 32 * q;
+      if (c < nch) acc += dot8(uc[q], wr[c]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    z[j] = acc + b3[p];
+  }
+}
+
+template <bool SELECT>
+__global__ void __launch_bounds__(256)
+head_fwd_kernel(const __nv_bfloat16* __restrict__ u, int h2s, const __nv_bfloat16* __restrict__ W3,
+                const float* __restrict__ b3, const int32_t* __restrict__ cand, int Q, int rows,
+                float* __restrict__ z_out, float theta, int pmax, int32_t* __restrict__ routes) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= rows) return;
+  const int32_t* cr = cand + (int64_t)i * Q;
+  uint4 uc[kUChunks];
+  float z[kMaxQ];
+  head_logits(u + (int64_t)i * h2s, h2s / 8, W3, h2s, b3, cr, Q, lane, uc, z);
+  if (z_out) {
+#pragma unroll
+    for (int j = 0; j < kMaxQ; ++j)
+      if (j < Q && lane == j) z_out[(int64_t)i * Q + j] = z[j];
+  }
+  if (!SELECT || lane != 0) return;
+  int32_t cp[kMaxQ];
+  float zmax = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < kMaxQ; ++j) {
+    cp[j] = j < Q ? cr[j] : -1;
+    if (cp[j] >= 0) zmax = fmaxf(zmax, z[j]);
+  }
+  const float thr = zmax - theta;
+  int32_t* out = routes + (int64_t)i * pmax;
+  out[0] = cp[0];
+  uint32_t taken = 1u;  // slot 0 (the home) is always probed
+  for (int r = 1; r < pmax; ++r) {
+    int best = -1;
+    float bz = 0.f;
+    int32_t bp = 0;
+#pragma unroll
+    for (int j = 1; j < kMaxQ; ++j) {
+      if (cp[j] < 0 || ((taken >> j) & 1u) || !(z[j] >= thr)) continue;
+      if (best < 0 || z[j] > bz || (z[j] == bz && cp[j] < bp)) { best = j; bz = z[j]; bp = cp[j]; }
+    }
+    out[r] = best < 0 ? -1 : bp;
+    if (best >= 0) taken |= 1u << best;
+  }
+}
+
+// Shortlist cross-entropy and its backward through the last layer, one warp per
+// row: dz_j = (softmax_j - q_j) / B (FP32); dW3[cand_j] += dz_j u, db3[cand_j] +=
+// dz_j (FP32 atomics); dh2 = (sum_j dz_j W3[cand_j][:h2]) * [h2 > 0], written as
+// BF16 for the layer-2 GEMMs and summed (FP32) into db2.
+__global__ void __launch_bounds__(256)
+head_bwd_kernel(const __nv_bfloat16* __restrict__ u, int h2s, int h2,
+                const __nv_bfloat16* __restrict__ W3, const float* __restrict__ b3,
+                const int32_t* __restrict__ cand, int Q, const int32_t* __restrict__ labels,
+                int kt, int B, float* __restrict__ gW3, float* __restrict__ gb3,
+                float* __restrict__ gb2, __nv_bfloat16* __restrict__ dh2,
+                float* __restrict__ loss) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= B) return;
+  const int32_t* cr = cand + (int64_t)i * Q;
+  const int nch = h2s / 8, nch2 = h2 / 8;
+  uint4 uc[kUChunks];
+  float z[kMaxQ];
+  head_logits(u + (int64_t)i * h2s, nch, W3, h2s, b3, cr, Q, lane, uc, z);
+  // targets: labels found in the shortlist, counted per slot
+  int32_t cp[kMaxQ];
+#pragma unroll
+  for (int j = 0; j < kMaxQ; ++j) cp[j] = j < Q ? cr[j] : -1;
+  float cnt[kMaxQ];
+#pragma unroll
+  for (int j = 0; j < kMaxQ; ++j) cnt[j] = 0.f;
+  for (int l = lane; l < kt; l += 32) {
+    const int32_t lab = labels[(int64_t)i * kt + l];
+#pragma unroll
+    for (int j = 0; j < kMaxQ; ++j) cnt[j] += (cp[j] >= 0 && lab == cp[j]) ? 1.f : 0.f;
+  }
+  float hits = 0.f;
+#pragma unroll
+  for (int j = 0; j < kMaxQ; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt[j] += __shfl_xor_sync(0xffffffffu, cnt[j], o);
+    hits += cnt[j];
+  }
+  __nv_bfloat16* drow = dh2 + (int64_t)i * h2;
+  if (hits == 0.f) {  // no target: neither loss nor gradient
+    for (int c = lane; c < h2; c += 32) drow[c] = __float2bfloat16_rn(0.f);
+    return;
+  }
+  float zmax = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < kMaxQ; ++j)
+    if (cp[j] >= 0) zmax = fmaxf(zmax, z[j]);
+  float sum = 0.f;
+#pragma unroll
+  for (int j = 0; j < kMaxQ; ++j)
+    if (cp[j] >= 0) sum += expf(z[j] - zmax);
+  const float lse = zmax + logf(sum);
+  const float inv_b = 1.f / (float)B;
+  float dz[kMaxQ];
+  float l = 0.f;
+#pragma unroll
+  for (int j = 0; j < kMaxQ; ++j) {
+    dz[j] = 0.f;
+    if (cp[j] < 0) continue;
+    const float qj = cnt[j] / hits;
+    dz[j] = (expf(z[j] - lse) - qj) * inv_b;
+    if (qj > 0.f) l -= qj * (z[j] - lse);
+  }
+  if (lane == 0) atomicAdd(loss, l * inv_b);
+  // last layer: bias and weight gradients of every shortlisted row of W3
+#pragma unroll
+  for (int j = 0; j < kMaxQ; ++j) {
+    if (cp[j] < 0) continue;
+    if (lane == 0) atomicAdd(&gb3[cp[j]], dz[j]);
+    float4* gr = reinterpret_cast<float4*>(gW3 + (int64_t)cp[j] * h2s);
+#pragma unroll
+    for (int q = 0; q < kUChunks; ++q) {
+      const int c = lane + 32 * q;
+      if (c >= nch) continue;
+      const __nv_bfloat162* x = reinterpret_cast<const __nv_bfloat162*>(&uc[q]);
+      const float2 a0 = __bfloat1622float2(x[0]), a1 = __bfloat1622float2(x[1]);
+      const float2 a2 = __bfloat1622float2(x[2]), a3 = __bfloat1622float2(x[3]);
+      atomicAdd(&gr[2 * c], make_float4(dz[j] * a0.x, dz[j] * a0.y, dz[j] * a1.x, dz[j] * a1.y));
+      atomicAdd(&gr[2 * c + 1], make_float4(dz[j] * a2.x, dz[j] * a2.y, dz[j] * a3.x, dz[j] * a3.y));
+    }
+  }
+  // hidden gradient through the h2 columns of the shortlisted rows, ReLU mask
+#pragma unroll
+  for (int q = 0; q < kUChunks; ++q) {
+    const int c = lane + 32 * q;
+    if (c >= nch2) continue;
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMaxQ; ++j) {
+      if (cp[j] < 0) continue;
+      const uint4 w = reinterpret_cast<const uint4*>(W3 + (int64_t)cp[j] * h2s)[c];
+      const __nv_bfloat162* wv = reinterpret_cast<const __nv_bfloat162*>(&w);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(wv[e]);
+        acc[2 * e] = fmaf(dz[j], f.x, acc[2 * e]);
+        acc[2 * e + 1] = fmaf(dz[j], f.y, acc[2 * e + 1]);
+      }
+    }
+    const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&uc[q]);
+    __align__(16) __nv_bfloat16 outv[8];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 h = __bfloat1622float2(hv[e]);
+      const float d0 = h.x > 0.f ? acc[2 * e] : 0.f;
+      const float d1 = h.y > 0.f ? acc[2 * e + 1] : 0.f;
+      atomicAdd(&gb2[8 * c + 2 * e], d0);
+      atomicAdd(&gb2[8 * c + 2 * e + 1], d1);
+      outv[2 * e] = __float2bfloat16_rn(d0);
+      outv[2 * e + 1] = __float2bfloat16_rn(d1);
+    }
+    reinterpret_cast<uint4*>(drow)[c] = *reinterpret_cast<const uint4*>(outv);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -332,14 +550,13 @@ bdg_status bdg_router_info(const bdg_router* r, float** params, float** grads, i
   return BDG_OK;
 }
 
-// Forward pass into caller-provided buffers: h1b [B][h1], h2b [B][h2s] (h2, then
-// the +-1 code), z [B][m].
-static bdg_status router_fwd(bdg_router* r, const void* x, const uint64_t* codes, int B, float* z,
-                             void* h1b, void* h2b, cudaStream_t st) {
+// Hidden layers into caller-provided buffers: h1b [B][h1], h2b [B][h2s] (h2,
+// then the +-1 code).
+static bdg_status router_hidden(bdg_router* r, const void* x, const uint64_t* codes, int B,
+                                void* h1b, void* h2b, cudaStream_t st) {
   const Offs o = param_offsets(r->d_in, r->h1, r->h2, r->h2s, r->m);
   const __nv_bfloat16* W1 = r->wb;
   const __nv_bfloat16* W2 = W1 + (int64_t)r->h1 * r->d_in;
-  const __nv_bfloat16* W3 = W2 + (int64_t)r->h2 * r->h1;
   BDG_TRY(bdg_gemm_bf16_ld(x, W1, B, r->h1, r->d_in, r->w + o.b1, nullptr, r->h1, 1, nullptr,
                            h1b, r->h1, nullptr, r->err, st));
   BDG_TRY(bdg_gemm_bf16_ld(h1b, W2, B, r->h2, r->h1, r->w + o.b2, nullptr, r->h2, 1, nullptr,
@@ -351,8 +568,38 @@ static bdg_status router_fwd(bdg_router* r, const void* x, const uint64_t* codes
     BDG_CUDA_TRY(cudaGetLastError());
     bdg_note_launch();
   }
+  return BDG_OK;
+}
+
+// Forward pass into caller-provided buffers: h1b [B][h1], h2b [B][h2s], z [B][m].
+static bdg_status router_fwd(bdg_router* r, const void* x, const uint64_t* codes, int B, float* z,
+                             void* h1b, void* h2b, cudaStream_t st) {
+  const Offs o = param_offsets(r->d_in, r->h1, r->h2, r->h2s, r->m);
+  const __nv_bfloat16* W3 = r->wb + (int64_t)r->h1 * r->d_in + (int64_t)r->h2 * r->h1;
+  BDG_TRY(router_hidden(r, x, codes, B, h1b, h2b, st));
   BDG_TRY(bdg_gemm_bf16_ld(h2b, W3, B, r->m, r->h2s, r->w + o.b3, nullptr, r->m, 0, z, nullptr,
                            r->m, nullptr, r->err, st));
+  return BDG_OK;
+}
+
+// One Adam step on the FP32 master weights from r->grad, then fresh BF16 copies.
+static bdg_status router_adam(bdg_router* r, float lr, cudaStream_t st) {
+  const int d = r->d_in, H1 = r->h1, H2 = r->h2, H2S = r->h2s, m = r->m;
+  const Offs o = param_offsets(d, H1, H2, H2S, m);
+  r->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)r->step), c2 = 1.f - powf(b2, (float)r->step);
+  adam_kernel<<<bdg_cdiv(r->n_params, 256), 256, 0, st>>>(r->w, r->grad, r->adam_m, r->adam_v,
+                                                          r->n_params, lr, b1, b2, 1e-8f, c1, c2);
+  bdg_note_launch();
+  f32_to_bf16<<<bdg_cdiv((int64_t)H1 * d, 256), 256, 0, st>>>(r->w + o.W1, r->wb,
+                                                              (int64_t)H1 * d);
+  f32_to_bf16<<<bdg_cdiv((int64_t)H2 * H1, 256), 256, 0, st>>>(
+      r->w + o.W2, r->wb + (int64_t)H1 * d, (int64_t)H2 * H1);
+  f32_to_bf16<<<bdg_cdiv((int64_t)m * H2S, 256), 256, 0, st>>>(
+      r->w + o.W3, r->wb + (int64_t)H1 * d + (int64_t)H2 * H1, (int64_t)m * H2S);
+  bdg_note_launch(3);
+  BDG_CUDA_TRY(cudaGetLastError());
   return BDG_OK;
 }
 
@@ -432,21 +679,7 @@ bdg_status bdg_router_train_step(bdg_router* r, const void* x, const uint64_t* c
   T((const __nv_bfloat16*)x, B, d, xT);
   BDG_TRY(bdg_gemm_bf16(dh1T, xT, H1, d, B, nullptr, nullptr, 0, r->grad + o.W1, nullptr, nullptr,
                         r->err, (void*)st));
-  if (apply_update) {
-    r->step += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - powf(b1, (float)r->step), c2 = 1.f - powf(b2, (float)r->step);
-    adam_kernel<<<bdg_cdiv(r->n_params, 256), 256, 0, st>>>(r->w, r->grad, r->adam_m, r->adam_v,
-                                                            r->n_params, lr, b1, b2, 1e-8f, c1, c2);
-    bdg_note_launch();
-    f32_to_bf16<<<bdg_cdiv((int64_t)H1 * d, 256), 256, 0, st>>>(r->w + o.W1, r->wb,
-                                                                (int64_t)H1 * d);
-    f32_to_bf16<<<bdg_cdiv((int64_t)H2 * H1, 256), 256, 0, st>>>(
-        r->w + o.W2, r->wb + (int64_t)H1 * d, (int64_t)H2 * H1);
-    f32_to_bf16<<<bdg_cdiv((int64_t)m * H2S, 256), 256, 0, st>>>(
-        r->w + o.W3, r->wb + (int64_t)H1 * d + (int64_t)H2 * H1, (int64_t)m * H2S);
-    bdg_note_launch(3);
-  }
+  if (apply_update) BDG_TRY(router_adam(r, lr, st));
   BDG_CUDA_TRY(cudaGetLastError());
   return BDG_OK;
 }
@@ -472,6 +705,142 @@ bdg_status bdg_router_route(bdg_router* r, const void* x, const uint64_t* codes,
     bdg_note_launch();
   }
   return BDG_OK;
+}
+
+
+// ---- shortlist head (see head_fwd_kernel / head_bwd_kernel)
+static bdg_status check_shortlist(const bdg_router* r, int32_t Q, const char* who) {
+  if (!r) return bdg_set_error(BDG_EINVAL, "%s: router is NULL", who);
+  if (Q < 1 || Q > kMaxQ)
+    return bdg_set_error(BDG_EINVAL, "%s: Q = %d (1..%d)", who, Q, kMaxQ);
+  if (r->h2s > kUChunks * 32 * 8)
+    return bdg_set_error(BDG_EUNSUPPORTED, "%s: last-layer input of %d values (at most %d)", who,
+                         r->h2s, kUChunks * 32 * 8);
+  return BDG_OK;
+}
+
+bdg_status bdg_router_forward_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
+                                        const int32_t* cand, int32_t Q, int32_t B,
+                                        float* logits, void* stream) {
+  BDG_TRY(check_shortlist(r, Q, "router_forward_shortlist"));
+  if (!x || !cand || !logits || B < 1 || B > r->cap_b || (r->cb && !codes))
+    return bdg_set_error(BDG_EINVAL, "router_forward_shortlist: B = %d (1..%d)%s", B, r->cap_b,
+                         r->cb && !codes ? ", codes required" : "");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* p = (char*)r->ws;
+  void* h1b = p; p += al((int64_t)r->cap_b * r->h1 * 2);
+  void* h2b = p;
+  BDG_TRY(router_hidden(r, x, codes, B, h1b, h2b, st));
+  const Offs o = param_offsets(r->d_in, r->h1, r->h2, r->h2s, r->m);
+  const __nv_bfloat16* W3 = r->wb + (int64_t)r->h1 * r->d_in + (int64_t)r->h2 * r->h1;
+  head_fwd_kernel<false><<<bdg_cdiv(B, 8), 256, 0, st>>>((const __nv_bfloat16*)h2b, r->h2s, W3,
+                                                          r->w + o.b3, cand, Q, B, logits, 0.f,
+                                                          1, nullptr);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
+
+bdg_status bdg_router_train_step_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
+                                           const int32_t* cand, int32_t Q, const int32_t* labels,
+                                           int32_t kt, int32_t B, float lr, int32_t apply_update,
+                                           void* stream) {
+  BDG_TRY(check_shortlist(r, Q, "router_train_step_shortlist"));
+  if (!x || !cand || !labels || B < 8 || B > r->cap_b || (B & 7) || kt < 1 ||
+      (r->cb && !codes))
+    return bdg_set_error(BDG_EINVAL,
+                         "router_train_step_shortlist: B = %d (8..%d, multiple of 8), kt = %d%s",
+                         B, r->cap_b, kt, r->cb && !codes ? ", codes required" : "");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = r->d_in, H1 = r->h1, H2 = r->h2, H2S = r->h2s, m = r->m;
+  const int64_t cap = r->cap_b;
+  const Offs o = param_offsets(d, H1, H2, H2S, m);
+  char* p = (char*)r->ws;
+  __nv_bfloat16* h1b = (__nv_bfloat16*)p; p += al(cap * H1 * 2);
+  __nv_bfloat16* h2b = (__nv_bfloat16*)p; p += al(cap * H2S * 2);
+  p += al(cap * m * 4) * 2 + al(cap * m * 2) * 2 + al(cap * H2S * 2);  // dense-head buffers
+  __nv_bfloat16* dh2 = (__nv_bfloat16*)p;  p += al(cap * H2 * 2);
+  __nv_bfloat16* h1T = (__nv_bfloat16*)p;  p += al(cap * H1 * 2);
+  __nv_bfloat16* dh1 = (__nv_bfloat16*)p;  p += al(cap * H1 * 2);
+  __nv_bfloat16* xT = (__nv_bfloat16*)p;   p += al(cap * d * 2);
+  __nv_bfloat16* dh2T = (__nv_bfloat16*)p; p += al(cap * H2 * 2);
+  __nv_bfloat16* dh1T = (__nv_bfloat16*)p; p += al(cap * H1 * 2);
+  p += al((int64_t)H2S * m * 2);           // W3T (dense head only)
+  __nv_bfloat16* W2T = (__nv_bfloat16*)p;
+  const __nv_bfloat16* W2 = r->wb + (int64_t)H1 * d;
+  const __nv_bfloat16* W3 = W2 + (int64_t)H2 * H1;
+  auto T = [&](const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    transpose_bf16<<<grid, block, 0, st>>>(in, rows, cols, out);
+    bdg_note_launch();
+  };
+  BDG_CUDA_TRY(cudaMemsetAsync(r->grad, 0, r->n_params * 4, st));
+  BDG_CUDA_TRY(cudaMemsetAsync(r->loss, 0, 4, st));
+  BDG_TRY(router_hidden(r, x, codes, B, h1b, h2b, st));
+  head_bwd_kernel<<<bdg_cdiv(B, 8), 256, 0, st>>>(h2b, H2S, H2, W3, r->w + o.b3, cand, Q, labels,
+                                                  kt, B, r->grad + o.W3, r->grad + o.b3,
+                                                  r->grad + o.b2, dh2, r->loss);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  // layer 2: dW2 = dh2^T h1, dh1 = (dh2 W2) * [h1 > 0], db1 = colsum(dh1)
+  T(dh2, B, H2, dh2T);
+  T(h1b, B, H1, h1T);
+  T(W2, H2, H1, W2T);
+  BDG_TRY(bdg_gemm_bf16(dh2T, h1T, H2, H1, B, nullptr, nullptr, 0, r->grad + o.W2, nullptr,
+                        nullptr, r->err, (void*)st));
+  BDG_TRY(bdg_gemm_bf16(dh2, W2T, B, H1, H2, nullptr, h1b, 0, nullptr, dh1, r->grad + o.b1,
+                        r->err, (void*)st));
+  // layer 1: dW1 = dh1^T x
+  T(dh1, B, H1, dh1T);
+  T((const __nv_bfloat16*)x, B, d, xT);
+  BDG_TRY(bdg_gemm_bf16(dh1T, xT, H1, d, B, nullptr, nullptr, 0, r->grad + o.W1, nullptr, nullptr,
+                        r->err, (void*)st));
+  if (apply_update) BDG_TRY(router_adam(r, lr, st));
+  BDG_CUDA_TRY(cudaGetLastError());
+  return BDG_OK;
+}
+
+bdg_status bdg_router_route_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
+                                      const int32_t* cand, int32_t Q, int64_t N, float theta,
+                                      int32_t pmax, int32_t* routes, float* logits,
+                                      void* stream) {
+  BDG_TRY(check_shortlist(r, Q, "router_route_shortlist"));
+  if (!x || !cand || !routes || N < 0 || pmax < 1 || pmax > Q || (r->cb && !codes) ||
+      !(theta >= 0.f))
+    return bdg_set_error(BDG_EINVAL, "router_route_shortlist: N = %lld, pmax = %d (1..Q = %d), "
+                         "theta = %g (>= 0)%s", (long long)N, pmax, Q, (double)theta,
+                         r->cb && !codes ? ", codes required" : "");
+  if (N == 0) return BDG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // inference runs in chunks of up to 2^18 points with its own stream-ordered
+  // workspace (h1 and [h2 | s] of one chunk)
+  const int64_t chunk = N < (1 << 18) ? N : (1 << 18);
+  void* ws = nullptr;
+  const size_t b1 = al(chunk * r->h1 * 2), b2 = al(chunk * r->h2s * 2);
+  if (cudaMallocAsync(&ws, b1 + b2, st) != cudaSuccess) {
+    cudaGetLastError();
+    return bdg_set_error(BDG_ENOMEM, "router_route_shortlist: workspace of %zu bytes", b1 + b2);
+  }
+  const Offs o = param_offsets(r->d_in, r->h1, r->h2, r->h2s, r->m);
+  const __nv_bfloat16* W3 = r->wb + (int64_t)r->h1 * r->d_in + (int64_t)r->h2 * r->h1;
+  bdg_status s = BDG_OK;
+  for (int64_t c0 = 0; c0 < N && s == BDG_OK; c0 += chunk) {
+    const int B = (int)((N - c0) < chunk ? (N - c0) : chunk);
+    void* h1b = ws;
+    void* h2b = (char*)ws + b1;
+    s = router_hidden(r, (const __nv_bfloat16*)x + c0 * r->d_in,
+                      r->cb ? codes + c0 * (r->cb / 64) : nullptr, B, h1b, h2b, st);
+    if (s != BDG_OK) break;
+    bdg_prof_scope prof("router_head", st);
+    head_fwd_kernel<true><<<bdg_cdiv(B, 8), 256, 0, st>>>(
+        (const __nv_bfloat16*)h2b, r->h2s, W3, r->w + o.b3, cand + c0 * Q, Q, B,
+        logits ? logits + c0 * Q : nullptr, theta, pmax, routes + c0 * pmax);
+    if (cudaGetLastError() != cudaSuccess)
+      s = bdg_set_error(BDG_ECUDA, "router_route_shortlist: head launch failed");
+    bdg_note_launch();
+  }
+  cudaFreeAsync(ws, st);
+  return s;
 }
 
 }  // extern "C"

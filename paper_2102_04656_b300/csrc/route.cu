@@ -187,11 +187,89 @@ __global__ void coarse_trim_kernel(int32_t* __restrict__ routes, int64_t n, int 
   }
 }
 
+// Distance-gap rule: slot s >= 1 stays only if its centre is at most delta
+// farther from the point than the home's centre.
+__global__ void gap_trim_kernel(int32_t* __restrict__ routes, const int32_t* __restrict__ rdist,
+                                int64_t n, int t, int delta) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n * t) return;
+  const int64_t i = x / t;
+  const int s = (int)(x - i * t);
+  if (s > 0 && rdist[x] - rdist[i * t] > delta) routes[x] = -1;
+}
+
 }  // namespace
+
+bdg_status bdg_launch_routes_gap(int32_t* routes, const int32_t* rdist, int64_t n, int t,
+                                 int delta, cudaStream_t st) {
+  if (n == 0) return BDG_OK;
+  gap_trim_kernel<<<bdg_cdiv(n * t, 256), 256, 0, st>>>(routes, rdist, n, t, delta);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
 
 bdg_status bdg_launch_route(const uint64_t* codes, int64_t n, int W, const uint64_t* cent, int m,
                             int t, int32_t* routes, int32_t* rdist, cudaStream_t st) {
   BDG_DISPATCH_W(W, route_w, codes, n, cent, m, t, routes, rdist, nullptr, st);
+}
+
+// ---- routing on the tensor cores. The t nearest centres of a point are its t
+// nearest "homes" in one partition whose homes are the m centres: the Reduce-1
+// tile of knn_tc.cu (FP8 +-1 MMA, fused (d, id) top-k) with the points as
+// visitors, k = t and no self pair. Centre index order is the home position
+// order, so ties fall by (d, c) exactly as in route_kernel; results are
+// identical. Work: n * m * bits MMA ops, against n * m * W XOR + POPC word pairs
+// on the ALU path.
+// Each 128-point item loads its visitors' codes into tensor memory once and
+// then runs m / 128 tiles, so the tensor path pays off only with many centres
+// (measured on B300: 10M points x 10,000 centres, 256-bit: 94-119 ms against
+// 169-212 ms on the ALU; 2M x 256 centres, 512-bit: 4.0 against 1.8 ms).
+constexpr int kRouteTcMinCentres = 1024;
+bool bdg_route_tc_ok(int W, int64_t n, int m, int t) {
+  return bdg_knn_tc_supported(W, t) && n < (int64_t(1) << 31) && m >= kRouteTcMinCentres &&
+         m < (1 << 21);
+}
+
+size_t bdg_route_tc_bytes(int64_t n, int m, int W, int t) {
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const int tile_v = bdg_knn_tile_visitors(W);
+  return al(bdg_csr_centres_bytes(n, m, tile_v)) + al(bdg_knn_tc_hexp_bytes(m, 1, W)) +
+         al((size_t)n) + al(64) + al((size_t)n * t * 4);
+}
+
+bdg_status bdg_launch_route_tc(const uint64_t* codes, int64_t n, int W, const uint64_t* cent,
+                               int m, int t, int32_t* routes, int32_t* rdist, void* scratch,
+                               size_t scratch_bytes, cudaStream_t st) {
+  if (n == 0) return BDG_OK;
+  if (scratch_bytes < bdg_route_tc_bytes(n, m, W, t))
+    return bdg_set_error(BDG_EINVAL, "route: tensor-path scratch too small");
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const int tile_v = bdg_knn_tile_visitors(W);
+  char* p = (char*)scratch;
+  bdg_csr csr;
+  BDG_TRY(bdg_build_csr_centres(cent, m, n, tile_v, p, &csr, st));
+  p += al(bdg_csr_centres_bytes(n, m, tile_v));
+  uint8_t* hexp = (uint8_t*)p;   p += al(bdg_knn_tc_hexp_bytes(m, 1, W));
+  int8_t* fixflag = (int8_t*)p;  p += al((size_t)n);
+  int32_t* err = (int32_t*)p;    p += al(64);
+  if (!rdist) rdist = (int32_t*)p;
+  BDG_CUDA_TRY(cudaMemsetAsync(fixflag, 0, al((size_t)n) + al(64), st));
+  bdg_knn_args a;
+  a.codes = codes; a.csr = csr; a.N = m; a.m = 1; a.t = 1; a.k = t; a.bits = 64 * W;
+  a.tile_v = tile_v; a.partial = nullptr; a.out_ids = routes; a.out_dist = rdist;
+  a.item_counter = csr.counters + 2;
+  a.out_by_pos = 1;
+  a.fixflag = nullptr;
+  a.home_kth = nullptr;
+  a.merge_running = 0;
+  a.prof = "route";
+  bdg_knn_tc_args ta;
+  ta.base = a;
+  ta.hexp = hexp;
+  ta.fixflag = fixflag;
+  ta.err = err;
+  return bdg_launch_knn_tc(ta, W, true, st);
 }
 
 bdg_status bdg_launch_routes_coarse(int32_t* routes, int64_t n, int t, int m, int64_t coarse,

@@ -33,17 +33,18 @@ class TrainConfig:
     k_labels: int = 32
 
 
-def prior_params(base_flat, d_in: int, h1: int, h2: int, m: int, centres):
+def prior_params(base_flat, d_in: int, h1: int, h2: int, m: int, centres, scale: float = 1.0):
     """Packed router parameters with a code input of the last layer: W1, b1, W2,
     b2 from ``base_flat`` (a packed d_in -> h1 -> h2 -> m vector), W3 =
-    [0 | (2 c_p - 1) / 2] with c_p the bits of centre p, b3 = 0. The logits are
-    then bits / 2 - d(y, c_p). centres: int64 [m, W] packed codes."""
+    [0 | scale (2 c_p - 1) / 2] with c_p the bits of centre p, b3 = 0. The logits
+    are then scale (bits / 2 - d(y, c_p)). centres: int64 [m, W] packed codes.
+    A power-of-two scale keeps the BF16 weights and FP32 sums exact."""
     W = centres.shape[1]
     bits = 64 * W
     n12 = h1 * d_in + h1 + h2 * h1 + h2
     shifts = torch.arange(64, device=centres.device, dtype=torch.int64)
     cb = ((centres[:, :, None] >> shifts) & 1).reshape(m, bits).to(torch.float32)
-    w3 = torch.cat([torch.zeros(m, h2, device=centres.device), cb - 0.5], dim=1)
+    w3 = torch.cat([torch.zeros(m, h2, device=centres.device), scale * (cb - 0.5)], dim=1)
     return torch.cat([base_flat[:n12].to(centres.device, torch.float32), w3.reshape(-1),
                       torch.zeros(m, device=centres.device)]).contiguous()
 
@@ -107,3 +108,72 @@ def train_router(feats_bf16, labels, m: int, init_params, cfg: TrainConfig, seed
 def learned_routes(router: Router, feats_bf16, home, P: int, codes=None):
     """int32 [N, P]: home first, then the router's P - 1 best other partitions."""
     return router.route(feats_bf16, home.to(torch.int32).contiguous(), P, codes=codes)
+
+
+# ---------------------------------------------------------------------------
+# Shortlist routing: the router scores only each point's Q nearest centres (the
+# Map step's shortlist, slot 0 = home) and chooses how many of them to probe.
+def train_router_shortlist(feats_bf16, codes, cand, labels, m: int, init_params,
+                           cfg: TrainConfig, seed: int, log=None) -> Router:
+    """Train the shortlist head (and the layers below it) with Adam on
+    (features, codes, shortlist, labels): labels are the homes of each row's
+    exact neighbours, home included. Seeded batch order. Returns the Router."""
+    S, d = feats_bf16.shape
+    h1, h2 = cfg.hidden
+    B = min(cfg.batch, S - S % 8)
+    r = Router(init_params, d, h1, h2, m, max_batch=max(B, 8), code_bits=64 * codes.shape[1])
+    rng = np.random.default_rng(seed)
+    for ep in range(cfg.epochs):
+        order = torch.from_numpy(rng.permutation(S)).to(feats_bf16.device)
+        last = None
+        for s in range(0, S - B + 1, B):
+            idx = order[s:s + B]
+            last = r.train_step_shortlist(feats_bf16[idx].contiguous(), cand[idx].contiguous(),
+                                          labels[idx].contiguous(), cfg.lr,
+                                          codes=codes[idx].contiguous())
+        if log is not None and last is not None:
+            log(ep, float(last.item()))
+    return r
+
+
+def prior_scale_loss(feats_bf16, codes, cand, labels, m: int, base_flat, centres, scales,
+                     hidden=(512, 512), batch: int = 4096):
+    """Shortlist cross-entropy of the untrained prior (logits a (bits/2 - d)) at
+    each scale a, on the first rows of the given set (no update): {a: loss}."""
+    d = feats_bf16.shape[1]
+    h1, h2 = hidden
+    B = min(batch, feats_bf16.shape[0] - feats_bf16.shape[0] % 8)
+    out = {}
+    for a in scales:
+        init = prior_params(base_flat, d, h1, h2, m, centres, scale=a)
+        r = Router(init, d, h1, h2, m, max_batch=B, code_bits=64 * codes.shape[1])
+        loss = r.train_step_shortlist(feats_bf16[:B].contiguous(), cand[:B].contiguous(),
+                                      labels[:B].contiguous(), 0.0, apply_update=False,
+                                      codes=codes[:B].contiguous())
+        out[a] = float(loss.item())
+        r.free()
+    return out
+
+
+def label_recall(routes, labels):
+    """Share of the rows' labels (homes of their exact neighbours, -1 ignored)
+    found among the rows' probed partitions: the id-based recall of a
+    partitioned build for those rows (a neighbour is found exactly when its home
+    is probed). routes: int32 [S, P] (-1 = none), labels: int32 [S, k]."""
+    hit = (labels[:, :, None] == routes[:, None, :]) & (routes[:, None, :] >= 0)
+    valid = labels >= 0
+    return float((hit.any(2) & valid).sum().item()) / max(1, int(valid.sum().item()))
+
+
+def calibrate(choose, values, labels, target: float):
+    """The first value (in the given order, cheapest first) whose routes reach
+    label recall >= target on the held-out rows; the last value if none does.
+    choose(v) -> routes of the held-out rows. Returns (value, recall, mean probes)."""
+    best = None
+    for v in values:
+        r = choose(v)
+        rec = label_recall(r, labels)
+        best = (v, rec, float((r >= 0).sum(1).float().mean().item()))
+        if rec >= target:
+            break
+    return best

@@ -191,6 +191,34 @@ def test_route_bit_exact(bdg, bits, t):
     assert np.array_equal(d.cpu().numpy(), d_o)
 
 
+@pytest.mark.parametrize("kernel", ["popc", "tc"])
+@pytest.mark.parametrize("bits,n,m,t", [(256, 3000, 2000, 16), (512, 1500, 1100, 8),
+                                        (256, 700, 1200, 1)])
+def test_route_kernels_bit_exact(bdg, kernel, bits, n, m, t, monkeypatch):
+    """Routing on the tensor cores (256/512-bit codes) and on the ALU give the
+    oracle's routes and distances, ties by centre index (duplicate centres,
+    ragged last centre tile, t up to 16)."""
+    monkeypatch.setenv("BDG_KNN_KERNEL", kernel)
+    c = datagen.make_codes(datagen.MixtureSpec(n, 64, 40, bits, seed=n + m))
+    ce = datagen.random_codes(m, bits, seed=m)
+    ce[5] = ce[m - 1]
+    ce[6] = c[3]  # a centre equal to a point: distance 0, not a self pair
+    r, d = bdg.route(c.cuda(), ce.cuda(), t)
+    r_o, d_o = oracle.route(_np(c), _np(ce), t)
+    assert np.array_equal(r.cpu().numpy(), r_o)
+    assert np.array_equal(d.cpu().numpy(), d_o)
+
+
+def test_routes_gap_bit_exact(bdg):
+    c = datagen.make_codes(datagen.MixtureSpec(5000, 64, 40, 256, seed=81))
+    ce = datagen.random_codes(1500, 256, seed=82)
+    r, d = bdg.route(c.cuda(), ce.cuda(), 8)
+    r_o, d_o = oracle.route(_np(c), _np(ce), 8)
+    for delta in (-1, 0, 2, 5, 300):
+        got = bdg.routes_gap(r.clone(), d, delta).cpu().numpy()
+        assert np.array_equal(got, oracle.routes_gap(r_o, d_o, delta)), delta
+
+
 # ------------------------------------------------------------------ partitioned build
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("bits,n,m,t,k", [(512, 20000, 16, 3, 64), (256, 9000, 40, 5, 32),
@@ -570,6 +598,70 @@ def test_build_plan_replays_bit_exact(bdg, kernel, tmp_path, monkeypatch):
     ids2, _ = oracle.knn_partitioned(_np(c2.cpu()), r2, 64)
     assert np.array_equal(plan.graph.ids.cpu().numpy(), ids2)
     plan.free()
+
+
+# ------------------------------------------------------------------ size classes
+def _class_routes(seed):
+    """Routes over 24 partitions whose home sets fall in all three size classes
+    (>= 4096, 512..4095, < 512 homes), t = 3 distinct partitions per point."""
+    rng = np.random.default_rng(seed)
+    sizes = [5000, 4096, 3000, 2100, 900, 512, 511, 400, 300, 200, 100, 60, 30, 8, 1, 0,
+             700, 1500, 2500, 350, 45, 3, 2, 77]
+    home = np.repeat(np.arange(24), sizes)
+    rng.shuffle(home)
+    n = home.size
+    r = np.empty((n, 3), np.int32)
+    r[:, 0] = home
+    for i in range(n):
+        r[i, 1:] = rng.choice(np.setdiff1d(np.arange(24), [home[i]]), 2, replace=False)
+    return r
+
+
+@pytest.mark.parametrize("kmap", [("tc", "popc32", "popc"), ("popc", "tc", "popc32"),
+                                  ("popc32", "popc32", "tc")])
+def test_size_class_variants_bit_exact(bdg, kmap):
+    """A build whose partition size classes run on different Reduce-1 variants
+    (tensor cores, popcount with 64- and 32-visitor sub-tiles) equals the oracle."""
+    r = _class_routes(7)
+    n, k = r.shape[0], 32
+    c = datagen.make_codes(datagen.MixtureSpec(n, 64, 40, 256, seed=700 + len(kmap[0])))
+    entry = torch.from_numpy(_entry(n, 32, 2)).cuda()
+    g = bdg.build_graph(c.cuda(), k, m=24, t=3, routes=torch.from_numpy(r).cuda(), entry=entry,
+                        class_kernel=kmap)
+    ids_o, dist_o = oracle.knn_partitioned(_np(c), r, k)
+    assert np.array_equal(g.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(g.dists.cpu().numpy(), dist_o)
+
+
+def test_build_plan_tunes_each_size_class(bdg, tmp_path, monkeypatch):
+    """The plan's autotuner times every variant on every size class, keeps the
+    fastest per class, caches the choice and builds the oracle's graph."""
+    monkeypatch.setenv("BDG_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    r = _class_routes(8)
+    n, k = r.shape[0], 32
+    c = datagen.make_codes(datagen.MixtureSpec(n, 64, 40, 256, seed=801)).cuda()
+    rt = torch.from_numpy(r).cuda()
+    entry = torch.from_numpy(_entry(n, 32, 2)).cuda()
+    plan = bdg.BuildPlan(c, k, m=24, t=3, routes=rt, entry=entry, kernel="auto")
+    plan.run()
+    torch.cuda.synchronize()
+    ids_o, dist_o = oracle.knn_partitioned(_np(c.cpu()), r, k)
+    assert np.array_equal(plan.graph.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(plan.graph.dists.cpu().numpy(), dist_o)
+    for cl in plan.classes:
+        assert set(cl["tuned_ms"]) == {"popc", "tc", "popc32"}
+        assert cl["variant"] == min(cl["tuned_ms"], key=cl["tuned_ms"].get)
+    line = (tmp_path / "tune.txt").read_text().split()
+    assert line[0].startswith("classes2|") and len(line) == 1 + 3 + 9
+    plan.free()
+    # a second plan of the same shape takes the cached choice without timing
+    plan2 = bdg.BuildPlan(c, k, m=24, t=3, routes=rt, entry=entry, kernel="auto")
+    assert [cl["variant"] for cl in plan2.classes] == [cl["variant"] for cl in plan.classes]
+    assert all(not cl["tuned_ms"] for cl in plan2.classes)
+    plan2.run()
+    torch.cuda.synchronize()
+    assert np.array_equal(plan2.graph.ids.cpu().numpy(), ids_o)
+    plan2.free()
 
 
 # ------------------------------------------------------------------ coarse_num (Section 3.2)

@@ -209,3 +209,104 @@ def test_prior_router_routes_like_nearest_centres(bdg):
     got = learned.learned_routes(r, x, torch.from_numpy(want[:, 0].copy()).cuda(), P,
                                  codes=ct.cuda()).cpu().numpy()
     assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------- shortlist head
+def _code_net(seed, d, h1, h2, m, bits):
+    flat, params = _net(seed, d, h1, h2, m)
+    rng = np.random.default_rng(seed + 1)
+    params["W3"] = rng.uniform(-0.1, 0.1, (m, h2 + bits))
+    params["b3"] = rng.uniform(-0.2, 0.2, m)
+    o = np.cumsum([0, h1 * d, h1, h2 * h1, h2])
+    flat = np.concatenate([flat[:o[-1]], params["W3"].reshape(-1), params["b3"]]).astype(np.float32)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):  # the oracle sees the fp32 values
+        params[k] = params[k].astype(np.float32).astype(np.float64)
+    return flat, params
+
+
+def _shortlist(B, m, Q, seed, holes=True):
+    rng = np.random.default_rng(seed)
+    cand = np.stack([rng.permutation(m)[:Q] for _ in range(B)]).astype(np.int32)
+    if holes:
+        cand[::7, Q - 1] = -1
+        cand[3::11, 2:] = -1
+    return cand
+
+
+def test_shortlist_forward_loss_and_gradients(bdg):
+    """Shortlist head: logits, loss and gradients of every parameter against the
+    float64 oracle, with missing candidates and rows without a shortlisted label."""
+    d, h1, h2, m, B, kt, bits, Q = 64, 32, 48, 64, 256, 16, 128, 8
+    flat, params = _code_net(41, d, h1, h2, m, bits)
+    r = bdg.Router(torch.from_numpy(flat).cuda(), d, h1, h2, m, max_batch=256, code_bits=bits)
+    x, lab = _batch(B, d, m, kt, 42)
+    ct, cu = _rand_codes(B, bits, 43)
+    s = omlp.code_pm(cu, bits)
+    cand = _shortlist(B, m, Q, 44)
+    lab[1::4, :3] = cand[1::4, :3]  # make sure many rows have shortlisted labels
+    xb, cd, cn = _bf16(x).cuda(), ct.cuda(), torch.from_numpy(cand).cuda()
+    z = r.forward_shortlist(xb, cn, codes=cd).cpu().numpy()
+    z_o, _ = omlp.shortlist_forward(params, x, cand, bf16=True, s=s)
+    fin = np.isfinite(z_o)
+    assert np.array_equal(np.isfinite(z), fin)
+    assert np.abs(z[fin] - z_o[fin]).max() <= 1e-2 * np.abs(z_o[fin]).max()
+    r.train_step_shortlist(xb, cn, torch.from_numpy(lab).cuda(), lr=0.0, apply_update=False,
+                           codes=cd)
+    torch.cuda.synchronize()
+    q = omlp.shortlist_targets(lab, cand)
+    assert (q.sum(1) == 0).any() and (q.sum(1) > 0).sum() > B // 2
+    loss_o, g_o, _ = omlp.shortlist_loss_and_grads(params, x, cand, q, bf16=True, s=s)
+    assert abs(float(r.loss.item()) - loss_o) <= 1e-3 * abs(loss_o)
+    g = r.unpack(r.grads.cpu())
+    for name in ["W1", "b1", "W2", "b2", "W3", "b3"]:
+        a, b_ = g[name].double().numpy(), g_o[name]
+        rel = np.linalg.norm(a - b_) / (np.linalg.norm(b_) + 1e-30)
+        assert rel <= 2e-2, (name, rel)
+    assert int(r.err.item()) == 0
+
+
+@pytest.mark.parametrize("theta,pmax", [(0.0, 4), (0.3, 8), (1.5, 5), (100.0, 8)])
+def test_shortlist_route_choice_bit_exact(bdg, theta, pmax):
+    """The probe choice of bdg_router_route_shortlist equals the oracle's rule
+    applied to the kernel's own FP32 logits (the decision is taken in FP32 on
+    both sides); the logits equal those of the forward entry point."""
+    d, h1, h2, m, N, bits, Q = 64, 32, 32, 304, 3000, 256, 8
+    flat, params = _code_net(51, d, h1, h2, m, bits)
+    r = bdg.Router(torch.from_numpy(flat).cuda(), d, h1, h2, m, max_batch=512, code_bits=bits)
+    x = _bf16(np.random.default_rng(52).standard_normal((N, d))).cuda()
+    ct, _ = _rand_codes(N, bits, 53)
+    cand = _shortlist(N, m, Q, 54)
+    cn = torch.from_numpy(cand).cuda()
+    routes, z = r.route_shortlist(x, cn, theta, pmax, codes=ct.cuda(), logits=True)
+    z = z.cpu().numpy()
+    want = omlp.shortlist_select(z, cand, theta, pmax)
+    assert np.array_equal(routes.cpu().numpy(), want)
+    z2 = r.forward_shortlist(x[:512], cn[:512], codes=ct[:512].cuda()).cpu().numpy()
+    assert np.array_equal(z2, z[:512])
+
+
+def test_shortlist_prior_routes_by_distance_gap(bdg):
+    """Untrained router with the prior at scale 1/8: the probe choice with theta =
+    (delta + 1/2) / 8 keeps exactly the shortlisted centres within delta of the
+    nearest one (distances from bdg_route, whose parity with the oracle is
+    tested), in (d, c) order."""
+    from paper_2102_04656_b300 import learned
+    d, h1, h2, m, N, bits, Q = 64, 32, 32, 1104, 4000, 256, 8
+    flat, _ = _net(61, d, h1, h2, m)
+    c = datagen.make_codes(datagen.MixtureSpec(N, 64, 30, bits, seed=62)).cuda()
+    cent = datagen.random_codes(m, bits, seed=63).cuda()
+    cent[9] = cent[400]
+    cand, rdist = bdg.route(c, cent, Q)
+    a = 0.125
+    init = learned.prior_params(torch.from_numpy(flat).cuda(), d, h1, h2, m, cent, scale=a)
+    r = bdg.Router(init, d, h1, h2, m, max_batch=512, code_bits=bits)
+    x = _bf16(np.random.default_rng(64).standard_normal((N, d))).cuda()
+    gap = (rdist - rdist[:, :1]).cpu().numpy()
+    cn = cand.cpu().numpy()
+    for delta, pmax in ((0, 3), (2, 8), (5, 6)):
+        got = r.route_shortlist(x, cand, a * (delta + 0.5), pmax, codes=c).cpu().numpy()
+        for i in range(N):
+            want = [int(cn[i, 0])] + [int(cn[i, j]) for j in range(1, Q)
+                                      if gap[i, j] <= delta][:pmax - 1]
+            want += [-1] * (pmax - len(want))
+            assert got[i].tolist() == want, (i, delta)

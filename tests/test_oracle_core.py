@@ -395,6 +395,41 @@ def test_routes_coarse_hand_worked_fixture(oracle_lib):
         assert np.array_equal(got, want), coarse
 
 
+def test_routes_gap_hand_worked(oracle_lib):
+    # point 0: centres 3, 1, 4 at 10, 12, 17 -> delta 2 keeps 3, 1; delta 7 keeps all
+    # point 1: centres 2, 0, 1 at 5, 5, 6 (a tie with the home) -> delta 0 keeps 2, 0
+    routes = np.array([[3, 1, 4], [2, 0, 1]], np.int32)
+    rdist = np.array([[10, 12, 17], [5, 5, 6]], np.int32)
+    assert oracle_lib.routes_gap(routes, rdist, 2).tolist() == [[3, 1, -1], [2, 0, 1]]
+    assert oracle_lib.routes_gap(routes, rdist, 0).tolist() == [[3, -1, -1], [2, 0, -1]]
+    assert oracle_lib.routes_gap(routes, rdist, 7).tolist() == [[3, 1, 4], [2, 0, 1]]
+    assert oracle_lib.routes_gap(routes, rdist, -1).tolist() == [[3, -1, -1], [2, -1, -1]]
+
+
+def test_routes_gap_against_per_bit_distances(oracle_lib):
+    """Kept slots are exactly those whose centre's per-bit Hamming distance to
+    the point exceeds the home centre's by at most delta; they form a prefix of
+    the nearest-centre order; more delta never keeps fewer."""
+    import datagen
+    bits, n, m, t = 128, 400, 30, 6
+    c = datagen.random_codes(n, bits, seed=71).numpy().view(np.uint64)
+    ce = datagen.random_codes(m, bits, seed=72).numpy().view(np.uint64)
+    r, d = oracle_lib.route(c, ce, t)
+    ub, ucb = datagen.unpack_bits(c, bits), datagen.unpack_bits(ce, bits)
+    prev = None
+    for delta in (-1, 0, 1, 3, 8, bits):
+        got = oracle_lib.routes_gap(r, d, delta)
+        for i in range(n):
+            dd = [int((ub[i] != ucb[r[i, s]]).sum()) for s in range(t)]
+            want = [int(r[i, s]) if s == 0 or dd[s] - dd[0] <= delta else -1 for s in range(t)]
+            assert got[i].tolist() == want
+        nk = (got >= 0).sum(1)
+        assert np.array_equal(got >= 0, np.arange(t)[None, :] < nk[:, None])
+        if prev is not None:
+            assert (nk >= prev).all()
+        prev = nk
+
+
 def _random_routes(n, m, t, seed):
     rng = np.random.default_rng(seed)
     sizes = rng.zipf(1.6, m).astype(np.float64)  # skewed partition sizes

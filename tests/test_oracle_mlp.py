@@ -162,3 +162,114 @@ def test_excluded_partition_is_left_out_of_the_softmax():
             flat[idx] = old
             fd = (lp - lm) / (2 * eps)
             assert abs(fd - g[name].reshape(-1)[idx]) < 1e-6 * max(1.0, abs(fd)), name
+
+
+# ---------------------------------------------------------------- shortlist head
+def _params_code(rng, d_in=6, h=5, m=9, cb=64, scale=0.5):
+    p = _params(rng, d_in, h, m, scale)
+    p["W3"] = rng.standard_normal((m, h + cb)) * scale
+    return p
+
+
+def test_shortlist_gradients_match_finite_differences():
+    rng = np.random.default_rng(10)
+    p = _params_code(rng)
+    B, Q, m = 6, 4, 9
+    x = rng.standard_normal((B, 6))
+    s = np.where(rng.random((B, 64)) < 0.5, 1.0, -1.0)
+    cand = np.array([rng.permutation(m)[:Q] for _ in range(B)])
+    cand[1, 3] = -1
+    cand[4, 2:] = -1
+    q = rng.random((B, Q)) * (cand >= 0)
+    q[2] = 0.0  # a row without target
+    q /= np.maximum(q.sum(1, keepdims=True), 1e-300)
+    _, g, _ = mlp.shortlist_loss_and_grads(p, x, cand, q, bf16=False, s=s)
+    eps = 1e-6
+    for name, w in p.items():
+        flat = w.reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 9)):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp, _, _ = mlp.shortlist_loss_and_grads(p, x, cand, q, bf16=False, s=s)
+            flat[idx] = old - eps
+            lm, _, _ = mlp.shortlist_loss_and_grads(p, x, cand, q, bf16=False, s=s)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - g[name].reshape(-1)[idx]) < 1e-6 * max(1.0, abs(fd)), name
+
+
+def test_shortlist_of_every_partition_is_the_dense_softmax():
+    """With every partition shortlisted (in index order) the shortlist head is the
+    full softmax cross-entropy over all m logits: loss, gradients and logits equal
+    the dense forms (which the finite-difference pin above checks)."""
+    rng = np.random.default_rng(11)
+    m, B = 7, 5
+    p = _params_code(rng, m=m, cb=64)
+    x = rng.standard_normal((B, 6))
+    s = np.where(rng.random((B, 64)) < 0.5, 1.0, -1.0)
+    labels = rng.integers(-1, m, size=(B, 6))
+    cand = np.tile(np.arange(m), (B, 1))
+    qs = mlp.shortlist_targets(labels, cand)
+    qd = mlp.label_targets(labels, m)
+    assert np.allclose(qs, qd)
+    ls, gs, zs = mlp.shortlist_loss_and_grads(p, x, cand, qs, bf16=False, s=s)
+    ld, gd, zd = mlp.loss_and_grads(p, x, qd, bf16=False, s=s)
+    assert abs(ls - ld) < 1e-12
+    assert np.allclose(zs, zd, rtol=0, atol=1e-12)
+    for k in gd:
+        assert np.allclose(gs[k], gd[k], rtol=0, atol=1e-12), k
+
+
+def test_shortlist_targets_hand_worked():
+    # row 0: labels 4, 4, 9 (9 not shortlisted) -> q = 1 on partition 4 (slot 1)
+    # row 1: labels 3, 5, 5, 8 over shortlist [5, 3, 8] -> 2/4, 1/4, 1/4
+    # row 2: no label shortlisted -> zero row
+    labels = np.array([[4, 4, 9, -1], [3, 5, 5, 8], [1, 1, 2, 2]])
+    cand = np.array([[7, 4, -1], [5, 3, 8], [6, 0, 3]])
+    q = mlp.shortlist_targets(labels, cand)
+    want = np.array([[0, 1, 0], [0.5, 0.25, 0.25], [0, 0, 0]])
+    assert np.allclose(q, want)
+
+
+def test_shortlist_select_hand_worked():
+    z = np.array([[1.0, 3.0, 2.5, 0.0, 2.5]], np.float32)
+    cand = np.array([[7, 2, 9, 4, 1]])
+    # largest logit 3.0: with theta = 1 the threshold is 2.0; kept (by -z, then
+    # partition): 2 (3.0), 1 (2.5), 9 (2.5); the home 7 is always slot 0
+    assert mlp.shortlist_select(z, cand, 1.0, 4).tolist() == [[7, 2, 1, 9]]
+    assert mlp.shortlist_select(z, cand, 1.0, 3).tolist() == [[7, 2, 1]]
+    assert mlp.shortlist_select(z, cand, 0.4, 4).tolist() == [[7, 2, -1, -1]]
+    assert mlp.shortlist_select(z, cand, 0.0, 2).tolist() == [[7, 2]]
+    assert mlp.shortlist_select(z, cand, 10.0, 6).tolist() == [[7, 2, 1, 9, 4, -1]]
+    # a missing candidate is never kept
+    cand2 = np.array([[7, 2, -1, 4, 1]])
+    assert mlp.shortlist_select(z, cand2, 10.0, 5).tolist() == [[7, 2, 1, 4, -1]]
+
+
+def test_shortlist_prior_margin_rule_is_the_distance_gap_rule(oracle_lib):
+    """With the prior weights at temperature a = 2^-3 (W3 = [0 | a (c_p - 1/2)],
+    b3 = 0) the shortlisted logits are a (bits/2 - d(y, c_p)), and keeping the
+    partitions within theta = a (delta + 1/2) of the largest logit keeps exactly
+    the shortlisted centres within delta of the nearest one: checked against the C
+    oracle's routes and distances."""
+    import datagen
+    rng = np.random.default_rng(12)
+    bits, m, n, Q, h = 128, 40, 300, 8, 5
+    codes = datagen.random_codes(n, bits, seed=5).numpy().view(np.uint64)
+    cent = datagen.random_codes(m, bits, seed=6).numpy().view(np.uint64)
+    r, d = oracle_lib.route(codes, cent, Q)
+    a = 0.125
+    p = _params(rng, 6, h, m)
+    p["W3"] = np.concatenate([np.zeros((m, h)), a * (mlp.code_pm(cent, bits) / 2.0)], axis=1)
+    p["b3"] = np.zeros(m)
+    x = rng.standard_normal((n, 6))
+    s = mlp.code_pm(codes, bits)
+    z, _ = mlp.shortlist_forward(p, x, r, bf16=True, s=s)
+    assert np.array_equal(z, a * (bits / 2.0 - d))
+    for delta, pmax in ((0, 4), (3, 8), (6, 5)):
+        sel = mlp.shortlist_select(z.astype(np.float32), r, a * (delta + 0.5), pmax)
+        for i in range(n):
+            want = [int(r[i, 0])] + [int(r[i, j]) for j in range(1, Q)
+                                     if d[i, j] - d[i, 0] <= delta][:pmax - 1]
+            want += [-1] * (pmax - len(want))
+            assert sel[i].tolist() == want
