@@ -210,6 +210,16 @@ bdg_status bdg_build_plan_kernel_ms(bdg_build_plan* plan, float* ms);
 /* The plan's graph (rows rewritten by every run), the chosen kernel (1 popcount,
  * 2 tensor) and, when the autotuner ran, both measured build times in ms (-1 if
  * not measured). */
+/* One build from host memory: copies host_codes ([N][W], the plan's codes
+ * size) into the device codes the plan was created with, replays the build and
+ * copies the graph rows back into host_ids (and host_dists unless NULL), each
+ * [N][k] int32, all enqueued on `stream` (asynchronous: synchronise the stream
+ * before reading the rows or reusing host_codes; page-locked host buffers let
+ * the copies run asynchronously). Plans on different streams overlap one
+ * build's copies with another's kernels. The paper's records arrive from and
+ * leave for disk; this is the host-memory boundary of one build. */
+bdg_status bdg_build_plan_run_host(bdg_build_plan* plan, const uint64_t* host_codes,
+                                   int32_t* host_ids, int32_t* host_dists, void* stream);
 bdg_status bdg_build_plan_info(const bdg_build_plan* plan, const bdg_graph** graph,
                                int32_t* kernel, float* ms_popc, float* ms_tc);
 /* The plan's Reduce-1 variant per partition size class (variant[3]: 1 popcount,
@@ -276,6 +286,17 @@ bdg_status bdg_build_sharded(const uint64_t* codes, int64_t N, int32_t bits, int
 bdg_status bdg_search_sharded(const bdg_graph* const* shards, int32_t S, const uint64_t* queries,
                               int64_t nq, const int32_t* ef, int32_t ef_max, int32_t R,
                               int32_t* out_ids, int32_t* out_dist, void* stream);
+
+/* Merge of partial k-lists (Shuffle 2 + Reduce 2 of Section 3.2 across GPUs):
+ * for each of n points, S sorted rows of k (id, distance) pairs from disjoint
+ * candidate sets (e.g. the rows that S ranks built over disjoint sets of
+ * partitions) become the first k pairs of their union by (distance, id).
+ * ids/dists: [S][n][k] int32 (device; id -1 = padding, skipped); out_ids /
+ * out_dists: [n][k], padded with (-1, bits + 1). 1 <= S <= 32, S k <= 6144.
+ * Asynchronous on `stream`. */
+bdg_status bdg_merge_lists(const int32_t* ids, const int32_t* dists, int32_t S, int64_t n,
+                           int32_t k, int32_t bits, int32_t* out_ids, int32_t* out_dists,
+                           void* stream);
 
 /* (Not in the paper) a search layout that trades device memory for latency:
  * stores, next to the graph's rows, the codes of every row's neighbours
@@ -434,12 +455,17 @@ bdg_status bdg_router_train_step_shortlist(bdg_router* r, const void* x, const u
                                            void* stream);
 /* routes: [N][pmax] int32 (device): the probe choice above, -1 after the last
  * kept partition; logits: [N][Q] FP32 or NULL. 1 <= pmax <= Q, theta >= 0.
- * Runs in chunks of up to 2^18 points with a stream-ordered workspace of
- * chunk x (h1 + h2 + code_bits) BF16 values; BDG_ENOMEM if it cannot be had. */
+ * order: NULL, or a permutation of 0..N-1 (device int32 [N]) in which the
+ * points are processed (results land in their own rows either way): points
+ * sharing a home share most of their shortlist, so the home order lets
+ * consecutive points reuse the same rows of W3 from cache. Runs in chunks of
+ * 2^16 points with a stream-ordered workspace of chunk x (h1 + h2 +
+ * code_bits) BF16 values (plus the chunk's gathered inputs with an order);
+ * BDG_ENOMEM if it cannot be had. */
 bdg_status bdg_router_route_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
                                       const int32_t* cand, int32_t Q, int64_t N, float theta,
-                                      int32_t pmax, int32_t* routes, float* logits,
-                                      void* stream);
+                                      int32_t pmax, const int32_t* order, int32_t* routes,
+                                      float* logits, void* stream);
 
 /* The router's tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulation):
  *   C[M][N] = epilogue(A[M][K] * B[N][K]^T), A and B row-major with K contiguous;

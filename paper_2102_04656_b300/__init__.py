@@ -56,6 +56,8 @@ def lib():
                                 _c_void_p, _c_void_p]
         L.bdg_routes_coarse.argtypes = [_c_void_p, _i64, _i32, _i32, _i64, _c_void_p, _c_void_p]
         L.bdg_routes_gap.argtypes = [_c_void_p, _c_void_p, _i64, _i32, _i32, _c_void_p]
+        L.bdg_merge_lists.argtypes = [_c_void_p, _c_void_p, _i32, _i64, _i32, _i32, _c_void_p,
+                                      _c_void_p, _c_void_p]
         L.bdg_bkmeans.argtypes = [_c_void_p, _i64, _i32, _c_void_p, _i64, _i32, _i32, _c_void_p,
                                   _c_void_p, _c_void_p]
         L.bdg_build_graph.argtypes = [_c_void_p, _i64, _i32, _i32, ctypes.POINTER(_Partitions),
@@ -158,6 +160,20 @@ def routes_gap(routes, rdist, delta: int, stream=None):
     _check(lib().bdg_routes_gap(_ptr(routes), _ptr(rdist), routes.shape[0], routes.shape[1],
                                 int(delta), _stream(stream)))
     return routes
+
+
+def merge_lists(ids, dists, bits: int, stream=None):
+    """First k of the union of S partial rows per point by (distance, id)
+    (bdg_merge_lists): ids/dists int32 [S, n, k] (disjoint candidate sets, -1 =
+    padding) -> (ids, dists) int32 [n, k]."""
+    _dev(ids, torch.int32, "ids", 3)
+    _dev(dists, torch.int32, "dists", 3)
+    S, n, k = ids.shape
+    oi = torch.empty(n, k, dtype=torch.int32, device=ids.device)
+    od = torch.empty(n, k, dtype=torch.int32, device=ids.device)
+    _check(lib().bdg_merge_lists(_ptr(ids), _ptr(dists), S, n, k, bits, _ptr(oi), _ptr(od),
+                                 _stream(stream)))
+    return oi, od
 
 
 def knn_rows(codes, rows, k: int, stream=None):
@@ -452,7 +468,7 @@ def _router_sigs(L):
                                                   _i32, _c_void_p]
     L.bdg_router_route_shortlist.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32,
                                              _i64, ctypes.c_float, _i32, _c_void_p, _c_void_p,
-                                             _c_void_p]
+                                             _c_void_p, _c_void_p]
     L._router_sigs = True
 
 
@@ -584,20 +600,26 @@ class Router:
         return self.loss
 
     def route_shortlist(self, x, cand, theta: float, pmax: int, codes=None, logits=False,
-                        stream=None):
+                        order=None, stream=None):
         """Probed partitions int32 [N, pmax] (-1 = none): the home cand[:, 0], then
         the shortlisted partitions within theta of the largest shortlisted logit.
-        With logits=True also returns the float32 [N, Q] logits."""
+        With logits=True also returns the float32 [N, Q] logits. order: optional
+        int32 [N] permutation the points are processed in (e.g. by home)."""
         _dev(x, torch.bfloat16, "x", 2)
         N = x.shape[0]
         c = self._codes(codes, N)
         cand = self._cand(cand, N)
+        if order is not None:
+            _dev(order, torch.int32, "order", 1)
+            if order.numel() != N:
+                raise ValueError("order must hold N entries")
         routes = torch.empty(N, pmax, dtype=torch.int32, device=x.device)
         z = (torch.empty(N, cand.shape[1], dtype=torch.float32, device=x.device)
              if logits else None)
         _check(lib().bdg_router_route_shortlist(self._h, _ptr(x), _ptr(c), _ptr(cand),
                                                 cand.shape[1], N, float(theta), pmax,
-                                                _ptr(routes), _ptr(z), _stream(stream)))
+                                                _ptr(order), _ptr(routes), _ptr(z),
+                                                _stream(stream)))
         return (routes, z) if logits else routes
 
     def free(self):
@@ -697,6 +719,8 @@ class BuildPlan:
                                                 ctypes.POINTER(_Partitions), _c_void_p,
                                                 ctypes.POINTER(_c_void_p)]
             L.bdg_build_plan_run.argtypes = [_c_void_p, _c_void_p]
+            L.bdg_build_plan_run_host.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p,
+                                                  _c_void_p]
             L.bdg_build_plan_kernel_ms.argtypes = [_c_void_p, ctypes.POINTER(ctypes.c_float)]
             L.bdg_build_plan_info.argtypes = [_c_void_p, ctypes.POINTER(_c_void_p),
                                               ctypes.POINTER(_i32),
@@ -745,6 +769,27 @@ class BuildPlan:
 
     def run(self, stream=None):
         _check(lib().bdg_build_plan_run(self._h, _stream(stream)))
+
+    def run_host(self, host_codes, host_ids, host_dists=None, stream=None):
+        """One build from host memory (bdg_build_plan_run_host): host_codes int64
+        [N, W] and host_ids / host_dists int32 [N, k] CPU tensors (page-locked for
+        asynchronous copies); asynchronous on `stream`."""
+        for t, nm, dt in ((host_codes, "host_codes", torch.int64),
+                          (host_ids, "host_ids", torch.int32),
+                          (host_dists, "host_dists", torch.int32)):
+            if t is not None and (t.is_cuda or not t.is_contiguous() or t.dtype != dt):
+                raise ValueError(f"{nm} must be a contiguous CPU {dt} tensor")
+        if tuple(host_codes.shape) != tuple(self._keep[0].shape):
+            raise ValueError("host_codes must have the shape of the plan's codes")
+        if tuple(host_ids.shape) != (self.graph.n, self.graph.k):
+            raise ValueError("host_ids must be [N, k]")
+        if host_dists is not None and tuple(host_dists.shape) != tuple(host_ids.shape):
+            raise ValueError("host_dists must be [N, k]")
+        _check(lib().bdg_build_plan_run_host(self._h, ctypes.c_void_p(host_codes.data_ptr()),
+                                             ctypes.c_void_p(host_ids.data_ptr()),
+                                             None if host_dists is None else
+                                             ctypes.c_void_p(host_dists.data_ptr()),
+                                             _stream(stream)))
 
     def kernel_ms(self) -> float:
         ms = ctypes.c_float()

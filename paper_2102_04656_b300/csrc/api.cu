@@ -700,6 +700,24 @@ bdg_status bdg_build_plan_run(bdg_build_plan* plan, void* stream) {
   return BDG_OK;
 }
 
+bdg_status bdg_build_plan_run_host(bdg_build_plan* plan, const uint64_t* host_codes,
+                                   int32_t* host_ids, int32_t* host_dists, void* stream) {
+  if (!plan || !plan->exec) return bdg_set_error(BDG_EINVAL, "plan: not instantiated");
+  if (!host_codes || !host_ids)
+    return bdg_set_error(BDG_EINVAL, "plan_run_host: host codes and ids are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bdg_graph* g = plan->g;
+  const size_t code_bytes = (size_t)g->n * g->W * 8, row_bytes = (size_t)g->n * g->k * 4;
+  BDG_CUDA_TRY(cudaMemcpyAsync(const_cast<uint64_t*>(g->codes), host_codes, code_bytes,
+                               cudaMemcpyHostToDevice, st));
+  BDG_CUDA_TRY(cudaGraphLaunch(plan->exec, st));
+  bdg_note_launch((int)plan->launches);
+  BDG_CUDA_TRY(cudaMemcpyAsync(host_ids, g->ids, row_bytes, cudaMemcpyDeviceToHost, st));
+  if (host_dists)
+    BDG_CUDA_TRY(cudaMemcpyAsync(host_dists, g->dists, row_bytes, cudaMemcpyDeviceToHost, st));
+  return BDG_OK;
+}
+
 bdg_status bdg_build_plan_kernel_ms(bdg_build_plan* plan, float* ms) {
   if (!plan || !ms) return bdg_set_error(BDG_EINVAL, "plan: null argument");
   BDG_CUDA_TRY(cudaEventSynchronize(plan->ev1));
@@ -1067,6 +1085,20 @@ bdg_status bdg_search_sharded(const bdg_graph* const* shards, int32_t S, const u
   }
   return bdg_launch_shard_merge(ids, dist, S, nq, R, off, ef, ef_max, shards[0]->bits, out_ids,
                                 out_dist, st);
+}
+
+bdg_status bdg_merge_lists(const int32_t* ids, const int32_t* dists, int32_t S, int64_t n,
+                           int32_t k, int32_t bits, int32_t* out_ids, int32_t* out_dists,
+                           void* stream) {
+  if (S < 1 || S > BDG_MAX_SHARDS || k < 1 || S * k > 6144 || n < 0 || bits < 64 || bits > 1024)
+    return bdg_set_error(BDG_EINVAL, "merge_lists: S = %d, k = %d, n = %lld, bits = %d "
+                         "(1 <= S <= %d, S k <= 6144)", S, k, (long long)n, bits,
+                         BDG_MAX_SHARDS);
+  if (n > 0 && (!ids || !dists || !out_ids || !out_dists))
+    return bdg_set_error(BDG_EINVAL, "merge_lists: null pointer");
+  bdg_shard_offsets off{};
+  return bdg_launch_shard_merge(ids, dists, S, n, k, off, nullptr, 0, bits, out_ids, out_dists,
+                                (cudaStream_t)stream);
 }
 
 bdg_status bdg_rerank(const float* feats, int64_t N, int32_t D, const float* qfeats,

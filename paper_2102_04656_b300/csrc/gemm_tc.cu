@@ -5,18 +5,22 @@
 // of the result (bias gradients), output FP32 or BF16.
 //
 // Persistent: one CTA per SM walks the 128 x 128 output tiles (n fastest, so
-// consecutive tiles of a CTA share their A rows in L2). Warps 4-7 stream 64-wide
-// K slabs of A and B into a 4-stage shared-memory ring with 16-byte cp.async
-// (zero-filled past the matrix edges) in the K-major no-swizzle core-matrix
-// layout; one thread of warp 8 issues tcgen05.mma kind::f16 (M = 128, N = 128,
-// K = 16 per instruction) into one of two TMEM accumulators, so the MMAs of the
-// next tile run while warps 0-3 drain the previous one. The epilogue reads its
-// accumulator rows (thread = row = TMEM lane) into a per-warp shared-memory
-// tile, hands the accumulator back, and then writes the tile row by row with
-// the 32 lanes on 32 consecutive columns: coalesced stores, coalesced bias and
-// mask reads, per-column sums in registers. Every mbarrier wait is bounded and
-// reports through an error word.
+// consecutive tiles of a CTA share their A rows in L2). One thread of warp 4
+// streams 64-wide K slabs of A and B into a 4-stage shared-memory ring with TMA
+// tensor copies (cp.async.bulk.tensor, 128-byte swizzle, zero fill past the
+// matrix edges) completing on mbarriers; one thread of warp 5 issues
+// tcgen05.mma kind::f16 (M = 128, N = 128, K = 16 per instruction) into one of
+// two TMEM accumulators, so the MMAs of the next tile run while warps 0-3 drain
+// the previous one. The epilogue reads its accumulator rows (thread = row =
+// TMEM lane) into a per-warp shared-memory tile, hands the accumulator back,
+// and then writes the tile row by row, each lane on 4 consecutive columns: 16-
+// or 8-byte coalesced stores, coalesced bias and mask reads, per-column sums in
+// registers. Every mbarrier wait is bounded and reports through an error word.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "common.cuh"
 #include "tc05.cuh"
@@ -24,13 +28,18 @@
 namespace {
 
 constexpr int kBM = 128, kBN = 128, kBK = 64;   // tile; K slab = 64 bf16 = 128 bytes
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr int kAcc = 2;                         // TMEM accumulators (128 columns each)
-constexpr int kThreads = 288;                   // 0-3 epilogue, 4-7 producer, 8 MMA
+constexpr int kThreads = 192;                   // 0-3 epilogue, 4 producer, 5 MMA
 constexpr uint32_t kSlab = kBM * kBK * 2;       // 16 KB per operand per stage
-constexpr uint32_t kRing = kStages * 2 * kSlab;  // 128 KB
-constexpr int kLd = kBN + 1;                    // staging row stride (floats): no bank conflicts
-constexpr uint32_t kStageBytes = 4u * 32 * kLd * 4;  // 4 warps x 32 rows x 129 floats
+constexpr uint32_t kRing = kStages * 2 * kSlab;  // 192 KB: the copies in flight
+// the epilogue stages half a tile (64 columns) at a time; row stride 68 floats:
+// 16-byte aligned rows, and a thread writing its row 16 bytes at a time or half
+// a warp reading one row 16 bytes per lane meet no bank conflicts
+constexpr int kHalfN = kBN / 2;
+constexpr int kLd = kHalfN + 4;
+constexpr uint32_t kStageBytes = 4u * 32 * kLd * 4;  // 4 warps x 32 rows x 68 floats
+static_assert(kRing + kStageBytes + 256 <= 232448, "shared memory per block exceeds 227 KB");
 constexpr uint32_t kPolls = 1u << 20;
 
 struct GemmArgs {
@@ -46,24 +55,49 @@ struct GemmArgs {
   int ldo;                 // row stride of the output (elements)
   float* colsum;           // [N] or NULL: += column sums of the result (before rounding)
   int32_t* err;
+  int vec_out;             // outputs 16-byte aligned with ldo % 4 == 0: 4-column stores
+  int direct;              // bias, BF16 output only (no mask, FP32 or column sums), M and N
+                           // multiples of the tile, ldo % 8 == 0, 16-byte aligned bias and
+                           // output: every thread stores its own row
 };
 
-// byte offset of (row r, 16-byte chunk c) inside one 128 x 128 B slab (K-major, no swizzle)
-__device__ __forceinline__ uint32_t slab_off(int r, int c) {
-  return (uint32_t)((r >> 3) * 1024 + c * 128 + (r & 7) * 16);
+// One 2D TMA box (64 K-elements x 128 rows of BF16) into shared memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst), "l"(map), "r"(x), "r"(y),
+      "r"(tc05::smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
+          tc05::smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
 }
 
-__device__ __forceinline__ void cp16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-               "r"(src_bytes)
-               : "memory");
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the
+// 128-byte swizzle: 8-row groups 1024 bytes apart (stride byte offset), the
+// leading byte offset unused, swizzle mode 2 (128 bytes).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused): 16 bytes
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 1024 bytes
+  d |= (uint64_t)1 << 46;                  // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_bf16_kernel(GemmArgs g, const __grid_constant__ CUtensorMap mapA,
+                 const __grid_constant__ CUtensorMap mapB) {
   extern __shared__ __align__(1024) uint8_t sm[];
   float* stage = reinterpret_cast<float*>(sm + kRing);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kRing + kStageBytes);
-  uint64_t* full = bars;                  // [kStages], 128 producer arrivals
+  uint64_t* full = bars;                  // [kStages], producer expect-tx + TMA bytes
   uint64_t* empty = bars + kStages;       // [kStages], MMA commit
   uint64_t* tfull = bars + 2 * kStages;   // [kAcc], MMA commit: accumulator ready
   uint64_t* tempty = tfull + kAcc;        // [kAcc], 4 epilogue warps: accumulator read
@@ -77,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
   if (warp == 0) tc05::tmem_alloc(tslot, kAcc * kBN);
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      tc05::mbar_init(&full[s], 128);
+      tc05::mbar_init(&full[s], 1);
       tc05::mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < kAcc; ++b) {
@@ -92,55 +126,32 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
   tc05::fence_after();
   const uint32_t tmem = *tslot;
 
-  if (warp >= 4 && warp < 8) {
-    // ---------------- producers: 128 threads, 2 x 1024 16-byte chunks per stage
-    const int p = tid - 128;
-    uint32_t gs = 0;  // slabs issued by this CTA so far (ring position)
-    bool ok = true;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int m0 = (tile / tiles_n) * kBM, n0 = (tile % tiles_n) * kBN;
-      for (int j = 0; j < nk; ++j, ++gs) {
-        const uint32_t s = gs % kStages, use = gs / kStages;
-        if (use > 0 && !tc05::mbar_wait(&empty[s], (use - 1) & 1, kPolls)) {
-          atomicExch(g.err, 11);
-          ok = false;
-          break;
-        }
-        const uint32_t sa = tc05::smem_u32(sm + s * 2 * kSlab), sb = sa + kSlab;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int x = p + 128 * q;                   // 0..1023
-          const int rr = x & 7, c = (x >> 3) & 7, grp = x >> 6;  // row-in-group fastest
-          const int r = grp * 8 + rr;
-          const int kk = j * kBK + c * 8;              // first element of the chunk
-          const int kv = max(0, min(8, g.K - kk));     // valid elements in this chunk
-          {
-            const int gr = m0 + r;
-            const bool in = gr < g.M && kv > 0;
-            const __nv_bfloat16* src = in ? g.A + (int64_t)gr * g.K + kk : g.A;
-            cp16(sa + slab_off(r, c), src, in ? kv * 2 : 0);
+  if (warp == 4) {
+    // ---------------- producer: one thread, two TMA boxes per stage
+    if (lane == 0) {
+      uint32_t gs = 0;  // slabs issued by this CTA so far (ring position)
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int m0 = (tile / tiles_n) * kBM, n0 = (tile % tiles_n) * kBN;
+        for (int j = 0; j < nk; ++j, ++gs) {
+          const uint32_t s = gs % kStages, use = gs / kStages;
+          if (use > 0 && !tc05::mbar_wait(&empty[s], (use - 1) & 1, kPolls)) {
+            atomicExch(g.err, 11);
+            ok = false;
+            break;
           }
-          {
-            const int gr = n0 + r;
-            const bool in = gr < g.N && kv > 0;
-            const __nv_bfloat16* src = in ? g.B + (int64_t)gr * g.K + kk : g.B;
-            cp16(sb + slab_off(r, c), src, in ? kv * 2 : 0);
-          }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        if (gs > 0) {  // the previous slab has landed: publish it to the tensor core
-          asm volatile("cp.async.wait_group 1;" ::: "memory");
-          tc05::fence_proxy_async();
-          tc05::mbar_arrive(&full[(gs - 1) % kStages]);
+          const uint32_t sa = tc05::smem_u32(sm + s * 2 * kSlab), sb = sa + kSlab;
+          expect_tx(&full[s], 2 * kSlab);
+          tma_load_2d(sa, &mapA, j * kBK, m0, &full[s]);
+          tma_load_2d(sb, &mapB, j * kBK, n0, &full[s]);
         }
       }
+      // copies issued but possibly never consumed (an MMA wait gave up): wait
+      // for them, bounded, before the CTA exits
+      for (uint32_t q = gs > kStages ? gs - kStages : 0; q < gs; ++q)
+        tc05::mbar_wait(&full[q % kStages], (q / kStages) & 1, kPolls);
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (ok && gs > 0) {
-      tc05::fence_proxy_async();
-      tc05::mbar_arrive(&full[(gs - 1) % kStages]);
-    }
-  } else if (warp == 8) {
+  } else if (warp == 5) {
     // ---------------- MMA issuer
     if (lane == 0) {
       constexpr uint32_t id = tc05::idesc(1u, 1u, kBM, kBN);  // BF16 x BF16 -> F32
@@ -163,9 +174,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
           tc05::fence_after();
           const uint32_t sa = tc05::smem_u32(sm + s * 2 * kSlab), sb = sa + kSlab;
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {  // 16 bf16 = 32 bytes = 2 core matrices
-            const uint64_t ad = tc05::sdesc(sa + kk * 256, 128, 1024);
-            const uint64_t bd = tc05::sdesc(sb + kk * 256, 128, 1024);
+          for (int kk = 0; kk < kBK / 16; ++kk) {  // 16 bf16 = 32 bytes within the swizzle atom
+            const uint64_t ad = sdesc_sw128(sa + kk * 32);
+            const uint64_t bd = sdesc_sw128(sb + kk * 32);
             tc05::mma_f16(tmem + b * kBN, ad, bd, id, (j > 0 || kk > 0) ? 1u : 0u);
           }
           tc05::commit(&empty[s]);
@@ -175,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
       tc05::commit(drain);
       if (!tc05::mbar_wait(drain, 0, kPolls)) atomicExch(g.err, 15);
     }
-  } else {
+  } else if (warp < 4) {
     // ---------------- epilogue: warp w owns rows 32w .. 32w + 31 of each tile
     float* st = stage + warp * 32 * kLd;
     uint32_t it = 0;
@@ -188,40 +199,136 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
         break;
       }
       tc05::fence_after();
-      // accumulator rows -> this warp's staging tile (thread = row)
+      const int row0 = m0 + 32 * warp;
+      if (g.direct) {
+        // inference layers (bias, optional ReLU, BF16 out, whole tile inside the
+        // matrix): each thread converts its own row and stores it, 8 values per
+        // 16-byte store, straight from the accumulator
+        const int row = row0 + lane;
+        __nv_bfloat16* orow = g.out_bf16 + (int64_t)row * g.ldo + n0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kBN; c0 += 32) {
+        for (int c0 = 0; c0 < kBN; c0 += 32) {
+          uint32_t v[32];
+          tc05::ld32(tmem + ((uint32_t)(32 * warp) << 16) + b * kBN + c0, v);
+          tc05::wait_ld();
+          if (c0 == kBN - 32) {  // the whole accumulator is read: hand it back
+            tc05::fence_before();
+            __syncwarp();
+            if (lane == 0) tc05::mbar_arrive(&tempty[b]);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 b0 = *reinterpret_cast<const float4*>(g.bias + n0 + c0 + 8 * q);
+            const float4 b1 = *reinterpret_cast<const float4*>(g.bias + n0 + c0 + 8 * q + 4);
+            float x[8] = {__uint_as_float(v[8 * q]) + b0.x, __uint_as_float(v[8 * q + 1]) + b0.y,
+                          __uint_as_float(v[8 * q + 2]) + b0.z, __uint_as_float(v[8 * q + 3]) + b0.w,
+                          __uint_as_float(v[8 * q + 4]) + b1.x, __uint_as_float(v[8 * q + 5]) + b1.y,
+                          __uint_as_float(v[8 * q + 6]) + b1.z, __uint_as_float(v[8 * q + 7]) + b1.w};
+            if (g.relu) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) x[e] = fmaxf(x[e], 0.f);
+            }
+            uint4 pk;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(x[0], x[1]);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(x[2], x[3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(x[4], x[5]);
+            __nv_bfloat162 h3 = __floats2bfloat162_rn(x[6], x[7]);
+            pk.x = *reinterpret_cast<uint32_t*>(&h0);
+            pk.y = *reinterpret_cast<uint32_t*>(&h1);
+            pk.z = *reinterpret_cast<uint32_t*>(&h2);
+            pk.w = *reinterpret_cast<uint32_t*>(&h3);
+            *reinterpret_cast<uint4*>(orow + c0 + 8 * q) = pk;
+          }
+        }
+        continue;
+      }
+      float csum[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      // the accumulator rows (thread = row): the first half into this warp's
+      // staging tile, the second half into registers; then the accumulator is
+      // handed back before any output is written
+      uint32_t v1[kHalfN];
+#pragma unroll
+      for (int c0 = 0; c0 < kHalfN; c0 += 32) {
         uint32_t v[32];
         tc05::ld32(tmem + ((uint32_t)(32 * warp) << 16) + b * kBN + c0, v);
+        tc05::ld32(tmem + ((uint32_t)(32 * warp) << 16) + b * kBN + kHalfN + c0,
+                   *reinterpret_cast<uint32_t(*)[32]>(&v1[c0]));
         tc05::wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) st[lane * kLd + c0 + j] = __uint_as_float(v[j]);
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(&st[lane * kLd + c0 + 4 * q]) =
+              make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                          __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
       }
       tc05::fence_before();
       __syncwarp();
-      if (lane == 0) tc05::mbar_arrive(&tempty[b]);  // the accumulator is free again
-      // staging tile -> output, row by row, lanes on consecutive columns
-      const int row0 = m0 + 32 * warp;
-#pragma unroll 1
-      for (int c0 = 0; c0 < kBN; c0 += 32) {
-        const int col = n0 + c0 + lane;
-        const bool cin = col < g.N;
-        const float bv = (g.bias && cin) ? g.bias[col] : 0.f;
-        float csum = 0.f;
-        for (int r = 0; r < 32; ++r) {
+      if (lane == 0) tc05::mbar_arrive(&tempty[b]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {  // two halves of 64 columns
+        if (h == 1) {
+          __syncwarp();  // the first half is written out: stage the second
+#pragma unroll
+          for (int q = 0; q < kHalfN / 4; ++q)
+            *reinterpret_cast<float4*>(&st[lane * kLd + 4 * q]) =
+                make_float4(__uint_as_float(v1[4 * q]), __uint_as_float(v1[4 * q + 1]),
+                            __uint_as_float(v1[4 * q + 2]), __uint_as_float(v1[4 * q + 3]));
+          __syncwarp();
+        }
+        // staging half -> output: half-warp rows, each lane on 4 consecutive columns
+        const int col = n0 + h * kHalfN + 4 * (lane & 15);
+        const int nc = max(0, min(4, g.N - col));  // valid columns of this lane
+        float bv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) bv[e] = (g.bias && e < nc) ? g.bias[col + e] : 0.f;
+        for (int r2 = 0; r2 < 32; r2 += 2) {
+          const int r = r2 + (lane >> 4);
           const int row = row0 + r;
-          if (row >= g.M) break;
-          float x = st[r * kLd + c0 + lane] + bv;
-          if (g.relu) x = fmaxf(x, 0.f);
-          if (g.mask && cin && !(__bfloat162float(g.mask[(int64_t)row * g.ldm + col]) > 0.f))
-            x = 0.f;
-          if (cin) {
-            if (g.out_f32) g.out_f32[(int64_t)row * g.ldo + col] = x;
-            if (g.out_bf16) g.out_bf16[(int64_t)row * g.ldo + col] = __float2bfloat16_rn(x);
-            csum += x;
+          if (row0 + r2 >= g.M) break;
+          const float4 a4 = *reinterpret_cast<const float4*>(&st[r * kLd + 4 * (lane & 15)]);
+          float x[4] = {a4.x + bv[0], a4.y + bv[1], a4.z + bv[2], a4.w + bv[3]};
+          const bool rin = row < g.M;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (g.relu) x[e] = fmaxf(x[e], 0.f);
+            if (g.mask && rin && e < nc &&
+                !(__bfloat162float(g.mask[(int64_t)row * g.ldm + col + e]) > 0.f))
+              x[e] = 0.f;
+            if (e >= nc || !rin) x[e] = 0.f;
+            csum[h][e] += x[e];
+          }
+          if (nc == 0 || !rin) continue;
+          const int64_t o = (int64_t)row * g.ldo + col;
+          if (g.vec_out && nc == 4) {
+            if (g.out_f32)
+              *reinterpret_cast<float4*>(g.out_f32 + o) = make_float4(x[0], x[1], x[2], x[3]);
+            if (g.out_bf16) {
+              __nv_bfloat162 p0 = __floats2bfloat162_rn(x[0], x[1]);
+              __nv_bfloat162 p1 = __floats2bfloat162_rn(x[2], x[3]);
+              uint2 pk;
+              pk.x = *reinterpret_cast<uint32_t*>(&p0);
+              pk.y = *reinterpret_cast<uint32_t*>(&p1);
+              *reinterpret_cast<uint2*>(g.out_bf16 + o) = pk;
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (e >= nc) break;
+              if (g.out_f32) g.out_f32[o + e] = x[e];
+              if (g.out_bf16) g.out_bf16[o + e] = __float2bfloat16_rn(x[e]);
+            }
           }
         }
-        if (g.colsum && cin) atomicAdd(&g.colsum[col], csum);
+      }
+      if (g.colsum) {  // the two half-warps' sums of each column, one atomic per column
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = n0 + h * kHalfN + 4 * (lane & 15);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float tot = csum[h][e] + __shfl_xor_sync(0xffffffffu, csum[h][e], 16);
+            if (lane < 16 && col + e < g.N) atomicAdd(&g.colsum[col + e], tot);
+          }
+        }
       }
       __syncwarp();  // the staging tile is reused by the next tile
     }
@@ -235,8 +342,47 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(GemmArgs g) {
 
 size_t bdg_gemm_smem_bytes() { return (size_t)kRing + kStageBytes + 256; }
 
+namespace {
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of a row-major [rows][K] BF16 matrix: boxes of 64 K-elements
+// (128 bytes) x 128 rows, 128-byte swizzle, zeros outside the matrix.
+bdg_status encode_operand(CUtensorMap* map, const void* base, int rows, int K) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return bdg_set_error(BDG_ECUDA, "gemm: cuTensorMapEncodeTiled is unavailable");
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return bdg_set_error(BDG_EINVAL, "gemm: tensor map of a %d x %d operand refused (%d)", rows,
+                         K, (int)r);
+  return BDG_OK;
+}
+
+}  // namespace
+
 // C = epilogue(A * B^T) with row strides for the mask and the output; see GemmArgs.
-// K % 8 == 0 (16-byte rows); ldm, ldo >= N.
+// K % 8 == 0 (16-byte rows), A and B 16-byte aligned; ldm, ldo >= N.
 bdg_status bdg_gemm_bf16_ld(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
                             const float* bias, const void* mask, int32_t ldm, int32_t relu,
                             float* out_f32, void* out_bf16, int32_t ldo, float* colsum,
@@ -244,16 +390,26 @@ bdg_status bdg_gemm_bf16_ld(const void* A, const void* B, int32_t M, int32_t N, 
   if (M <= 0 || N <= 0 || K <= 0 || (K & 7) || ldm < N || ldo < N)
     return bdg_set_error(BDG_EINVAL, "gemm: M=%d N=%d K=%d ldm=%d ldo=%d (K %% 8 == 0)", M, N,
                          K, ldm, ldo);
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+    return bdg_set_error(BDG_EINVAL, "gemm: A and B must be 16-byte aligned");
+  CUtensorMap mapA, mapB;
+  BDG_TRY(encode_operand(&mapA, A, M, K));
+  BDG_TRY(encode_operand(&mapB, B, N, K));
+  const bool vec = (ldo % 4 == 0) && ((uintptr_t)out_f32 % 16 == 0) &&
+                   ((uintptr_t)out_bf16 % 16 == 0);
+  const bool direct = bias && out_bf16 && !out_f32 && !mask && !colsum && (M % kBM == 0) &&
+                      (N % kBN == 0) && (ldo % 8 == 0) && ((uintptr_t)bias % 16 == 0) &&
+                      ((uintptr_t)out_bf16 % 16 == 0);
   GemmArgs g{(const __nv_bfloat16*)A, (const __nv_bfloat16*)B, M, N, K, bias,
              (const __nv_bfloat16*)mask, ldm, relu, out_f32, (__nv_bfloat16*)out_bf16, ldo,
-             colsum, err};
+             colsum, err, vec ? 1 : 0, direct ? 1 : 0};
   const size_t smem = bdg_gemm_smem_bytes();
   BDG_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   const int64_t ntiles = (int64_t)((N + kBN - 1) / kBN) * ((M + kBM - 1) / kBM);
   const int grid = (int)(ntiles < bdg_num_sms() ? ntiles : bdg_num_sms());
   bdg_prof_scope prof("gemm", st);
-  gemm_bf16_kernel<<<grid, kThreads, smem, st>>>(g);
+  gemm_bf16_kernel<<<grid, kThreads, smem, st>>>(g, mapA, mapB);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   return BDG_OK;

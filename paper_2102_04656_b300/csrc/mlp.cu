@@ -308,47 +308,132 @@ __device__ __forceinline__ void head_logits(const __nv_bfloat16* __restrict__ ur
   }
 }
 
-template <bool SELECT>
+// Inference head: UC 16-byte chunks of u per lane (u held as FP32 in registers),
+// a candidate's W3 chunks requested before its products are summed, and the
+// probe choice made by all lanes at once (lane j ranks candidate j).
+template <int UC>
 __global__ void __launch_bounds__(256)
-head_fwd_kernel(const __nv_bfloat16* __restrict__ u, int h2s, const __nv_bfloat16* __restrict__ W3,
-                const float* __restrict__ b3, const int32_t* __restrict__ cand, int Q, int rows,
-                float* __restrict__ z_out, float theta, int pmax, int32_t* __restrict__ routes) {
+head_route_kernel(const __nv_bfloat16* __restrict__ u, int h2s,
+                  const __nv_bfloat16* __restrict__ W3, const float* __restrict__ b3,
+                  const int32_t* __restrict__ cand, int Q, int rows, float* __restrict__ z_out,
+                  float theta, int pmax, int32_t* __restrict__ routes,
+                  const int32_t* __restrict__ out_row, int64_t n_out) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= rows) return;
+  // the output row of this input row (out_row: a processing order's rows)
+  const int64_t orow = out_row ? (int64_t)out_row[i] : (int64_t)i;
+  if (orow < 0 || orow >= n_out) return;
+  const int nch = h2s / 8;
   const int32_t* cr = cand + (int64_t)i * Q;
-  uint4 uc[kUChunks];
-  float z[kMaxQ];
-  head_logits(u + (int64_t)i * h2s, h2s / 8, W3, h2s, b3, cr, Q, lane, uc, z);
-  if (z_out) {
+  const int32_t myp = lane < Q ? cr[lane] : -1;  // lane j's candidate
+  float uf[UC][8];
+  {
+    const uint4* urow = reinterpret_cast<const uint4*>(u + (int64_t)i * h2s);
 #pragma unroll
-    for (int j = 0; j < kMaxQ; ++j)
-      if (j < Q && lane == j) z_out[(int64_t)i * Q + j] = z[j];
-  }
-  if (!SELECT || lane != 0) return;
-  int32_t cp[kMaxQ];
-  float zmax = -INFINITY;
+    for (int q = 0; q < UC; ++q) {
+      const int c = lane + 32 * q;
+      const uint4 x = c < nch ? urow[c] : make_uint4(0, 0, 0, 0);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&x);
 #pragma unroll
-  for (int j = 0; j < kMaxQ; ++j) {
-    cp[j] = j < Q ? cr[j] : -1;
-    if (cp[j] >= 0) zmax = fmaxf(zmax, z[j]);
-  }
-  const float thr = zmax - theta;
-  int32_t* out = routes + (int64_t)i * pmax;
-  out[0] = cp[0];
-  uint32_t taken = 1u;  // slot 0 (the home) is always probed
-  for (int r = 1; r < pmax; ++r) {
-    int best = -1;
-    float bz = 0.f;
-    int32_t bp = 0;
-#pragma unroll
-    for (int j = 1; j < kMaxQ; ++j) {
-      if (cp[j] < 0 || ((taken >> j) & 1u) || !(z[j] >= thr)) continue;
-      if (best < 0 || z[j] > bz || (z[j] == bz && cp[j] < bp)) { best = j; bz = z[j]; bp = cp[j]; }
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(h[e]);
+        uf[q][2 * e] = f.x;
+        uf[q][2 * e + 1] = f.y;
+      }
     }
-    out[r] = best < 0 ? -1 : bp;
-    if (best >= 0) taken |= 1u << best;
   }
+  float zl = -INFINITY;  // lane j ends with z_j
+  for (int j = 0; j < Q; ++j) {
+    const int32_t p = __shfl_sync(0xffffffffu, myp, j);
+    if (p < 0) continue;
+    const uint4* wr = reinterpret_cast<const uint4*>(W3 + (int64_t)p * h2s);
+    uint4 w[UC];
+#pragma unroll
+    for (int q = 0; q < UC; ++q) {
+      const int c = lane + 32 * q;
+      w[q] = c < nch ? wr[c] : make_uint4(0, 0, 0, 0);
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < UC; ++q) {
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&w[q]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(h[e]);
+        acc = fmaf(uf[q][2 * e], f.x, acc);
+        acc = fmaf(uf[q][2 * e + 1], f.y, acc);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == j) zl = acc + b3[p];
+  }
+  if (z_out && lane < Q) z_out[orow * Q + lane] = zl;
+  if (routes == nullptr) return;
+  // probe choice: the home, then the others within theta of the best, by (-z, p)
+  float zmax = myp >= 0 ? zl : -INFINITY;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+  const float thr = zmax - theta;
+  const bool kept = lane >= 1 && myp >= 0 && zl >= thr;
+  int rank = 0;  // kept candidates ahead of this one
+  for (int j = 1; j < Q; ++j) {
+    const float zj = __shfl_sync(0xffffffffu, zl, j);
+    const int32_t pj = __shfl_sync(0xffffffffu, myp, j);
+    const bool kj = pj >= 0 && zj >= thr;
+    rank += (kj && (zj > zl || (zj == zl && pj < myp))) ? 1 : 0;
+  }
+  const int nkept = __popc(__ballot_sync(0xffffffffu, kept));
+  int32_t* out = routes + orow * pmax;
+  if (lane == 0) out[0] = myp;
+  if (kept && rank < pmax - 1) out[1 + rank] = myp;
+  if (lane >= nkept && lane < pmax - 1) out[1 + lane] = -1;
+}
+
+// dst[j] = src[idx[j]] for rows of row_words 32-bit words; an index outside
+// [0, n_src) gives a zero row
+__global__ void gather_words(const uint32_t* __restrict__ src, int64_t n_src, int row_words,
+                             const int32_t* __restrict__ idx, int64_t n,
+                             uint32_t* __restrict__ dst) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n * row_words) return;
+  const int64_t j = x / row_words;
+  const int w = (int)(x - j * row_words);
+  const int32_t r = idx[j];
+  dst[x] = (r >= 0 && r < n_src) ? src[(int64_t)r * row_words + w] : 0u;
+}
+
+bdg_status gather_rows_words(const void* src, int64_t n_src, int row_words, const int32_t* idx,
+                             int64_t n, void* dst, cudaStream_t st) {
+  if (n == 0) return BDG_OK;
+  gather_words<<<bdg_cdiv(n * row_words, 256), 256, 0, st>>>(
+      (const uint32_t*)src, n_src, row_words, idx, n, (uint32_t*)dst);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
+
+bdg_status launch_head_route(const __nv_bfloat16* u, int h2s, const __nv_bfloat16* W3,
+                             const float* b3, const int32_t* cand, int Q, int rows, float* z_out,
+                             float theta, int pmax, int32_t* routes, cudaStream_t st,
+                             const int32_t* out_row = nullptr, int64_t n_out = -1) {
+  const int uc = (h2s / 8 + 31) / 32;
+  const int grid = bdg_cdiv(rows, 8);
+  if (n_out < 0) n_out = rows;
+  if (uc <= 1)
+    head_route_kernel<1><<<grid, 256, 0, st>>>(u, h2s, W3, b3, cand, Q, rows, z_out, theta, pmax, routes, out_row, n_out);
+  else if (uc <= 2)
+    head_route_kernel<2><<<grid, 256, 0, st>>>(u, h2s, W3, b3, cand, Q, rows, z_out, theta, pmax, routes, out_row, n_out);
+  else if (uc <= 3)
+    head_route_kernel<3><<<grid, 256, 0, st>>>(u, h2s, W3, b3, cand, Q, rows, z_out, theta, pmax, routes, out_row, n_out);
+  else if (uc <= 4)
+    head_route_kernel<4><<<grid, 256, 0, st>>>(u, h2s, W3, b3, cand, Q, rows, z_out, theta, pmax, routes, out_row, n_out);
+  else
+    head_route_kernel<8><<<grid, 256, 0, st>>>(u, h2s, W3, b3, cand, Q, rows, z_out, theta, pmax, routes, out_row, n_out);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
 }
 
 // Shortlist cross-entropy and its backward through the last layer, one warp per
@@ -708,7 +793,7 @@ bdg_status bdg_router_route(bdg_router* r, const void* x, const uint64_t* codes,
 }
 
 
-// ---- shortlist head (see head_fwd_kernel / head_bwd_kernel)
+// ---- shortlist head (see head_route_kernel / head_bwd_kernel)
 static bdg_status check_shortlist(const bdg_router* r, int32_t Q, const char* who) {
   if (!r) return bdg_set_error(BDG_EINVAL, "%s: router is NULL", who);
   if (Q < 1 || Q > kMaxQ)
@@ -733,12 +818,8 @@ bdg_status bdg_router_forward_shortlist(bdg_router* r, const void* x, const uint
   BDG_TRY(router_hidden(r, x, codes, B, h1b, h2b, st));
   const Offs o = param_offsets(r->d_in, r->h1, r->h2, r->h2s, r->m);
   const __nv_bfloat16* W3 = r->wb + (int64_t)r->h1 * r->d_in + (int64_t)r->h2 * r->h1;
-  head_fwd_kernel<false><<<bdg_cdiv(B, 8), 256, 0, st>>>((const __nv_bfloat16*)h2b, r->h2s, W3,
-                                                          r->w + o.b3, cand, Q, B, logits, 0.f,
-                                                          1, nullptr);
-  BDG_CUDA_TRY(cudaGetLastError());
-  bdg_note_launch();
-  return BDG_OK;
+  return launch_head_route((const __nv_bfloat16*)h2b, r->h2s, W3, r->w + o.b3, cand, Q, B, logits,
+                           0.f, 1, nullptr, st);
 }
 
 bdg_status bdg_router_train_step_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
@@ -802,8 +883,8 @@ bdg_status bdg_router_train_step_shortlist(bdg_router* r, const void* x, const u
 
 bdg_status bdg_router_route_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
                                       const int32_t* cand, int32_t Q, int64_t N, float theta,
-                                      int32_t pmax, int32_t* routes, float* logits,
-                                      void* stream) {
+                                      int32_t pmax, const int32_t* order, int32_t* routes,
+                                      float* logits, void* stream) {
   BDG_TRY(check_shortlist(r, Q, "router_route_shortlist"));
   if (!x || !cand || !routes || N < 0 || pmax < 1 || pmax > Q || (r->cb && !codes) ||
       !(theta >= 0.f))
@@ -812,32 +893,53 @@ bdg_status bdg_router_route_shortlist(bdg_router* r, const void* x, const uint64
                          r->cb && !codes ? ", codes required" : "");
   if (N == 0) return BDG_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  // inference runs in chunks of up to 2^18 points with its own stream-ordered
-  // workspace (h1 and [h2 | s] of one chunk)
-  const int64_t chunk = N < (1 << 18) ? N : (1 << 18);
+  // inference runs in chunks of 2^16 points with its own stream-ordered
+  // workspace: h1 and [h2 | s] of one chunk (160 MB at 512-wide layers and
+  // 256-bit codes, mostly held in L2 between the layers), and with an order the
+  // chunk's gathered inputs
+  const int64_t chunk = N < (1 << 16) ? N : (1 << 16);
+  const int cw = r->cb / 64;
   void* ws = nullptr;
   const size_t b1 = al(chunk * r->h1 * 2), b2 = al(chunk * r->h2s * 2);
-  if (cudaMallocAsync(&ws, b1 + b2, st) != cudaSuccess) {
+  const size_t bx = order ? al(chunk * r->d_in * 2) : 0, bc = order && cw ? al(chunk * cw * 8) : 0,
+               bq = order ? al(chunk * Q * 4) : 0;
+  if (cudaMallocAsync(&ws, b1 + b2 + bx + bc + bq, st) != cudaSuccess) {
     cudaGetLastError();
-    return bdg_set_error(BDG_ENOMEM, "router_route_shortlist: workspace of %zu bytes", b1 + b2);
+    return bdg_set_error(BDG_ENOMEM, "router_route_shortlist: workspace of %zu bytes",
+                         b1 + b2 + bx + bc + bq);
   }
   const Offs o = param_offsets(r->d_in, r->h1, r->h2, r->h2s, r->m);
   const __nv_bfloat16* W3 = r->wb + (int64_t)r->h1 * r->d_in + (int64_t)r->h2 * r->h1;
+  char* gx = (char*)ws + b1 + b2;
+  char* gc = gx + bx;
+  char* gq = gc + bc;
   bdg_status s = BDG_OK;
   for (int64_t c0 = 0; c0 < N && s == BDG_OK; c0 += chunk) {
     const int B = (int)((N - c0) < chunk ? (N - c0) : chunk);
     void* h1b = ws;
     void* h2b = (char*)ws + b1;
-    s = router_hidden(r, (const __nv_bfloat16*)x + c0 * r->d_in,
-                      r->cb ? codes + c0 * (r->cb / 64) : nullptr, B, h1b, h2b, st);
+    const void* xc = (const __nv_bfloat16*)x + c0 * r->d_in;
+    const uint64_t* cc = cw ? codes + c0 * cw : nullptr;
+    const int32_t* qc = cand + c0 * Q;
+    if (order) {  // this chunk's rows of the processing order, gathered
+      s = gather_rows_words(x, N, r->d_in / 2, order + c0, B, gx, st);
+      if (s == BDG_OK && cw) s = gather_rows_words(codes, N, cw * 2, order + c0, B, gc, st);
+      if (s == BDG_OK) s = gather_rows_words(cand, N, Q, order + c0, B, gq, st);
+      if (s != BDG_OK) break;
+      xc = gx;
+      cc = cw ? (const uint64_t*)gc : nullptr;
+      qc = (const int32_t*)gq;
+    }
+    s = router_hidden(r, xc, cc, B, h1b, h2b, st);
     if (s != BDG_OK) break;
     bdg_prof_scope prof("router_head", st);
-    head_fwd_kernel<true><<<bdg_cdiv(B, 8), 256, 0, st>>>(
-        (const __nv_bfloat16*)h2b, r->h2s, W3, r->w + o.b3, cand + c0 * Q, Q, B,
-        logits ? logits + c0 * Q : nullptr, theta, pmax, routes + c0 * pmax);
-    if (cudaGetLastError() != cudaSuccess)
-      s = bdg_set_error(BDG_ECUDA, "router_route_shortlist: head launch failed");
-    bdg_note_launch();
+    if (order)
+      s = launch_head_route((const __nv_bfloat16*)h2b, r->h2s, W3, r->w + o.b3, qc, Q, B, logits,
+                            theta, pmax, routes, st, order + c0, N);
+    else
+      s = launch_head_route((const __nv_bfloat16*)h2b, r->h2s, W3, r->w + o.b3, qc, Q, B,
+                            logits ? logits + c0 * Q : nullptr, theta, pmax, routes + c0 * pmax,
+                            st);
   }
   cudaFreeAsync(ws, st);
   return s;

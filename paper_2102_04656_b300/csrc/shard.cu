@@ -1,7 +1,10 @@
 // shard.cu -- the merge step of a multi-shard search (Sections 3.4 and 4): every
 // shard answered the query with its own sorted list of R (distance, local id)
 // pairs; the answer is the first min(ef, R) of all shards' pairs by
-// (distance, global id), global id = shard offset + local id.
+// (distance, global id), global id = shard offset + local id. The same kernel
+// merges the partial k-lists of a partition-sharded build (Shuffle 2 and
+// Reduce 2 of Section 3.2): S lists of k keys per point, all offsets zero, the
+// first k kept (ef == NULL).
 //
 // One warp per query. The S lists are staged in shared memory as keys
 // (d << 32 | global id), padding as +inf; each valid key's place in the answer
@@ -28,7 +31,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 shard_merge_kernel(const int32_t* __restrict__ ids, const int32_t* __restrict__ dist, int S,
                    int64_t nq, int R, const __grid_constant__ bdg_shard_offsets off,
                    const int32_t* __restrict__ ef,
-                   int ef_max, int bits, int32_t* __restrict__ out_ids,
+                   int ef_max, int bits, int fixed_r, int32_t* __restrict__ out_ids,
                    int32_t* __restrict__ out_dist) {
   extern __shared__ __align__(16) uint64_t merge_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -49,8 +52,13 @@ shard_merge_kernel(const int32_t* __restrict__ ids, const int32_t* __restrict__ 
       valid += __popc(__ballot_sync(0xffffffffu, ok));
     }
     __syncwarp();
-    const int e = ef[q];
-    const int rq = (e >= 1 && e <= ef_max) ? min(min(e, R), valid) : 0;
+    int rq;
+    if (fixed_r > 0) {  // every row keeps its first fixed_r keys
+      rq = min(fixed_r, valid);
+    } else {
+      const int e = ef[q];
+      rq = (e >= 1 && e <= ef_max) ? min(min(e, R), valid) : 0;
+    }
     for (int i = lane; i < total; i += 32) {
       const uint64_t key = keys[i];
       if (key == BDG_KEY_INF) continue;
@@ -92,7 +100,7 @@ bdg_status bdg_launch_shard_merge(const int32_t* ids, const int32_t* dist, int S
   const int grid = (int)(need < cap ? need : cap);
   bdg_prof_scope prof("shard_merge", st);
   shard_merge_kernel<<<grid, kWarps * 32, smem, st>>>(ids, dist, S, nq, R, off, ef, ef_max,
-                                                       bits, out_ids, out_dist);
+                                                       bits, ef ? 0 : R, out_ids, out_dist);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   return BDG_OK;

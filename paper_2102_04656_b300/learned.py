@@ -165,14 +165,31 @@ def label_recall(routes, labels):
     return float((hit.any(2) & valid).sum().item()) / max(1, int(valid.sum().item()))
 
 
-def calibrate(choose, values, labels, target: float):
+def tie_aware_recall(routes, ids, dists, home, k: int):
+    """Tie-aware recall@k of a partitioned build for rows whose exact neighbour
+    lists are known beyond k (ids/dists int32 [S, k'] with k' > k, ascending):
+    a listed neighbour is found exactly when its home is probed; with d_k the
+    exact k-th distance, the row's result counts the found neighbours below d_k
+    plus, at d_k, as many found ones as the exact top k holds there (the listed
+    neighbours stand in for all points at d_k). routes: int32 [S, P] (-1 = none)."""
+    nh = home[ids.long().clamp(min=0)]
+    found = ((nh[:, :, None] == routes[:, None, :]) & (routes[:, None, :] >= 0)).any(2)
+    found &= ids >= 0
+    dk = dists[:, k - 1:k]
+    below = (found & (dists < dk)).sum(1)
+    at_found = (found & (dists == dk)).sum(1)
+    at_exact = (dists[:, :k] == dk).sum(1)
+    return float((below + torch.minimum(at_found, at_exact)).sum().item()) / (ids.shape[0] * k)
+
+
+def calibrate(choose, values, score, target: float):
     """The first value (in the given order, cheapest first) whose routes reach
-    label recall >= target on the held-out rows; the last value if none does.
-    choose(v) -> routes of the held-out rows. Returns (value, recall, mean probes)."""
+    score(routes) >= target on the held-out rows; the last value if none does.
+    choose(v) -> routes of the held-out rows. Returns (value, score, mean probes)."""
     best = None
     for v in values:
         r = choose(v)
-        rec = label_recall(r, labels)
+        rec = score(r)
         best = (v, rec, float((r >= 0).sum(1).float().mean().item()))
         if rec >= target:
             break

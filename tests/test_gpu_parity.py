@@ -600,6 +600,62 @@ def test_build_plan_replays_bit_exact(bdg, kernel, tmp_path, monkeypatch):
     plan.free()
 
 
+def test_build_plan_run_host_bit_exact(bdg, tmp_path, monkeypatch):
+    """bdg_build_plan_run_host: host codes in, host rows out, on a side stream;
+    two different code sets in a row give their own oracle graphs."""
+    monkeypatch.setenv("BDG_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    n, bits, k, m, t = 6000, 256, 16, 8, 3
+    dev = datagen.random_codes(n, bits, seed=1).cuda()
+    sample = torch.from_numpy(datagen.sample_ids(n, 512, 3)).cuda()
+    entry = torch.from_numpy(_entry(n, 32, 4)).cuda()
+    plan = bdg.BuildPlan(dev, k, m=m, t=t, bk_sample=sample, bk_iters=4, entry=entry)
+    st = torch.cuda.Stream()
+    for seed in (21, 22):
+        spec = datagen.MixtureSpec(n, 64, 30, bits, seed=seed)
+        hc = datagen.make_codes(spec).pin_memory()
+        hi = torch.empty(n, k, dtype=torch.int32).pin_memory()
+        hd = torch.empty(n, k, dtype=torch.int32).pin_memory()
+        plan.run_host(hc, hi, hd, stream=st)
+        st.synchronize()
+        cent_o, _, _ = oracle.bkmeans(_np(hc), sample.cpu().numpy(), m, 4)
+        r_o, _ = oracle.route(_np(hc), cent_o, t)
+        ids_o, dist_o = oracle.knn_partitioned(_np(hc), r_o, k)
+        assert np.array_equal(hi.numpy(), ids_o)
+        assert np.array_equal(hd.numpy(), dist_o)
+    with pytest.raises(ValueError):
+        plan.run_host(hc.cuda(), hi, hd)
+    plan.free()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_partition_sharded_build_merge_bit_exact(bdg, world):
+    """The compute steps of the partition-sharded build on one GPU: each rank's
+    build over its LPT-assigned partitions (other slots -1), then the merge of
+    the ranks' partial rows (bdg_merge_lists) equals the single build and the
+    oracle; the collective between them is tested with gloo ranks on CPU."""
+    from paper_2102_04656_b300 import distributed as D
+    n, bits, k, m, t = 12000, 256, 32, 20, 4
+    c = datagen.make_codes(datagen.MixtureSpec(n, 64, 30, bits, seed=90 + world))
+    ce = datagen.random_codes(m, bits, seed=91)
+    cd = c.cuda()
+    routes, _ = bdg.route(cd, ce.cuda(), t)
+    entry = torch.from_numpy(_entry(n, 32, 2)).cuda()
+    hc, vc = D.partition_counts(routes, m)
+    owner = D.assign_partitions(hc.cpu().numpy(), vc.cpu().numpy(), world)
+    parts_i, parts_d = [], []
+    for rank in range(world):
+        g = bdg.build_graph(cd, k, m=m, t=t, routes=D.rank_routes(routes, owner, rank),
+                            entry=entry)
+        parts_i.append(g.ids.clone())
+        parts_d.append(g.dists.clone())
+        g.free()
+    mi, md = bdg.merge_lists(torch.stack(parts_i).contiguous(), torch.stack(parts_d).contiguous(),
+                             bits)
+    ids_o, dist_o = oracle.knn_partitioned(_np(c), routes.cpu().numpy(), k)
+    assert np.array_equal(mi.cpu().numpy(), ids_o)
+    assert np.array_equal(md.cpu().numpy(), dist_o)
+
+
 # ------------------------------------------------------------------ size classes
 def _class_routes(seed):
     """Routes over 24 partitions whose home sets fall in all three size classes

@@ -63,6 +63,23 @@ def test_gemm_epilogues(bdg):
     assert np.allclose(cs.cpu().numpy(), wantm.sum(0), rtol=1e-4, atol=1e-3)
 
 
+@pytest.mark.parametrize("relu", [True, False])
+def test_gemm_whole_tile_bias_bf16_epilogue(bdg, relu):
+    """Whole-tile shapes with bias and BF16 output take the direct epilogue
+    (each thread stores its own row)."""
+    rng = np.random.default_rng(9)
+    M, N, K = 384, 256, 200
+    A = _bf16(rng.standard_normal((M, K)))
+    B = _bf16(rng.standard_normal((N, K)))
+    bias = torch.from_numpy(rng.standard_normal(N).astype(np.float32))
+    Cb, err = bdg.gemm_bf16(A.cuda(), B.cuda(), bias=bias.cuda(), relu=relu, out="bf16")
+    want = A.double().numpy() @ B.double().numpy().T + bias.double().numpy()
+    if relu:
+        want = np.maximum(want, 0)
+    assert int(err.item()) == 0
+    assert np.allclose(Cb.float().cpu().numpy(), want, rtol=2 ** -7, atol=1e-3)
+
+
 def _net(seed, d=128, h1=64, h2=64, m=40):
     flat = datagen.router_init(d, h1, h2, m, seed)
     o = np.cumsum([0, h1 * d, h1, h2 * h1, h2, m * h2, m])
@@ -283,6 +300,12 @@ def test_shortlist_route_choice_bit_exact(bdg, theta, pmax):
     assert np.array_equal(routes.cpu().numpy(), want)
     z2 = r.forward_shortlist(x[:512], cn[:512], codes=ct[:512].cuda()).cpu().numpy()
     assert np.array_equal(z2, z[:512])
+    # processing the points in another order (here a permutation) changes nothing
+    perm = torch.from_numpy(np.random.default_rng(55).permutation(N).astype(np.int32)).cuda()
+    routes_p, z_p = r.route_shortlist(x, cn, theta, pmax, codes=ct.cuda(), logits=True,
+                                      order=perm)
+    assert torch.equal(routes_p, routes)
+    assert np.array_equal(z_p.cpu().numpy(), z)
 
 
 def test_shortlist_prior_routes_by_distance_gap(bdg):
