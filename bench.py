@@ -54,8 +54,9 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--recall-rows", type=int, default=2000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--case", choices=["full", "small"], default="full",
-                    help="small: one 500k-point partitioned build (profiling case)")
+    ap.add_argument("--case", choices=["full", "small", "router"], default="full",
+                    help="small: one 500k-point partitioned build; router: routing and the "
+                         "shortlist router on 2M points (profiling cases)")
     ap.add_argument("--search-entry", type=int, default=16384,
                     help="long-link entry sample size of the search graph")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
@@ -1051,9 +1052,43 @@ def run_small_case(a):
                       "k": w["k"], "builds": max(1, a.warmup) + a.steps}))
 
 
+def run_router_case(a):
+    """Profiling case of the learned routing path (2M points of the learned
+    workload's generator, m = 10,000 centres, 256-bit codes): the Map step's 8
+    nearest centres on the tensor cores, then the shortlist router (prior
+    weights, untrained) choosing the probes: routing, GEMM and head kernels."""
+    from paper_2102_04656_b300 import build as bdg_build
+    bdg_build.build()
+    import paper_2102_04656_b300 as bdg
+    from paper_2102_04656_b300 import learned
+    w = datagen.WORKLOADS["learned_100m_256b"]
+    base = w["spec"]
+    n, m = 2_000_000, w["m"]
+    spec = datagen.MixtureSpec(n, base.dim, base.components, base.bits, base.sigma, base.seed)
+    codes, feats = datagen.make_codes(spec, device="cuda", with_features=True)
+    xb = feats.to(torch.bfloat16).contiguous()
+    del feats
+    sample = torch.from_numpy(datagen.sample_ids(n, 64 * m, spec.seed + 3)).cuda()
+    cent, _ = bdg.bkmeans(codes, sample, m, w["bk_iters"])
+    init = learned.prior_params(torch.from_numpy(datagen.router_init(base.dim, 512, 512, m,
+                                                                     spec.seed + 5)).cuda(),
+                                base.dim, 512, 512, m, cent, scale=0.25)
+    r = bdg.Router(init, base.dim, 512, 512, m, max_batch=4096, code_bits=spec.bits)
+    for i in range(max(1, a.warmup) + a.steps):
+        cand, _ = bdg.route(codes, cent, w["t"])
+        routes = r.route_shortlist(xb, cand, 1.0, w["t"], codes=codes)
+        torch.cuda.synchronize()
+    r.free()
+    print(json.dumps({"case": "router", "N": n, "m": m, "bits": spec.bits, "Q": w["t"],
+                      "runs": max(1, a.warmup) + a.steps,
+                      "mean_probes": float((routes >= 0).sum(1).float().mean().item())}))
+
+
 def run_ours(a):
     if a.case == "small":
         return run_small_case(a)
+    if a.case == "router":
+        return run_router_case(a)
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)

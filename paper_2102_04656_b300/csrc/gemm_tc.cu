@@ -10,12 +10,14 @@
 // tensor copies (cp.async.bulk.tensor, 128-byte swizzle, zero fill past the
 // matrix edges) completing on mbarriers; one thread of warp 5 issues
 // tcgen05.mma kind::f16 (M = 128, N = 128, K = 16 per instruction) into one of
-// two TMEM accumulators, so the MMAs of the next tile run while warps 0-3 drain
-// the previous one. The epilogue reads its accumulator rows (thread = row =
-// TMEM lane) into a per-warp shared-memory tile, hands the accumulator back,
-// and then writes the tile row by row, each lane on 4 consecutive columns: 16-
-// or 8-byte coalesced stores, coalesced bias and mask reads, per-column sums in
-// registers. Every mbarrier wait is bounded and reports through an error word.
+// two TMEM accumulators, so the MMAs of the next tile run while eight epilogue
+// warps (two per scheduler: each reads its TMEM lane quarter and one half of
+// the columns) drain the previous one. Inference layers (bias, ReLU, BF16 out,
+// whole tiles) are written straight from the accumulator, each thread storing
+// its own row 16 bytes at a time; the general epilogue stages a warp's block in
+// shared memory and writes it row by row, each lane on 4 consecutive columns
+// (coalesced stores, bias and mask reads, per-column sums in registers). Every
+// mbarrier wait is bounded and reports through an error word.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -28,9 +30,9 @@
 namespace {
 
 constexpr int kBM = 128, kBN = 128, kBK = 64;   // tile; K slab = 64 bf16 = 128 bytes
-constexpr int kStages = 6;
+constexpr int kStages = 4;
 constexpr int kAcc = 2;                         // TMEM accumulators (128 columns each)
-constexpr int kThreads = 192;                   // 0-3 epilogue, 4 producer, 5 MMA
+constexpr int kThreads = 320;  // warps 0-3 and 6-9 epilogue, 4 producer, 5 MMA
 constexpr uint32_t kSlab = kBM * kBK * 2;       // 16 KB per operand per stage
 constexpr uint32_t kRing = kStages * 2 * kSlab;  // 192 KB: the copies in flight
 // the epilogue stages half a tile (64 columns) at a time; row stride 68 floats:
@@ -38,7 +40,8 @@ constexpr uint32_t kRing = kStages * 2 * kSlab;  // 192 KB: the copies in flight
 // a warp reading one row 16 bytes per lane meet no bank conflicts
 constexpr int kHalfN = kBN / 2;
 constexpr int kLd = kHalfN + 4;
-constexpr uint32_t kStageBytes = 4u * 32 * kLd * 4;  // 4 warps x 32 rows x 68 floats
+constexpr int kEpiWarps = 8;
+constexpr uint32_t kStageBytes = kEpiWarps * 32u * kLd * 4;  // 8 warps x 32 rows x 68 floats
 static_assert(kRing + kStageBytes + 256 <= 232448, "shared memory per block exceeds 227 KB");
 constexpr uint32_t kPolls = 1u << 20;
 
@@ -116,7 +119,7 @@ gemm_bf16_kernel(GemmArgs g, const __grid_constant__ CUtensorMap mapA,
     }
     for (int b = 0; b < kAcc; ++b) {
       tc05::mbar_init(&tfull[b], 1);
-      tc05::mbar_init(&tempty[b], 4);
+      tc05::mbar_init(&tempty[b], kEpiWarps);
     }
     tc05::mbar_init(drain, 1);
     tc05::mbar_fence_init();
@@ -186,9 +189,13 @@ gemm_bf16_kernel(GemmArgs g, const __grid_constant__ CUtensorMap mapA,
       tc05::commit(drain);
       if (!tc05::mbar_wait(drain, 0, kPolls)) atomicExch(g.err, 15);
     }
-  } else if (warp < 4) {
-    // ---------------- epilogue: warp w owns rows 32w .. 32w + 31 of each tile
-    float* st = stage + warp * 32 * kLd;
+  } else {
+    // ---------------- epilogue: 8 warps; warp w reads TMEM lanes 32 (w % 4) ..
+    // + 31 (the rows it may access) and one half of the tile's columns: warps
+    // 0-3 columns 0-63, warps 6-9 columns 64-127
+    const int quad = warp & 3, half = warp >= 6 ? 1 : 0;
+    const int ew = quad + 4 * half;  // 0..7
+    float* st = stage + ew * 32 * kLd;
     uint32_t it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int m0 = (tile / tiles_n) * kBM, n0 = (tile % tiles_n) * kBN;
@@ -199,27 +206,28 @@ gemm_bf16_kernel(GemmArgs g, const __grid_constant__ CUtensorMap mapA,
         break;
       }
       tc05::fence_after();
-      const int row0 = m0 + 32 * warp;
+      const int row0 = m0 + 32 * quad;
+      const int cb = n0 + kHalfN * half;  // first column of this warp's half
+      const uint32_t tbase = tmem + ((uint32_t)(32 * quad) << 16) + b * kBN + kHalfN * half;
       if (g.direct) {
         // inference layers (bias, optional ReLU, BF16 out, whole tile inside the
         // matrix): each thread converts its own row and stores it, 8 values per
         // 16-byte store, straight from the accumulator
-        const int row = row0 + lane;
-        __nv_bfloat16* orow = g.out_bf16 + (int64_t)row * g.ldo + n0;
-#pragma unroll 1
-        for (int c0 = 0; c0 < kBN; c0 += 32) {
+        __nv_bfloat16* orow = g.out_bf16 + (int64_t)(row0 + lane) * g.ldo + cb;
+#pragma unroll
+        for (int c0 = 0; c0 < kHalfN; c0 += 32) {
           uint32_t v[32];
-          tc05::ld32(tmem + ((uint32_t)(32 * warp) << 16) + b * kBN + c0, v);
+          tc05::ld32(tbase + c0, v);
           tc05::wait_ld();
-          if (c0 == kBN - 32) {  // the whole accumulator is read: hand it back
+          if (c0 == kHalfN - 32) {  // this warp's part of the accumulator is read
             tc05::fence_before();
             __syncwarp();
             if (lane == 0) tc05::mbar_arrive(&tempty[b]);
           }
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float4 b0 = *reinterpret_cast<const float4*>(g.bias + n0 + c0 + 8 * q);
-            const float4 b1 = *reinterpret_cast<const float4*>(g.bias + n0 + c0 + 8 * q + 4);
+            const float4 b0 = *reinterpret_cast<const float4*>(g.bias + cb + c0 + 8 * q);
+            const float4 b1 = *reinterpret_cast<const float4*>(g.bias + cb + c0 + 8 * q + 4);
             float x[8] = {__uint_as_float(v[8 * q]) + b0.x, __uint_as_float(v[8 * q + 1]) + b0.y,
                           __uint_as_float(v[8 * q + 2]) + b0.z, __uint_as_float(v[8 * q + 3]) + b0.w,
                           __uint_as_float(v[8 * q + 4]) + b1.x, __uint_as_float(v[8 * q + 5]) + b1.y,
@@ -242,17 +250,15 @@ gemm_bf16_kernel(GemmArgs g, const __grid_constant__ CUtensorMap mapA,
         }
         continue;
       }
-      float csum[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-      // the accumulator rows (thread = row): the first half into this warp's
-      // staging tile, the second half into registers; then the accumulator is
-      // handed back before any output is written
-      uint32_t v1[kHalfN];
+      // the general epilogue: this warp's 32 x 64 block of the accumulator into
+      // its staging tile (thread = row), the accumulator handed back, then the
+      // block written row by row with half-warps on rows and each lane on 4
+      // consecutive columns: coalesced stores, bias and mask reads, per-column
+      // sums in registers
 #pragma unroll
       for (int c0 = 0; c0 < kHalfN; c0 += 32) {
         uint32_t v[32];
-        tc05::ld32(tmem + ((uint32_t)(32 * warp) << 16) + b * kBN + c0, v);
-        tc05::ld32(tmem + ((uint32_t)(32 * warp) << 16) + b * kBN + kHalfN + c0,
-                   *reinterpret_cast<uint32_t(*)[32]>(&v1[c0]));
+        tc05::ld32(tbase + c0, v);
         tc05::wait_ld();
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -263,71 +269,54 @@ gemm_bf16_kernel(GemmArgs g, const __grid_constant__ CUtensorMap mapA,
       tc05::fence_before();
       __syncwarp();
       if (lane == 0) tc05::mbar_arrive(&tempty[b]);
+      const int col = cb + 4 * (lane & 15);
+      const int nc = max(0, min(4, g.N - col));  // valid columns of this lane
+      float bv[4], csum[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {  // two halves of 64 columns
-        if (h == 1) {
-          __syncwarp();  // the first half is written out: stage the second
+      for (int e = 0; e < 4; ++e) bv[e] = (g.bias && e < nc) ? g.bias[col + e] : 0.f;
+      for (int r2 = 0; r2 < 32; r2 += 2) {
+        const int r = r2 + (lane >> 4);
+        const int row = row0 + r;
+        if (row0 + r2 >= g.M) break;
+        const float4 a4 = *reinterpret_cast<const float4*>(&st[r * kLd + 4 * (lane & 15)]);
+        float x[4] = {a4.x + bv[0], a4.y + bv[1], a4.z + bv[2], a4.w + bv[3]};
+        const bool rin = row < g.M;
 #pragma unroll
-          for (int q = 0; q < kHalfN / 4; ++q)
-            *reinterpret_cast<float4*>(&st[lane * kLd + 4 * q]) =
-                make_float4(__uint_as_float(v1[4 * q]), __uint_as_float(v1[4 * q + 1]),
-                            __uint_as_float(v1[4 * q + 2]), __uint_as_float(v1[4 * q + 3]));
-          __syncwarp();
+        for (int e = 0; e < 4; ++e) {
+          if (g.relu) x[e] = fmaxf(x[e], 0.f);
+          if (g.mask && rin && e < nc &&
+              !(__bfloat162float(g.mask[(int64_t)row * g.ldm + col + e]) > 0.f))
+            x[e] = 0.f;
+          if (e >= nc || !rin) x[e] = 0.f;
+          csum[e] += x[e];
         }
-        // staging half -> output: half-warp rows, each lane on 4 consecutive columns
-        const int col = n0 + h * kHalfN + 4 * (lane & 15);
-        const int nc = max(0, min(4, g.N - col));  // valid columns of this lane
-        float bv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) bv[e] = (g.bias && e < nc) ? g.bias[col + e] : 0.f;
-        for (int r2 = 0; r2 < 32; r2 += 2) {
-          const int r = r2 + (lane >> 4);
-          const int row = row0 + r;
-          if (row0 + r2 >= g.M) break;
-          const float4 a4 = *reinterpret_cast<const float4*>(&st[r * kLd + 4 * (lane & 15)]);
-          float x[4] = {a4.x + bv[0], a4.y + bv[1], a4.z + bv[2], a4.w + bv[3]};
-          const bool rin = row < g.M;
+        if (nc == 0 || !rin) continue;
+        const int64_t o = (int64_t)row * g.ldo + col;
+        if (g.vec_out && nc == 4) {
+          if (g.out_f32)
+            *reinterpret_cast<float4*>(g.out_f32 + o) = make_float4(x[0], x[1], x[2], x[3]);
+          if (g.out_bf16) {
+            __nv_bfloat162 p0 = __floats2bfloat162_rn(x[0], x[1]);
+            __nv_bfloat162 p1 = __floats2bfloat162_rn(x[2], x[3]);
+            uint2 pk;
+            pk.x = *reinterpret_cast<uint32_t*>(&p0);
+            pk.y = *reinterpret_cast<uint32_t*>(&p1);
+            *reinterpret_cast<uint2*>(g.out_bf16 + o) = pk;
+          }
+        } else {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            if (g.relu) x[e] = fmaxf(x[e], 0.f);
-            if (g.mask && rin && e < nc &&
-                !(__bfloat162float(g.mask[(int64_t)row * g.ldm + col + e]) > 0.f))
-              x[e] = 0.f;
-            if (e >= nc || !rin) x[e] = 0.f;
-            csum[h][e] += x[e];
-          }
-          if (nc == 0 || !rin) continue;
-          const int64_t o = (int64_t)row * g.ldo + col;
-          if (g.vec_out && nc == 4) {
-            if (g.out_f32)
-              *reinterpret_cast<float4*>(g.out_f32 + o) = make_float4(x[0], x[1], x[2], x[3]);
-            if (g.out_bf16) {
-              __nv_bfloat162 p0 = __floats2bfloat162_rn(x[0], x[1]);
-              __nv_bfloat162 p1 = __floats2bfloat162_rn(x[2], x[3]);
-              uint2 pk;
-              pk.x = *reinterpret_cast<uint32_t*>(&p0);
-              pk.y = *reinterpret_cast<uint32_t*>(&p1);
-              *reinterpret_cast<uint2*>(g.out_bf16 + o) = pk;
-            }
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              if (e >= nc) break;
-              if (g.out_f32) g.out_f32[o + e] = x[e];
-              if (g.out_bf16) g.out_bf16[o + e] = __float2bfloat16_rn(x[e]);
-            }
+            if (e >= nc) break;
+            if (g.out_f32) g.out_f32[o + e] = x[e];
+            if (g.out_bf16) g.out_bf16[o + e] = __float2bfloat16_rn(x[e]);
           }
         }
       }
       if (g.colsum) {  // the two half-warps' sums of each column, one atomic per column
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int col = n0 + h * kHalfN + 4 * (lane & 15);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float tot = csum[h][e] + __shfl_xor_sync(0xffffffffu, csum[h][e], 16);
-            if (lane < 16 && col + e < g.N) atomicAdd(&g.colsum[col + e], tot);
-          }
+        for (int e = 0; e < 4; ++e) {
+          const float tot = csum[e] + __shfl_xor_sync(0xffffffffu, csum[e], 16);
+          if (lane < 16 && col + e < g.N) atomicAdd(&g.colsum[col + e], tot);
         }
       }
       __syncwarp();  // the staging tile is reused by the next tile

@@ -344,30 +344,38 @@ head_route_kernel(const __nv_bfloat16* __restrict__ u, int h2s,
     }
   }
   float zl = -INFINITY;  // lane j ends with z_j
-  for (int j = 0; j < Q; ++j) {
-    const int32_t p = __shfl_sync(0xffffffffu, myp, j);
-    if (p < 0) continue;
-    const uint4* wr = reinterpret_cast<const uint4*>(W3 + (int64_t)p * h2s);
-    uint4 w[UC];
+  for (int j0 = 0; j0 < Q; j0 += 2) {  // two candidates' W3 rows in flight at once
+    int32_t p2[2];
+    uint4 w[2][UC];
 #pragma unroll
-    for (int q = 0; q < UC; ++q) {
-      const int c = lane + 32 * q;
-      w[q] = c < nch ? wr[c] : make_uint4(0, 0, 0, 0);
-    }
-    float acc = 0.f;
+    for (int u2 = 0; u2 < 2; ++u2) {
+      const int j = j0 + u2;
+      p2[u2] = __shfl_sync(0xffffffffu, myp, j < Q ? j : 0);
+      if (j >= Q) p2[u2] = -1;
+      const uint4* wr = reinterpret_cast<const uint4*>(W3 + (int64_t)(p2[u2] < 0 ? 0 : p2[u2]) * h2s);
 #pragma unroll
-    for (int q = 0; q < UC; ++q) {
-      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&w[q]);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 f = __bfloat1622float2(h[e]);
-        acc = fmaf(uf[q][2 * e], f.x, acc);
-        acc = fmaf(uf[q][2 * e + 1], f.y, acc);
+      for (int q = 0; q < UC; ++q) {
+        const int c = lane + 32 * q;
+        w[u2][q] = (p2[u2] >= 0 && c < nch) ? wr[c] : make_uint4(0, 0, 0, 0);
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == j) zl = acc + b3[p];
+    for (int u2 = 0; u2 < 2; ++u2) {
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < UC; ++q) {
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&w[u2][q]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(h[e]);
+          acc = fmaf(uf[q][2 * e], f.x, acc);
+          acc = fmaf(uf[q][2 * e + 1], f.y, acc);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (p2[u2] >= 0 && lane == j0 + u2) zl = acc + b3[p2[u2]];
+    }
   }
   if (z_out && lane < Q) z_out[orow * Q + lane] = zl;
   if (routes == nullptr) return;
