@@ -1008,11 +1008,15 @@ def _learned_bench(bdg, device, kernel, n=100_000_000, lr=1e-3, lr_epochs=4):
                              2.0 * n * (base.dim * 512 + 512 * 512), prof["gemm"], bf16,
                              "TFLOP/s", f"{pk} burst BF16"),
         "router_head": _roof("head_route_kernel (shortlist head + probe choice)", "hbm",
-                             float(n) * (Q + 1) * (512 + spec.bits) * 2, prof["router_head"],
-                             _hbm_peak()[0], "GB/s", _hbm_peak()[1],
-                             note="bytes: the row's [h2 | s] and Q rows of W3 per point; W3 "
-                                  "(15 MB) is read from L2"),
+                             float(n) * ((512 + spec.bits) * 2 + 2 * Q * 4),
+                             prof["router_head"], _hbm_peak()[0], "GB/s", _hbm_peak()[1],
+                             note="bytes: the row's [h2 | s] in BF16, its Q shortlist ids in and "
+                                  "its Q routes out; the Q gathered rows of W3 per point come "
+                                  "from L2 (W3 is 15 MB) and are not counted"),
     }
+    out["roofline"]["router_head"]["l2_gather_gbs"] = (
+        float(n) * Q * (512 + spec.bits) * 2 / (prof["router_head"] * 1e-3) / 1e9
+        if prof["router_head"] else None)
     del lroutes
     out["arms"] = arms
     ok = {name: v for name, v in arms.items()
@@ -1029,6 +1033,20 @@ def _learned_bench(bdg, device, kernel, n=100_000_000, lr=1e-3, lr_epochs=4):
                            and lr_["total_ms"] < ok[best]["total_ms"]),
     }
     router.free()
+    # Reduce-1 variant per partition size class, tuned by a build plan on the
+    # first 10M points of this workload (m = 10,000: about 1,000 homes per
+    # partition, the small-partition regime)
+    n_t = min(n, 10_000_000)
+    ct = codes[:n_t].contiguous()
+    st_sample = torch.from_numpy(datagen.sample_ids(n_t, 64 * m, spec.seed + 3)).to(device)
+    st_entry = torch.from_numpy(datagen.sample_ids(n_t, 256, spec.seed + 4).astype(np.int32)).to(device)
+    plan = bdg.BuildPlan(ct, k, m=m, t=3, bk_sample=st_sample, bk_iters=w["bk_iters"],
+                         entry=st_entry, kernel="auto")
+    plan.run()
+    torch.cuda.synchronize()
+    out["size_classes"] = {"N": n_t, "m": m, "t": 3, "classes": plan.classes,
+                           "reduce1_ms": plan.kernel_ms()}
+    plan.free()
     return out
 
 
@@ -1156,6 +1174,7 @@ def run_ours(a):
     route_ms = tot.value / max(1, nl.value)
     kernel_used = plan.kernel
     tuned = plan.tuned_ms
+    plan_classes = plan.classes
     plan.free()
 
     # end to end through the public API with host buffers: every step is one
@@ -1285,6 +1304,7 @@ def run_ours(a):
                    "bk_sample": int(sample.numel()), "bk_iters": w["bk_iters"],
                    "reduce1_kernel": kernel_used, "kernel_choice": a.kernel,
                    "autotune_ms": tuned if a.kernel == "auto" else None,
+                   "size_classes": plan_classes,
                    "step": "one CUDA-graph replay of the whole build",
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "parallelism": f"independent problem per GPU x{ws}"},
