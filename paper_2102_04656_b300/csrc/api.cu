@@ -287,8 +287,12 @@ namespace {
 // scratch layout (routes, centres, Bk-means, CSR, partial lists, expanded
 // homes, fix-up flags), so that a build can be enqueued into caller-provided
 // scratch (bdg_build_graph) or captured once into a CUDA graph (build plans).
+constexpr int kLocPivots = 16;      // pivot homes per partition of the locality order
+constexpr int64_t kLocMinHomes = 2048;  // mean |H_p| from which the order is built
+
 struct BuildCfg {
   int W, m, t, tile_v;
+  int pivots;  // locality order of H_p over this many pivot homes (0: id order)
   bool need_routes, need_bk, use_tc, tc_ok, route_tc;
   int kmap[BDG_SIZE_CLASSES];  // Reduce-1 variant (BDG_KV_*) per partition size class
   int64_t coarse;
@@ -352,7 +356,10 @@ bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_
   c->b_routes = c->need_routes || m == 1 ? al((size_t)N * t * 4) : 0;
   c->b_cent = c->need_bk ? al((size_t)m * W * 8) : 0;
   c->b_bk = c->need_bk ? al(bdg_bkmeans_scratch_bytes(P->bk_sample_size, m, W)) : 0;
-  c->b_csr = al(bdg_csr_bytes(N, m, t, W, c->tile_v));
+  // homes in locality order for the tensor path where partitions span many
+  // tiles (own tile first in round A; candidate words keep (d, id) order)
+  c->pivots = c->tc_ok && m > 1 && N / m >= kLocMinHomes ? kLocPivots : 0;
+  c->b_csr = al(bdg_csr_bytes(N, m, t, W, c->tile_v, c->pivots));
   c->b_part = t > 1 ? al((size_t)N * k * 8) : 0;  // running k-lists
   c->b_hexp = c->tc_ok ? al(bdg_knn_tc_hexp_bytes(N, m, W)) : 0;
   c->b_fix = c->tc_ok ? al((size_t)N * t) + al(64) : 0;
@@ -433,7 +440,7 @@ bdg_status build_enqueue(const BuildCfg& c, const int* kmap, bdg_graph* g, const
     BDG_TRY(bdg_launch_fill_pad(g->ids, g->dists, N * (int64_t)k, bits, st));
   }
   bdg_csr csr;
-  BDG_TRY(bdg_build_csr(codes, N, W, routes, m, t, c.tile_v, csr_mem, &csr, st));
+  BDG_TRY(bdg_build_csr(codes, N, W, routes, m, t, c.tile_v, c.pivots, csr_mem, &csr, st));
   // Reduce 1: round A = every point against its home partition (it starts the
   // point's running k-list); then one sub-round per further route slot, each
   // point visiting one partition, its threshold starting at the k-th key of its

@@ -278,6 +278,83 @@ __global__ void centres_plan_kernel(int64_t n, int m, int tile_v, int32_t* __res
   }
 }
 
+// ---- locality order of H_p (tensor path): the homes of p sorted by (nearest of
+// P pivot homes, id). The pivots are the homes at positions (2i + 1) |H_p| / (2P)
+// of H_p in id order, and a home's nearest pivot is the first one at the least
+// Hamming distance. One warp per partition: a counting pass, a scan over the P
+// counts and a stable scatter in id order (ranks among equal keys by lane).
+// The order changes no result: candidate words carry the id rank (loc_idr), so
+// they still order by (d, id).
+template <int W>
+__global__ void __launch_bounds__(128)
+locality_kernel(const uint64_t* __restrict__ home_codes, const int32_t* __restrict__ home_ids,
+                const int32_t* __restrict__ home_off, const int32_t* __restrict__ eoff, int m,
+                int P, int32_t* __restrict__ home_loc, int32_t* __restrict__ loc_idr) {
+  __shared__ uint64_t piv_all[4][BDG_MAX_PIVOTS * W];
+  __shared__ int32_t cnt_all[4][BDG_MAX_PIVOTS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * 4 + warp;
+  if (p >= m) return;  // whole warps only: no block-wide barrier below
+  const int h0 = home_off[p], nh = home_off[p + 1] - h0;
+  const int64_t e0 = eoff[p];
+  const int npad = (nh + BDG_TC_TILE - 1) & ~(BDG_TC_TILE - 1);
+  uint64_t* piv = piv_all[warp];
+  int32_t* cnt = cnt_all[warp];
+  const int np = min(P, nh);  // pivots (none for an empty partition)
+  for (int x = lane; x < np * W; x += 32) {
+    const int i = x / W, w = x % W;
+    const int pos = (int)(((2LL * i + 1) * nh) / (2LL * np));
+    piv[x] = home_codes[(int64_t)(h0 + pos) * W + w];
+  }
+  for (int i = lane; i < BDG_MAX_PIVOTS; i += 32) cnt[i] = 0;
+  __syncwarp();
+  auto nearest = [&](int x) -> int {
+    uint64_t hc[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) hc[w] = home_codes[(int64_t)(h0 + x) * W + w];
+    int best = 0, bd = INT_MAX;
+    for (int i = 0; i < np; ++i) {
+      int d = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) d += __popcll(hc[w] ^ piv[i * W + w]);
+      if (d < bd) { bd = d; best = i; }
+    }
+    return best;
+  };
+  for (int x0 = 0; x0 < nh; x0 += 32) {
+    const int x = x0 + lane;
+    if (x < nh) atomicAdd(&cnt[nearest(x)], 1);
+  }
+  __syncwarp();
+  {  // exclusive scan of the counts (np <= 32: one per lane) into cursors
+    const int cv = lane < np ? cnt[lane] : 0;
+    int incl = cv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    __syncwarp();
+    if (lane < np) cnt[lane] = incl - cv;
+    __syncwarp();
+  }
+  for (int x0 = 0; x0 < nh; x0 += 32) {
+    const int x = x0 + lane;
+    const int key = x < nh ? nearest(x) : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const int rank = __popc(same & ((1u << lane) - 1u));
+    const int pos = key >= 0 ? cnt[key] + rank : 0;
+    __syncwarp();
+    if (key >= 0 && rank == 0) cnt[key] += __popc(same);  // the group's first lane advances it
+    __syncwarp();
+    if (key >= 0) {
+      loc_idr[e0 + pos] = x;
+      home_loc[h0 + pos] = home_ids[h0 + x];
+    }
+  }
+  for (int q = nh + lane; q < npad; q += 32) loc_idr[e0 + q] = 0;
+}
+
 }  // namespace
 
 size_t bdg_csr_centres_bytes(int64_t n, int m, int tile_v) {
@@ -304,6 +381,7 @@ bdg_status bdg_build_csr_centres(const uint64_t* cent, int m, int64_t n, int til
   c->item_off_a = c->item_off;
   c->slot_zero = c->visit_slot;
   c->home_blocks = nullptr;
+  c->home_loc = c->loc_idr = nullptr;
   c->m = 1;
   c->t = 1;
   BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, 8 * 4, st));
@@ -340,6 +418,8 @@ bdg_status bdg_build_csr_rows(const uint64_t* codes, int64_t N, const int32_t* r
   c->home_codes = const_cast<uint64_t*>(codes);  // identity order: read the codes in place
   c->item_off_a = c->item_off;
   c->slot_zero = c->visit_slot;
+  c->home_blocks = nullptr;
+  c->home_loc = c->loc_idr = nullptr;
   c->m = 1;
   c->t = 1;
   BDG_CUDA_TRY(cudaMemsetAsync(c->counters, 0, 8 * 4, st));
@@ -373,17 +453,19 @@ __global__ void item_table_kernel(int m, int rounds, const int32_t* __restrict__
   for (int32_t it = io[r]; it < io[r + 1]; ++it) out[it] = r;
 }
 
-size_t bdg_csr_bytes(int64_t N, int m, int t, int W, int tile_v) {
+size_t bdg_csr_bytes(int64_t N, int m, int t, int W, int tile_v, int pivots) {
   const size_t ts = t > 1 ? (size_t)(t - 1) : 1;
   const size_t blk = (size_t)((N + bdg_home_block(N, m) - 1) / bdg_home_block(N, m)) * m * 4;
   const size_t stride = (size_t)bdg_csr_item_stride(N, m, tile_v);
   return al((m + 1) * 4) * 3 + al(ts * (m + 1) * 4) * 2 + al(N * 4) + al(N * W * 8) +
          al(N * t * 4) + al(N * t) + al(m * 4) + al(bdg_csr_counter_words(m, t) * 4) + al(N) +
-         al(blk) + al(stride * 4) + al(ts * stride * 4);
+         al(blk) + al(stride * 4) + al(ts * stride * 4) +
+         (pivots > 1 ? al(N * 4) + al((N + (int64_t)BDG_TC_TILE * m) * 4) : 0);
 }
 
 bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
-                         int t, int tile_v, void* mem, bdg_csr* c, cudaStream_t st) {
+                         int t, int tile_v, int pivots, void* mem, bdg_csr* c,
+                         cudaStream_t st) {
   if (m > kMaxSortM)
     return bdg_set_error(BDG_EUNSUPPORTED, "m = %d partitions exceeds %d", m, kMaxSortM);
   bdg_prof_scope prof("bucket", st);
@@ -405,6 +487,13 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   c->item_stride = bdg_csr_item_stride(N, m, tile_v);
   c->item_lo_a = (int32_t*)p;  p += al((size_t)c->item_stride * 4);
   c->item_lo = (int32_t*)p;    p += al(ts * (size_t)c->item_stride * 4);
+  c->home_loc = c->loc_idr = nullptr;
+  if (pivots > 1) {
+    if (pivots > BDG_MAX_PIVOTS || (W != 4 && W != 8))
+      return bdg_set_error(BDG_EINVAL, "locality order: %d pivots at %d-bit codes", pivots, 64 * W);
+    c->home_loc = (int32_t*)p;   p += al(N * 4);
+    c->loc_idr = (int32_t*)p;    p += al((N + (int64_t)BDG_TC_TILE * m) * 4);
+  }
   c->counters = (int32_t*)p;
   int32_t* hcnt = c->counters;
   int32_t* vcnt = c->counters + m;
@@ -458,5 +547,17 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
                                                           W, c->home_codes);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
+  if (pivots > 1) {
+    if (W == 4)
+      locality_kernel<4><<<bdg_cdiv(m, 4), 128, 0, st>>>(c->home_codes, c->home_ids, c->home_off,
+                                                         c->eoff, m, pivots, c->home_loc,
+                                                         c->loc_idr);
+    else
+      locality_kernel<8><<<bdg_cdiv(m, 4), 128, 0, st>>>(c->home_codes, c->home_ids, c->home_off,
+                                                         c->eoff, m, pivots, c->home_loc,
+                                                         c->loc_idr);
+    BDG_CUDA_TRY(cudaGetLastError());
+    bdg_note_launch();
+  }
   return BDG_OK;
 }

@@ -96,7 +96,7 @@ struct bdg_csr {
   int8_t* visit_slot;  // [N * t]  slot s of that partition in the visitor's route list
   int32_t* part_order; // [m]      partitions by decreasing |H_p| (then p)
   int32_t* item_off;   // [m + 1]  work items per partition in part_order order
-  int32_t* eoff;       // [m + 1]  row offsets of H_p in the 64-row-padded expanded operand
+  int32_t* eoff;       // [m + 1]  row offsets of H_p in the 128-row-padded expanded operand
   int32_t* counters;   // [2 * m + 4] scratch counters
   // round A of a partitioned build visits every point in its home partition
   // (its visitors are H_p itself); the visit_* fields above then hold only the
@@ -110,6 +110,13 @@ struct bdg_csr {
   int32_t* item_lo;
   int64_t item_stride;
   int m, t;
+  // Locality order of each H_p for the tensor path (both null: id order). The
+  // homes of p sorted by (nearest of a few pivot homes of p, id): home_loc holds
+  // their ids (round A visits the homes in this order), loc_idr, per row of the
+  // 128-row-padded expanded operand, the id rank of the home in that row (its
+  // position in home_ids; 0 in padding rows).
+  int32_t* home_loc;   // [N]
+  int32_t* loc_idr;    // [eoff[m]]
 };
 // items of one round are at most ceil(visits / tile_v) + m <= N / tile_v + m + 1
 inline int64_t bdg_csr_item_stride(int64_t N, int m, int tile_v) {
@@ -134,15 +141,18 @@ inline bdg_csr bdg_csr_subround(const bdg_csr& c, int s) {
 inline bdg_csr bdg_csr_round_a(const bdg_csr& c) {
   bdg_csr a = c;
   a.visit_off = c.home_off;
-  a.visit_ids = c.home_ids;
+  a.visit_ids = c.home_loc ? c.home_loc : c.home_ids;
   a.visit_slot = c.slot_zero;
   a.item_off = c.item_off_a;
   a.item_lo = c.item_lo_a;
   return a;
 }
-size_t bdg_csr_bytes(int64_t N, int m, int t, int W, int tile_v);
+// pivots > 1: also the locality order of every H_p over `pivots` pivot homes
+size_t bdg_csr_bytes(int64_t N, int m, int t, int W, int tile_v, int pivots);
 bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
-                         int t, int tile_v, void* mem, bdg_csr* csr, cudaStream_t st);
+                         int t, int tile_v, int pivots, void* mem, bdg_csr* csr,
+                         cudaStream_t st);
+constexpr int BDG_MAX_PIVOTS = 32;
 // one partition: every point is a home (identity order, codes used in place);
 // the visitors are the given rows
 size_t bdg_csr_rows_bytes(int64_t N, int64_t nrows, int tile_v);

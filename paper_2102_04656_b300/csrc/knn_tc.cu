@@ -44,7 +44,7 @@ constexpr int kM = 128;         // visitors per item (TMEM lanes)
 constexpr int kNT = BDG_TC_TILE;  // homes per tile (TMEM columns per accumulator)
 constexpr int kSub = 64;        // columns the epilogue reads from TMEM at a time
 constexpr int kMaxStages = 4;   // home-tile ring in shared memory (2 stages of 64 KB at 512 bits)
-constexpr int kCap = 188;       // candidate slots per row
+constexpr int kCap = 180;       // candidate slots per row
 constexpr int kHalf = 16;       // compaction is checked every 16 columns
 constexpr int kSortN = 128;     // keys sorted per row at selection (sub-rounds)
 constexpr int kOutSlot = 96;    // first slot of a row's ranked words (round A / one round)
@@ -56,6 +56,7 @@ static_assert(kOutSlot >= kNeedMax && kOutSlot + kNeedMax <= kCap,
 // slot each row is at
 constexpr int kCandStride = kM;
 constexpr int kThreads = 192;   // warps 0-3 epilogue, warp 4 producer, warp 5 MMA
+constexpr int kIdrSlots = 8;    // tiles of home id ranks in flight (locality order)
 constexpr uint32_t kPolls = 1u << 20;
 constexpr int kPosBits = 21;    // home position bits in a candidate word
 constexpr uint32_t kPosMask = (1u << kPosBits) - 1;
@@ -73,10 +74,11 @@ struct TcCfg {
   static constexpr uint32_t OFF_B = 0;
   static constexpr uint32_t OFF_CAND = OFF_B + STAGES * B_BYTES;
   static constexpr uint32_t OFF_SORT = OFF_CAND + CAND_BYTES;     // 4 warps x 128 keys
-  static constexpr uint32_t OFF_BAR = OFF_SORT + 4 * kSortN * 8;
+  static constexpr uint32_t OFF_IDR = OFF_SORT + 4 * kSortN * 8;   // kIdrSlots x 128 id ranks
+  static constexpr uint32_t OFF_BAR = OFF_IDR + kIdrSlots * kNT * 4;
   static constexpr uint32_t SMEM = OFF_BAR + 256;
-  static_assert(OFF_B % 16 == 0 && OFF_CAND % 16 == 0 &&
-                    OFF_SORT % 16 == 0 && OFF_BAR % 16 == 0,
+  static_assert(OFF_B % 16 == 0 && OFF_CAND % 16 == 0 && OFF_SORT % 16 == 0 &&
+                    OFF_IDR % 16 == 0 && OFF_BAR % 16 == 0,
                 "shared-memory regions must be 16-byte aligned");
   static_assert(SMEM <= 232448, "shared memory per block exceeds 227 KB");
   static_assert(kAccCols + KB / 4 <= kTmemCols, "visitor operand does not fit in TMEM");
@@ -110,12 +112,14 @@ __device__ __forceinline__ void arrive_expect_tx(uint64_t* bar, uint32_t bytes) 
 }
 
 // Expanded home operand: row e of the 128-padded order of partition p holds
-// home_codes[home_off[p] + (e - eoff[p])] (zeros past |H_p|) as KB bytes of
-// E4M3 in the K-major core-matrix layout (8-row groups of KB * 8 bytes).
+// home_codes[home_off[p] + r] with r = e - eoff[p] (id order) or r = loc_idr[e]
+// (locality order), zeros past |H_p|, as KB bytes of E4M3 in the K-major
+// core-matrix layout (8-row groups of KB * 8 bytes).
 template <int W>
 __global__ void expand_homes_kernel(const uint64_t* __restrict__ home_codes,
                                     const int32_t* __restrict__ home_off,
-                                    const int32_t* __restrict__ eoff, int m, int64_t max_rows,
+                                    const int32_t* __restrict__ eoff,
+                                    const int32_t* __restrict__ loc_idr, int m, int64_t max_rows,
                                     uint8_t* __restrict__ hexp) {
   constexpr int KB = 64 * W, Q = 4 * W;  // 16-bit chunks per code
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,8 +138,9 @@ __global__ void expand_homes_kernel(const uint64_t* __restrict__ home_codes,
   const int64_t local = e - eoff[lo];
   const int32_t nh = home_off[lo + 1] - home_off[lo];
   uint4 v = make_uint4(0, 0, 0, 0);
-  if (local < nh) {
-    const uint64_t word = home_codes[(int64_t)(home_off[lo] + local) * W + (q >> 2)];
+  if (local < nh) {  // locality order: row e holds the home of id rank loc_idr[e]
+    const int64_t src = home_off[lo] + (loc_idr ? (int64_t)loc_idr[e] : local);
+    const uint64_t word = home_codes[src * W + (q >> 2)];
     v = expand16((uint32_t)(word >> (16 * (q & 3))) & 0xFFFFu);
   }
   *reinterpret_cast<uint4*>(hexp + grp * (int64_t)(KB * 8) + (int64_t)q * 128 + rr * 16) = v;
@@ -164,14 +169,17 @@ __device__ __forceinline__ int count_le(const uint32_t* crow, int cnt, int dm) {
   return c2;
 }
 
-// Exact compaction of one row's list. Every listed word is below thr_w, and the
-// list is in position order (words are appended by increasing position and
-// compaction keeps their order). Once it holds need_k words, the bound becomes
-// the need_k-th smallest distance and the words above it are dropped; if ties
-// at that distance still leave more than `limit` words, the need_k-th smallest
-// word itself becomes the bound, leaving exactly need_k. Returns the new count.
+// Exact compaction of one row's list. Every listed word is below thr_w. Once
+// the list holds need_k words, the bound becomes the need_k-th smallest
+// distance and the words above it are dropped; if ties at that distance still
+// leave more than `limit` words, the need_k-th smallest word itself becomes the
+// bound, leaving exactly need_k. `ordered`: the list is in word order within a
+// distance (homes in id order: words are appended by increasing position and
+// compaction keeps their order); otherwise (locality order) the word is found
+// by a radix descent over the low `rank_bits` bits of the words at that
+// distance. Returns the new count.
 __device__ __forceinline__ int compact_exact(uint32_t* crow, int cnt, uint32_t& thr_w, int need_k,
-                                             int bits, int limit) {
+                                             int bits, int limit, bool ordered, int rank_bits) {
   if (cnt < need_k) return cnt;
   // the k-th distance: binary search over [0, td], td the bound's distance;
   // between compactions it usually drops by a few units, so [td - 7, td] is
@@ -195,10 +203,27 @@ __device__ __forceinline__ int compact_exact(uint32_t* crow, int cnt, uint32_t& 
     for (int x = 0; x < cnt; ++x) c_lt += ((int)(crow[x * kCandStride] >> kPosBits) < lo);
     const int want = need_k - c_lt;  // 1-based rank among the words at distance lo
     uint32_t wk = thr_w - 1u;
-    int seen = 0;
-    for (int x = 0; x < cnt; ++x) {
-      const uint32_t e = crow[x * kCandStride];
-      if ((int)(e >> kPosBits) == lo && ++seen == want) { wk = e; break; }
+    if (ordered) {
+      int seen = 0;
+      for (int x = 0; x < cnt; ++x) {
+        const uint32_t e = crow[x * kCandStride];
+        if ((int)(e >> kPosBits) == lo && ++seen == want) { wk = e; break; }
+      }
+    } else {
+      // the want-th smallest low field among the words at distance lo (the words
+      // differ): bit by bit from the top, count the words at lo whose field
+      // matches the prefix chosen so far followed by a 0
+      const uint32_t dlo = (uint32_t)lo << kPosBits;
+      uint32_t pref = 0;
+      int need = want;
+      for (int bit = rank_bits - 1; bit >= 0; --bit) {
+        const uint32_t mask = ~((1u << bit) - 1u);  // distance and the field's bits >= bit
+        int c0 = 0;
+#pragma unroll 8
+        for (int x = 0; x < cnt; ++x) c0 += ((crow[x * kCandStride] & mask) == (dlo | pref)) ? 1 : 0;
+        if (c0 < need) { need -= c0; pref |= 1u << bit; }
+      }
+      wk = dlo | pref;
     }
     thr_w = wk + 1u;
     cnt = compact_row(crow, cnt, thr_w);
@@ -221,9 +246,11 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   uint64_t* tfull = bars + 2 * kMaxStages;  // [kAcc]
   uint64_t* tempty = tfull + kAcc;        // [kAcc]
   uint64_t* drain = tempty + kAcc;        // MMA drain at exit
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
-  int32_t* s_item = reinterpret_cast<int32_t*>(drain + 2);
-  volatile int32_t* s_abort = reinterpret_cast<int32_t*>(drain + 3);
+  uint64_t* idr_full = drain + 1;         // [kIdrSlots] a tile's home id ranks landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(idr_full + kIdrSlots);
+  int32_t* s_item = reinterpret_cast<int32_t*>(idr_full + kIdrSlots) + 1;
+  volatile int32_t* s_abort = reinterpret_cast<int32_t*>(idr_full + kIdrSlots) + 2;
+  int32_t* idr_sm = reinterpret_cast<int32_t*>(sm + C::OFF_IDR);
 
   const bdg_knn_args& a = ta.base;
   const bdg_csr& c = a.csr;
@@ -243,6 +270,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       tc05::mbar_init(&tempty[i], 4);
     }
     tc05::mbar_init(drain, 1);
+    for (int i = 0; i < kIdrSlots; ++i) tc05::mbar_init(&idr_full[i], 1);
     *s_abort = 0;
     tc05::mbar_fence_init();
   }
@@ -253,6 +281,13 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   const uint32_t id_mma = tc05::idesc(0u, 0u, kM, kNT);  // E4M3 x E4M3 -> F32
   uint32_t g = 0;       // tiles processed by this CTA so far (drives barrier phases)
   uint32_t nprod = 0;   // tiles whose copies the producer issued
+  // Locality order (loc_idr set): the operand rows are the homes sorted by pivot,
+  // each tile comes with the id ranks of its 128 homes, candidate words carry
+  // those ranks, and round A starts every item at its own tile (its visitors are
+  // that tile's homes) and wraps around.
+  const int32_t* loc_idr = c.loc_idr;
+  const bool ordered = loc_idr == nullptr;
+  const bool own_first = loc_idr != nullptr && !a.merge_running;
 
   for (;;) {
     __syncthreads();
@@ -269,6 +304,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
     const int nh = c.home_off[p + 1] - h0;
     const int ntiles = (nh + kNT - 1) / kNT;
     const int64_t e0 = c.eoff[p];
+    const int rank_bits = nh > 1 ? 32 - __clz(nh - 1) : 1;  // bits of an id rank in H_p
     if (nh > (int)kPosMask) {  // positions do not fit a candidate word: popcount fixup
       for (int r = tid; r < nv; r += kThreads) ta.fixflag[v0 + r] = 1;
       if (tid == 0) ta.err[1] = 1;
@@ -308,9 +344,19 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           if (use > 0 && !tc05::mbar_wait(&empty[st], (use - 1) & 1, kPolls)) {
             atomicExch(ta.err, 1); *s_abort = 1; break;
           }
+          const int jt = own_first ? (j + tile) % ntiles : j;  // the home tile
           arrive_expect_tx(&full[st], C::B_BYTES);
           bulk_g2s(tc05::smem_u32(sm + C::OFF_B + st * C::B_BYTES),
-                   ta.hexp + (e0 + (int64_t)j * kNT) * KB, C::B_BYTES, &full[st]);
+                   ta.hexp + (e0 + (int64_t)jt * kNT) * KB, C::B_BYTES, &full[st]);
+          if (loc_idr) {
+            // slot gg % kIdrSlots is free: the epilogue is at most kIdrSlots - 1
+            // tiles behind (this copy needed the MMAs of tile gg - kStages, those
+            // needed the accumulator of tile gg - kStages - kAcc read)
+            const uint32_t is = gg % kIdrSlots;
+            arrive_expect_tx(&idr_full[is], kNT * 4);
+            bulk_g2s(tc05::smem_u32(idr_sm + is * kNT), loc_idr + e0 + (int64_t)jt * kNT,
+                     kNT * 4, &idr_full[is]);
+          }
           ++nprod;
         }
       }
@@ -373,7 +419,10 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       float lim = lim_of(thr_w);
       for (int j = 0; j < ntiles; ++j) {
         const uint32_t gg = g + j, b = gg % kAcc;
-        bool ok = !*s_abort && tc05::mbar_wait(&tfull[b], (gg / kAcc) & 1, kPolls);
+        const int jt = own_first ? (j + tile) % ntiles : j;  // the home tile
+        bool ok = !*s_abort && tc05::mbar_wait(&tfull[b], (gg / kAcc) & 1, kPolls) &&
+                  (!loc_idr ||
+                   tc05::mbar_wait(&idr_full[gg % kIdrSlots], (gg / kIdrSlots) & 1, kPolls));
         ok = __all_sync(0xffffffffu, ok);  // the warp leaves together
         if (!ok) {
           if (lane == 0) { atomicExch(ta.err, 3); *s_abort = 1; }
@@ -392,7 +441,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             __syncwarp();
             if (lane == 0) tc05::mbar_arrive(&tempty[b]);
           }
-          const uint32_t pos0 = (uint32_t)(j * kNT + sub * kSub);
+          const uint32_t pos0 = (uint32_t)(jt * kNT + sub * kSub);
           const int nvalid = min(kSub, nh - (int)pos0);
           if (nvalid <= 0) continue;  // past the partition's last home
           if (nvalid < kSub) {  // ragged last columns: missing homes read as d = bits + 1
@@ -420,7 +469,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             // serialise the warp); only needed before an append, so skipped groups
             // do not pay for the check
             if (__any_sync(0xffffffffu, cnt > kCap - kHalf)) {
-              cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kCap - kHalf);
+              cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kCap - kHalf, ordered, rank_bits);
               if (cnt > kCap - kHalf) {  // cannot happen (need_k <= 65); kept as a guard:
                 overflow = true;         // the popcount kernel redoes this row
                 thr_w = 0u;
@@ -432,12 +481,28 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             // words below the threshold advance it
             uint32_t* const wp0 = crow + cnt * kCandStride;
             uint32_t* wp = wp0;
-            const uint32_t posq = pos0 + (uint32_t)(half * kHalf);
+            // the low bits of a word: the home's position (id order) or its id
+            // rank (locality order, from the tile's ranks in shared memory)
+            uint32_t lw[kHalf];
+            if (loc_idr) {
+              const uint4* ir = reinterpret_cast<const uint4*>(
+                  idr_sm + (gg % kIdrSlots) * kNT + sub * kSub + half * kHalf);
+  #pragma unroll
+              for (int q = 0; q < kHalf / 4; ++q) {
+                const uint4 t4 = ir[q];
+                lw[4 * q] = (uint32_t)t4.x; lw[4 * q + 1] = (uint32_t)t4.y;
+                lw[4 * q + 2] = (uint32_t)t4.z; lw[4 * q + 3] = (uint32_t)t4.w;
+              }
+            } else {
+              const uint32_t posq = pos0 + (uint32_t)(half * kHalf);
+  #pragma unroll
+              for (int c2 = 0; c2 < kHalf; ++c2) lw[c2] = posq + c2;
+            }
   #pragma unroll
             for (int c2 = 0; c2 < kHalf; ++c2) {
               const float dot = __uint_as_float(v[half * kHalf + c2]);
               const uint32_t fb = __float_as_uint(fmaf(dot, -0.5f, hmagic));
-              const uint32_t word = fb * (1u << kPosBits) + (posq + c2);
+              const uint32_t word = fb * (1u << kPosBits) + lw[c2];
               *wp = word;
               wp += (word < thr_w) ? kCandStride : 0;
             }
@@ -453,7 +518,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         // slots 0..; then each warp writes its 32 rows, coalesced, without the
         // self pair.
         if (__any_sync(0xffffffffu, !overflow && cnt > need_k)) {
-          if (!overflow && cnt > need_k) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, need_k);
+          if (!overflow && cnt > need_k) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, need_k, ordered, rank_bits);
         }
         if (cnt > need_k) overflow = true;  // cannot happen; the popcount kernel would redo it
         int self_j = kNeedMax;  // sorted index of the self pair (none: kNeedMax)
@@ -536,7 +601,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         // list's k-th key (they cannot enter); then each warp sorts, row by row,
         // the few surviving keys and merges them into the running list.
         if (__any_sync(0xffffffffu, !overflow && cnt > need_k)) {
-          if (!overflow && cnt > need_k) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, need_k);
+          if (!overflow && cnt > need_k) cnt = compact_exact(crow, cnt, thr_w, need_k, bits, need_k, ordered, rank_bits);
         }
         if (cnt > need_k) overflow = true;  // cannot happen; the popcount kernel would redo it
         if (!overflow) {
@@ -633,6 +698,9 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
     // copies issued but possibly never consumed: wait for their completion
     for (uint32_t gg = (nprod > kStages ? nprod - kStages : 0); gg < nprod; ++gg)
       tc05::mbar_wait(&full[gg % kStages], (gg / kStages) & 1, kPolls);
+    if (loc_idr)
+      for (uint32_t gg = (nprod > kIdrSlots ? nprod - kIdrSlots : 0); gg < nprod; ++gg)
+        tc05::mbar_wait(&idr_full[gg % kIdrSlots], (gg / kIdrSlots) & 1, kPolls);
   }
   tc05::fence_before();
   __syncthreads();
@@ -648,7 +716,7 @@ bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
     const int64_t nthreads = ((max_rows + 7) / 8) * 8 * (4 * W);
     bdg_prof_scope prof(a.prof ? a.prof : "expand", st);
     expand_homes_kernel<W><<<bdg_cdiv(nthreads, 256), 256, 0, st>>>(
-        a.csr.home_codes, a.csr.home_off, a.csr.eoff, a.m, max_rows, ta.hexp);
+        a.csr.home_codes, a.csr.home_off, a.csr.eoff, a.csr.loc_idr, a.m, max_rows, ta.hexp);
     BDG_CUDA_TRY(cudaGetLastError());
     bdg_note_launch();
   }
