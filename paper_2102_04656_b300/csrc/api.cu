@@ -357,8 +357,10 @@ bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_
   c->b_cent = c->need_bk ? al((size_t)m * W * 8) : 0;
   c->b_bk = c->need_bk ? al(bdg_bkmeans_scratch_bytes(P->bk_sample_size, m, W)) : 0;
   // homes in locality order for the tensor path where partitions span many
-  // tiles (own tile first in round A; candidate words keep (d, id) order)
-  c->pivots = c->tc_ok && m > 1 && N / m >= kLocMinHomes ? kLocPivots : 0;
+  // tiles (own tile first in round A; candidate words keep (d, id) order); with
+  // 512-bit codes only: with 256-bit codes (k = 32, ~10,000 homes per
+  // partition) it measured slower
+  c->pivots = c->tc_ok && W == 8 && m > 1 && N / m >= kLocMinHomes ? kLocPivots : 0;
   c->b_csr = al(bdg_csr_bytes(N, m, t, W, c->tile_v, c->pivots));
   c->b_part = t > 1 ? al((size_t)N * k * 8) : 0;  // running k-lists
   c->b_hexp = c->tc_ok ? al(bdg_knn_tc_hexp_bytes(N, m, W)) : 0;

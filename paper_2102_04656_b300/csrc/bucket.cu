@@ -281,34 +281,30 @@ __global__ void centres_plan_kernel(int64_t n, int m, int tile_v, int32_t* __res
 // ---- locality order of H_p (tensor path): the homes of p sorted by (nearest of
 // P pivot homes, id). The pivots are the homes at positions (2i + 1) |H_p| / (2P)
 // of H_p in id order, and a home's nearest pivot is the first one at the least
-// Hamming distance. One warp per partition: a counting pass, a scan over the P
-// counts and a stable scatter in id order (ranks among equal keys by lane).
-// The order changes no result: candidate words carry the id rank (loc_idr), so
-// they still order by (d, id).
+// Hamming distance. The order changes no result: candidate words carry the id
+// rank (loc_idr), so they still order by (d, id).
+//
+// Keys: block (p, y) takes the chunks y, y + gridDim.y, ... of 256 homes of p,
+// with p's pivots in shared memory; one thread per home.
 template <int W>
-__global__ void __launch_bounds__(128)
-locality_kernel(const uint64_t* __restrict__ home_codes, const int32_t* __restrict__ home_ids,
-                const int32_t* __restrict__ home_off, const int32_t* __restrict__ eoff, int m,
-                int P, int32_t* __restrict__ home_loc, int32_t* __restrict__ loc_idr) {
-  __shared__ uint64_t piv_all[4][BDG_MAX_PIVOTS * W];
-  __shared__ int32_t cnt_all[4][BDG_MAX_PIVOTS];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = blockIdx.x * 4 + warp;
-  if (p >= m) return;  // whole warps only: no block-wide barrier below
+__global__ void __launch_bounds__(256)
+pivot_key_kernel(const uint64_t* __restrict__ home_codes, const int32_t* __restrict__ home_off,
+                 int m, int P, int8_t* __restrict__ key) {
+  __shared__ uint64_t piv[BDG_MAX_PIVOTS * W];
+  const int p = blockIdx.x;
   const int h0 = home_off[p], nh = home_off[p + 1] - h0;
-  const int64_t e0 = eoff[p];
-  const int npad = (nh + BDG_TC_TILE - 1) & ~(BDG_TC_TILE - 1);
-  uint64_t* piv = piv_all[warp];
-  int32_t* cnt = cnt_all[warp];
-  const int np = min(P, nh);  // pivots (none for an empty partition)
-  for (int x = lane; x < np * W; x += 32) {
+  const int np = min(P, nh);
+  if (np <= 1) {  // one pivot or none: every key is 0
+    for (int x = blockIdx.y * 256 + threadIdx.x; x < nh; x += gridDim.y * 256) key[h0 + x] = 0;
+    return;
+  }
+  for (int x = threadIdx.x; x < np * W; x += 256) {
     const int i = x / W, w = x % W;
     const int pos = (int)(((2LL * i + 1) * nh) / (2LL * np));
     piv[x] = home_codes[(int64_t)(h0 + pos) * W + w];
   }
-  for (int i = lane; i < BDG_MAX_PIVOTS; i += 32) cnt[i] = 0;
-  __syncwarp();
-  auto nearest = [&](int x) -> int {
+  __syncthreads();
+  for (int x = blockIdx.y * 256 + threadIdx.x; x < nh; x += gridDim.y * 256) {
     uint64_t hc[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) hc[w] = home_codes[(int64_t)(h0 + x) * W + w];
@@ -319,40 +315,61 @@ locality_kernel(const uint64_t* __restrict__ home_codes, const int32_t* __restri
       for (int w = 0; w < W; ++w) d += __popcll(hc[w] ^ piv[i * W + w]);
       if (d < bd) { bd = d; best = i; }
     }
-    return best;
-  };
-  for (int x0 = 0; x0 < nh; x0 += 32) {
-    const int x = x0 + lane;
-    if (x < nh) atomicAdd(&cnt[nearest(x)], 1);
+    key[h0 + x] = (int8_t)best;
   }
+}
+
+// Stable counting sort of each H_p by key, one block of 32 warps per partition:
+// warp w owns the w-th of 32 consecutive segments of H_p; the warps count their
+// keys, an exclusive scan over (key, warp) gives each warp's cursors, and every
+// warp then places its segment in order (ranks among equal keys by lane).
+__global__ void __launch_bounds__(1024)
+pivot_sort_kernel(const int8_t* __restrict__ key, const int32_t* __restrict__ home_ids,
+                  const int32_t* __restrict__ home_off, const int32_t* __restrict__ eoff,
+                  int32_t* __restrict__ home_loc, int32_t* __restrict__ loc_idr) {
+  __shared__ int32_t wcnt[32][BDG_MAX_PIVOTS];
+  const int p = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h0 = home_off[p], nh = home_off[p + 1] - h0;
+  const int64_t e0 = eoff[p];
+  const int npad = (nh + BDG_TC_TILE - 1) & ~(BDG_TC_TILE - 1);
+  const int seg = (nh + 31) / 32;
+  const int s0 = min(nh, warp * seg), s1 = min(nh, s0 + seg);
+  if (lane < BDG_MAX_PIVOTS) wcnt[warp][lane] = 0;
   __syncwarp();
-  {  // exclusive scan of the counts (np <= 32: one per lane) into cursors
-    const int cv = lane < np ? cnt[lane] : 0;
-    int incl = cv;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    __syncwarp();
-    if (lane < np) cnt[lane] = incl - cv;
+  for (int x0 = s0; x0 < s1; x0 += 32) {
+    const int x = x0 + lane;
+    const int kx = x < s1 ? (int)key[h0 + x] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, kx);
+    if (kx >= 0 && __popc(same & ((1u << lane) - 1u)) == 0) wcnt[warp][kx] += __popc(same);
     __syncwarp();
   }
-  for (int x0 = 0; x0 < nh; x0 += 32) {
+  __syncthreads();
+  if (threadIdx.x == 0) {  // cursors: keys in order, warps in order within a key
+    int run = 0;
+    for (int kk = 0; kk < BDG_MAX_PIVOTS; ++kk)
+      for (int w = 0; w < 32; ++w) {
+        const int cv = wcnt[w][kk];
+        wcnt[w][kk] = run;
+        run += cv;
+      }
+  }
+  __syncthreads();
+  for (int x0 = s0; x0 < s1; x0 += 32) {
     const int x = x0 + lane;
-    const int key = x < nh ? nearest(x) : -1;
-    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const int kx = x < s1 ? (int)key[h0 + x] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, kx);
     const int rank = __popc(same & ((1u << lane) - 1u));
-    const int pos = key >= 0 ? cnt[key] + rank : 0;
+    const int pos = kx >= 0 ? wcnt[warp][kx] + rank : 0;
     __syncwarp();
-    if (key >= 0 && rank == 0) cnt[key] += __popc(same);  // the group's first lane advances it
+    if (kx >= 0 && rank == 0) wcnt[warp][kx] += __popc(same);  // the group's first lane advances it
     __syncwarp();
-    if (key >= 0) {
+    if (kx >= 0) {
       loc_idr[e0 + pos] = x;
       home_loc[h0 + pos] = home_ids[h0 + x];
     }
   }
-  for (int q = nh + lane; q < npad; q += 32) loc_idr[e0 + q] = 0;
+  for (int q = nh + (int)threadIdx.x; q < npad; q += 1024) loc_idr[e0 + q] = 0;
 }
 
 }  // namespace
@@ -460,7 +477,7 @@ size_t bdg_csr_bytes(int64_t N, int m, int t, int W, int tile_v, int pivots) {
   return al((m + 1) * 4) * 3 + al(ts * (m + 1) * 4) * 2 + al(N * 4) + al(N * W * 8) +
          al(N * t * 4) + al(N * t) + al(m * 4) + al(bdg_csr_counter_words(m, t) * 4) + al(N) +
          al(blk) + al(stride * 4) + al(ts * stride * 4) +
-         (pivots > 1 ? al(N * 4) + al((N + (int64_t)BDG_TC_TILE * m) * 4) : 0);
+         (pivots > 1 ? al(N * 4) + al((N + (int64_t)BDG_TC_TILE * m) * 4) + al(N) : 0);
 }
 
 bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t* routes, int m,
@@ -494,6 +511,8 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
     c->home_loc = (int32_t*)p;   p += al(N * 4);
     c->loc_idr = (int32_t*)p;    p += al((N + (int64_t)BDG_TC_TILE * m) * 4);
   }
+  int8_t* loc_key = pivots > 1 ? (int8_t*)p : nullptr;  // nearest pivot per home position
+  if (pivots > 1) p += al(N);
   c->counters = (int32_t*)p;
   int32_t* hcnt = c->counters;
   int32_t* vcnt = c->counters + m;
@@ -548,16 +567,16 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   if (pivots > 1) {
+    const dim3 kgrid(m, 32);
     if (W == 4)
-      locality_kernel<4><<<bdg_cdiv(m, 4), 128, 0, st>>>(c->home_codes, c->home_ids, c->home_off,
-                                                         c->eoff, m, pivots, c->home_loc,
-                                                         c->loc_idr);
+      pivot_key_kernel<4><<<kgrid, 256, 0, st>>>(c->home_codes, c->home_off, m, pivots, loc_key);
     else
-      locality_kernel<8><<<bdg_cdiv(m, 4), 128, 0, st>>>(c->home_codes, c->home_ids, c->home_off,
-                                                         c->eoff, m, pivots, c->home_loc,
-                                                         c->loc_idr);
+      pivot_key_kernel<8><<<kgrid, 256, 0, st>>>(c->home_codes, c->home_off, m, pivots, loc_key);
     BDG_CUDA_TRY(cudaGetLastError());
-    bdg_note_launch();
+    pivot_sort_kernel<<<m, 1024, 0, st>>>(loc_key, c->home_ids, c->home_off, c->eoff,
+                                          c->home_loc, c->loc_idr);
+    BDG_CUDA_TRY(cudaGetLastError());
+    bdg_note_launch(2);
   }
   return BDG_OK;
 }

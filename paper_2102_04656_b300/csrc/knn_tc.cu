@@ -146,6 +146,16 @@ __global__ void expand_homes_kernel(const uint64_t* __restrict__ home_codes,
   *reinterpret_cast<uint4*>(hexp + grp * (int64_t)(KB * 8) + (int64_t)q * 128 + rr * 16) = v;
 }
 
+// The j-th tile an item visits in locality order: tile `own` first, then
+// alternately the next tile to the right and to the left while both sides have
+// tiles, then the rest of the longer side (a bijection on [0, n)).
+__device__ __forceinline__ int spiral_tile(int j, int own, int n) {
+  if (j == 0) return own;
+  const int s = min(own, n - 1 - own);  // tiles on the shorter side
+  if (j <= 2 * s) return own + ((j & 1) ? (j + 1) / 2 : -(j / 2));
+  return own + (n - 1 - own > own ? j - s : -(j - s));
+}
+
 __device__ __forceinline__ uint32_t cidx(int c, int r) {  // candidate slot c of row r
   return (uint32_t)(c * kCandStride + r);
 }
@@ -282,12 +292,12 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   uint32_t g = 0;       // tiles processed by this CTA so far (drives barrier phases)
   uint32_t nprod = 0;   // tiles whose copies the producer issued
   // Locality order (loc_idr set): the operand rows are the homes sorted by pivot,
-  // each tile comes with the id ranks of its 128 homes, candidate words carry
-  // those ranks, and round A starts every item at its own tile (its visitors are
-  // that tile's homes) and wraps around.
+  // each tile comes with the id ranks of its 128 homes, and candidate words
+  // carry those ranks. In round A an item visits the tiles in a spiral from its
+  // own tile (its visitors are that tile's homes); sub-round items visit the
+  // tiles in order.
   const int32_t* loc_idr = c.loc_idr;
   const bool ordered = loc_idr == nullptr;
-  const bool own_first = loc_idr != nullptr && !a.merge_running;
 
   for (;;) {
     __syncthreads();
@@ -305,6 +315,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
     const int ntiles = (nh + kNT - 1) / kNT;
     const int64_t e0 = c.eoff[p];
     const int rank_bits = nh > 1 ? 32 - __clz(nh - 1) : 1;  // bits of an id rank in H_p
+    const int start = loc_idr != nullptr && !a.merge_running ? tile : -1;  // spiral start
     if (nh > (int)kPosMask) {  // positions do not fit a candidate word: popcount fixup
       for (int r = tid; r < nv; r += kThreads) ta.fixflag[v0 + r] = 1;
       if (tid == 0) ta.err[1] = 1;
@@ -344,7 +355,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           if (use > 0 && !tc05::mbar_wait(&empty[st], (use - 1) & 1, kPolls)) {
             atomicExch(ta.err, 1); *s_abort = 1; break;
           }
-          const int jt = own_first ? (j + tile) % ntiles : j;  // the home tile
+          const int jt = start >= 0 ? spiral_tile(j, start, ntiles) : j;  // the home tile
           arrive_expect_tx(&full[st], C::B_BYTES);
           bulk_g2s(tc05::smem_u32(sm + C::OFF_B + st * C::B_BYTES),
                    ta.hexp + (e0 + (int64_t)jt * kNT) * KB, C::B_BYTES, &full[st]);
@@ -419,7 +430,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       float lim = lim_of(thr_w);
       for (int j = 0; j < ntiles; ++j) {
         const uint32_t gg = g + j, b = gg % kAcc;
-        const int jt = own_first ? (j + tile) % ntiles : j;  // the home tile
+        const int jt = start >= 0 ? spiral_tile(j, start, ntiles) : j;  // the home tile
         bool ok = !*s_abort && tc05::mbar_wait(&tfull[b], (gg / kAcc) & 1, kPolls) &&
                   (!loc_idr ||
                    tc05::mbar_wait(&idr_full[gg % kIdrSlots], (gg / kIdrSlots) & 1, kPolls));

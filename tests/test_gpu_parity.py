@@ -92,8 +92,9 @@ def test_exact_knn_all_equal_codes(bdg, kernel):
 def test_heavy_ties_bit_exact(bdg, bits, k, m, t, kernel):
     """Codes drawn from 40 distinct values: every row meets long runs of equal
     distances, so the lists keep filling with ties at the k-th distance. With
-    m = 2 the partitions hold ~3,000 homes each, so the tensor path sorts them
-    into locality order and the ties at the k-th distance are cut by id rank."""
+    m = 2 the partitions hold ~3,000 homes each, so with 512-bit codes the
+    tensor path sorts them into locality order and the ties at the k-th distance
+    are cut by id rank."""
     n = 6000
     base = datagen.random_codes(40, bits, seed=bits + k)
     pick = np.random.default_rng(bits * 7 + m).integers(0, 40, n)
@@ -225,12 +226,13 @@ def test_routes_gap_bit_exact(bdg):
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("bits,n,m,t,k", [(512, 20000, 16, 3, 64), (256, 9000, 40, 5, 32),
                                           (256, 3000, 8, 8, 16), (128, 5000, 64, 2, 8),
-                                          (512, 20000, 4, 3, 64), (256, 30000, 8, 4, 32)])
+                                          (512, 20000, 4, 3, 64), (512, 30000, 8, 4, 32),
+                                          (256, 30000, 8, 4, 32)])
 def test_partitioned_build_bit_exact(bdg, bits, n, m, t, k, kernel):
-    """Bk-means, routing and Reduce 1 against the oracle. The last two cases
-    have partitions of 3,000-5,000 homes: the tensor path then streams the homes
-    in locality order (nearest of 16 pivot homes) and round A starts every item
-    at its own tile."""
+    """Bk-means, routing and Reduce 1 against the oracle. The last three cases
+    have partitions of 3,000-5,000 homes: with 512-bit codes the tensor path then
+    streams the homes in locality order (nearest of 16 pivot homes) and round A
+    spirals out from every item's own tile."""
     if kernel == "tc" and not _tc_ok(bits, k):
         pytest.skip("tensor path: 256/512-bit codes and k <= 64")
     spec = datagen.MixtureSpec(n, 64, 48, bits, seed=n + m)
