@@ -44,12 +44,16 @@ constexpr int kM = 128;         // visitors per item (TMEM lanes)
 constexpr int kNT = BDG_TC_TILE;  // homes per tile (TMEM columns per accumulator)
 constexpr int kSub = 64;        // columns the epilogue reads from TMEM at a time
 constexpr int kMaxStages = 4;   // home-tile ring in shared memory (2 stages of 64 KB at 512 bits)
-constexpr int kCap = 180;       // candidate slots per row
+// candidate slots per row: 188 with the homes in id order; 180 in locality order,
+// whose tiles' id ranks take 4 KB of shared memory
+template <bool LOC>
+struct CapOf { static constexpr int v = LOC ? 180 : 188; };
 constexpr int kHalf = 16;       // compaction is checked every 16 columns
 constexpr int kSortN = 128;     // keys sorted per row at selection (sub-rounds)
 constexpr int kOutSlot = 96;    // first slot of a row's ranked words (round A / one round)
 constexpr int kNeedMax = 65;    // k + 1 for the largest k the kernel takes
-static_assert(kOutSlot >= kNeedMax && kOutSlot + kNeedMax <= kCap,
+static_assert(kOutSlot >= kNeedMax && kOutSlot + kNeedMax <= CapOf<true>::v &&
+                  kOutSlot + kNeedMax <= CapOf<false>::v,
               "ranked words need k + 1 free slots after the list");
 // words between a row's candidate slots: slot c of row r is word c * kM + r, so
 // the 32 lanes of a warp (32 rows) always touch 32 different banks, whatever
@@ -65,17 +69,18 @@ constexpr int kAcc = 3;                  // accumulators: the MMAs run up to 2 t
 constexpr uint32_t kAccCols = kAcc * kNT;  // accumulators in TMEM columns [0, 384)
 constexpr uint32_t kTmemCols = 512;        // + the visitors' operand in [384, 384 + KB / 4)
 
-template <int W>
+template <int W, bool LOC>
 struct TcCfg {
   static constexpr int KB = 64 * W;               // bytes of one expanded code
   static constexpr uint32_t B_BYTES = kNT * KB;
   static constexpr int STAGES = W >= 8 ? 2 : kMaxStages;
-  static constexpr uint32_t CAND_BYTES = ((kCap * kCandStride * 4) + 15) & ~15u;
+  static constexpr int CAP = CapOf<LOC>::v;
+  static constexpr uint32_t CAND_BYTES = ((CAP * kCandStride * 4) + 15) & ~15u;
   static constexpr uint32_t OFF_B = 0;
   static constexpr uint32_t OFF_CAND = OFF_B + STAGES * B_BYTES;
   static constexpr uint32_t OFF_SORT = OFF_CAND + CAND_BYTES;     // 4 warps x 128 keys
   static constexpr uint32_t OFF_IDR = OFF_SORT + 4 * kSortN * 8;   // kIdrSlots x 128 id ranks
-  static constexpr uint32_t OFF_BAR = OFF_IDR + kIdrSlots * kNT * 4;
+  static constexpr uint32_t OFF_BAR = OFF_IDR + (LOC ? kIdrSlots * kNT * 4 : 0);
   static constexpr uint32_t SMEM = OFF_BAR + 256;
   static_assert(OFF_B % 16 == 0 && OFF_CAND % 16 == 0 && OFF_SORT % 16 == 0 &&
                     OFF_IDR % 16 == 0 && OFF_BAR % 16 == 0,
@@ -241,10 +246,11 @@ __device__ __forceinline__ int compact_exact(uint32_t* crow, int cnt, uint32_t& 
   return cnt;
 }
 
-template <int W>
+template <int W, bool LOC>
 __global__ void __launch_bounds__(kThreads, 1)
 knn_tc_kernel(bdg_knn_tc_args ta) {
-  using C = TcCfg<W>;
+  using C = TcCfg<W, LOC>;
+  constexpr int kCap = C::CAP;
   constexpr int KB = C::KB;
   extern __shared__ __align__(1024) uint8_t sm[];
   uint32_t* cand = reinterpret_cast<uint32_t*>(sm + C::OFF_CAND);
@@ -296,8 +302,8 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   // carry those ranks. In round A an item visits the tiles in a spiral from its
   // own tile (its visitors are that tile's homes); sub-round items visit the
   // tiles in order.
-  const int32_t* loc_idr = c.loc_idr;
-  const bool ordered = loc_idr == nullptr;
+  const int32_t* loc_idr = LOC ? c.loc_idr : nullptr;
+  const bool ordered = !LOC;
 
   for (;;) {
     __syncthreads();
@@ -718,9 +724,20 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   if (warp == 0) tc05::tmem_dealloc(tmem, kTmemCols);
 }
 
+template <int W, bool LOC>
+bdg_status launch_main(const bdg_knn_tc_args& ta, cudaStream_t st) {
+  using C = TcCfg<W, LOC>;
+  BDG_CUDA_TRY(cudaFuncSetAttribute(knn_tc_kernel<W, LOC>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+  bdg_prof_scope prof(ta.base.prof ? ta.base.prof : "knn", st);
+  knn_tc_kernel<W, LOC><<<bdg_num_sms(), kThreads, C::SMEM, st>>>(ta);
+  BDG_CUDA_TRY(cudaGetLastError());
+  bdg_note_launch();
+  return BDG_OK;
+}
+
 template <int W>
 bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
-  using C = TcCfg<W>;
   const bdg_knn_args& a = ta.base;
   if (expand) {  // expanded home operand (rows are bounded by N + BDG_TC_TILE m)
     const int64_t max_rows = a.N + (int64_t)BDG_TC_TILE * a.m;
@@ -731,14 +748,11 @@ bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
     BDG_CUDA_TRY(cudaGetLastError());
     bdg_note_launch();
   }
-  BDG_CUDA_TRY(cudaFuncSetAttribute(knn_tc_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)C::SMEM));
-  const int grid = bdg_num_sms();
-  {
-    bdg_prof_scope prof(a.prof ? a.prof : "knn", st);
-    knn_tc_kernel<W><<<grid, kThreads, C::SMEM, st>>>(ta);
-    BDG_CUDA_TRY(cudaGetLastError());
-    bdg_note_launch();
+  // homes in locality order (id ranks with every tile) or in id order
+  if (a.csr.loc_idr) {
+    BDG_TRY((launch_main<W, true>(ta, st)));
+  } else {
+    BDG_TRY((launch_main<W, false>(ta, st)));
   }
   // rows whose candidate list overflowed: exact recomputation by the popcount kernel
   BDG_CUDA_TRY(cudaMemsetAsync(a.item_counter, 0, sizeof(int32_t), st));
