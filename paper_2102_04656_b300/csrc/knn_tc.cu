@@ -19,13 +19,18 @@
 //     hands the accumulator to the epilogue;
 //   * epilogue (4 warps, one thread per visitor row = TMEM lane): reads its
 //     row's dot products, 64 at a time, and appends the values under its threshold as
-//     words (d << 21 | home position) to a per-row candidate list in shared
-//     memory. The homes of a partition are stored in ascending id order, so
-//     word order is (d, id) order. When a row's list is nearly full, the warp
-//     compacts all its rows together: the threshold of each row becomes its
-//     exact k-th smallest distance so far (binary search over its list), or its
-//     exact k-th smallest word when ties at that distance fill the list. The
-//     threshold only tightens, so every final neighbour is kept.
+//     words (d << 21 | id rank of the home in H_p) to a per-row candidate list
+//     in shared memory, so word order is (d, id) order. When a row's list is
+//     nearly full, the warp compacts all its rows together: the threshold of
+//     each row becomes its exact k-th smallest distance so far (binary search
+//     over its list), or its exact k-th smallest word when ties at that
+//     distance fill the list. The threshold only tightens, so every final
+//     neighbour is kept;
+//   * lookup (one thread of warp 6): takes the next work item from the round's
+//     counter and reads its partition's offsets while the current item runs.
+// The homes are streamed in id order, or in locality order (sorted by nearest
+// pivot home, with every tile's id ranks copied beside it); in locality order
+// a round-A item starts at its own tile and spirals out.
 // At the end of an item, in round A (and in a single-round build) each thread
 // cuts its row's list to its k + 1 best words, ranks them by counting and
 // writes its row without the self pair; in the sub-rounds each warp sorts, row
@@ -59,7 +64,7 @@ static_assert(kOutSlot >= kNeedMax && kOutSlot + kNeedMax <= CapOf<true>::v &&
 // the 32 lanes of a warp (32 rows) always touch 32 different banks, whatever
 // slot each row is at
 constexpr int kCandStride = kM;
-constexpr int kThreads = 192;   // warps 0-3 epilogue, warp 4 producer, warp 5 MMA
+constexpr int kThreads = 224;   // warps 0-3 epilogue, 4 producer, 5 MMA, 6 next-item lookup
 constexpr int kIdrSlots = 8;    // tiles of home id ranks in flight (locality order)
 constexpr uint32_t kPolls = 1u << 20;
 constexpr int kPosBits = 21;    // home position bits in a candidate word
@@ -81,7 +86,7 @@ struct TcCfg {
   static constexpr uint32_t OFF_SORT = OFF_CAND + CAND_BYTES;     // 4 warps x 128 keys
   static constexpr uint32_t OFF_IDR = OFF_SORT + 4 * kSortN * 8;   // kIdrSlots x 128 id ranks
   static constexpr uint32_t OFF_BAR = OFF_IDR + (LOC ? kIdrSlots * kNT * 4 : 0);
-  static constexpr uint32_t SMEM = OFF_BAR + 256;
+  static constexpr uint32_t SMEM = OFF_BAR + 320;
   static_assert(OFF_B % 16 == 0 && OFF_CAND % 16 == 0 && OFF_SORT % 16 == 0 &&
                     OFF_IDR % 16 == 0 && OFF_BAR % 16 == 0,
                 "shared-memory regions must be 16-byte aligned");
@@ -264,8 +269,10 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   uint64_t* drain = tempty + kAcc;        // MMA drain at exit
   uint64_t* idr_full = drain + 1;         // [kIdrSlots] a tile's home id ranks landed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(idr_full + kIdrSlots);
-  int32_t* s_item = reinterpret_cast<int32_t*>(idr_full + kIdrSlots) + 1;
-  volatile int32_t* s_abort = reinterpret_cast<int32_t*>(idr_full + kIdrSlots) + 2;
+  volatile int32_t* s_abort = reinterpret_cast<int32_t*>(idr_full + kIdrSlots) + 1;
+  // two item records (item, p, tile, v0, nv, h0, nh, eoff[p]): the current one
+  // and the next, looked up by warp 6 while the current item runs
+  int32_t* s_info = reinterpret_cast<int32_t*>(idr_full + kIdrSlots) + 4;  // [2][8]
   int32_t* idr_sm = reinterpret_cast<int32_t*>(sm + C::OFF_IDR);
 
   const bdg_knn_args& a = ta.base;
@@ -305,21 +312,36 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   const int32_t* loc_idr = LOC ? c.loc_idr : nullptr;
   const bool ordered = !LOC;
 
-  for (;;) {
+  // the next work item from the round's counter, and its partition's offsets
+  auto lookup = [&](int32_t* dst) {
+    const int item = item_begin + atomicAdd(a.item_counter, 1);
+    dst[0] = item;
+    if (item < item_end) {
+      const int lo = c.item_lo[item];  // rank of the item's partition in part_order
+      const int p = c.part_order[lo];
+      const int tile = item - c.item_off[lo];
+      const int v0 = c.visit_off[p] + tile * kM;
+      dst[1] = p;
+      dst[2] = tile;
+      dst[3] = v0;
+      dst[4] = min(kM, c.visit_off[p + 1] - v0);
+      dst[5] = c.home_off[p];
+      dst[6] = c.home_off[p + 1] - dst[5];
+      dst[7] = c.eoff[p];
+    }
+  };
+  if (tid == 6 * 32) lookup(s_info);
+
+  for (uint32_t it = 0;; ++it) {
     __syncthreads();
-    if (tid == 0) *s_item = item_begin + atomicAdd(a.item_counter, 1);
-    __syncthreads();
-    const int item = *s_item;
+    const int32_t* inf = s_info + 8 * (it & 1);
+    const int item = inf[0];
     if (item >= item_end || *s_abort) break;
-    const int lo = c.item_lo[item];  // rank of the item's partition in part_order
-    const int p = c.part_order[lo];
-    const int tile = item - c.item_off[lo];
-    const int v0 = c.visit_off[p] + tile * kM;
-    const int nv = min(kM, c.visit_off[p + 1] - v0);
-    const int h0 = c.home_off[p];
-    const int nh = c.home_off[p + 1] - h0;
+    const int p = inf[1], tile = inf[2], v0 = inf[3], nv = inf[4], h0 = inf[5], nh = inf[6];
+    const int64_t e0 = inf[7];
     const int ntiles = (nh + kNT - 1) / kNT;
-    const int64_t e0 = c.eoff[p];
+    // warp 6 looks up the next item meanwhile (read after the next barrier)
+    if (tid == 6 * 32) lookup(s_info + 8 * ((it + 1) & 1));
     const int rank_bits = nh > 1 ? 32 - __clz(nh - 1) : 1;  // bits of an id rank in H_p
     const int start = loc_idr != nullptr && !a.merge_running ? tile : -1;  // spiral start
     if (nh > (int)kPosMask) {  // positions do not fit a candidate word: popcount fixup
@@ -398,7 +420,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           tc05::commit(&tfull[b]);
         }
       }
-    } else {
+    } else if (warp < 4) {
       // ---------------- epilogue: thread r owns visitor row r (TMEM lane r)
       // A candidate word is (d << 21) | position of the home in H_p. The homes of
       // a partition are stored in ascending id order, so word order is exactly
