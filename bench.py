@@ -634,7 +634,7 @@ def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
         return float((below + at).sum().item()) / (hd.shape[0] * topk)
 
     curve = []
-    for e in (64, 128, 256, 512, 1024):
+    for e in (64, 128, 256, 512, 1024, 2048):
         efv = torch.full((nq,), e, dtype=torch.int32, device=device)
         _, hd, exq = bdg.search(g, qcodes[qs], efv[:qs.numel()], topk, ef_max=e,
                                 expansions=True)
@@ -660,7 +660,7 @@ def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
         qps_at[gt] = {"0.9": max(ok) if ok else None}
     # the codes' ceiling: an exhaustive Hamming scan's top R re-ranked in FP32
     cap = {}
-    for Rr in (100, 512, 1024):
+    for Rr in (100, 512, 1024, 2048):
         bk = torch.full((qs.numel(), Rr), float("inf"), device=device)
         bi = torch.zeros((qs.numel(), Rr), dtype=torch.int64, device=device)
         for s0 in range(0, n, 1 << 20):

@@ -326,7 +326,8 @@ void bdg_graph_free(bdg_graph* g);
  * min(ef[q], R) pool keys ascending, padded to R.
  * queries: [nq][W]. ef: [nq] int32 (a per-query pool size; batches may mix
  * sizes). ef_max (host): an upper bound of ef over the batch, 1 <= ef_max <=
- * 1024; it sizes the per-query pool. A query whose ef is outside [1, ef_max]
+ * 2048; it sizes the per-query pool (shared memory: 19.3 KB per query in
+ * flight above 1024, 9.8 KB up to 1024). A query whose ef is outside [1, ef_max]
  * gets a row of padding and expansions = -1. out_ids/out_dist: [nq][R].
  * expansions: optional out [nq] int32 (nodes whose lists were scanned). */
 bdg_status bdg_search(const bdg_graph* g, const uint64_t* queries, int64_t nq, const int32_t* ef,
@@ -339,7 +340,7 @@ bdg_status bdg_search(const bdg_graph* g, const uint64_t* queries, int64_t nq, c
  * (distance, id). feats: [N][D] f32, qfeats: [nq][D] f32, cand: [nq][R] int32.
  * out_ids: [nq][k] int32, out_d2: [nq][k] f32 (padded with -1 / +inf).
  * D in {128, 256, 512, 1024}; feats/qfeats 16-byte aligned; 1 <= k <= 32;
- * 1 <= R <= 1024. Candidate ids outside [0, N) are skipped like -1. */
+ * 1 <= R <= 2048. Candidate ids outside [0, N) are skipped like -1. */
 bdg_status bdg_rerank(const float* feats, int64_t N, int32_t D, const float* qfeats,
                       const int32_t* cand, int64_t nq, int32_t R, int32_t k, int32_t* out_ids,
                       float* out_d2, void* stream);

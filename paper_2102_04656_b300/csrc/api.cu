@@ -997,7 +997,7 @@ bdg_status bdg_search(const bdg_graph* g, const uint64_t* queries, int64_t nq, c
                       int32_t ef_max, int32_t R, int32_t* out_ids, int32_t* out_dist,
                       int32_t* expansions, void* stream) {
   if (!g) return bdg_set_error(BDG_EINVAL, "search: graph is NULL");
-  if (nq < 0 || R < 1 || ef_max < 1 || ef_max > 1024)
+  if (nq < 0 || R < 1 || ef_max < 1 || ef_max > 2048)
     return bdg_set_error(BDG_EINVAL, "search: nq=%lld R=%d ef_max=%d", (long long)nq, R, ef_max);
   if (nq > 0 && (!queries || !ef || !out_ids || !out_dist))
     return bdg_set_error(BDG_EINVAL, "search: null pointer");
@@ -1113,7 +1113,7 @@ bdg_status bdg_merge_lists(const int32_t* ids, const int32_t* dists, int32_t S, 
 bdg_status bdg_rerank(const float* feats, int64_t N, int32_t D, const float* qfeats,
                       const int32_t* cand, int64_t nq, int32_t R, int32_t k, int32_t* out_ids,
                       float* out_d2, void* stream) {
-  if (nq < 0 || N < 1 || R < 1 || R > 1024 || k < 1 || k > 32)
+  if (nq < 0 || N < 1 || R < 1 || R > 2048 || k < 1 || k > 32)
     return bdg_set_error(BDG_EINVAL, "rerank: N=%lld nq=%lld R=%d k=%d", (long long)N,
                          (long long)nq, R, k);
   if (D != 128 && D != 256 && D != 512 && D != 1024)

@@ -27,18 +27,22 @@
 namespace {
 
 constexpr int kWarps = 4;
-// visited-id hash slots per warp: a small table leaves room for more warps per SM,
-// which hides more gather latency than the re-scores it causes cost
-constexpr int kHash = 256;
+// visited-id hash slots per warp (2^bits): a small table (256) leaves room for
+// more warps per SM, which hides more gather latency than the re-scores it
+// causes cost; pools above 1,024 keys (~2,000 expansions x 32 neighbours per
+// query) take 2,048 slots: with 256 nearly every neighbour was re-scored
+template <int CAPW>
+struct HashOf { static constexpr int bits = CAPW >= 64 ? 11 : 8; };
 constexpr int kProbe = 8;
 constexpr int kSmallBatch = 8;  // accepted keys ranked by counting instead of a sort
 
 template <int CAPW>
 struct PoolSmem {
+  static constexpr int HASH = 1 << HashOf<CAPW>::bits;
   uint64_t key[CAPW * 32];
   uint8_t expd[CAPW * 32];
   uint64_t nk[32];
-  int32_t hash[kHash];
+  int32_t hash[HASH];
 };
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
@@ -48,11 +52,13 @@ __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < 
 // (recorded now), kSeen if it was, kFull if its probe window is full (not
 // recorded: the id is re-scored and checked against the pool).
 constexpr int kNew = 0, kSeen = 1, kFull = 2;
+template <int HBITS>
 __device__ __forceinline__ int hash_visit(int32_t* h, int32_t id) {
+  constexpr int kH = 1 << HBITS;
   uint32_t x = (uint32_t)id * 2654435761u;
-  uint32_t slot = x >> (32 - 8);  // kHash = 256
+  uint32_t slot = x >> (32 - HBITS);
   for (int p = 0; p < kProbe; ++p) {
-    const uint32_t sidx = (slot + p) & (kHash - 1);
+    const uint32_t sidx = (slot + p) & (kH - 1);
     const int32_t old = atomicCAS(&h[sidx], -1, id);
     if (old == -1) return kNew;
     if (old == id) return kSeen;
@@ -87,7 +93,7 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
     uint64_t y[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) y[w] = queries[q * W + w];
-    for (int x = lane; x < kHash; x += 32) sm.hash[x] = -1;
+    for (int x = lane; x < PoolSmem<CAPW>::HASH; x += 32) sm.hash[x] = -1;
 
     // long-link entry: nearest sampled point by (d, id)
     uint64_t best = BDG_KEY_INF;
@@ -113,7 +119,7 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
     if (lane == 0) {
       sm.key[0] = best;
       sm.expd[0] = 0;
-      hash_visit(sm.hash, bdg_key_id(best));
+      hash_visit<HashOf<CAPW>::bits>(sm.hash, bdg_key_id(best));
     }
     int size = 1, hint = 0, nexp = 0;
     // speculation: while a node is expanded, the neighbour list of the next
@@ -170,7 +176,7 @@ search_kernel(bdg_graph_view g, const uint64_t* __restrict__ queries, int64_t nq
         }
         uint64_t key = BDG_KEY_INF;
         bool acc = false;
-        const int hv = (nb >= 0 && nb < g.n) ? hash_visit(sm.hash, nb) : kSeen;
+        const int hv = (nb >= 0 && nb < g.n) ? hash_visit<HashOf<CAPW>::bits>(sm.hash, nb) : kSeen;
         if (hv != kSeen) {
           uint32_t d = 0;
           if constexpr (PACKED) {
@@ -329,7 +335,8 @@ bdg_status launch_w(const bdg_graph_view& g, const uint64_t* queries, int64_t nq
   if (ef_max <= 128) return launch_cap<W, 4>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
   if (ef_max <= 256) return launch_cap<W, 8>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
   if (ef_max <= 512) return launch_cap<W, 16>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
-  return launch_cap<W, 32>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
+  if (ef_max <= 1024) return launch_cap<W, 32>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
+  return launch_cap<W, 64>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
 }
 
 }  // namespace

@@ -411,8 +411,11 @@ def _write_graph(path, ids, bits, entry):
         f.write(np.ascontiguousarray(entry, np.int32).tobytes())
 
 
-@pytest.mark.parametrize("efs,R", [((64, 128, 256, 512), 100), ((1, 7, 33), 40), ((300,), 10)])
+@pytest.mark.parametrize("efs,R", [((64, 128, 256, 512), 100), ((1, 7, 33), 40), ((300,), 10),
+                                   ((1024, 2048), 2048), ((700, 1500), 100)])
 def test_search_bit_exact_with_expansions(bdg, efs, R):
+    """Pools of every size class, up to ef = 2,048 (the 64-chunk pool) with all
+    2,048 keys written."""
     spec = datagen.MixtureSpec(12000, 128, 128, 256, seed=31)
     c = datagen.make_codes(spec)
     q = datagen.make_codes(spec, n=700, seed_offset=2)
@@ -549,7 +552,8 @@ def _check_rerank(ids, d2, feats, qf, cand, k):
         assert set(ids[r][diff]) <= set(ids_o[r][diff]) | set(cand[r])
 
 
-@pytest.mark.parametrize("D,R,k", [(128, 100, 10), (256, 64, 32), (512, 37, 5), (1024, 1, 1)])
+@pytest.mark.parametrize("D,R,k", [(128, 100, 10), (256, 64, 32), (512, 37, 5), (1024, 1, 1),
+                                   (128, 2048, 10)])
 def test_rerank_within_tolerance(bdg, D, R, k):
     rng = np.random.default_rng(D + R)
     feats = rng.standard_normal((3000, D)).astype(np.float32)
