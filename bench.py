@@ -711,10 +711,10 @@ def _search_bench(bdg, device, steps, warmup, n_entry, kernel):
     }
 
 
-def _serve_bench(bdg, ctx, seconds):
-    """Continuous batching on the resident search graph: Poisson arrivals of
-    requests of 1..4096 queries (log-uniform sizes), per-request ef in {64, 256}
-    (50/50), at several offered loads; per-request latency p50/p99 and the
+def _serve_sweep(bdg, ctx, seconds, ef_choices, R, loads, rng):
+    """One serving sweep: for each offered load, Poisson arrivals of requests of
+    1..4096 queries (log-uniform sizes) with per-query ef drawn uniformly from
+    ef_choices, served by a fresh Server; per-request latency p50/p99, the
     achieved query rate, and recall@10 of the served answers against the exact
     FP32 neighbours of the sampled ground-truth queries."""
     import threading
@@ -726,10 +726,8 @@ def _serve_bench(bdg, ctx, seconds):
     gt_row[gt_q] = np.arange(gt_q.size)
     gt_ids = ctx["gt_ids"].cpu().numpy()
     out = []
-    rng = np.random.default_rng(1006)
-    for qps in (5_000, 20_000, 50_000, 100_000, 200_000, 500_000, 1_000_000, 2_000_000,
-                4_000_000):
-        srv = bdg.Server(g, feats, R=ctx["R"], k=ctx["topk"], ef_max=256, max_batch=4096,
+    for qps in loads:
+        srv = bdg.Server(g, feats, R=R, k=ctx["topk"], ef_max=max(ef_choices), max_batch=4096,
                          n_streams=4, memory_budget=2 << 30)
         sizes, t_arr = [], []
         t = 0.0
@@ -739,7 +737,8 @@ def _serve_bench(bdg, ctx, seconds):
             t_arr.append(t)
             t += rng.exponential(n / qps)  # arrivals at qps queries per second on average
         starts = rng.integers(0, nq_all - 4096, len(sizes))
-        efs = [np.where(rng.random(n) < 0.5, 64, 256).astype(np.int32) for n in sizes]
+        efs = [np.asarray(ef_choices, np.int32)[rng.integers(0, len(ef_choices), n)]
+               for n in sizes]
         reqs = [None] * len(sizes)
         t0 = time.perf_counter()
 
@@ -775,8 +774,25 @@ def _serve_bench(bdg, ctx, seconds):
                     "batches": st["batches"],
                     "recall@10": (hits / (judged * ctx["topk"])) if judged else None,
                     "recall_queries": judged})
+    return out
+
+
+def _serve_bench(bdg, ctx, seconds):
+    """Continuous batching on the resident search graph, two sweeps of offered
+    load: the configuration's mix (per-request ef in {64, 256}, R = 100
+    candidates re-ranked) up to saturation, and the operating point at
+    recall@10 >= 0.9 against exact FP32 (ef = R = 2048: the whole pool
+    re-ranked)."""
+    rng = np.random.default_rng(1006)
+    base = _serve_sweep(bdg, ctx, seconds, (64, 256), ctx["R"],
+                        (5_000, 20_000, 50_000, 100_000, 200_000, 500_000, 1_000_000,
+                         2_000_000, 4_000_000), rng)
+    high = _serve_sweep(bdg, ctx, seconds, (2048,), 2048,
+                        (20_000, 50_000, 100_000, 150_000, 200_000, 300_000), rng)
     return {"streams": 4, "max_batch": 4096, "memory_budget_bytes": 2 << 30,
-            "ef_mix": [64, 256], "request_sizes": "log-uniform 1..4096", "levels": out}
+            "ef_mix": [64, 256], "R": ctx["R"], "request_sizes": "log-uniform 1..4096",
+            "levels": base,
+            "at_recall_0.9": {"ef": 2048, "R": 2048, "levels": high}}
 
 
 def _exact_bench(bdg, device, steps=20, warmup=3, cpu=True):

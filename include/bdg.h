@@ -363,7 +363,8 @@ bdg_status bdg_search_rerank(const bdg_graph* g, const uint64_t* queries, const 
  * while batches run are admitted as streams and memory free up, so their work
  * overlaps with the running batches. Each query's result depends only on the
  * query and its ef. The graph and feats are borrowed and must outlive the
- * server. */
+ * server. 1 <= k <= 32, k <= R <= 2048, 1 <= ef_max <= 2048, 1 <= n_streams
+ * <= 16. */
 typedef struct bdg_server bdg_server;
 bdg_status bdg_server_create(const bdg_graph* g, const float* feats, int32_t D, int32_t R,
                              int32_t k, int32_t ef_max, int32_t max_batch, int32_t n_streams,

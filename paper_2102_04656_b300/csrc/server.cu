@@ -173,7 +173,7 @@ bdg_status bdg_server_create(const bdg_graph* g, const float* feats, int32_t D, 
   if (!out) return bdg_set_error(BDG_EINVAL, "server_create: out is NULL");
   *out = nullptr;
   if (!g || !feats || max_batch < 1 || n_streams < 1 || n_streams > 16 || k < 1 || k > 32 ||
-      R < k || R > 1024 || ef_max < 1 || ef_max > 1024)
+      R < k || R > 2048 || ef_max < 1 || ef_max > 2048)
     return bdg_set_error(BDG_EINVAL, "server_create: bad arguments");
   const int32_t* ids = nullptr;
   int64_t N = 0;

@@ -24,21 +24,22 @@ def bdg():
     return m
 
 
-def test_results_identical_alone_and_in_the_mix(bdg):
+@pytest.mark.parametrize("efs,R,ef_max", [((64, 256), 100, 256), ((1024, 2048), 2048, 2048)])
+def test_results_identical_alone_and_in_the_mix(bdg, efs, R, ef_max):
     spec = datagen.MixtureSpec(60_000, 128, 256, 256, seed=4242)
     codes, feats = datagen.make_codes(spec, device="cuda", with_features=True)
     qc, qf = datagen.make_codes(spec, device="cuda", n=3000, seed_offset=2, with_features=True)
     entry = torch.from_numpy(datagen.sample_ids(spec.n, 1024, 1).astype(np.int32)).cuda()
     g = bdg.build_graph(codes, 32, m=16, t=3, bk_sample=torch.from_numpy(
         datagen.sample_ids(spec.n, 1024, 2)).cuda(), bk_iters=6, entry=entry)
-    R, k = 100, 10
-    ef_all = datagen.ef_mix(3000, (64, 256), 3)
+    k = 10
+    ef_all = datagen.ef_mix(3000, efs, 3)
     qc_h, qf_h = qc.cpu().numpy(), qf.cpu().numpy()
     rng = np.random.default_rng(0)
     sizes = rng.integers(1, 200, 40)
     starts = np.concatenate([[0], np.cumsum(sizes)])[:-1] % (3000 - 200)
     budget = 250 * (8 * 4 + 4 * 128 + 4 + 8 * R + 8 * k)  # at most ~250 queries in flight
-    srv = bdg.Server(g, feats, R=R, k=k, ef_max=256, max_batch=256, n_streams=3,
+    srv = bdg.Server(g, feats, R=R, k=k, ef_max=ef_max, max_batch=256, n_streams=3,
                      memory_budget=budget)
     with pytest.raises(bdg.BDGError):
         srv.submit(qc_h[:300], qf_h[:300], ef_all[:300])  # more than max_batch
@@ -62,7 +63,7 @@ def test_results_identical_alone_and_in_the_mix(bdg):
         s, n = int(starts[i]), int(sizes[i])
         a_ids, a_d2 = bdg.search_rerank(g, qc[s:s + n].contiguous(), qf[s:s + n].contiguous(),
                                         feats, torch.from_numpy(ef_all[s:s + n]).cuda(), R, k,
-                                        ef_max=256)
+                                        ef_max=ef_max)
         assert np.array_equal(ids, a_ids.cpu().numpy()), i
         assert np.array_equal(d2, a_d2.cpu().numpy()), i
         assert lat > 0
