@@ -129,9 +129,9 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
  * (bdg_bkmeans_scratch_bytes > 16 MiB; S = 16384, m = 256, 512 bits needs about
  * 1.7 MiB) fail with BDG_EINVAL before any work. The first call on a device
  * looks up the array's device address (once per device, with that device
- * current) and caches it for the life of the process: make that first call
- * before any stream capture, and do not use the entry point after
- * cudaDeviceReset (the cached address then no longer names the array). All
+ * current) and caches it for the life of the process; do not use the entry
+ * point after cudaDeviceReset (the cached address then no longer names the
+ * array). All
  * calls share the one array, which keeps the last call's contents: calls that
  * may overlap on the GPU (different streams, or different host threads) race
  * and must be ordered by the caller. No cudaMalloc/cudaFree or allocating
