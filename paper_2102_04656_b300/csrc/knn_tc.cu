@@ -456,6 +456,12 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         return t ? (float)(bits - 2 * (int)((t - 1u) >> kPosBits)) : 3.0e38f;
       };
       float lim = lim_of(thr_w);
+      // a row's list is compacted once it holds more than trig words: at most
+      // kCap - 16 (room for the next 16 values); with small k (routing: the t
+      // nearest centres) after a few dozen, so that the bound tightens early.
+      // trig is also the compaction's tie limit, so a compaction always leaves
+      // at most trig words and never has to run again at once
+      const int trig = k <= 16 ? 2 * (k + 1) + 16 : min(kCap - kHalf, 4 * (k + 1) + 16);
       for (int j = 0; j < ntiles; ++j) {
         const uint32_t gg = g + j, b = gg % kAcc;
         const int jt = start >= 0 ? spiral_tile(j, start, ntiles) : j;  // the home tile
@@ -504,12 +510,12 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
               if (!__any_sync(0xffffffffu, fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) >= lim)) continue;
             }
             // compaction, taken by the whole warp at once as soon as one row's list
-            // could not take another 16 values (lanes compacting one by one would
+            // holds more than trig words (lanes compacting one by one would
             // serialise the warp); only needed before an append, so skipped groups
             // do not pay for the check
-            if (__any_sync(0xffffffffu, cnt > kCap - kHalf)) {
-              cnt = compact_exact(crow, cnt, thr_w, need_k, bits, kCap - kHalf, ordered, rank_bits);
-              if (cnt > kCap - kHalf) {  // cannot happen (need_k <= 65); kept as a guard:
+            if (__any_sync(0xffffffffu, cnt > trig)) {
+              cnt = compact_exact(crow, cnt, thr_w, need_k, bits, trig, ordered, rank_bits);
+              if (cnt > trig) {  // cannot happen (need_k <= 65); kept as a guard:
                 overflow = true;         // the popcount kernel redoes this row
                 thr_w = 0u;
                 cnt = 0;
