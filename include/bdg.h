@@ -461,7 +461,7 @@ bdg_status bdg_router_train_step_shortlist(bdg_router* r, const void* x, const u
  * points are processed (results land in their own rows either way): points
  * sharing a home share most of their shortlist, so the home order lets
  * consecutive points reuse the same rows of W3 from cache. Runs in chunks of
- * 2^16 points with a stream-ordered workspace of chunk x (h1 + h2 +
+ * 2^18 points with a stream-ordered workspace of chunk x (h1 + h2 +
  * code_bits) BF16 values (plus the chunk's gathered inputs with an order);
  * BDG_ENOMEM if it cannot be had. */
 bdg_status bdg_router_route_shortlist(bdg_router* r, const void* x, const uint64_t* codes,
