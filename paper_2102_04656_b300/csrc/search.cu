@@ -336,6 +336,7 @@ bdg_status launch_w(const bdg_graph_view& g, const uint64_t* queries, int64_t nq
   if (ef_max <= 256) return launch_cap<W, 8>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
   if (ef_max <= 512) return launch_cap<W, 16>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
   if (ef_max <= 1024) return launch_cap<W, 32>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
+  if (ef_max <= 1536) return launch_cap<W, 48>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
   return launch_cap<W, 64>(g, queries, nq, ef, R, out_ids, out_dist, expansions, st);
 }
 

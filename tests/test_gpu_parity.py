@@ -412,7 +412,8 @@ def _write_graph(path, ids, bits, entry):
 
 
 @pytest.mark.parametrize("efs,R", [((64, 128, 256, 512), 100), ((1, 7, 33), 40), ((300,), 10),
-                                   ((1024, 2048), 2048), ((700, 1500), 100)])
+                                   ((1024, 2048), 2048), ((700, 1500), 100),
+                                   ((513, 600, 1000), 64)])
 def test_search_bit_exact_with_expansions(bdg, efs, R):
     """Pools of every size class, up to ef = 2,048 (the 64-chunk pool) with all
     2,048 keys written."""
@@ -506,14 +507,17 @@ def test_search_on_loaded_adversarial_graphs(bdg, tmp_path):
         p = str(tmp_path / f"{name}.bdg")
         _write_graph(p, adj, 64, entry)
         g = bdg.load_graph(p, c_t)
-        for efs in ((1,), (2, 5), (64,)):
+        # ef_max = 1024: the same queries through the 1,024-key pool
+        for efs, ef_max in (((1,), 64), ((2, 5), 64), ((64,), 64), ((1,), 1024),
+                            ((2, 5, 64), 1024)):
             ef = datagen.ef_mix(len(q), efs, seed=1)
             ids, dist, ex = bdg.search(g, torch.from_numpy(q.view(np.int64)).cuda(),
-                                       torch.from_numpy(ef).cuda(), 20, ef_max=64, expansions=True)
+                                       torch.from_numpy(ef).cuda(), 20, ef_max=ef_max,
+                                       expansions=True)
             ids_o, dist_o, cnt_o = oracle.search(c, adj, entry, q, ef, 20)
-            assert np.array_equal(ids.cpu().numpy(), ids_o), (name, efs)
-            assert np.array_equal(dist.cpu().numpy(), dist_o), (name, efs)
-            assert np.array_equal(ex.cpu().numpy(), cnt_o[:, 0]), (name, efs)
+            assert np.array_equal(ids.cpu().numpy(), ids_o), (name, efs, ef_max)
+            assert np.array_equal(dist.cpu().numpy(), dist_o), (name, efs, ef_max)
+            assert np.array_equal(ex.cpu().numpy(), cnt_o[:, 0]), (name, efs, ef_max)
 
 
 def test_search_invalid_ef_rows_are_padding(bdg):
