@@ -326,8 +326,9 @@ void bdg_graph_free(bdg_graph* g);
  * min(ef[q], R) pool keys ascending, padded to R.
  * queries: [nq][W]. ef: [nq] int32 (a per-query pool size; batches may mix
  * sizes). ef_max (host): an upper bound of ef over the batch, 1 <= ef_max <=
- * 2048; it sizes the per-query pool (shared memory: 19.3 KB per query in
- * flight above 1024, 9.8 KB up to 1024). A query whose ef is outside [1, ef_max]
+ * 2048; it sizes the per-query pool (shared memory per query in flight:
+ * 26.3 KB above 1536, 14.8 KB up to 1536, 10.3 KB up to 1024, less below).
+ * A query whose ef is outside [1, ef_max]
  * gets a row of padding and expansions = -1. out_ids/out_dist: [nq][R].
  * expansions: optional out [nq] int32 (nodes whose lists were scanned). */
 bdg_status bdg_search(const bdg_graph* g, const uint64_t* queries, int64_t nq, const int32_t* ef,
