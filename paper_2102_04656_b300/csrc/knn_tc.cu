@@ -60,10 +60,11 @@ constexpr int kNeedMax = 65;    // k + 1 for the largest k the kernel takes
 static_assert(kOutSlot >= kNeedMax && kOutSlot + kNeedMax <= CapOf<true>::v &&
                   kOutSlot + kNeedMax <= CapOf<false>::v,
               "ranked words need k + 1 free slots after the list");
-// words between a row's candidate slots: slot c of row r is word c * kM + r, so
-// the 32 lanes of a warp (32 rows) always touch 32 different banks, whatever
-// slot each row is at
-constexpr int kCandStride = kM;
+// words between a row's candidate slots: slot c of row r is word c * (kM + 1) + r,
+// so the 32 lanes of a warp touch 32 different banks both when they are 32 rows
+// (whatever slot each row is at) and when they are 32 consecutive slots of one
+// row (the write-out)
+constexpr int kCandStride = kM + 1;
 constexpr int kThreads = 224;   // warps 0-3 epilogue, 4 producer, 5 MMA, 6 next-item lookup
 constexpr int kIdrSlots = 8;    // tiles of home id ranks in flight (locality order)
 constexpr uint32_t kPolls = 1u << 20;
@@ -73,6 +74,11 @@ constexpr uint32_t kPosMask = (1u << kPosBits) - 1;
 constexpr int kAcc = 3;                  // accumulators: the MMAs run up to 2 tiles ahead
 constexpr uint32_t kAccCols = kAcc * kNT;  // accumulators in TMEM columns [0, 384)
 constexpr uint32_t kTmemCols = 512;        // + the visitors' operand in [384, 384 + KB / 4)
+// barriers (full/empty per stage, tfull/tempty per accumulator, drain, id-rank
+// slots), the TMEM address, the abort flag and two item records
+constexpr uint32_t kBarBytes = 272;
+static_assert((2 * kMaxStages + 2 * kAcc + 1 + kIdrSlots) * 8 + 16 + 2 * 8 * 4 <= kBarBytes,
+              "barrier area too small");
 
 template <int W, bool LOC>
 struct TcCfg {
@@ -86,7 +92,7 @@ struct TcCfg {
   static constexpr uint32_t OFF_SORT = OFF_CAND + CAND_BYTES;     // 4 warps x 128 keys
   static constexpr uint32_t OFF_IDR = OFF_SORT + 4 * kSortN * 8;   // kIdrSlots x 128 id ranks
   static constexpr uint32_t OFF_BAR = OFF_IDR + (LOC ? kIdrSlots * kNT * 4 : 0);
-  static constexpr uint32_t SMEM = OFF_BAR + 320;
+  static constexpr uint32_t SMEM = OFF_BAR + kBarBytes;
   static_assert(OFF_B % 16 == 0 && OFF_CAND % 16 == 0 && OFF_SORT % 16 == 0 &&
                     OFF_IDR % 16 == 0 && OFF_BAR % 16 == 0,
                 "shared-memory regions must be 16-byte aligned");
@@ -171,22 +177,67 @@ __device__ __forceinline__ uint32_t cidx(int c, int r) {  // candidate slot c of
 }
 
 // Keep the row's candidates below thr_w, in order. Returns the new count.
+// Words are read eight at a time into registers before any is written back: a
+// kept word only moves down (to a slot already read), and the loads of a batch
+// do not wait for the stores of the previous one.
 __device__ __forceinline__ int compact_row(uint32_t* crow, int cnt, uint32_t thr_w) {
   int w = 0;
-#pragma unroll 8
-  for (int x = 0; x < cnt; ++x) {
-    const uint32_t e = crow[x * kCandStride];
-    if (e < thr_w) crow[(w++) * kCandStride] = e;
+  for (int x = 0; x < cnt; x += 8) {
+    uint32_t e[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) e[q] = x + q < cnt ? crow[(x + q) * kCandStride] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (e[q] < thr_w) crow[(w++) * kCandStride] = e[q];
   }
   return w;
 }
 
-// Number of listed words with distance <= dm.
-__device__ __forceinline__ int count_le(const uint32_t* crow, int cnt, int dm) {
-  int c2 = 0;
-#pragma unroll 8
-  for (int x = 0; x < cnt; ++x) c2 += ((int)(crow[x * kCandStride] >> kPosBits) <= dm);
-  return c2;
+// The smallest distance lo with at least need_k listed words at distance <= lo
+// (every listed word has d <= td, and there are at least need_k of them). One
+// pass over the list counts the words in 16 bins of 2^shift distances below
+// `base` (byte counters in two 64-bit registers) and the words below the bins;
+// the running count from the bottom then names the bin holding lo. A bin of
+// one distance is the answer; a wider bin is split again into 16, and when lo
+// lies below every bin the bins move down. After a small drop of the bound one
+// pass suffices; an open bound (td = bits) takes three.
+__device__ __forceinline__ int kth_dist(const uint32_t* crow, int cnt, int need_k, int td,
+                                        int bits) {
+  int base = td;
+  int shift = td >= bits ? 5 : 0;  // an open bound: bins of 32 distances first
+  for (int pass = 0; pass < 12; ++pass) {
+    uint64_t h0 = 0, h1 = 0;  // byte s: words with (base - d) >> shift == s
+    int below = 0;            // words with (base - d) >> shift >= 16
+    for (int x = 0; x < cnt; x += 8) {
+      uint32_t e[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) e[q] = x + q < cnt ? crow[(x + q) * kCandStride] : 0xFFFFFFFFu;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int t = base - (int)(e[q] >> kPosBits);  // < 0: above the bins (or no word)
+        const uint32_t sb = (uint32_t)t >> shift;      // huge when t < 0
+        const uint64_t inc = 1ull << (8 * (sb & 7u));
+        h0 += sb < 8u ? inc : 0ull;
+        h1 += (sb - 8u) < 8u ? inc : 0ull;
+        below += (t >= 0 && sb >= 16u) ? 1 : 0;
+      }
+    }
+    int run = below, bin = -1;
+#pragma unroll
+    for (int sb = 15; sb >= 0; --sb) {
+      run += (int)(((sb < 8 ? h0 : h1) >> (8 * (sb & 7))) & 0xFFu);
+      if (bin < 0 && run >= need_k) bin = sb;
+    }
+    if (below >= need_k) {  // below every bin: move the bins down
+      base -= 16 << shift;
+      shift = min(shift + 4, 6);
+      continue;
+    }
+    if (shift == 0) return base - bin;
+    base -= bin << shift;  // the bin (base - 2^shift, base]: split it into 16
+    shift = max(shift - 4, 0);
+  }
+  return 0;  // not reached: every pass narrows the range or moves below it
 }
 
 // Exact compaction of one row's list. Every listed word is below thr_w. Once
@@ -201,18 +252,9 @@ __device__ __forceinline__ int count_le(const uint32_t* crow, int cnt, int dm) {
 __device__ __forceinline__ int compact_exact(uint32_t* crow, int cnt, uint32_t& thr_w, int need_k,
                                              int bits, int limit, bool ordered, int rank_bits) {
   if (cnt < need_k) return cnt;
-  // the k-th distance: binary search over [0, td], td the bound's distance;
-  // between compactions it usually drops by a few units, so [td - 7, td] is
-  // tried first
+  // the k-th distance, found below td, the bound's distance
   const int td = min((int)((thr_w - 1u) >> kPosBits), bits);
-  int lo = 0, hi = td;
-  if (td >= 8) {
-    if (count_le(crow, cnt, td - 8) >= need_k) hi = td - 8; else lo = td - 7;
-  }
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (count_le(crow, cnt, mid) >= need_k) hi = mid; else lo = mid + 1;
-  }
+  const int lo = kth_dist(crow, cnt, need_k, td, bits);
   thr_w = min(thr_w, (uint32_t)(lo + 1) << kPosBits);
   cnt = compact_row(crow, cnt, thr_w);
   if (cnt > limit) {
