@@ -240,6 +240,43 @@ __device__ __forceinline__ int kth_dist(const uint32_t* crow, int cnt, int need_
   return 0;  // not reached: every pass narrows the range or moves below it
 }
 
+// The need_k-th smallest listed word, known to lie in [wbase, wbase + 2^rb)
+// (the words of one distance, rb the bits of their low field): the same search
+// over 16 bins of the low field, from its top four bits down; words below
+// wbase count below every bin.
+__device__ __forceinline__ uint32_t kth_word(const uint32_t* crow, int cnt, int need_k,
+                                            uint32_t wbase, int rb) {
+  uint32_t lo = wbase;
+  int shift = max(rb - 4, 0);
+  for (int pass = 0; pass < 8; ++pass) {
+    uint64_t h0 = 0, h1 = 0;  // byte s: words with (w - lo) >> shift == s
+    int below = 0;            // words below lo
+    for (int x = 0; x < cnt; x += 8) {
+      uint32_t e[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) e[q] = x + q < cnt ? crow[(x + q) * kCandStride] : 0xFFFFFFFFu;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t sb = (e[q] - lo) >> shift;  // huge below lo and for no word
+        const uint64_t inc = 1ull << (8 * (sb & 7u));
+        h0 += sb < 8u ? inc : 0ull;
+        h1 += (sb - 8u) < 8u ? inc : 0ull;
+        below += e[q] < lo ? 1 : 0;
+      }
+    }
+    int run = below, bin = -1;  // the lowest bin whose running count reaches need_k
+#pragma unroll
+    for (int sb = 0; sb < 16; ++sb) {
+      run += (int)(((sb < 8 ? h0 : h1) >> (8 * (sb & 7))) & 0xFFu);
+      if (bin < 0 && run >= need_k) bin = sb;
+    }
+    if (shift == 0) return lo + (uint32_t)bin;
+    lo += (uint32_t)bin << shift;
+    shift = max(shift - 4, 0);
+  }
+  return lo;  // not reached: the last pass has single-word bins
+}
+
 // Exact compaction of one row's list. Every listed word is below thr_w. Once
 // the list holds need_k words, the bound becomes the need_k-th smallest
 // distance and the words above it are dropped; if ties at that distance still
@@ -247,8 +284,8 @@ __device__ __forceinline__ int kth_dist(const uint32_t* crow, int cnt, int need_
 // bound, leaving exactly need_k. `ordered`: the list is in word order within a
 // distance (homes in id order: words are appended by increasing position and
 // compaction keeps their order); otherwise (locality order) the word is found
-// by a radix descent over the low `rank_bits` bits of the words at that
-// distance. Returns the new count.
+// by a search over the low `rank_bits` bits of the words at that distance.
+// Returns the new count.
 __device__ __forceinline__ int compact_exact(uint32_t* crow, int cnt, uint32_t& thr_w, int need_k,
                                              int bits, int limit, bool ordered, int rank_bits) {
   if (cnt < need_k) return cnt;
@@ -258,34 +295,24 @@ __device__ __forceinline__ int compact_exact(uint32_t* crow, int cnt, uint32_t& 
   thr_w = min(thr_w, (uint32_t)(lo + 1) << kPosBits);
   cnt = compact_row(crow, cnt, thr_w);
   if (cnt > limit) {
-    // words at distance lo are in position order: the bound is the
-    // (need_k - #{d < lo})-th of them
-    int c_lt = 0;
-#pragma unroll 8
-    for (int x = 0; x < cnt; ++x) c_lt += ((int)(crow[x * kCandStride] >> kPosBits) < lo);
-    const int want = need_k - c_lt;  // 1-based rank among the words at distance lo
-    uint32_t wk = thr_w - 1u;
+    uint32_t wk;
     if (ordered) {
+      // words at distance lo are in position order: the bound is the
+      // (need_k - #{d < lo})-th of them
+      int c_lt = 0;
+#pragma unroll 8
+      for (int x = 0; x < cnt; ++x) c_lt += ((int)(crow[x * kCandStride] >> kPosBits) < lo);
+      const int want = need_k - c_lt;  // 1-based rank among the words at distance lo
+      wk = thr_w - 1u;
       int seen = 0;
       for (int x = 0; x < cnt; ++x) {
         const uint32_t e = crow[x * kCandStride];
         if ((int)(e >> kPosBits) == lo && ++seen == want) { wk = e; break; }
       }
     } else {
-      // the want-th smallest low field among the words at distance lo (the words
-      // differ): bit by bit from the top, count the words at lo whose field
-      // matches the prefix chosen so far followed by a 0
-      const uint32_t dlo = (uint32_t)lo << kPosBits;
-      uint32_t pref = 0;
-      int need = want;
-      for (int bit = rank_bits - 1; bit >= 0; --bit) {
-        const uint32_t mask = ~((1u << bit) - 1u);  // distance and the field's bits >= bit
-        int c0 = 0;
-#pragma unroll 8
-        for (int x = 0; x < cnt; ++x) c0 += ((crow[x * kCandStride] & mask) == (dlo | pref)) ? 1 : 0;
-        if (c0 < need) { need -= c0; pref |= 1u << bit; }
-      }
-      wk = dlo | pref;
+      // the need_k-th smallest word: among those at distance lo, whose low
+      // fields (id ranks) have rank_bits bits
+      wk = kth_word(crow, cnt, need_k, (uint32_t)lo << kPosBits, rank_bits);
     }
     thr_w = wk + 1u;
     cnt = compact_row(crow, cnt, thr_w);
