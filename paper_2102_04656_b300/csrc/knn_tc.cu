@@ -193,47 +193,68 @@ __device__ __forceinline__ int compact_row(uint32_t* crow, int cnt, uint32_t thr
   return w;
 }
 
+// 16 byte counters in four words (counter s is byte s % 4 of c[s / 4]): adds
+// one to counter sb, nothing for sb >= 16. PTX shl yields 0 for a shift of 32
+// or more, so each word takes its one-hot byte without a select.
+__device__ __forceinline__ uint32_t shl_clamp(uint32_t a, uint32_t n) {
+  uint32_t r;
+  asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(n));
+  return r;
+}
+__device__ __forceinline__ void bin16_add(uint32_t (&c)[4], uint32_t sb) {
+  const uint32_t x = min(sb, 16u) << 3;  // bit of counter sb in the 128-bit row
+  c[0] += shl_clamp(1u, x);
+  c[1] += shl_clamp(1u, x - 32u);
+  c[2] += shl_clamp(1u, x - 64u);
+  c[3] += shl_clamp(1u, x - 96u);
+}
+__device__ __forceinline__ int bin16_get(const uint32_t (&c)[4], int s) {
+  return (int)((c[s >> 2] >> (8 * (s & 3))) & 0xFFu);
+}
+
 // The smallest distance lo with at least need_k listed words at distance <= lo
 // (every listed word has d <= td, and there are at least need_k of them). One
 // pass over the list counts the words in 16 bins of 2^shift distances below
-// `base` (byte counters in two 64-bit registers) and the words below the bins;
-// the running count from the bottom then names the bin holding lo. A bin of
-// one distance is the answer; a wider bin is split again into 16, and when lo
-// lies below every bin the bins move down. After a small drop of the bound one
-// pass suffices; an open bound (td = bits) takes three.
+// `base`; the words above the bins are known from earlier passes, so the words
+// below them follow, and the running count from the bottom names the bin
+// holding lo. A bin of one distance is the answer; a wider bin is split again
+// into 16, and when lo lies below every bin the bins move down. After a small
+// drop of the bound one pass suffices; an open bound (td = bits) takes three.
 __device__ __forceinline__ int kth_dist(const uint32_t* crow, int cnt, int need_k, int td,
                                         int bits) {
   int base = td;
   int shift = td >= bits ? 5 : 0;  // an open bound: bins of 32 distances first
+  int above = 0;                   // words with d > base
   for (int pass = 0; pass < 12; ++pass) {
-    uint64_t h0 = 0, h1 = 0;  // byte s: words with (base - d) >> shift == s
-    int below = 0;            // words with (base - d) >> shift >= 16
+    uint32_t c[4] = {0u, 0u, 0u, 0u};  // counter s: words with (base - d) >> shift == s
     for (int x = 0; x < cnt; x += 8) {
       uint32_t e[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) e[q] = x + q < cnt ? crow[(x + q) * kCandStride] : 0xFFFFFFFFu;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int t = base - (int)(e[q] >> kPosBits);  // < 0: above the bins (or no word)
-        const uint32_t sb = (uint32_t)t >> shift;      // huge when t < 0
-        const uint64_t inc = 1ull << (8 * (sb & 7u));
-        h0 += sb < 8u ? inc : 0ull;
-        h1 += (sb - 8u) < 8u ? inc : 0ull;
-        below += (t >= 0 && sb >= 16u) ? 1 : 0;
-      }
+      for (int q = 0; q < 8; ++q)  // above base (or no word): t < 0, a huge bin
+        bin16_add(c, (uint32_t)(base - (int)(e[q] >> kPosBits)) >> shift);
     }
-    int run = below, bin = -1;
+    int binned = 0;
 #pragma unroll
-    for (int sb = 15; sb >= 0; --sb) {
-      run += (int)(((sb < 8 ? h0 : h1) >> (8 * (sb & 7))) & 0xFFu);
-      if (bin < 0 && run >= need_k) bin = sb;
-    }
+    for (int sb = 0; sb < 16; ++sb) binned += bin16_get(c, sb);
+    const int below = cnt - above - binned;  // (base - d) >> shift >= 16
     if (below >= need_k) {  // below every bin: move the bins down
+      above += binned;
       base -= 16 << shift;
       shift = min(shift + 4, 6);
       continue;
     }
+    int run = below, bin = 0;
+#pragma unroll
+    for (int sb = 15; sb >= 0; --sb) {  // the highest bin (lowest d) reaching need_k
+      const int before = run;
+      run += bin16_get(c, sb);
+      if (before < need_k && run >= need_k) bin = sb;
+    }
     if (shift == 0) return base - bin;
+#pragma unroll
+    for (int sb = 0; sb < 16; ++sb) above += sb < bin ? bin16_get(c, sb) : 0;
     base -= bin << shift;  // the bin (base - 2^shift, base]: split it into 16
     shift = max(shift - 4, 0);
   }
@@ -241,36 +262,39 @@ __device__ __forceinline__ int kth_dist(const uint32_t* crow, int cnt, int need_
 }
 
 // The need_k-th smallest listed word, known to lie in [wbase, wbase + 2^rb)
-// (the words of one distance, rb the bits of their low field): the same search
-// over 16 bins of the low field, from its top four bits down; words below
-// wbase count below every bin.
+// (the words of one distance, rb the bits of their low field; no listed word
+// lies above that range): the same search over 16 bins of the low field, four
+// bits at a time from the top, the words below the bins following from the
+// count.
 __device__ __forceinline__ uint32_t kth_word(const uint32_t* crow, int cnt, int need_k,
                                             uint32_t wbase, int rb) {
   uint32_t lo = wbase;
-  int shift = max(rb - 4, 0);
+  // a multiple of 4, so that the 16 bins of a split cover exactly the bin split
+  int shift = rb > 4 ? (rb - 1) / 4 * 4 : 0;
+  int above = 0;  // words at or above the top of the bins
   for (int pass = 0; pass < 8; ++pass) {
-    uint64_t h0 = 0, h1 = 0;  // byte s: words with (w - lo) >> shift == s
-    int below = 0;            // words below lo
+    uint32_t c[4] = {0u, 0u, 0u, 0u};  // counter s: words with (w - lo) >> shift == s
     for (int x = 0; x < cnt; x += 8) {
       uint32_t e[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) e[q] = x + q < cnt ? crow[(x + q) * kCandStride] : 0xFFFFFFFFu;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint32_t sb = (e[q] - lo) >> shift;  // huge below lo and for no word
-        const uint64_t inc = 1ull << (8 * (sb & 7u));
-        h0 += sb < 8u ? inc : 0ull;
-        h1 += (sb - 8u) < 8u ? inc : 0ull;
-        below += e[q] < lo ? 1 : 0;
-      }
+      for (int q = 0; q < 8; ++q)  // below lo: no bin
+        bin16_add(c, e[q] >= lo ? (e[q] - lo) >> shift : 16u);
     }
-    int run = below, bin = -1;  // the lowest bin whose running count reaches need_k
+    int binned = 0;
 #pragma unroll
-    for (int sb = 0; sb < 16; ++sb) {
-      run += (int)(((sb < 8 ? h0 : h1) >> (8 * (sb & 7))) & 0xFFu);
-      if (bin < 0 && run >= need_k) bin = sb;
+    for (int sb = 0; sb < 16; ++sb) binned += bin16_get(c, sb);
+    int run = cnt - above - binned, bin = 0;  // starts with the words below lo
+#pragma unroll
+    for (int sb = 0; sb < 16; ++sb) {  // the lowest bin whose running count reaches need_k
+      const int before = run;
+      run += bin16_get(c, sb);
+      if (before < need_k && run >= need_k) bin = sb;
     }
     if (shift == 0) return lo + (uint32_t)bin;
+#pragma unroll
+    for (int sb = 0; sb < 16; ++sb) above += sb > bin ? bin16_get(c, sb) : 0;
     lo += (uint32_t)bin << shift;
     shift = max(shift - 4, 0);
   }
