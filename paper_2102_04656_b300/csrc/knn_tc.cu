@@ -664,12 +664,18 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           uint32_t wv[kNeedMax];  // the row's words in registers (missing ones: never below)
 #pragma unroll
           for (int j = 0; j < kNeedMax; ++j) wv[j] = j < cnt ? crow[j * kCandStride] : 0xFFFFFFFFu;
+          static_assert(kNeedMax % 4 == 1, "four partial counts + one");
           for (int i = 0; i < cnt; ++i) {
             const uint32_t wi = crow[i * kCandStride];
-            int rank = 0;
+            int r0 = wv[kNeedMax - 1] < wi ? 1 : 0, r1 = 0, r2 = 0, r3 = 0;  // four short chains
 #pragma unroll
-            for (int j = 0; j < kNeedMax; ++j) rank += (wv[j] < wi);
-            crow[(kOutSlot + rank) * kCandStride] = wi;
+            for (int j = 0; j < kNeedMax - 1; j += 4) {
+              r0 += wv[j] < wi ? 1 : 0;
+              r1 += wv[j + 1] < wi ? 1 : 0;
+              r2 += wv[j + 2] < wi ? 1 : 0;
+              r3 += wv[j + 3] < wi ? 1 : 0;
+            }
+            crow[(kOutSlot + (r0 + r1) + (r2 + r3)) * kCandStride] = wi;
           }
           for (int j0 = 0; j0 < cnt; j0 += 8) {
             int32_t h8[8];
