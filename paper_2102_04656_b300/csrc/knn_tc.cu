@@ -344,7 +344,9 @@ __device__ __forceinline__ int compact_exact(uint32_t* crow, int cnt, uint32_t& 
   return cnt;
 }
 
-template <int W, bool LOC>
+// RUN: a sub-round (rows merge into running lists) or round A / a single round;
+// compiled apart so that each path gets its own register allocation
+template <int W, bool LOC, bool RUN>
 __global__ void __launch_bounds__(kThreads, 1)
 knn_tc_kernel(bdg_knn_tc_args ta) {
   using C = TcCfg<W, LOC>;
@@ -436,7 +438,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
     // warp 6 looks up the next item meanwhile (read after the next barrier)
     if (tid == 6 * 32) lookup(s_info + 8 * ((it + 1) & 1));
     const int rank_bits = nh > 1 ? 32 - __clz(nh - 1) : 1;  // bits of an id rank in H_p
-    const int start = loc_idr != nullptr && !a.merge_running ? tile : -1;  // spiral start
+    const int start = loc_idr != nullptr && !RUN ? tile : -1;  // spiral start
     if (nh > (int)kPosMask) {  // positions do not fit a candidate word: popcount fixup
       for (int r = tid; r < nv; r += kThreads) ta.fixflag[v0 + r] = 1;
       if (tid == 0) ta.err[1] = 1;
@@ -530,7 +532,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
       // missing home of a ragged tile (those read as d = bits + 1)
       uint32_t thr_w = live ? (uint32_t)(bits + 1) << kPosBits : 0u;
       uint64_t kth = BDG_KEY_INF;  // sub-round: the running list's k-th key
-      if (live && a.home_kth != nullptr) {  // it bounds d, and no key above it can enter
+      if (RUN && live && a.home_kth != nullptr) {  // it bounds d, and no key above it can enter
         kth = a.home_kth[(int64_t)myvid * k + (k - 1)];
         if (kth < bdg_pad_key(bits)) thr_w = (uint32_t)(bdg_key_d(kth) + 1) << kPosBits;
       }
@@ -649,7 +651,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         }
       }
       const uint64_t pad = bdg_pad_key(bits);
-      if (!a.merge_running) {
+      if constexpr (!RUN) {
         // ---- round A or a single round. Each thread cuts its row's list to
         // exactly its need_k best words, ranks them by counting (word order is
         // (d, id) order) into slots kOutSlot.., and looks up their ids into
@@ -772,18 +774,20 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
         }
         __syncwarp();
         uint64_t* sb = sortbuf + warp * 128;
-        for (int rr = 0; rr < 32; ++rr) {
+        // only rows with keys to merge (or flagged) need the warp: most have none
+        unsigned todo = __ballot_sync(0xffffffffu, r < nv && live && (overflow || cnt > 0));
+        while (todo) {
+          const int rr = __ffs(todo) - 1;
+          todo &= todo - 1;
           const int row = warp * 32 + rr;
           const int n_r = __shfl_sync(0xffffffffu, cnt, rr);
           const int ovf = __shfl_sync(0xffffffffu, overflow ? 1 : 0, rr);
           const uint64_t kb = __shfl_sync(0xffffffffu, kth, rr);
           const int32_t vid = __shfl_sync(0xffffffffu, myvid, rr);
-          if (row >= nv || vid < 0) continue;  // no row, or an invalid id
           if (ovf) {  // recomputed by the popcount kernel
             if (lane == 0) { ta.fixflag[v0 + row] = 1; ta.err[1] = 1; }
             continue;
           }
-          if (n_r == 0) continue;  // nothing enters the running list
           // keys ascending: n_r <= 32 by one bitonic sort across the warp in
           // registers, else (n_r <= 64) two such sorts merged by ranks
 #pragma unroll
@@ -851,13 +855,13 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
   if (warp == 0) tc05::tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int W, bool LOC>
+template <int W, bool LOC, bool RUN>
 bdg_status launch_main(const bdg_knn_tc_args& ta, cudaStream_t st) {
   using C = TcCfg<W, LOC>;
-  BDG_CUDA_TRY(cudaFuncSetAttribute(knn_tc_kernel<W, LOC>,
+  BDG_CUDA_TRY(cudaFuncSetAttribute(knn_tc_kernel<W, LOC, RUN>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
   bdg_prof_scope prof(ta.base.prof ? ta.base.prof : "knn", st);
-  knn_tc_kernel<W, LOC><<<bdg_num_sms(), kThreads, C::SMEM, st>>>(ta);
+  knn_tc_kernel<W, LOC, RUN><<<bdg_num_sms(), kThreads, C::SMEM, st>>>(ta);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   return BDG_OK;
@@ -877,9 +881,11 @@ bdg_status launch_w(const bdg_knn_tc_args& ta, bool expand, cudaStream_t st) {
   }
   // homes in locality order (id ranks with every tile) or in id order
   if (a.csr.loc_idr) {
-    BDG_TRY((launch_main<W, true>(ta, st)));
+    if (a.merge_running) BDG_TRY((launch_main<W, true, true>(ta, st)));
+    else BDG_TRY((launch_main<W, true, false>(ta, st)));
   } else {
-    BDG_TRY((launch_main<W, false>(ta, st)));
+    if (a.merge_running) BDG_TRY((launch_main<W, false, true>(ta, st)));
+    else BDG_TRY((launch_main<W, false, false>(ta, st)));
   }
   // rows whose candidate list overflowed: exact recomputation by the popcount kernel
   BDG_CUDA_TRY(cudaMemsetAsync(a.item_counter, 0, sizeof(int32_t), st));
