@@ -235,6 +235,13 @@ bdg_status bdg_route(const uint64_t* codes, int64_t n, int32_t bits, const uint6
     return bdg_set_error(BDG_EINVAL, "route: null pointer");
   const int W = bits / 64;
   cudaStream_t st = (cudaStream_t)stream;
+  if (n > 0 && bdg_route_small_ok(W, m, t) && bdg_tc_default()) {  // few centres
+    keep_pool_cached();
+    Scratch sc;
+    const size_t b = bdg_route_small_bytes(m, W);
+    BDG_TRY(sc.alloc(b, st));
+    return bdg_launch_route_small(codes, n, W, centroids, m, t, routes, rdist, sc.p, b, st);
+  }
   if (n > 0 && bdg_route_tc_ok(W, n, m, t) && bdg_tc_default()) {
     keep_pool_cached();
     Scratch sc;
@@ -293,7 +300,7 @@ constexpr int64_t kLocMinHomes = 2048;  // mean |H_p| from which the order is bu
 struct BuildCfg {
   int W, m, t, tile_v;
   int pivots;  // locality order of H_p over this many pivot homes (0: id order)
-  bool need_routes, need_bk, use_tc, tc_ok, route_tc;
+  bool need_routes, need_bk, use_tc, tc_ok, route_tc, route_small;
   int kmap[BDG_SIZE_CLASSES];  // Reduce-1 variant (BDG_KV_*) per partition size class
   int64_t coarse;
   size_t b_routes, b_cent, b_bk, b_csr, b_part, b_hexp, b_fix, b_cnt, b_rtc, total;
@@ -367,8 +374,13 @@ bdg_status build_validate(const uint64_t* codes, int64_t N, int32_t bits, int32_
   c->b_fix = c->tc_ok ? al((size_t)N * t) + al(64) : 0;
   c->b_cnt = c->coarse > 0 ? al((size_t)m * 4) : 0;
   // library routing on the tensor cores where the codes allow it
-  c->route_tc = c->need_routes && bdg_route_tc_ok(W, N, m, t) && bdg_tc_default();
-  c->b_rtc = c->route_tc ? al(bdg_route_tc_bytes(N, m, W, t)) : 0;
+  // (all centres in shared memory when they are few)
+  c->route_small = c->need_routes && bdg_route_small_ok(W, m, t) && bdg_tc_default();
+  c->route_tc = c->need_routes && !c->route_small && bdg_route_tc_ok(W, N, m, t) &&
+                bdg_tc_default();
+  c->b_rtc = c->route_small ? al(bdg_route_small_bytes(m, W))
+             : c->route_tc  ? al(bdg_route_tc_bytes(N, m, W, t))
+                            : 0;
   c->total = c->b_routes + c->b_cent + c->b_bk + c->b_csr + c->b_part + c->b_hexp + c->b_fix +
              c->b_cnt + c->b_rtc;
   return BDG_OK;
@@ -429,7 +441,9 @@ bdg_status build_enqueue(const BuildCfg& c, const int* kmap, bdg_graph* g, const
     if (c.need_bk)
       BDG_TRY(bdg_launch_bkmeans(codes, N, W, P->bk_sample, P->bk_sample_size, m, P->bk_iters,
                                  cent, nullptr, bk, c.b_bk, st));
-    if (c.route_tc)
+    if (c.route_small)
+      BDG_TRY(bdg_launch_route_small(codes, N, W, cent, m, t, routes, nullptr, rtc, c.b_rtc, st));
+    else if (c.route_tc)
       BDG_TRY(bdg_launch_route_tc(codes, N, W, cent, m, t, routes, nullptr, rtc, c.b_rtc, st));
     else
       BDG_TRY(bdg_launch_route(codes, N, W, cent, m, t, routes, nullptr, st));

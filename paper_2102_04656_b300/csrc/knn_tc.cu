@@ -100,33 +100,6 @@ struct TcCfg {
   static_assert(kAccCols + KB / 4 <= kTmemCols, "visitor operand does not fit in TMEM");
 };
 
-// 16 code bits -> 16 bytes of E4M3 (+1.0 = 0x38 for a set bit, -1.0 = 0xB8 otherwise)
-__device__ __forceinline__ uint4 expand16(uint32_t bits16) {
-  uint32_t w[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const uint32_t nib = (bits16 >> (4 * i)) & 0xFu;
-    const uint32_t spread = ((nib * 0x00204081u) & 0x01010101u) << 7;  // bit j -> bit 8j+7
-    w[i] = 0xB8B8B8B8u ^ spread;
-  }
-  return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(dst), "l"(src), "r"(bytes), "r"(tc05::smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile(
-      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
-          tc05::smem_u32(bar)),
-      "r"(bytes)
-      : "memory");
-}
-
 // Expanded home operand: row e of the 128-padded order of partition p holds
 // home_codes[home_off[p] + r] with r = e - eoff[p] (id order) or r = loc_idr[e]
 // (locality order), zeros past |H_p|, as KB bytes of E4M3 in the K-major
@@ -157,7 +130,7 @@ __global__ void expand_homes_kernel(const uint64_t* __restrict__ home_codes,
   if (local < nh) {  // locality order: row e holds the home of id rank loc_idr[e]
     const int64_t src = home_off[lo] + (loc_idr ? (int64_t)loc_idr[e] : local);
     const uint64_t word = home_codes[src * W + (q >> 2)];
-    v = expand16((uint32_t)(word >> (16 * (q & 3))) & 0xFFFFu);
+    v = tc05::expand16((uint32_t)(word >> (16 * (q & 3))) & 0xFFFFu);
   }
   *reinterpret_cast<uint4*>(hexp + grp * (int64_t)(KB * 8) + (int64_t)q * 128 + rr * 16) = v;
 }
@@ -479,16 +452,16 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
             atomicExch(ta.err, 1); *s_abort = 1; break;
           }
           const int jt = start >= 0 ? spiral_tile(j, start, ntiles) : j;  // the home tile
-          arrive_expect_tx(&full[st], C::B_BYTES);
-          bulk_g2s(tc05::smem_u32(sm + C::OFF_B + st * C::B_BYTES),
+          tc05::arrive_expect_tx(&full[st], C::B_BYTES);
+          tc05::bulk_g2s(tc05::smem_u32(sm + C::OFF_B + st * C::B_BYTES),
                    ta.hexp + (e0 + (int64_t)jt * kNT) * KB, C::B_BYTES, &full[st]);
           if (loc_idr) {
             // slot gg % kIdrSlots is free: the epilogue is at most kIdrSlots - 1
             // tiles behind (this copy needed the MMAs of tile gg - kStages, those
             // needed the accumulator of tile gg - kStages - kAcc read)
             const uint32_t is = gg % kIdrSlots;
-            arrive_expect_tx(&idr_full[is], kNT * 4);
-            bulk_g2s(tc05::smem_u32(idr_sm + is * kNT), loc_idr + e0 + (int64_t)jt * kNT,
+            tc05::arrive_expect_tx(&idr_full[is], kNT * 4);
+            tc05::bulk_g2s(tc05::smem_u32(idr_sm + is * kNT), loc_idr + e0 + (int64_t)jt * kNT,
                      kNT * 4, &idr_full[is]);
           }
           ++nprod;

@@ -196,11 +196,15 @@ def test_route_bit_exact(bdg, bits, t):
 
 @pytest.mark.parametrize("kernel", ["popc", "tc"])
 @pytest.mark.parametrize("bits,n,m,t", [(256, 3000, 2000, 16), (512, 1500, 1100, 8),
-                                        (256, 700, 1200, 1)])
+                                        (256, 700, 1200, 1), (512, 4001, 256, 5),
+                                        (256, 3001, 200, 8), (512, 700, 17, 1),
+                                        (256, 129, 16, 3)])
 def test_route_kernels_bit_exact(bdg, kernel, bits, n, m, t, monkeypatch):
     """Routing on the tensor cores (256/512-bit codes) and on the ALU give the
     oracle's routes and distances, ties by centre index (duplicate centres,
-    ragged last centre tile, t up to 16)."""
+    ragged last centre tile, t up to 16). Up to 256 centres and t <= 8 the
+    tensor path keeps every centre in shared memory (m = 17 and 200 are not
+    multiples of 16; 129 and 4001 points leave a ragged last point tile)."""
     monkeypatch.setenv("BDG_KNN_KERNEL", kernel)
     c = datagen.make_codes(datagen.MixtureSpec(n, 64, 40, bits, seed=n + m))
     ce = datagen.random_codes(m, bits, seed=m)
