@@ -219,6 +219,70 @@ __global__ void scatter_kernel(const int32_t* __restrict__ routes, int64_t N, in
   }
 }
 
+// The same two passes with per-block aggregation, while the (t - 1) * m bins
+// fit in shared memory: a block takes `pts` points, counts its (slot,
+// partition) pairs there and touches each global counter once; the placement
+// pass also ranks each pair within its block and bin, reserves the block's
+// range of every bin with one global atomic and writes each pair at range start
+// + rank. (Few bins with many points per bin made the one-atomic-per-pair
+// passes contend.)
+constexpr int kAggThreads = 256;
+constexpr int kAggBins = 4096;      // (t - 1) * m at most
+constexpr int kAggEntries = 8192;   // pts * (t - 1) at most
+
+__global__ void __launch_bounds__(kAggThreads)
+count_agg_kernel(const int32_t* __restrict__ routes, int64_t N, int t, int m, int pts,
+                 int32_t* __restrict__ vcnt) {
+  __shared__ int32_t sh[kAggBins];
+  const int nb = (t - 1) * m, ns = t - 1;
+  for (int b = threadIdx.x; b < nb; b += kAggThreads) sh[b] = 0;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * pts;
+  for (int e = threadIdx.x; e < pts * ns; e += kAggThreads) {
+    const int64_t i = i0 + e / ns;
+    if (i >= N) break;
+    const int s = 1 + e % ns;
+    const int32_t p = routes[i * t + s];
+    if (p >= 0 && p < m) atomicAdd(&sh[(s - 1) * m + p], 1);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += kAggThreads)
+    if (sh[b] != 0) atomicAdd(&vcnt[b], sh[b]);
+}
+
+__global__ void __launch_bounds__(kAggThreads)
+scatter_agg_kernel(const int32_t* __restrict__ routes, int64_t N, int t, int m, int pts,
+                   int32_t* __restrict__ vcur, int32_t* __restrict__ visit_ids,
+                   int8_t* __restrict__ visit_slot) {
+  __shared__ int32_t sh[kAggBins];      // counts, then the block's first position per bin
+  __shared__ int32_t rank[kAggEntries];  // a pair's rank in its bin within the block (-1: none)
+  const int nb = (t - 1) * m, ns = t - 1;
+  for (int b = threadIdx.x; b < nb; b += kAggThreads) sh[b] = 0;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * pts;
+  for (int e = threadIdx.x; e < pts * ns; e += kAggThreads) {
+    const int64_t i = i0 + e / ns;
+    const int s = 1 + e % ns;
+    const int32_t p = i < N ? routes[i * t + s] : -1;
+    rank[e] = (p >= 0 && p < m) ? atomicAdd(&sh[(s - 1) * m + p], 1) : -1;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += kAggThreads) {
+    const int32_t c = sh[b];
+    sh[b] = c != 0 ? atomicAdd(&vcur[b], c) : 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < pts * ns; e += kAggThreads) {
+    const int32_t r = rank[e];
+    if (r < 0) continue;
+    const int64_t i = i0 + e / ns;
+    const int s = 1 + e % ns;
+    const int32_t pos = sh[(s - 1) * m + routes[i * t + s]] + r;
+    visit_ids[pos] = (int32_t)i;
+    visit_slot[pos] = (int8_t)s;
+  }
+}
+
 __global__ void gather_home_codes(const uint64_t* __restrict__ codes,
                                   const int32_t* __restrict__ home_ids,
                                   const int32_t* __restrict__ home_off, int m, int64_t N, int W,
@@ -540,7 +604,15 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch(2);
   // visits of slots >= 1 (their order within a list does not matter)
-  count_kernel<<<g, 256, 0, st>>>(routes, N, t, m, vcnt);
+  // points per aggregated block: a multiple of the block size, pts * (t - 1)
+  // pairs at most kAggEntries
+  const bool agg = t >= 2 && (int64_t)(t - 1) * m <= kAggBins;
+  const int pts = agg ? std::max(kAggThreads, kAggEntries / (t - 1) / kAggThreads * kAggThreads) : 0;
+  const int gagg = agg ? (int)bdg_cdiv(N, pts) : 0;
+  if (agg)
+    count_agg_kernel<<<gagg, kAggThreads, 0, st>>>(routes, N, t, m, pts, vcnt);
+  else
+    count_kernel<<<g, 256, 0, st>>>(routes, N, t, m, vcnt);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   int np2 = 1;
@@ -559,7 +631,11 @@ bdg_status bdg_build_csr(const uint64_t* codes, int64_t N, int W, const int32_t*
   bdg_note_launch();
   home_place<<<nblk, 32, sm_m, st>>>(routes, N, t, m, bp, bcnt, c->home_off, c->home_ids);
   BDG_CUDA_TRY(cudaGetLastError());
-  scatter_kernel<<<g, 256, 0, st>>>(routes, N, t, m, vcnt, c->visit_ids, c->visit_slot);
+  if (agg)
+    scatter_agg_kernel<<<gagg, kAggThreads, 0, st>>>(routes, N, t, m, pts, vcnt, c->visit_ids,
+                                                     c->visit_slot);
+  else
+    scatter_kernel<<<g, 256, 0, st>>>(routes, N, t, m, vcnt, c->visit_ids, c->visit_slot);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch(2);
   gather_home_codes<<<bdg_cdiv(N * W, 256), 256, 0, st>>>(codes, c->home_ids, c->home_off, m, N,
