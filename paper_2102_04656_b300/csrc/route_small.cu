@@ -7,8 +7,9 @@
 // then one chain of bits / 32 MMAs (M = 128, N = m rounded up to 16, K = 32)
 // into one TMEM accumulator: the dot product of two +-1 codes is
 // bits - 2 d(x, c), exact in FP32. Each epilogue thread owns one point (one TMEM
-// lane) and keeps its t best keys (d << 16 | c) in registers, so ties fall by
-// centre index exactly as in the ALU routing kernel: the results are identical.
+// lane) and keeps its 8 best keys (d << 16 | c) in registers, of which the first t
+// are its routes, so ties fall by centre index exactly as in the ALU routing
+// kernel: the results are identical.
 //
 // One CTA per SM, persistent over the point tiles (static round robin). Warps
 // 0-3 write the next tile's points into the second of two TMEM operand buffers
@@ -27,6 +28,27 @@ constexpr uint32_t kRsOperand0 = 256;
 constexpr uint32_t kRsPolls = 1u << 20;
 
 int padded_centres(int m) { return m < 16 ? 16 : (m + 15) / 16 * 16; }
+
+__device__ __forceinline__ void cas(uint32_t& a, uint32_t& b) {
+  const uint32_t lo = min(a, b);
+  b = max(a, b);
+  a = lo;
+}
+// ascending sort of 8 keys (Batcher's odd-even merge network, 19 comparators)
+__device__ __forceinline__ void sort8(uint32_t (&x)[8]) {
+  cas(x[0], x[1]); cas(x[2], x[3]); cas(x[4], x[5]); cas(x[6], x[7]);
+  cas(x[0], x[2]); cas(x[1], x[3]); cas(x[4], x[6]); cas(x[5], x[7]);
+  cas(x[1], x[2]); cas(x[5], x[6]);
+  cas(x[0], x[4]); cas(x[1], x[5]); cas(x[2], x[6]); cas(x[3], x[7]);
+  cas(x[2], x[4]); cas(x[3], x[5]);
+  cas(x[1], x[2]); cas(x[3], x[4]); cas(x[5], x[6]);
+}
+// ascending sort of a bitonic sequence of 8 keys (half-cleaners at distance 4, 2, 1)
+__device__ __forceinline__ void clean8(uint32_t (&x)[8]) {
+  cas(x[0], x[4]); cas(x[1], x[5]); cas(x[2], x[6]); cas(x[3], x[7]);
+  cas(x[0], x[2]); cas(x[1], x[3]); cas(x[4], x[6]); cas(x[5], x[7]);
+  cas(x[0], x[1]); cas(x[2], x[3]); cas(x[4], x[5]); cas(x[6], x[7]);
+}
 
 // Centre c < np as KB bytes of E4M3 (zeros for c >= m) in the K-major
 // core-matrix layout the MMA reads B in: 8-row groups of KB * 8 bytes, 16-byte
@@ -158,30 +180,33 @@ route_small_kernel(const uint64_t* __restrict__ codes, int64_t n,
       ok = __all_sync(0xffffffffu, !*s_abort && tc05::mbar_wait(acc_full, s & 1, kRsPolls));
       if (!ok) break;
       tc05::fence_after();
+      // the 8 smallest keys so far, ascending; eight new keys at a time are
+      // sorted by a 19-comparator network, the elementwise minimum with the
+      // kept keys in reverse order leaves the 8 smallest of both as a bitonic
+      // sequence, and 12 comparators sort it: no branches, and the comparators
+      // of a step are independent
       uint32_t best[kRsMaxT];
 #pragma unroll
       for (int j = 0; j < kRsMaxT; ++j) best[j] = 0xFFFFFFFFu;
-      uint32_t worst = 0xFFFFFFFFu;  // best[7]: a key above it cannot be among the t <= 8 best
       for (int c0 = 0; c0 < np; c0 += 32) {
         uint32_t v[32];
         tc05::ld32(tmem + lane_base + (uint32_t)c0, v);
         tc05::wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const uint32_t fb = __float_as_uint(fmaf(__uint_as_float(v[j]), -0.5f, hmagic));
-          const uint32_t key = c0 + j < m ? fb * 65536u + (uint32_t)(c0 + j) : 0xFFFFFFFFu;
-          if (key < worst) {
-            // one pass of a min/max bubble keeps best[] the 8 smallest keys in
-            // order (slots >= t are extra and never written out)
-            uint32_t x = key;
+        for (int g = 0; g < 32; g += 8) {
+          uint32_t x[8];
 #pragma unroll
-            for (int q = 0; q < kRsMaxT; ++q) {
-              const uint32_t lo = min(best[q], x);
-              x = max(best[q], x);
-              best[q] = lo;
-            }
-            worst = best[kRsMaxT - 1];
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t fb = __float_as_uint(fmaf(__uint_as_float(v[g + j]), -0.5f, hmagic));
+            x[j] = c0 + g + j < m ? fb * 65536u + (uint32_t)(c0 + g + j) : 0xFFFFFFFFu;
           }
+          sort8(x);
+          uint32_t y[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) y[j] = min(best[j], x[7 - j]);
+          clean8(y);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) best[j] = y[j];
         }
       }
       tc05::fence_before();
