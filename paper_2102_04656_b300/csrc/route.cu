@@ -78,10 +78,11 @@ route_kernel(const uint64_t* __restrict__ codes, int64_t n, const uint64_t* __re
 
 template <int W>
 bdg_status route_w(const uint64_t* codes, int64_t n, const uint64_t* cent, int m, int t,
-                   int32_t* routes, int32_t* rdist, unsigned long long* loss, cudaStream_t st) {
+                   int32_t* routes, int32_t* rdist, unsigned long long* loss, cudaStream_t st,
+                   const char* prof_name = "route") {
   if (n == 0) return BDG_OK;
   const int grid = bdg_cdiv(n, kRouteThreads);
-  bdg_prof_scope prof(loss ? "bkmeans_assign" : "route", st);
+  bdg_prof_scope prof(prof_name, st);
   if (t == 1)
     route_kernel<W, 1><<<grid, kRouteThreads, 0, st>>>(codes, n, cent, m, t, routes, rdist, loss);
   else if (t <= 4)
@@ -304,7 +305,7 @@ namespace {
 template <int W>
 bdg_status bk_assign_w(const uint64_t* scodes, int64_t S, const uint64_t* cent, int m,
                        int32_t* assign, int32_t* adist, unsigned long long* loss, cudaStream_t st) {
-  return route_w<W>(scodes, S, cent, m, 1, assign, adist, loss, st);
+  return route_w<W>(scodes, S, cent, m, 1, assign, adist, loss, st, "bkmeans_assign");
 }
 }  // namespace
 
