@@ -127,7 +127,7 @@ bdg_status bdg_knn_rows(const uint64_t* codes, int64_t N, int32_t bits, const in
  * 16 MiB array inside the library, reserved on every GPU that loads the
  * library until the process exits; calls needing more
  * (bdg_bkmeans_scratch_bytes > 16 MiB; S = 16384, m = 256, 512 bits needs about
- * 1.7 MiB) fail with BDG_EINVAL before any work. The first call on a device
+ * 1.8 MiB) fail with BDG_EINVAL before any work. The first call on a device
  * looks up the array's device address (once per device, with that device
  * current) and caches it for the life of the process; do not use the entry
  * point after cudaDeviceReset (the cached address then no longer names the

@@ -81,12 +81,17 @@ bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int
 size_t bdg_bkmeans_scratch_bytes(int64_t S, int m, int W);
 // routing on the tensor cores (route.cu): the t nearest centres of each point
 // as its t nearest homes in one partition whose homes are the centres
+// api.cu: whether "auto" takes the tensor-core paths (BDG_KNN_KERNEL=popc turns them off)
+bool bdg_tc_default();
 // route_small.cu: routing on the tensor cores with all centres in shared memory
 bool bdg_route_small_ok(int W, int m, int t);
 size_t bdg_route_small_bytes(int m, int W);
+// loss: optional, the sum over points of the distance to the nearest centre
 bdg_status bdg_launch_route_small(const uint64_t* codes, int64_t n, int W, const uint64_t* cent,
                                   int m, int t, int32_t* routes, int32_t* rdist, void* scratch,
-                                  size_t scratch_bytes, cudaStream_t st);
+                                  size_t scratch_bytes, cudaStream_t st,
+                                  unsigned long long* loss = nullptr,
+                                  const char* prof_name = "route");
 bool bdg_route_tc_ok(int W, int64_t n, int m, int t);
 size_t bdg_route_tc_bytes(int64_t n, int m, int W, int t);
 bdg_status bdg_launch_route_tc(const uint64_t* codes, int64_t n, int W, const uint64_t* cent,

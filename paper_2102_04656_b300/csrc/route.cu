@@ -297,8 +297,9 @@ bdg_status bdg_launch_routes_coarse(int32_t* routes, int64_t n, int t, int m, in
 
 size_t bdg_bkmeans_scratch_bytes(int64_t S, int m, int W) {
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  // + the expanded centres when the assignment runs on the tensor cores
   return al(S * W * 8) + al(S * 4) + al(S * 4) + al((size_t)m * 64 * W * 4) + al((size_t)m * 4) +
-         al(8 * 64);
+         al(8 * 64) + (bdg_route_small_ok(W, m, 1) ? al(bdg_route_small_bytes(m, W)) : 0);
 }
 
 namespace {
@@ -320,7 +321,11 @@ bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int
   int32_t* assign = (int32_t*)p;   p += al(S * 4);
   int32_t* adist = (int32_t*)p;    p += al(S * 4);
   int32_t* ones = (int32_t*)p;     p += al((size_t)m * 64 * W * 4);
-  int32_t* count = (int32_t*)p;
+  int32_t* count = (int32_t*)p;    p += al((size_t)m * 4) + al(8 * 64);
+  // the assignment on the tensor cores (all centres in shared memory) where it applies
+  const bool small = bdg_route_small_ok(W, m, 1) && bdg_tc_default();
+  void* rs_scratch = small ? (void*)p : nullptr;
+  const size_t rs_bytes = small ? bdg_route_small_bytes(m, W) : 0;
   gather_rows<<<bdg_cdiv(S * W, 256), 256, 0, st>>>(codes, N, sample, S, W, scodes);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
@@ -331,6 +336,9 @@ bdg_status bdg_launch_bkmeans(const uint64_t* codes, int64_t N, int W, const int
     unsigned long long* lptr = loss ? (unsigned long long*)(loss + it) : nullptr;
     bdg_status s;
     auto run = [&]() -> bdg_status {
+      if (small)
+        return bdg_launch_route_small(scodes, S, W, cent, m, 1, assign, adist, rs_scratch, rs_bytes,
+                                      st, lptr, "bkmeans_assign");
       BDG_DISPATCH_W(W, bk_assign_w, scodes, S, cent, m, assign, adist, lptr, st);
     };
     s = run();

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kRsThreads, 1)
 route_small_kernel(const uint64_t* __restrict__ codes, int64_t n,
                    const uint8_t* __restrict__ cexp, int m, int np, int t,
                    int32_t* __restrict__ routes, int32_t* __restrict__ rdist,
-                   int32_t* __restrict__ err) {
+                   unsigned long long* __restrict__ loss, int32_t* __restrict__ err) {
   constexpr int KB = 64 * W;               // bytes of one expanded code
   constexpr uint32_t kOpCols = KB / 4;     // TMEM columns of one point operand
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -213,6 +213,12 @@ route_small_kernel(const uint64_t* __restrict__ codes, int64_t n,
       __syncwarp();
       if (lane == 0) tc05::mbar_arrive(acc_free);
       const int64_t i = ((int64_t)blockIdx.x + (int64_t)s * gridDim.x) * 128 + tid;
+      if (loss) {  // Bk-means objective (Eq. 1): distance to the nearest centre, one atomic per warp
+        unsigned long long dsum = i < n ? (unsigned long long)(best[0] >> 16) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+        if (lane == 0) atomicAdd(loss, dsum);
+      }
       if (i < n) {
 #pragma unroll
         for (int j = 0; j < kRsMaxT; ++j) {
@@ -232,8 +238,8 @@ route_small_kernel(const uint64_t* __restrict__ codes, int64_t n,
 
 template <int W>
 bdg_status launch_w(const uint64_t* codes, int64_t n, const uint64_t* cent, int m, int t,
-                    int32_t* routes, int32_t* rdist, uint8_t* cexp, int32_t* err,
-                    cudaStream_t st) {
+                    int32_t* routes, int32_t* rdist, unsigned long long* loss, uint8_t* cexp,
+                    int32_t* err, cudaStream_t st) {
   constexpr int KB = 64 * W;
   const int np = padded_centres(m);
   const int64_t nthreads = (int64_t)np * 4 * W;  // one thread per 16-bit chunk
@@ -246,7 +252,7 @@ bdg_status launch_w(const uint64_t* codes, int64_t n, const uint64_t* cent, int 
   const int64_t ntile = (n + 127) / 128;
   const int grid = (int)std::min<int64_t>(ntile, bdg_num_sms());
   route_small_kernel<W><<<grid, kRsThreads, smem, st>>>(codes, n, cexp, m, np, t, routes, rdist,
-                                                         err);
+                                                         loss, err);
   BDG_CUDA_TRY(cudaGetLastError());
   bdg_note_launch();
   return BDG_OK;
@@ -264,7 +270,8 @@ size_t bdg_route_small_bytes(int m, int W) {
 
 bdg_status bdg_launch_route_small(const uint64_t* codes, int64_t n, int W, const uint64_t* cent,
                                   int m, int t, int32_t* routes, int32_t* rdist, void* scratch,
-                                  size_t scratch_bytes, cudaStream_t st) {
+                                  size_t scratch_bytes, cudaStream_t st, unsigned long long* loss,
+                                  const char* prof_name) {
   if (n == 0) return BDG_OK;
   if (!bdg_route_small_ok(W, m, t))
     return bdg_set_error(BDG_EINVAL, "route: W=%d m=%d t=%d outside the small tensor path", W, m, t);
@@ -273,7 +280,7 @@ bdg_status bdg_launch_route_small(const uint64_t* codes, int64_t n, int W, const
   uint8_t* cexp = (uint8_t*)scratch;
   int32_t* err = (int32_t*)((char*)scratch + bdg_route_small_bytes(m, W) - 256);
   BDG_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
-  bdg_prof_scope prof("route", st);
-  if (W == 4) return launch_w<4>(codes, n, cent, m, t, routes, rdist, cexp, err, st);
-  return launch_w<8>(codes, n, cent, m, t, routes, rdist, cexp, err, st);
+  bdg_prof_scope prof(prof_name, st);
+  if (W == 4) return launch_w<4>(codes, n, cent, m, t, routes, rdist, loss, cexp, err, st);
+  return launch_w<8>(codes, n, cent, m, t, routes, rdist, loss, cexp, err, st);
 }
