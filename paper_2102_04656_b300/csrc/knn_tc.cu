@@ -22,10 +22,10 @@
 //     words (d << 21 | id rank of the home in H_p) to a per-row candidate list
 //     in shared memory, so word order is (d, id) order. When a row's list is
 //     nearly full, the warp compacts all its rows together: the threshold of
-//     each row becomes its exact k-th smallest distance so far (binary search
-//     over its list), or its exact k-th smallest word when ties at that
-//     distance fill the list. The threshold only tightens, so every final
-//     neighbour is kept;
+//     each row becomes its exact k-th smallest distance so far (counted into
+//     16 bins just below the current threshold, usually in one pass over the
+//     list), or its exact k-th smallest word when ties at that distance fill
+//     the list. The threshold only tightens, so every final neighbour is kept;
 //   * lookup (one thread of warp 6): takes the next work item from the round's
 //     counter and reads its partition's offsets while the current item runs.
 // The homes are streamed in id order, or in locality order (sorted by nearest
@@ -35,7 +35,7 @@
 // cuts its row's list to its k + 1 best words, ranks them by counting and
 // writes its row without the self pair; in the sub-rounds each warp sorts, row
 // by row, the few candidates below the running list's k-th key and merges them
-// into that list.
+// into that list. Round A and the sub-rounds are separate instantiations (RUN).
 //
 // Every mbarrier wait is bounded; a wait that gives up sets the device error
 // word and the CTA drains (waits for its own copies and MMAs, bounded) and

@@ -1,12 +1,15 @@
 // route.cu -- nearest-centre routing (Map step, Section 3.2) and Bk-means
 // (Section 3.2, Eq. 1-2) on packed binary codes.
 //
-// Routing: one thread per point keeps its t best (distance, centre) keys in
-// registers while centre codes stream through shared memory in chunks (every
-// thread of the block reads the same centre word, a broadcast). The work is
-// n * m * W XOR+POPC word pairs, ALU (POPC) bound.
+// Routing on the ALU (the tensor-core paths for 256/512-bit codes are in
+// route_small.cu, up to 256 centres, and below, from 1,024 centres): one thread
+// per point keeps its t best (distance, centre) keys in registers while centre
+// codes stream through shared memory in chunks (every thread of the block reads
+// the same centre word, a broadcast). The work is n * m * W XOR+POPC word pairs,
+// ALU (POPC) bound.
 //
-// Bk-means: assign = routing with t = 1 over the down-sample; update = per-bit
+// Bk-means: assign = routing with t = 1 over the down-sample (route_small.cu
+// where it applies); update = per-bit
 // member counts by integer atomics (order-independent, so deterministic) and a
 // per-word majority with "tie keeps the previous bit" (the reading of Eq. 2's
 // sgn at zero); the objective of Eq. 1 (Hamming = squared L2 for 0/1 vectors)
@@ -223,9 +226,10 @@ bdg_status bdg_launch_route(const uint64_t* codes, int64_t n, int W, const uint6
 // identical. Work: n * m * bits MMA ops, against n * m * W XOR + POPC word pairs
 // on the ALU path.
 // Each 128-point item loads its visitors' codes into tensor memory once and
-// then runs m / 128 tiles, so the tensor path pays off only with many centres
+// then runs m / 128 tiles, so this path pays off only with many centres
 // (measured on B300: 10M points x 10,000 centres, 256-bit: 94-119 ms against
-// 169-212 ms on the ALU; 2M x 256 centres, 512-bit: 4.0 against 1.8 ms).
+// 169-212 ms on the ALU; 2M x 256 centres, 512-bit: 4.0 against 1.8 ms, where
+// route_small.cu's resident centres take 0.55 ms).
 constexpr int kRouteTcMinCentres = 1024;
 bool bdg_route_tc_ok(int W, int64_t n, int m, int t) {
   return bdg_knn_tc_supported(W, t) && n < (int64_t(1) << 31) && m >= kRouteTcMinCentres &&
