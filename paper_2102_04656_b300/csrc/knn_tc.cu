@@ -671,6 +671,7 @@ knn_tc_kernel(bdg_knn_tc_args ta) {
           }
         }
         __syncwarp();
+#pragma unroll 2
         for (int rr = 0; rr < 32; ++rr) {
           const int row = warp * 32 + rr;
           const int n_r = __shfl_sync(0xffffffffu, cnt, rr);
